@@ -64,7 +64,7 @@ class _Config(ctypes.Structure):
                 ("huber_k", ctypes.c_double), ("lambda0", ctypes.c_double),
                 ("lambda_up", ctypes.c_double), ("lambda_down", ctypes.c_double),
                 ("eps_step", ctypes.c_double), ("eps_cost", ctypes.c_double),
-                ("min_valid", ctypes.c_int),
+                ("accept_step", ctypes.c_double), ("min_valid", ctypes.c_int),
                 ("zmin", ctypes.c_double)]
 
 
@@ -93,7 +93,7 @@ def _load():
             lib.orc_linearize.argtypes = [dp, i, i, _Cam, i, dp, dp, u8p, i, dp, d, d, d, d,
                                           dp, dp, dp, ip, dp, dp, dp, u8p]
             lib.orc_track.argtypes = [dp, i, i, _Cam, dp, dp, u8p, i, P(_Config), dp, d, d,
-                                      P(_Result), dp, ip, i]
+                                      P(_Result), dp, ip, dp, i]
             for fn in (lib.orc_pyr_down, lib.orc_build_pyramid, lib.orc_se3_exp, lib.orc_se3_log,
                        lib.orc_se3_mul, lib.orc_backproject, lib.orc_ref_patch,
                        lib.orc_linearize, lib.orc_track):
@@ -235,8 +235,8 @@ def linearize(img_l, K0, level, x_r, I0_l, valid_l, T, a, b, huber_k=9.0, zmin=1
 # configuration and tracking
 # --------------------------------------------------------------------------
 DEFAULT_CONFIG = dict(levels=4, max_iters=[10] * 8, huber_k=9.0, lambda0=1e-4, lambda_up=4.0,
-                      lambda_down=0.5, eps_step=1e-6, eps_cost=1e-4, min_valid=16,
-                      zmin=1e-3)
+                      lambda_down=0.5, eps_step=1e-6, eps_cost=1e-4, accept_step=1e-4,
+                      min_valid=16, zmin=1e-3)
 
 
 def make_config(**kw) -> dict:
@@ -258,6 +258,7 @@ def _cconfig(c: dict) -> _Config:
     cc.lambda_down = float(c["lambda_down"])
     cc.eps_step = float(c["eps_step"])
     cc.eps_cost = float(c["eps_cost"])
+    cc.accept_step = float(c["accept_step"])
     cc.min_valid = int(c["min_valid"])
     cc.zmin = float(c["zmin"])
     return cc
@@ -278,13 +279,14 @@ def track(cur_levels, K0, x_r, I0, valid, cfg: dict, T_init, a0=0.0, b0=0.0) -> 
     mt = L * (1 + max(cfg["max_iters"][:L]))
     tc = np.zeros(max(mt, 1))
     ti = np.zeros(max(mt, 1), np.int32)
+    ts = np.zeros(max(mt, 1))
     _load().orc_track(_p(flat, ctypes.c_double), W0, H0, _cam(K0), _p(x_r, ctypes.c_double),
                       _p(I0, ctypes.c_double), _p(valid, ctypes.c_uint8), N, ctypes.byref(cc),
                       _p(T, ctypes.c_double), float(a0), float(b0), ctypes.byref(r),
-                      _p(tc, ctypes.c_double), _p(ti, ctypes.c_int), mt)
+                      _p(tc, ctypes.c_double), _p(ti, ctypes.c_int), _p(ts, ctypes.c_double), mt)
     n = min(r.passes, mt)
     trace = [dict(cost=float(tc[k]), level=int(ti[k]) >> 2, accepted=bool(ti[k] & 2),
-                  candidate=bool(ti[k] & 1)) for k in range(n)]
+                  candidate=bool(ti[k] & 1), step=float(ts[k])) for k in range(n)]
     return {"T": np.array(r.T[:]).reshape(3, 4), "a": r.a, "b": r.b, "cost": r.cost,
             "n_valid": r.n_valid, "iters_total": r.iters_total, "iters": list(r.iters[:L]),
             "passes": r.passes, "status": r.status, "trace": trace}

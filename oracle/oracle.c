@@ -354,11 +354,13 @@ void orc_linearize(const double* img, int W, int H, orc_cam K0, int level, const
  * Coarse-to-fine solve (Sec. IV-A: coarser level initialises the finer one,
  * bounded iterations per level; Sec. IV-C "Track": Cholesky solve of the
  * normal equations, then T <- T exp(delta)).
- * Reading: Levenberg-Marquardt with multiplicative damping of diag(H),
- * strict accept on the mean Huber energy E/n; a level stops after max_iters
- * candidates, once a step's rotational/translational part is below eps_step,
- * or when a rejected candidate raised the cost by no more than
- * eps_cost * cost (the cost is at its interpolation noise floor).
+ * Reading: Gauss-Newton steps safeguarded by Levenberg-Marquardt damping of
+ * diag(H).  A candidate is taken if it lowers the mean Huber energy E/n, or
+ * if its rotational/translational part is below accept_step * 2^level (small
+ * steps are Gauss-Newton steps, as in the paper; the safeguard only screens
+ * large ones).  A level stops after max_iters candidates, once a step is
+ * below eps_step, or when a rejected candidate raised the cost by no more
+ * than eps_cost * cost.
  * ------------------------------------------------------------------------ */
 static int cholesky_solve8(const double A[64], const double g[8], double delta[8])
 {
@@ -389,19 +391,20 @@ static int cholesky_solve8(const double A[64], const double g[8], double delta[8
     return 1;
 }
 
-static void trace_pass(orc_result* out, double* tc, int* ti, int max_trace, double cost,
-                       int level, int accepted, int candidate)
+static void trace_pass(orc_result* out, double* tc, int* ti, double* ts, int max_trace,
+                       double cost, int level, int accepted, int candidate, double step)
 {
     int k = out->passes;
     if (tc && k < max_trace) tc[k] = cost;
     if (ti && k < max_trace) ti[k] = level * 4 + 2 * accepted + candidate;
+    if (ts && k < max_trace) ts[k] = step;
     out->passes = k + 1;
 }
 
 void orc_track(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
                const double* I0, const uint8_t* valid, int N, const orc_config* cfg,
                const double T_init[12], double a0, double b0, orc_result* out,
-               double* trace_cost, int* trace_info, int max_trace)
+               double* trace_cost, int* trace_info, double* trace_step, int max_trace)
 {
     int L = cfg->levels;
     size_t off[8];
@@ -430,7 +433,8 @@ void orc_track(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
         orc_linearize(img, Ws[l], Hs[l], K0, l, x_r, I0l, vl, N, T, a, b, cfg->huber_k,
                       cfg->zmin, Hm, g, &E, &n, NULL, NULL, NULL, NULL);
         int enough = n >= cfg->min_valid && n > 0;
-        trace_pass(out, trace_cost, trace_info, max_trace, enough ? E / n : INFINITY, l, 0, 0);
+        trace_pass(out, trace_cost, trace_info, trace_step, max_trace, enough ? E / n : INFINITY,
+                   l, 0, 0, 0.0);
         if (!enough) {
             out->status |= ORC_TOO_FEW_POINTS;
             continue;
@@ -455,9 +459,11 @@ void orc_track(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
             orc_linearize(img, Ws[l], Hs[l], K0, l, x_r, I0l, vl, N, Tn, an, bn, cfg->huber_k,
                           cfg->zmin, Hn, gn, &En, &nn, NULL, NULL, NULL, NULL);
             ++it;
+            double m = 0;
+            for (int d = 0; d < 6; ++d) m = fmax(m, fabs(delta[d]));
             double cn = (nn >= cfg->min_valid && nn > 0) ? En / nn : INFINITY;
-            int accepted = cn < cost;
-            trace_pass(out, trace_cost, trace_info, max_trace, cn, l, accepted, 1);
+            int accepted = cn < cost || (cn < INFINITY && m < ldexp(cfg->accept_step, l));
+            trace_pass(out, trace_cost, trace_info, trace_step, max_trace, cn, l, accepted, 1, m);
             int flat = !accepted && cn - cost <= cfg->eps_cost * cost;
             if (accepted) {
                 memcpy(T, Tn, sizeof(T));
@@ -471,8 +477,6 @@ void orc_track(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
             } else {
                 lambda *= cfg->lambda_up;
             }
-            double m = 0;
-            for (int d = 0; d < 6; ++d) m = fmax(m, fabs(delta[d]));
             if (m < cfg->eps_step || flat) break;
         }
         out->iters[l] = it;

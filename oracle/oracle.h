@@ -40,6 +40,7 @@ typedef struct {
     double lambda0, lambda_up, lambda_down;
     double eps_step;
     double eps_cost;
+    double accept_step;
     int min_valid;
     double zmin;
 } orc_config;
@@ -93,11 +94,12 @@ void orc_linearize(const double* img, int W, int H, orc_cam K0, int level, const
  * (level-0 first, unpadded, dims from W0, H0).  I0: [L][N][8], valid: [L][N].
  * Optional trace (NULL to skip), one entry per linearisation pass, at most
  * max_trace entries: trace_cost = E/n of that pass (INFINITY if too few
- * samples), trace_info = level * 4 + 2 * accepted + is_candidate. */
+ * samples), trace_info = level * 4 + 2 * accepted + is_candidate,
+ * trace_step = max |delta_xi| of the candidate (0 for a level start). */
 void orc_track(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
                const double* I0, const uint8_t* valid, int N, const orc_config* cfg,
                const double T_init[12], double a0, double b0, orc_result* out,
-               double* trace_cost, int* trace_info, int max_trace);
+               double* trace_cost, int* trace_info, double* trace_step, int max_trace);
 
 #ifdef __cplusplus
 }
