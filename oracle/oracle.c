@@ -356,9 +356,9 @@ void orc_linearize(const double* img, int W, int H, orc_cam K0, int level, const
  * normal equations, then T <- T exp(delta)).
  * Reading: Gauss-Newton steps safeguarded by Levenberg-Marquardt damping of
  * diag(H).  A candidate is taken if it lowers the mean Huber energy E/n, or
- * if its rotational/translational part is below accept_step * 2^level (small
- * steps are Gauss-Newton steps, as in the paper; the safeguard only screens
- * large ones).  A level stops after max_iters candidates, once a step is
+ * if its rotational/translational part is below accept_step (small steps are
+ * Gauss-Newton steps, as in the paper; the safeguard only screens large
+ * ones).  A level stops after max_iters candidates, once a step is
  * below eps_step, or when a rejected candidate raised the cost by no more
  * than eps_cost * cost.
  * ------------------------------------------------------------------------ */
@@ -421,6 +421,22 @@ void orc_track(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
     }
     double T[12], a = a0, b = b0;
     memcpy(T, T_init, sizeof(T));
+    /* Reading: the initial rotation is projected back onto SO(3) by
+     * Gram-Schmidt on its rows (r0 normalised, r1 made orthogonal to r0 and
+     * normalised, r2 = r0 x r1) once per frame, so a caller's accumulated
+     * rounding does not carry into the solve; inside a frame poses are only
+     * composed with exact exponentials. */
+    {
+        double n0 = sqrt(T[0] * T[0] + T[1] * T[1] + T[2] * T[2]);
+        for (int c = 0; c < 3; ++c) T[c] /= n0;
+        double d = T[4] * T[0] + T[5] * T[1] + T[6] * T[2];
+        for (int c = 0; c < 3; ++c) T[4 + c] -= d * T[c];
+        double n1 = sqrt(T[4] * T[4] + T[5] * T[5] + T[6] * T[6]);
+        for (int c = 0; c < 3; ++c) T[4 + c] /= n1;
+        T[8] = T[1] * T[6] - T[2] * T[5];
+        T[9] = T[2] * T[4] - T[0] * T[6];
+        T[10] = T[0] * T[5] - T[1] * T[4];
+    }
     memset(out, 0, sizeof(*out));
     out->cost = NAN;
     double Hm[64], g[8], E;
@@ -462,7 +478,7 @@ void orc_track(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
             double m = 0;
             for (int d = 0; d < 6; ++d) m = fmax(m, fabs(delta[d]));
             double cn = (nn >= cfg->min_valid && nn > 0) ? En / nn : INFINITY;
-            int accepted = cn < cost || (cn < INFINITY && m < ldexp(cfg->accept_step, l));
+            int accepted = cn < cost || (cn < INFINITY && m < cfg->accept_step);
             trace_pass(out, trace_cost, trace_info, trace_step, max_trace, cn, l, accepted, 1, m);
             int flat = !accepted && cn - cost <= cfg->eps_cost * cost;
             if (accepted) {
