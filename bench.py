@@ -1,0 +1,510 @@
+"""Benchmark: frames tracked per second on a synthetic sequence.
+
+Default workload (config "c2"): one camera stream, 640x480 uint8 frames
+(fx = fy = 525) from a 300-frame seeded sequence at 30 Hz (0.5 m/s, 30 deg/s,
+exposure affine a in [-0.1, 0.1], b in [-10, 10], sigma 2 noise), 2000 map
+points with depth 0.5-8 m, 4 pyramid levels, Huber k = 9, <= 10 LM iterations
+per level, constant-velocity initial pose, a new reference every 8 frames (or
+sooner if tracking degrades).  A step is one tracked frame: build the CUR
+pyramid of the frame (already in device memory) and run the whole
+coarse-to-fine solve.  Reference refreshes are timed separately.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOPS_PER_SAMPLE = 160      # algorithmic FP32 flops per residual sample per pass
+I34 = np.hstack([np.eye(3), np.zeros((3, 1))])
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c2"])
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="frames the oracle tracks for cpu_baseline (0 = auto, ~10-30 s)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+class Workload:
+    """C2: the frames, the reference keyframes and their map points."""
+
+    def __init__(self, seed=1, frames=300, N=2000, W=640, H=480, f=525.0, L=4):
+        import synth
+        self.cam = synth.camera_for(W, H, f)
+        self.seq = synth.sequence(seed, frames, self.cam, synth.ROOM_LARGE, 0.5, 30.0)
+        self.frames = [self.seq.frame(k)[0] for k in range(frames)]
+        self.N, self.L = N, L
+        self.refs = {}
+        self.name = (f"C2 single stream: {W}x{H} uint8, fx=fy={f:g}, {frames}-frame sequence "
+                     f"(0.5 m/s, 30 deg/s), N={N} points, L={L}, Huber 9, <=10 LM iters/level, "
+                     f"const-velocity init, reference every 8 frames")
+
+    def ref_points(self, r):
+        import synth
+        if r not in self.refs:
+            self.refs[r] = synth.reference_points(self.seq, r, self.N, 0.5, 8.0)[1]
+        return self.refs[r]
+
+    def T_ref_world(self, r):
+        import synth
+        return synth.pose_inv(self.seq.T_wc[r])
+
+
+def pose_mul(A, B):
+    return np.hstack([A[:, :3] @ B[:, :3], (A[:, :3] @ B[:, 3] + A[:, 3])[:, None]])
+
+
+def orthonormalised(T):
+    """Rotation projected back onto SO(3) (Gram-Schmidt on the rows): the
+    constant-velocity extrapolation would otherwise amplify rounding."""
+    q0 = T[0, :3] / np.linalg.norm(T[0, :3])
+    q1 = T[1, :3] - (T[1, :3] @ q0) * q0
+    q1 = q1 / np.linalg.norm(q1)
+    out = T.copy()
+    out[:, :3] = np.stack([q0, q1, np.cross(q0, q1)])
+    return out
+
+
+def pose_inv(A):
+    R = A[:, :3].T
+    return np.hstack([R, (-R @ A[:, 3])[:, None]])
+
+
+class SequenceDriver:
+    """Host-side loop around the tracker, shaped like the paper's tween-frame
+    schedule (Sec. III, Sec. IV-D): constant-velocity initial pose, affine
+    brightness carried over from the previous frame of the same reference; a
+    frame is accepted if the tracker reports no failure, at least half of the
+    8N samples are valid and the robust photometric error (mean Huber energy)
+    is below `max_cost`.  A rejected frame, or the `interval`-th frame since
+    the last reference, is handed to the indirect pipeline, which here is the
+    renderer's true pose and depth: that frame becomes the new reference."""
+
+    def __init__(self, wl: Workload, interval=8, max_cost=2.5):
+        self.wl = wl
+        self.interval = interval
+        self.max_cost = max_cost
+        self.rejected = 0
+        self.r = 0
+        self.since = 0
+        self.Tw = {0: wl.T_ref_world(0)}   # estimated world->camera per frame
+        self.ab = (0.0, 0.0)
+        self.need_refresh = True
+
+    def init_for(self, k):
+        wl = self.wl
+        Tprev = self.Tw[k - 1]
+        M = pose_mul(Tprev, pose_inv(self.Tw[k - 2])) if (k - 2) in self.Tw else np.hstack(
+            [np.eye(3), np.zeros((3, 1))])
+        return pose_mul(pose_mul(M, Tprev), pose_inv(wl.T_ref_world(self.r)))
+
+    def ab_init(self):
+        return self.ab
+
+    def record(self, k, res):
+        self.Tw[k] = orthonormalised(pose_mul(res["T"], self.wl.T_ref_world(self.r)))
+        self.ab = (float(res["a"]), float(res["b"]))
+        self.Tw.pop(k - 3, None)
+        self.since += 1
+        bad = (res["status"] != 0 or res["n_valid"] < 0.5 * 8 * self.wl.N
+               or not res["cost"] <= self.max_cost)
+        if bad:
+            # the indirect pipeline re-localises this frame
+            self.Tw[k] = self.wl.T_ref_world(k)
+            self.rejected += 1
+        if self.since >= self.interval or bad:
+            self.need_refresh = True
+
+    def refresh(self, k):
+        """The reference becomes frame k (its true pose, as the indirect
+        pipeline would provide); returns True if a refresh happened."""
+        if not self.need_refresh:
+            return False
+        self.r = k
+        self.Tw[k] = self.wl.T_ref_world(k)
+        self.ab = (0.0, 0.0)
+        self.since = 0
+        self.need_refresh = False
+        return True
+
+
+def pose_error(wl, k, r, T):
+    import synth
+    Tt = synth.relative(wl.seq.T_wc[r], wl.seq.T_wc[k])
+    dR = T[:, :3].T @ Tt[:, :3]
+    s = 0.5 * np.linalg.norm([dR[2, 1] - dR[1, 2], dR[0, 2] - dR[2, 0], dR[1, 0] - dR[0, 1]])
+    return float(np.arctan2(s, 0.5 * (np.trace(dR) - 1))), float(np.linalg.norm(T[:, 3] - Tt[:, 3]))
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_track_sequence(wl, frames, inits=None):
+    """Tracks frames 1..frames with the FP64 oracle; returns (seconds spent in
+    pyramid+track, results, inits used).  inits: optional {k: (r, T_init)} to
+    replay exactly the GPU's initial states and references."""
+    import oracle
+    K = wl.cam.K
+    trk = oracle.OracleTracker(wl.cam.W, wl.cam.H, K, levels=wl.L)
+    drv = SequenceDriver(wl)
+    t_track = 0.0
+    out, used = {}, {}
+    cur_ref = None
+    for k in range(1, frames + 1):
+        if inits is not None:
+            r, T_init, ab = inits[k]
+        else:
+            drv.refresh(k - 1)
+            r, T_init, ab = drv.r, drv.init_for(k), drv.ab_init()
+        if r != cur_ref:
+            trk.build_pyramid(0, wl.frames[r])
+            trk.set_map_points(wl.ref_points(r))
+            cur_ref = r
+        t0 = time.perf_counter()
+        trk.build_pyramid(1, wl.frames[k])
+        res = trk.track_frame(T_init, ab)
+        t_track += time.perf_counter() - t0
+        out[k] = res
+        used[k] = (r, T_init, ab)
+        if inits is None:
+            drv.record(k, res)
+    return t_track, out, used
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = Workload()
+    W = args.warmup
+    K = args.steps
+    t, res, _ = oracle_track_sequence(wl, min(len(wl.frames) - 1, W + K))
+    # time only the K frames after the warm-up ones: re-run them is wasteful,
+    # so time per frame is taken over the whole bounded run
+    n = min(len(wl.frames) - 1, W + K)
+    fps = n / t
+    line = {"metric": "frames tracked/s", "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": K, "warmup": W, "ms_per_step": 1000.0 * t / n, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": {"workload": wl.name},
+            "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n} frames of the sequence, pyramid + track per frame"},
+            "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import paper_2607_16897_gb300 as glt
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = Workload(seed=1 + rank)      # replicas: one independent stream per GPU
+    Wd, Hd, L, N = wl.cam.W, wl.cam.H, wl.L, wl.N
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    trk = glt.Tracker(Wd, Hd, wl.cam.K, levels=L, max_points=N)
+    frames_dev = torch.from_numpy(np.stack(wl.frames)).to(f"cuda:{local}")
+    frames_pin = torch.from_numpy(np.stack(wl.frames)).pin_memory()
+    init_dev = torch.zeros(14, dtype=torch.float64, device=f"cuda:{local}")
+    init_pin = torch.zeros(14, dtype=torch.float64).pin_memory()
+    out_dev = torch.zeros(glt.RESULT_BYTES, dtype=torch.uint8, device=f"cuda:{local}")
+    out_pin = torch.zeros(glt.RESULT_BYTES, dtype=torch.uint8).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+    uvd_dev = {}
+
+    def refresh_dev(r):
+        if r not in uvd_dev:
+            uvd_dev[r] = torch.from_numpy(wl.ref_points(r)).to(f"cuda:{local}")
+        trk.build_pyramid(glt.GLT_REF, frames_dev[r], stream=sh)
+        trk.set_map_points(uvd_dev[r], stream=sh)
+
+    nF = len(wl.frames)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev_ref = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+
+    def run_steps(nsteps, timed, record):
+        drv = SequenceDriver(wl)
+        k = 0
+        n_ref = 0
+        for i in range(nsteps):
+            k += 1
+            if k >= nF:            # restart the sequence
+                k = 1
+                drv = SequenceDriver(wl)
+            did = drv.refresh(k - 1)
+            r_used = drv.r
+            if did:
+                with torch.cuda.stream(stream):
+                    if timed:
+                        ev_ref[n_ref][0].record(stream)
+                    refresh_dev(drv.r)
+                    if timed:
+                        ev_ref[n_ref][1].record(stream)
+                n_ref += 1
+            T_init, ab = drv.init_for(k), drv.ab_init()
+            init_pin.copy_(torch.from_numpy(np.concatenate([T_init.ravel(), list(ab)])))
+            with torch.cuda.stream(stream):
+                init_dev.copy_(init_pin, non_blocking=True)
+                flush.zero_()                    # L2 flushed between steps
+                if timed:
+                    ev[i][0].record(stream)
+                trk.build_pyramid(glt.GLT_CUR, frames_dev[k], stream=sh)
+                if timed:
+                    ev[i][1].record(stream)
+                trk.track_frame_async(init_dev, out_dev, stream=sh)
+                if timed:
+                    ev[i][2].record(stream)
+                out_pin.copy_(out_dev, non_blocking=True)
+            stream.synchronize()
+            res = glt.parse_results(out_pin.numpy())[0]
+            drv.record(k, res)
+            if record is not None:
+                record.append((k, r_used, T_init, ab, res))
+        return n_ref
+
+    # warm-up (untimed), then the timed steps
+    run_steps(max(args.warmup, 3), False, None)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    rec = []
+    t_wall0 = time.perf_counter()
+    n_ref = run_steps(args.steps, True, rec)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    step_ms = [e0.elapsed_time(e2) for e0, _, e2 in ev]
+    pyr_ms = [e0.elapsed_time(e1) for e0, e1, _ in ev]
+    trk_ms = [e1.elapsed_time(e2) for _, e1, e2 in ev]
+    ref_ms = [a.elapsed_time(b) for a, b in ev_ref[:n_ref]]
+    dev_s = sum(step_ms) / 1000.0
+    if dist:
+        t = torch.tensor([dev_s, t_wall], device=f"cuda:{local}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_s, t_wall = float(t[0]), float(t[1])
+    value = world * args.steps / dev_s
+    passes = [r[4]["passes"] for r in rec]
+
+    # accuracy vs ground truth along the sequence
+    gt = [pose_error(wl, k, r, res["T"]) for (k, r, _, _, res) in rec]
+    accuracy = {"median_rot_deg": float(np.rad2deg(np.median([e[0] for e in gt]))),
+                "median_trans_mm": float(1000 * np.median([e[1] for e in gt])),
+                "max_rot_deg": float(np.rad2deg(max(e[0] for e in gt))),
+                "max_trans_mm": float(1000 * max(e[1] for e in gt)),
+                "status_nonzero": int(sum(1 for r in rec if r[4]["status"]))}
+    # e2e through the C ABI with host buffers (pinned), H2D + D2H inside
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, glt, trk, wl, frames_pin, stream)
+
+    # oracle on a bounded sample, same initial states and references
+    cpu = None
+    parity = None
+    if rank == 0 and not args.no_cpu:
+        cpu, parity = run_cpu_baseline(args, wl, rec)
+
+    # roofline of the dominant kernel (the persistent tracker)
+    mean_trk = statistics.mean(trk_ms) / 1000.0
+    samples_per_launch = statistics.mean(p * 8 * N for p in passes)
+    achieved = FLOPS_PER_SAMPLE * samples_per_launch / mean_trk / 1e12
+    peaks, src = measured_peaks()
+    peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "track_kernel",
+            "peak_source": f"FP32 FMA peak from unit counts (152 SMs x 128 lanes x 2) at "
+                           f"{peaks.get('sm_max_mhz', 2070.0):g} MHz ({src} clock)",
+            "launch_ms": statistics.mean(trk_ms), "passes_per_launch": statistics.mean(passes),
+            "samples_per_launch": samples_per_launch}
+    if rank == 0:
+        line = {"metric": "frames tracked/s", "value": value, "unit": "frames/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1000.0 * dev_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl.name, "global_batch": world, "streams_per_gpu": 1,
+                           "parallelism": f"replicas x{world}",
+                           "l2": "flushed between steps (256 MB write, outside the step events)",
+                           "timing": "sum of per-step CUDA-event times (pyramid + track)"},
+                "breakdown_ms": {"pyramid": statistics.mean(pyr_ms),
+                                 "track": statistics.mean(trk_ms),
+                                 "reference_refresh": statistics.mean(ref_ms) if ref_ms else None,
+                                 "wall_per_step": 1000.0 * t_wall / args.steps},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": args.steps * L + n_ref * L,
+                "parity_vs_oracle": parity, "accuracy_vs_truth": accuracy}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_e2e(args, glt, trk, wl, frames_pin, stream):
+    """Same frames through glt_build_pyramid / glt_set_map_points /
+    glt_track_frame with HOST (pinned) buffers: every step copies its frame
+    H2D and reads its result back."""
+    import torch
+    sh = stream.cuda_stream
+    nF = len(wl.frames)
+    h2d = d2h = 0
+    drv = SequenceDriver(wl)
+    k = 0
+    refs_pin = {}
+    steps = args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        k += 1
+        if k >= nF:
+            k = 1
+            drv = SequenceDriver(wl)
+        if drv.refresh(k - 1):
+            r = drv.r
+            if r not in refs_pin:
+                refs_pin[r] = torch.from_numpy(wl.ref_points(r)).pin_memory()
+            trk.build_pyramid(glt.GLT_REF, frames_pin[r].numpy(), stream=sh)
+            trk.set_map_points(refs_pin[r].numpy(), stream=sh)
+            h2d += wl.frames[r].nbytes + refs_pin[r].numel() * 4
+        T_init = drv.init_for(k)
+        trk.build_pyramid(glt.GLT_CUR, frames_pin[k].numpy(), stream=sh)
+        res = trk.track_frame(T_init, drv.ab_init(), stream=sh)
+        h2d += wl.frames[k].nbytes + 14 * 8
+        d2h += glt.RESULT_BYTES
+        drv.record(k, res)
+    t = time.perf_counter() - t0
+    return {"value": steps / t, "unit": "frames/s", "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h / steps,
+            "note": "host-pinned frames and map points through the C ABI, reference refreshes "
+                    "included, host sync per frame"}
+
+
+def run_cpu_baseline(args, wl, rec):
+    """The oracle on the first n timed frames with the GPU run's initial
+    states and references: frames/s on one host core, and the pose
+    difference GPU vs oracle for the same inputs."""
+    n = args.cpu_sample if args.cpu_sample > 0 else 299
+    n = min(n, len(rec))
+    inits = {k: (r, T_init, ab) for (k, r, T_init, ab, _) in rec[:n]}
+    assert sorted(inits) == list(range(1, n + 1))
+    t, out, _ = oracle_track_sequence(wl, n, inits=inits)
+    gpu = {k: res for (k, _, _, _, res) in rec[:n]}
+    rot, trans = [], []
+    for k in range(1, n + 1):
+        dR = gpu[k]["T"][:, :3].T @ out[k]["T"][:, :3]
+        s = 0.5 * np.linalg.norm([dR[2, 1] - dR[1, 2], dR[0, 2] - dR[2, 0], dR[1, 0] - dR[0, 1]])
+        rot.append(float(np.arctan2(s, 0.5 * (np.trace(dR) - 1))))
+        trans.append(float(np.linalg.norm(gpu[k]["T"][:, 3] - out[k]["T"][:, 3])))
+    cpu = {"value": n / t, "unit": "frames/s", "cores": 1, "kind": "oracle",
+           "sample": f"frames 1..{n} of the sequence (pyramid + track each, FP64 C oracle, "
+                     f"same initial states and references as the GPU run)"}
+    parity = {"frames": n, "max_rot_rad": max(rot), "max_trans_m": max(trans),
+              "tolerance": {"rot_rad": 1e-5, "trans_m": 1e-5}}
+    return cpu, parity
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,327 @@
+"""Python binding of libglt.so: GB300-native pose-only direct photometric tracking.
+
+Argument marshalling only.  Every step of the method runs in the library's
+sm_103a kernels; PyTorch is used for device memory (``data_ptr()``) and
+streams (``torch.cuda.current_stream().cuda_stream``).  The functions
+``glt_*`` are the C entry points of ``include/glt.h`` under the same names;
+``Tracker`` and ``Batch`` wrap them for numpy / torch callers.
+
+Importing this package needs the built library (``build.build()``); there is
+no fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libglt.so")
+
+GLT_OK = 0
+GLT_ERR_INVALID_ARG = -1
+GLT_ERR_CUDA = -2
+GLT_ERR_NO_REFERENCE = -3
+GLT_ERR_CAPACITY = -4
+GLT_TRACK_TOO_FEW_POINTS = 1
+GLT_TRACK_NOT_PD = 2
+GLT_REF, GLT_CUR = 0, 1
+GLT_FP32, GLT_MIXED = 0, 1
+MAX_LEVELS = 8
+
+
+class glt_config(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("levels", ctypes.c_int),
+                ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double),
+                ("cy", ctypes.c_double), ("max_points", ctypes.c_int),
+                ("max_iters", ctypes.c_int * MAX_LEVELS), ("huber_k", ctypes.c_double),
+                ("lambda0", ctypes.c_double), ("lambda_up", ctypes.c_double),
+                ("lambda_down", ctypes.c_double), ("eps_step", ctypes.c_double),
+                ("eps_cost", ctypes.c_double), ("accept_step", ctypes.c_double),
+                ("min_valid", ctypes.c_int),
+                ("zmin", ctypes.c_double), ("precision", ctypes.c_int), ("cluster", ctypes.c_int),
+                ("threads", ctypes.c_int)]
+
+
+class glt_result(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_double * 12), ("a", ctypes.c_double), ("b", ctypes.c_double),
+                ("cost", ctypes.c_double), ("n_valid", ctypes.c_int),
+                ("iters_total", ctypes.c_int), ("iters", ctypes.c_int * MAX_LEVELS),
+                ("passes", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+RESULT_BYTES = ctypes.sizeof(glt_result)
+RESULT_DTYPE = np.dtype({"names": ["T", "a", "b", "cost", "n_valid", "iters_total", "iters",
+                                   "passes", "status"],
+                         "formats": [(np.float64, (12,)), np.float64, np.float64, np.float64,
+                                     np.int32, np.int32, (np.int32, (MAX_LEVELS,)), np.int32,
+                                     np.int32],
+                         "offsets": [glt_result.T.offset, glt_result.a.offset,
+                                     glt_result.b.offset, glt_result.cost.offset,
+                                     glt_result.n_valid.offset, glt_result.iters_total.offset,
+                                     glt_result.iters.offset, glt_result.passes.offset,
+                                     glt_result.status.offset],
+                         "itemsize": RESULT_BYTES})
+
+# name -> (restype, argtypes) of every entry point declared in include/glt.h
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+SIGNATURES = {
+    "glt_default_config": (None, [_P(glt_config), _i, _i, _d, _d, _d, _d]),
+    "glt_create": (_i, [_P(glt_config), _P(_vp)]),
+    "glt_destroy": (None, [_vp]),
+    "glt_build_pyramid": (_i, [_vp, _i, _vp, _i, _i, _vp]),
+    "glt_set_map_points": (_i, [_vp, _vp, _i, _i, _vp]),
+    "glt_track_frame": (_i, [_vp, _P(_d), _P(_d), _P(glt_result), _vp]),
+    "glt_track_frame_async": (_i, [_vp, _vp, _vp, _vp]),
+    "glt_debug_linearize": (_i, [_vp, _i, _P(_d), _d, _d, _P(_d), _P(_d), _P(_d), _P(_i),
+                                 _P(ctypes.c_float), _vp]),
+    "glt_get_pyramid": (_i, [_vp, _i, _i, _P(ctypes.c_uint8), _vp]),
+    "glt_get_trace": (_i, [_vp, _P(_d), _P(_i), _i, _P(_i), _vp]),
+    "glt_batch_create": (_i, [_P(_vp), _i, _P(_vp)]),
+    "glt_batch_destroy": (None, [_vp]),
+    "glt_batch_build_pyramid": (_i, [_vp, _vp, _vp]),
+    "glt_batch_track": (_i, [_vp, _vp, _vp, _vp]),
+    "glt_batch_capture": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "glt_batch_replay": (_i, [_vp, _vp]),
+    "glt_batch_autotune": (_i, [_vp, _vp, _vp, _i, _P(_i), _P(_i), _P(ctypes.c_float), _vp]),
+    "glt_batch_set_shape": (_i, [_vp, _i, _i]),
+    "glt_last_error": (ctypes.c_char_p, []),
+    "glt_version": (ctypes.c_char_p, []),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is not built; run paper_2607_16897_gb300.build.build() "
+            "(the CUDA library is required, there is no fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+globals().update({name: getattr(_lib, name) for name in SIGNATURES})
+
+
+class GltError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str):
+    if rc != GLT_OK:
+        raise GltError(f"{what} failed ({rc}): {_lib.glt_last_error().decode()}")
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(t) -> int:
+    return int(t.data_ptr())
+
+
+def _is_cuda_tensor(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+def default_config(width, height, K, **kw) -> glt_config:
+    fx, fy, cx, cy = (float(k) for k in K)
+    c = glt_config()
+    _lib.glt_default_config(ctypes.byref(c), int(width), int(height), fx, fy, cx, cy)
+    for k, v in kw.items():
+        if k == "max_iters":
+            v = list(v)
+            v = (v + [v[-1]] * MAX_LEVELS)[:MAX_LEVELS]
+            for i in range(MAX_LEVELS):
+                c.max_iters[i] = int(v[i])
+        elif k == "precision" and isinstance(v, str):
+            c.precision = {"fp32": GLT_FP32, "mixed": GLT_MIXED}[v]
+        else:
+            if not hasattr(c, k):
+                raise KeyError(k)
+            setattr(c, k, v)
+    return c
+
+
+def result_to_dict(r) -> dict:
+    """glt_result (ctypes struct or numpy structured record) -> dict."""
+    if isinstance(r, glt_result):
+        T = np.array(r.T[:]).reshape(3, 4)
+        return {"T": T, "a": r.a, "b": r.b, "cost": r.cost, "n_valid": r.n_valid,
+                "iters_total": r.iters_total, "iters": list(r.iters[:]), "passes": r.passes,
+                "status": r.status}
+    return {"T": np.array(r["T"]).reshape(3, 4), "a": float(r["a"]), "b": float(r["b"]),
+            "cost": float(r["cost"]), "n_valid": int(r["n_valid"]),
+            "iters_total": int(r["iters_total"]), "iters": [int(x) for x in r["iters"]],
+            "passes": int(r["passes"]), "status": int(r["status"])}
+
+
+def parse_results(buf) -> list:
+    """Device or host byte buffer of S glt_result structs -> list of dicts."""
+    if _is_cuda_tensor(buf):
+        buf = buf.cpu().numpy()
+    arr = np.frombuffer(np.ascontiguousarray(buf).tobytes(), dtype=RESULT_DTYPE)
+    return [result_to_dict(r) for r in arr]
+
+
+class Tracker:
+    """One camera stream: glt_create / glt_build_pyramid / glt_set_map_points /
+    glt_track_frame / glt_debug_linearize on numpy or torch inputs."""
+
+    def __init__(self, width, height, K, **cfg):
+        self.cfg = default_config(width, height, K, **cfg)
+        self.W, self.H, self.L = int(width), int(height), int(self.cfg.levels)
+        h = ctypes.c_void_p()
+        _check(_lib.glt_create(ctypes.byref(self.cfg), ctypes.byref(h)), "glt_create")
+        self.handle = h
+        self.N = 0
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.glt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_pyramid(self, slot, img, stream=None):
+        if _is_cuda_tensor(img):
+            assert img.dtype.itemsize == 1 and img.is_contiguous()
+            pitch = img.shape[-1]
+            _check(_lib.glt_build_pyramid(self.handle, slot, _dptr(img), pitch, 1,
+                                          _stream_handle(stream)), "glt_build_pyramid")
+        else:
+            a = np.ascontiguousarray(img, np.uint8)
+            _check(_lib.glt_build_pyramid(self.handle, slot, a.ctypes.data, a.shape[1], 0,
+                                          _stream_handle(stream)), "glt_build_pyramid")
+            # pageable H2D copies are staged before the call returns
+
+    def set_map_points(self, uvd, stream=None):
+        if _is_cuda_tensor(uvd):
+            n = uvd.shape[0]
+            _check(_lib.glt_set_map_points(self.handle, _dptr(uvd), n, 1, _stream_handle(stream)),
+                   "glt_set_map_points")
+        else:
+            a = np.ascontiguousarray(uvd, np.float32).reshape(-1, 3)
+            n = a.shape[0]
+            _check(_lib.glt_set_map_points(self.handle, a.ctypes.data, n, 0,
+                                           _stream_handle(stream)), "glt_set_map_points")
+        self.N = n
+
+    def track_frame(self, T_init, ab_init=(0.0, 0.0), stream=None) -> dict:
+        T = np.ascontiguousarray(T_init, np.float64).reshape(12)
+        ab = np.ascontiguousarray(ab_init, np.float64).reshape(2)
+        r = glt_result()
+        _check(_lib.glt_track_frame(self.handle, T.ctypes.data_as(_P(_d)),
+                                    ab.ctypes.data_as(_P(_d)), ctypes.byref(r),
+                                    _stream_handle(stream)), "glt_track_frame")
+        return result_to_dict(r)
+
+    def track_frame_async(self, init_dev, out_dev, stream=None):
+        _check(_lib.glt_track_frame_async(self.handle, _dptr(init_dev), _dptr(out_dev),
+                                          _stream_handle(stream)), "glt_track_frame_async")
+
+    def debug_linearize(self, level, T, a, b, want_res=True, stream=None) -> dict:
+        T = np.ascontiguousarray(T, np.float64).reshape(12)
+        H = np.zeros(64)
+        g = np.zeros(8)
+        E = ctypes.c_double()
+        n = ctypes.c_int()
+        res = np.zeros(max(self.N, 1) * 8, np.float32) if want_res else None
+        _check(_lib.glt_debug_linearize(self.handle, int(level), T.ctypes.data_as(_P(_d)),
+                                        float(a), float(b), H.ctypes.data_as(_P(_d)),
+                                        g.ctypes.data_as(_P(_d)), ctypes.byref(E),
+                                        ctypes.byref(n),
+                                        res.ctypes.data_as(_P(ctypes.c_float)) if want_res else None,
+                                        _stream_handle(stream)), "glt_debug_linearize")
+        out = {"H": H.reshape(8, 8), "g": g, "E": E.value, "n": n.value}
+        if want_res:
+            out["res"] = res[:self.N * 8].reshape(self.N, 8)
+        return out
+
+    def get_pyramid(self, slot, level, stream=None) -> np.ndarray:
+        w, h = self.W >> level, self.H >> level
+        out = np.zeros((h, w), np.uint8)
+        _check(_lib.glt_get_pyramid(self.handle, slot, level, out.ctypes.data_as(_P(ctypes.c_uint8)),
+                                    _stream_handle(stream)), "glt_get_pyramid")
+        return out
+
+    def get_trace(self, stream=None) -> list:
+        m = self.L * (1 + max(self.cfg.max_iters[:self.L]))
+        cost = np.zeros(max(m, 1))
+        info = np.zeros(max(m, 1), np.int32)
+        cnt = ctypes.c_int()
+        _check(_lib.glt_get_trace(self.handle, cost.ctypes.data_as(_P(_d)),
+                                  info.ctypes.data_as(_P(_i)), m, ctypes.byref(cnt),
+                                  _stream_handle(stream)), "glt_get_trace")
+        return [dict(cost=float(cost[k]), level=int(info[k]) >> 2, accepted=bool(info[k] & 2),
+                     candidate=bool(info[k] & 1)) for k in range(cnt.value)]
+
+
+class Batch:
+    """S trackers tracked in one persistent launch (glt_batch_*)."""
+
+    def __init__(self, trackers):
+        self.trackers = list(trackers)
+        arr = (ctypes.c_void_p * len(self.trackers))(*[t.handle for t in self.trackers])
+        h = ctypes.c_void_p()
+        _check(_lib.glt_batch_create(arr, len(self.trackers), ctypes.byref(h)), "glt_batch_create")
+        self.handle = h
+        self.S = len(self.trackers)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.glt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_pyramid(self, frame_ptrs_dev, stream=None):
+        _check(_lib.glt_batch_build_pyramid(self.handle, _dptr(frame_ptrs_dev),
+                                            _stream_handle(stream)), "glt_batch_build_pyramid")
+
+    def track(self, init_dev, out_dev, stream=None):
+        _check(_lib.glt_batch_track(self.handle, _dptr(init_dev), _dptr(out_dev),
+                                    _stream_handle(stream)), "glt_batch_track")
+
+    def capture(self, frame_ptrs_dev, init_dev, out_dev, stream):
+        _check(_lib.glt_batch_capture(self.handle, _dptr(frame_ptrs_dev), _dptr(init_dev),
+                                      _dptr(out_dev), _stream_handle(stream)), "glt_batch_capture")
+
+    def replay(self, stream=None):
+        _check(_lib.glt_batch_replay(self.handle, _stream_handle(stream)), "glt_batch_replay")
+
+    def set_shape(self, cluster, threads):
+        _check(_lib.glt_batch_set_shape(self.handle, int(cluster), int(threads)),
+               "glt_batch_set_shape")
+
+    def autotune(self, init_dev, out_dev, reps=3, stream=None):
+        c, t, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        _check(_lib.glt_batch_autotune(self.handle, _dptr(init_dev), _dptr(out_dev), int(reps),
+                                       ctypes.byref(c), ctypes.byref(t), ctypes.byref(ms),
+                                       _stream_handle(stream)), "glt_batch_autotune")
+        return c.value, t.value, ms.value
+
+
+def version() -> str:
+    return _lib.glt_version().decode()

@@ -1,0 +1,742 @@
+// C ABI of libglt.so (declared in include/glt.h): argument checking, device
+// memory ownership, stream ordering, and the batch / CUDA-graph / autotuner
+// plumbing around the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "glt_internal.h"
+
+namespace glt {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return GLT_ERR_CUDA;
+}
+
+static int invalid(const char* msg)
+{
+    set_error(msg);
+    return GLT_ERR_INVALID_ARG;
+}
+
+#define GLT_CHECK(call, what)                               \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);  \
+    } while (0)
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static bool finite_all(const double* v, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+template <class T>
+static cudaError_t dalloc(T** p, size_t count)
+{
+    return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+static void free_tracker(glt_tracker* t)
+{
+    if (!t) return;
+    for (int s = 0; s < 2; ++s) cudaFree(t->pyr[s].base);
+    cudaFree(t->packed);
+    cudaFree(t->uvd_dev);
+    cudaFree(t->pt);
+    cudaFree(t->dz);
+    cudaFree(t->I0);
+    cudaFree(t->desc_dev);
+    cudaFree(t->desc_ptr_dev);
+    cudaFree(t->user_dev);
+    cudaFree(t->trace_count);
+    cudaFree(t->jobs_dev);
+    cudaFree(t->pack_dev);
+    cudaFree(t->init_dev);
+    cudaFree(t->result_dev);
+    cudaFree(t->trace_cost);
+    cudaFree(t->trace_info);
+    cudaFree(t->lin_partials);
+    cudaFree(t->lin_counter);
+    cudaFree(t->lin_out);
+    cudaFree(t->lin_res);
+    cudaFreeHost(t->h_init);
+    cudaFreeHost(t->h_result);
+    cudaFreeHost(t->h_lin);
+    delete t;
+}
+
+static int check_config(const glt_config* c)
+{
+    if (!c) return invalid("config is NULL");
+    if (c->width < 16 || c->height < 16 || c->width > (1 << 15) || c->height > (1 << 15))
+        return invalid("width/height must be in [16, 32768]");
+    if (c->levels < 1 || c->levels > GLT_MAX_LEVELS) return invalid("levels must be in [1, 8]");
+    if ((c->width >> (c->levels - 1)) < 8 || (c->height >> (c->levels - 1)) < 8)
+        return invalid("the coarsest level must be at least 8 x 8 pixels");
+    if (!(c->fx > 0 && c->fy > 0) || !std::isfinite(c->fx) || !std::isfinite(c->fy) ||
+        !std::isfinite(c->cx) || !std::isfinite(c->cy))
+        return invalid("intrinsics must be finite with fx, fy > 0");
+    if (c->max_points < 1 || c->max_points > (1 << 22)) return invalid("max_points must be in [1, 4194304]");
+    for (int l = 0; l < c->levels; ++l)
+        if (c->max_iters[l] < 0 || c->max_iters[l] > 1000) return invalid("max_iters must be in [0, 1000]");
+    if (!(c->huber_k > 0) || !std::isfinite(c->huber_k)) return invalid("huber_k must be > 0");
+    if (!(c->lambda0 > 0) || !(c->lambda_up >= 1) || !(c->lambda_down > 0) || !(c->lambda_down <= 1))
+        return invalid("LM damping factors out of range");
+    if (!(c->eps_step >= 0) || !(c->eps_cost >= 0) || !(c->accept_step >= 0))
+        return invalid("eps_step / eps_cost / accept_step must be >= 0");
+    if (c->min_valid < 1) return invalid("min_valid must be >= 1");
+    if (!(c->zmin > 0)) return invalid("zmin must be > 0");
+    if (c->precision != GLT_FP32 && c->precision != GLT_MIXED) return invalid("unknown precision");
+    if (c->cluster < 0 || c->cluster > 16) return invalid("cluster must be in [0, 16]");
+    if (c->threads != 0 && c->threads != 128 && c->threads != 256 && c->threads != 512)
+        return invalid("threads must be 0, 128, 256 or 512");
+    return GLT_OK;
+}
+
+// CTAs per stream for n points when the caller left it to the library.
+static void resolve_shape(glt_tracker* t)
+{
+    const bool mixed = t->cfg.precision == GLT_MIXED;
+    int threads = t->cfg.threads ? t->cfg.threads : 256;
+    int cluster = t->cfg.cluster;
+    if (cluster == 0) {
+        cluster = (t->N + threads - 1) / threads;
+        cluster = std::min(16, std::max(1, cluster));
+    }
+    while (cluster > 1 && !track_shape_ok(cluster, threads, mixed)) cluster = cluster > 8 ? 8 : cluster - 1;
+    t->cluster = cluster;
+    t->threads = threads;
+}
+
+}  // namespace glt
+
+using namespace glt;
+
+extern "C" {
+
+const char* glt_last_error(void) { return g_err.c_str(); }
+
+const char* glt_version(void) { return "glt 0.1 (sm_103a)"; }
+
+void glt_default_config(glt_config* c, int width, int height, double fx, double fy, double cx,
+                        double cy)
+{
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->width = width;
+    c->height = height;
+    c->levels = 4;
+    c->fx = fx;
+    c->fy = fy;
+    c->cx = cx;
+    c->cy = cy;
+    c->max_points = 4096;
+    for (int l = 0; l < GLT_MAX_LEVELS; ++l) c->max_iters[l] = 10;
+    c->huber_k = 9.0;
+    c->lambda0 = 1e-4;
+    c->lambda_up = 4.0;
+    c->lambda_down = 0.5;
+    c->eps_step = 1e-6;
+    c->eps_cost = 1e-4;
+    c->accept_step = 1e-4;
+    c->min_valid = 16;
+    c->zmin = 1e-3;
+    c->precision = GLT_FP32;
+    c->cluster = 0;
+    c->threads = 0;
+}
+
+int glt_create(const glt_config* cfg, glt_tracker** out)
+{
+    if (!out) return invalid("out is NULL");
+    *out = nullptr;
+    int rc = check_config(cfg);
+    if (rc != GLT_OK) return rc;
+    glt_tracker* t = new glt_tracker();
+    t->cfg = *cfg;
+    t->L = cfg->levels;
+    cudaError_t e = cudaGetDevice(&t->device);
+    if (e != cudaSuccess) {
+        delete t;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+#define ALLOC(call)                                 \
+    do {                                            \
+        cudaError_t e2 = (call);                    \
+        if (e2 != cudaSuccess) {                    \
+            free_tracker(t);                        \
+            return cuda_fail(e2, "device allocation"); \
+        }                                           \
+    } while (0)
+    size_t pix = 0;
+    for (int l = 0; l < t->L; ++l) {
+        t->W[l] = cfg->width >> l;
+        t->H[l] = cfg->height >> l;
+        t->pitch[l] = (int)align_up((size_t)t->W[l] + 8, 16);
+        t->poff[l] = pix;
+        pix += (size_t)t->W[l] * t->H[l];
+    }
+    for (int s = 0; s < 2; ++s) {
+        size_t off = 0;
+        for (int l = 0; l < t->L; ++l) {
+            t->pyr[s].off[l] = off;
+            off = align_up(off + (size_t)t->pitch[l] * t->H[l], 256);
+        }
+        t->pyr[s].bytes = off + 256;
+        ALLOC(dalloc(&t->pyr[s].base, t->pyr[s].bytes));
+        ALLOC(cudaMemset(t->pyr[s].base, 0, t->pyr[s].bytes));
+    }
+    if (cfg->precision == GLT_MIXED) ALLOC(dalloc(&t->packed, pix));
+    const int maxp = cfg->max_points;
+    t->Npad = (int)align_up((size_t)maxp, 32);
+    ALLOC(dalloc(&t->uvd_dev, (size_t)maxp * 3));
+    ALLOC(dalloc(&t->pt, (size_t)t->Npad));
+    ALLOC(dalloc(&t->dz, (size_t)t->Npad));
+    ALLOC(dalloc(&t->I0, (size_t)t->L * t->Npad * 8));
+    ALLOC(dalloc(&t->desc_dev, 1));
+    ALLOC(dalloc(&t->desc_ptr_dev, 1));
+    ALLOC(dalloc(&t->user_dev, 1));
+    ALLOC(dalloc(&t->trace_count, 1));
+    ALLOC(dalloc(&t->jobs_dev, (size_t)2 * GLT_MAX_LEVELS));
+    ALLOC(dalloc(&t->pack_dev, (size_t)GLT_MAX_LEVELS));
+    ALLOC(dalloc(&t->init_dev, 14));
+    ALLOC(dalloc(&t->result_dev, 1));
+    int maxit = 0;
+    for (int l = 0; l < t->L; ++l) maxit = std::max(maxit, cfg->max_iters[l]);
+    t->max_trace = t->L * (1 + maxit);
+    ALLOC(dalloc(&t->trace_cost, (size_t)t->max_trace));
+    ALLOC(dalloc(&t->trace_info, (size_t)t->max_trace));
+    t->lin_blocks = (maxp + 127) / 128;
+    ALLOC(dalloc(&t->lin_partials, (size_t)t->lin_blocks * kAccPad));
+    ALLOC(dalloc(&t->lin_counter, 1));
+    ALLOC(cudaMemset(t->lin_counter, 0, sizeof(unsigned)));
+    ALLOC(dalloc(&t->lin_out, (size_t)kAccPad));
+    ALLOC(dalloc(&t->lin_res, (size_t)maxp * 8));
+    ALLOC(cudaMallocHost(reinterpret_cast<void**>(&t->h_init), 14 * sizeof(double)));
+    ALLOC(cudaMallocHost(reinterpret_cast<void**>(&t->h_result), sizeof(glt_result)));
+    ALLOC(cudaMallocHost(reinterpret_cast<void**>(&t->h_lin), kAccPad * sizeof(double)));
+
+    // descriptor
+    StreamDesc& D = t->desc_host;
+    std::memset(&D, 0, sizeof(D));
+    for (int l = 0; l < t->L; ++l) {
+        D.lv[l].img = t->pyr[GLT_CUR].base + t->pyr[GLT_CUR].off[l];
+        D.lv[l].packed = t->packed ? t->packed + t->poff[l] : nullptr;
+        D.lv[l].W = t->W[l];
+        D.lv[l].H = t->H[l];
+        D.lv[l].pitch = t->pitch[l];
+    }
+    D.L = t->L;
+    D.N = 0;
+    D.Npad = t->Npad;
+    D.fx = (float)cfg->fx;
+    D.fy = (float)cfg->fy;
+    D.huber_k = (float)cfg->huber_k;
+    D.zmin = (float)cfg->zmin;
+    D.pt = t->pt;
+    D.dz = t->dz;
+    D.I0 = t->I0;
+    for (int l = 0; l < GLT_MAX_LEVELS; ++l) D.max_iters[l] = l < t->L ? cfg->max_iters[l] : 0;
+    D.min_valid = cfg->min_valid;
+    D.max_trace = t->max_trace;
+    D.lambda0 = cfg->lambda0;
+    D.lambda_up = cfg->lambda_up;
+    D.lambda_down = cfg->lambda_down;
+    D.eps_step = cfg->eps_step;
+    D.eps_cost = cfg->eps_cost;
+    D.accept_step = cfg->accept_step;
+    D.trace_cost = t->trace_cost;
+    D.trace_info = t->trace_info;
+    D.trace_count = t->trace_count;
+    ALLOC(cudaMemcpy(t->desc_dev, &D, sizeof(D), cudaMemcpyHostToDevice));
+    ALLOC(cudaMemcpy(t->desc_ptr_dev, &t->desc_dev, sizeof(StreamDesc*), cudaMemcpyHostToDevice));
+    const int zero = 0;
+    ALLOC(cudaMemcpy(t->user_dev, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    ALLOC(cudaMemcpy(t->trace_count, &zero, sizeof(int), cudaMemcpyHostToDevice));
+
+    // pyramid jobs per slot: level l-1 -> l
+    std::vector<PyrJob> jobs(2 * GLT_MAX_LEVELS);
+    for (int s = 0; s < 2; ++s)
+        for (int l = 1; l < t->L; ++l) {
+            PyrJob& J = jobs[s * GLT_MAX_LEVELS + (l - 1)];
+            J.src = t->pyr[s].base + t->pyr[s].off[l - 1];
+            J.dst = t->pyr[s].base + t->pyr[s].off[l];
+            J.sW = t->W[l - 1];
+            J.sH = t->H[l - 1];
+            J.sp = t->pitch[l - 1];
+            J.dW = t->W[l];
+            J.dH = t->H[l];
+            J.dp = t->pitch[l];
+        }
+    ALLOC(cudaMemcpy(t->jobs_dev, jobs.data(), jobs.size() * sizeof(PyrJob), cudaMemcpyHostToDevice));
+    std::vector<PackJob> packs(GLT_MAX_LEVELS);
+    for (int l = 0; l < t->L; ++l) {
+        packs[l].src = t->pyr[GLT_CUR].base + t->pyr[GLT_CUR].off[l];
+        packs[l].dst = t->packed ? t->packed + t->poff[l] : nullptr;
+        packs[l].W = t->packed ? t->W[l] : 0;
+        packs[l].H = t->H[l];
+        packs[l].sp = t->pitch[l];
+    }
+    ALLOC(cudaMemcpy(t->pack_dev, packs.data(), packs.size() * sizeof(PackJob), cudaMemcpyHostToDevice));
+#undef ALLOC
+    resolve_shape(t);
+    *out = t;
+    return GLT_OK;
+}
+
+void glt_destroy(glt_tracker* trk) { free_tracker(trk); }
+
+int glt_build_pyramid(glt_tracker* t, int slot, const uint8_t* img, int pitch_bytes, int is_device,
+                      void* stream)
+{
+    if (!t || !img) return invalid("tracker or image is NULL");
+    if (slot != GLT_REF && slot != GLT_CUR) return invalid("slot must be GLT_REF or GLT_CUR");
+    if (pitch_bytes < t->cfg.width) return invalid("pitch_bytes < width");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Pyramid& P = t->pyr[slot];
+    GLT_CHECK(cudaMemcpy2DAsync(P.base + P.off[0], (size_t)t->pitch[0], img, (size_t)pitch_bytes,
+                                (size_t)t->W[0], (size_t)t->H[0],
+                                is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
+              "level-0 copy");
+    for (int l = 1; l < t->L; ++l)
+        GLT_CHECK(launch_pyr_down(t->jobs_dev + slot * GLT_MAX_LEVELS + (l - 1), 1,
+                                  pyr_tiles_x(t->W[l]), pyr_tiles_y(t->H[l]), s),
+                  "pyramid kernel");
+    if (slot == GLT_CUR && t->packed) {
+        GLT_CHECK(launch_pack(t->pack_dev, t->L, t->W[0] * t->H[0], s), "pack kernel");
+    }
+    P.built = true;
+    return GLT_OK;
+}
+
+int glt_set_map_points(glt_tracker* t, const float* uvd, int n, int is_device, void* stream)
+{
+    if (!t) return invalid("tracker is NULL");
+    if (n < 0 || (n > 0 && !uvd)) return invalid("bad point array");
+    if (n > t->cfg.max_points) {
+        set_error("more map points than max_points");
+        return GLT_ERR_CAPACITY;
+    }
+    if (!t->pyr[GLT_REF].built) {
+        set_error("glt_build_pyramid(GLT_REF) must come first");
+        return GLT_ERR_NO_REFERENCE;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const float* src = uvd;
+    if (n > 0 && !is_device) {
+        GLT_CHECK(cudaMemcpyAsync(t->uvd_dev, uvd, (size_t)n * 3 * sizeof(float),
+                                  cudaMemcpyHostToDevice, s),
+                  "map point upload");
+        src = t->uvd_dev;
+    }
+    t->N = n;
+    t->desc_host.N = n;
+    GLT_CHECK(cudaMemcpyAsync(t->desc_dev, &t->desc_host, sizeof(StreamDesc), cudaMemcpyHostToDevice, s),
+              "descriptor upload");
+    if (n > 0) GLT_CHECK(launch_set_points(t, src, n, s), "map point kernel");
+    t->have_points = true;
+    t->version++;
+    resolve_shape(t);
+    return GLT_OK;
+}
+
+static int track_prereq(glt_tracker* t)
+{
+    if (!t) return invalid("tracker is NULL");
+    if (!t->have_points) {
+        set_error("glt_set_map_points must come first");
+        return GLT_ERR_NO_REFERENCE;
+    }
+    if (!t->pyr[GLT_CUR].built) return invalid("glt_build_pyramid(GLT_CUR) must come first");
+    return GLT_OK;
+}
+
+int glt_track_frame_async(glt_tracker* t, const double* init_dev, glt_result* out_dev, void* stream)
+{
+    int rc = track_prereq(t);
+    if (rc != GLT_OK) return rc;
+    if (!init_dev || !out_dev) return invalid("init_dev / out_dev is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    GLT_CHECK(launch_track(t->desc_ptr_dev, t->user_dev, 1, t->cluster, t->threads,
+                           t->cfg.precision == GLT_MIXED, init_dev, out_dev, s),
+              "track kernel");
+    return GLT_OK;
+}
+
+int glt_track_frame(glt_tracker* t, const double T_init[12], const double ab_init[2], glt_result* out,
+                    void* stream)
+{
+    int rc = track_prereq(t);
+    if (rc != GLT_OK) return rc;
+    if (!T_init || !ab_init || !out) return invalid("NULL argument");
+    if (!finite_all(T_init, 12) || !finite_all(ab_init, 2)) return invalid("non-finite initial state");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::memcpy(t->h_init, T_init, 12 * sizeof(double));
+    t->h_init[12] = ab_init[0];
+    t->h_init[13] = ab_init[1];
+    GLT_CHECK(cudaMemcpyAsync(t->init_dev, t->h_init, 14 * sizeof(double), cudaMemcpyHostToDevice, s),
+              "init upload");
+    GLT_CHECK(launch_track(t->desc_ptr_dev, t->user_dev, 1, t->cluster, t->threads,
+                           t->cfg.precision == GLT_MIXED, t->init_dev, t->result_dev, s),
+              "track kernel");
+    GLT_CHECK(cudaMemcpyAsync(t->h_result, t->result_dev, sizeof(glt_result), cudaMemcpyDeviceToHost, s),
+              "result download");
+    GLT_CHECK(cudaStreamSynchronize(s), "track");
+    *out = *t->h_result;
+    return GLT_OK;
+}
+
+int glt_debug_linearize(glt_tracker* t, int level, const double T[12], double a, double b,
+                        double H[64], double g[8], double* E, int* n, float* res, void* stream)
+{
+    int rc = track_prereq(t);
+    if (rc != GLT_OK) return rc;
+    if (level < 0 || level >= t->L) return invalid("level out of range");
+    if (!T || !H || !g || !E || !n) return invalid("NULL argument");
+    if (!finite_all(T, 12) || !std::isfinite(a) || !std::isfinite(b)) return invalid("non-finite state");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (t->N == 0) {
+        std::memset(H, 0, 64 * sizeof(double));
+        std::memset(g, 0, 8 * sizeof(double));
+        *E = 0.0;
+        *n = 0;
+        return GLT_OK;
+    }
+    PassParams P;
+    make_pass_params(T, a, b, level, P);
+    GLT_CHECK(launch_linearize(t, P, res != nullptr, s), "linearize kernel");
+    GLT_CHECK(cudaMemcpyAsync(t->h_lin, t->lin_out, kAccPad * sizeof(double), cudaMemcpyDeviceToHost, s),
+              "linearize download");
+    if (res)
+        GLT_CHECK(cudaMemcpyAsync(res, t->lin_res, (size_t)t->N * 8 * sizeof(float), cudaMemcpyDeviceToHost, s),
+                  "residual download");
+    GLT_CHECK(cudaStreamSynchronize(s), "linearize");
+    int idx = 0;
+    for (int i = 0; i < 8; ++i)
+        for (int j = i; j < 8; ++j) {
+            H[8 * i + j] = t->h_lin[idx];
+            H[8 * j + i] = t->h_lin[idx];
+            ++idx;
+        }
+    for (int i = 0; i < 8; ++i) g[i] = t->h_lin[kIdxG + i];
+    *E = t->h_lin[kIdxE];
+    *n = (int)t->h_lin[kIdxN];
+    return GLT_OK;
+}
+
+int glt_get_pyramid(glt_tracker* t, int slot, int level, uint8_t* out, void* stream)
+{
+    if (!t || !out) return invalid("NULL argument");
+    if (slot != GLT_REF && slot != GLT_CUR) return invalid("bad slot");
+    if (level < 0 || level >= t->L) return invalid("level out of range");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const Pyramid& P = t->pyr[slot];
+    GLT_CHECK(cudaMemcpy2DAsync(out, (size_t)t->W[level], P.base + P.off[level], (size_t)t->pitch[level],
+                                (size_t)t->W[level], (size_t)t->H[level], cudaMemcpyDeviceToHost, s),
+              "pyramid download");
+    GLT_CHECK(cudaStreamSynchronize(s), "pyramid download");
+    return GLT_OK;
+}
+
+int glt_get_trace(glt_tracker* t, double* cost, int* info, int max, int* count, void* stream)
+{
+    if (!t || !count || max < 0 || (max > 0 && (!cost || !info))) return invalid("bad argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int passes = 0;
+    GLT_CHECK(cudaMemcpyAsync(&passes, t->trace_count, sizeof(int), cudaMemcpyDeviceToHost, s), "trace");
+    GLT_CHECK(cudaStreamSynchronize(s), "trace");
+    int k = std::min(std::min(passes, t->max_trace), max);
+    if (k > 0) {
+        GLT_CHECK(cudaMemcpyAsync(cost, t->trace_cost, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, s), "trace");
+        GLT_CHECK(cudaMemcpyAsync(info, t->trace_info, (size_t)k * sizeof(int), cudaMemcpyDeviceToHost, s), "trace");
+        GLT_CHECK(cudaStreamSynchronize(s), "trace");
+    }
+    *count = k;
+    return GLT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched form
+// ---------------------------------------------------------------------------
+static void free_batch(glt_batch* b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->descs_dev);
+    cudaFree(b->users_dev);
+    cudaFree(b->copy_dev);
+    cudaFree(b->jobs_dev);
+    cudaFree(b->pack_dev);
+    delete b;
+}
+
+int glt_batch_create(glt_tracker* const* trackers, int S, glt_batch** out)
+{
+    if (!out) return invalid("out is NULL");
+    *out = nullptr;
+    if (!trackers || S < 1 || S > 65535) return invalid("need 1..65535 trackers");
+    const int prec = trackers[0] ? trackers[0]->cfg.precision : -1;
+    for (int i = 0; i < S; ++i) {
+        if (!trackers[i]) return invalid("NULL tracker in batch");
+        if (trackers[i]->cfg.precision != prec) return invalid("all trackers of a batch need the same precision");
+        if (trackers[i]->device != trackers[0]->device) return invalid("all trackers must be on one device");
+    }
+    glt_batch* b = new glt_batch();
+    b->S = S;
+    b->precision = prec;
+    b->trk.assign(trackers, trackers + S);
+    b->order.resize(S);
+    for (int i = 0; i < S; ++i) b->order[i] = i;
+    // longest streams first (points x level-0 pixels as the work estimate)
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+        const double wx = (double)trackers[x]->cfg.max_points * trackers[x]->cfg.width;
+        const double wy = (double)trackers[y]->cfg.max_points * trackers[y]->cfg.width;
+        return wx > wy;
+    });
+    for (int i = 0; i < S; ++i) b->Lmax = std::max(b->Lmax, trackers[i]->L);
+#define BALLOC(call)                                  \
+    do {                                              \
+        cudaError_t e2 = (call);                      \
+        if (e2 != cudaSuccess) {                      \
+            free_batch(b);                            \
+            return cuda_fail(e2, "batch allocation"); \
+        }                                             \
+    } while (0)
+    std::vector<StreamDesc*> dp(S);
+    std::vector<int> users(S);
+    for (int i = 0; i < S; ++i) {
+        dp[i] = trackers[b->order[i]]->desc_dev;
+        users[i] = b->order[i];
+    }
+    BALLOC(dalloc(&b->descs_dev, (size_t)S));
+    BALLOC(dalloc(&b->users_dev, (size_t)S));
+    BALLOC(cudaMemcpy(b->descs_dev, dp.data(), S * sizeof(StreamDesc*), cudaMemcpyHostToDevice));
+    BALLOC(cudaMemcpy(b->users_dev, users.data(), S * sizeof(int), cudaMemcpyHostToDevice));
+    std::vector<CopyJob> copies(S);
+    std::vector<PyrJob> jobs((size_t)std::max(1, b->Lmax - 1) * S);
+    std::vector<PackJob> packs((size_t)b->Lmax * S);
+    for (int i = 0; i < S; ++i) {
+        glt_tracker* t = trackers[i];
+        copies[i].dst = t->pyr[GLT_CUR].base + t->pyr[GLT_CUR].off[0];
+        copies[i].W = t->W[0];
+        copies[i].H = t->H[0];
+        copies[i].dp = t->pitch[0];
+        for (int l = 1; l < b->Lmax; ++l) {
+            PyrJob& J = jobs[(size_t)(l - 1) * S + i];
+            std::memset(&J, 0, sizeof(J));
+            if (l < t->L) {
+                J.src = t->pyr[GLT_CUR].base + t->pyr[GLT_CUR].off[l - 1];
+                J.dst = t->pyr[GLT_CUR].base + t->pyr[GLT_CUR].off[l];
+                J.sW = t->W[l - 1];
+                J.sH = t->H[l - 1];
+                J.sp = t->pitch[l - 1];
+                J.dW = t->W[l];
+                J.dH = t->H[l];
+                J.dp = t->pitch[l];
+            }
+        }
+        for (int l = 0; l < b->Lmax; ++l) {
+            PackJob& P = packs[(size_t)l * S + i];
+            std::memset(&P, 0, sizeof(P));
+            if (l < t->L && t->packed) {
+                P.src = t->pyr[GLT_CUR].base + t->pyr[GLT_CUR].off[l];
+                P.dst = t->packed + t->poff[l];
+                P.W = t->W[l];
+                P.H = t->H[l];
+                P.sp = t->pitch[l];
+            }
+        }
+    }
+    BALLOC(dalloc(&b->copy_dev, (size_t)S));
+    BALLOC(dalloc(&b->jobs_dev, jobs.size()));
+    BALLOC(dalloc(&b->pack_dev, packs.size()));
+    BALLOC(cudaMemcpy(b->copy_dev, copies.data(), S * sizeof(CopyJob), cudaMemcpyHostToDevice));
+    BALLOC(cudaMemcpy(b->jobs_dev, jobs.data(), jobs.size() * sizeof(PyrJob), cudaMemcpyHostToDevice));
+    BALLOC(cudaMemcpy(b->pack_dev, packs.data(), packs.size() * sizeof(PackJob), cudaMemcpyHostToDevice));
+#undef BALLOC
+    b->cluster = 2;
+    b->threads = 256;
+    if (!track_shape_ok(b->cluster, b->threads, prec == GLT_MIXED)) b->cluster = 1;
+    *out = b;
+    return GLT_OK;
+}
+
+void glt_batch_destroy(glt_batch* b) { free_batch(b); }
+
+static int batch_pyramid(glt_batch* b, const uint8_t* const* frames_dev, cudaStream_t s)
+{
+    int maxbytes = 0, maxw[GLT_MAX_LEVELS] = {}, maxh[GLT_MAX_LEVELS] = {}, maxpix = 0;
+    for (glt_tracker* t : b->trk) {
+        maxbytes = std::max(maxbytes, t->W[0] * t->H[0]);
+        maxpix = std::max(maxpix, t->W[0] * t->H[0]);
+        for (int l = 0; l < t->L; ++l) {
+            maxw[l] = std::max(maxw[l], t->W[l]);
+            maxh[l] = std::max(maxh[l], t->H[l]);
+        }
+    }
+    GLT_CHECK(launch_copy_frames(frames_dev, b->copy_dev, b->S, maxbytes, s), "batch copy kernel");
+    for (int l = 1; l < b->Lmax; ++l)
+        GLT_CHECK(launch_pyr_down(b->jobs_dev + (size_t)(l - 1) * b->S, b->S, pyr_tiles_x(maxw[l]),
+                                  pyr_tiles_y(maxh[l]), s),
+                  "batch pyramid kernel");
+    if (b->precision == GLT_MIXED)
+        GLT_CHECK(launch_pack(b->pack_dev, b->Lmax * b->S, maxpix, s), "batch pack kernel");
+    for (glt_tracker* t : b->trk) t->pyr[GLT_CUR].built = true;
+    return GLT_OK;
+}
+
+int glt_batch_build_pyramid(glt_batch* b, const uint8_t* const* frames_dev, void* stream)
+{
+    if (!b || !frames_dev) return invalid("NULL argument");
+    return batch_pyramid(b, frames_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
+static int batch_prereq(glt_batch* b)
+{
+    if (!b) return invalid("batch is NULL");
+    for (glt_tracker* t : b->trk)
+        if (!t->have_points) {
+            set_error("every tracker of the batch needs map points");
+            return GLT_ERR_NO_REFERENCE;
+        }
+    return GLT_OK;
+}
+
+int glt_batch_track(glt_batch* b, const double* init_dev, glt_result* out_dev, void* stream)
+{
+    int rc = batch_prereq(b);
+    if (rc != GLT_OK) return rc;
+    if (!init_dev || !out_dev) return invalid("NULL argument");
+    GLT_CHECK(launch_track(b->descs_dev, b->users_dev, b->S, b->cluster, b->threads,
+                           b->precision == GLT_MIXED, init_dev, out_dev,
+                           reinterpret_cast<cudaStream_t>(stream)),
+              "batch track kernel");
+    return GLT_OK;
+}
+
+int glt_batch_capture(glt_batch* b, const uint8_t* const* frames_dev, const double* init_dev,
+                      glt_result* out_dev, void* stream)
+{
+    int rc = batch_prereq(b);
+    if (rc != GLT_OK) return rc;
+    if (!frames_dev || !init_dev || !out_dev) return invalid("NULL argument");
+    if (!stream) return invalid("graph capture needs a non-default stream");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    GLT_CHECK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int r1 = batch_pyramid(b, frames_dev, s);
+    cudaError_t e1 = launch_track(b->descs_dev, b->users_dev, b->S, b->cluster, b->threads,
+                                  b->precision == GLT_MIXED, init_dev, out_dev, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (r1 != GLT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r1;
+    }
+    if (e1 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(e1, "capture track kernel");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+    b->graph = g;
+    GLT_CHECK(cudaGraphInstantiate(&b->exec, g, 0), "graph instantiate");
+    return GLT_OK;
+}
+
+int glt_batch_replay(glt_batch* b, void* stream)
+{
+    if (!b || !b->exec) return invalid("no captured graph");
+    GLT_CHECK(cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream)), "graph launch");
+    return GLT_OK;
+}
+
+int glt_batch_set_shape(glt_batch* b, int cluster, int threads)
+{
+    if (!b) return invalid("batch is NULL");
+    if (!track_shape_ok(cluster, threads, b->precision == GLT_MIXED)) return invalid("shape cannot launch");
+    b->cluster = cluster;
+    b->threads = threads;
+    return GLT_OK;
+}
+
+int glt_batch_autotune(glt_batch* b, const double* init_dev, glt_result* out_dev, int reps,
+                       int* best_cluster, int* best_threads, float* best_ms, void* stream)
+{
+    int rc = batch_prereq(b);
+    if (rc != GLT_OK) return rc;
+    if (!init_dev || !out_dev || reps < 1) return invalid("bad argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int shapes[][2] = {{1, 128}, {1, 256}, {2, 128}, {2, 256}, {4, 128}, {4, 256},
+                             {8, 128}, {8, 256}, {1, 512}, {2, 512}};
+    cudaEvent_t e0, e1;
+    GLT_CHECK(cudaEventCreate(&e0), "event");
+    GLT_CHECK(cudaEventCreate(&e1), "event");
+    float best = 1e30f;
+    int bc = b->cluster, bt = b->threads;
+    const bool mixed = b->precision == GLT_MIXED;
+    for (auto& sh : shapes) {
+        if (!track_shape_ok(sh[0], sh[1], mixed)) continue;
+        cudaError_t e = launch_track(b->descs_dev, b->users_dev, b->S, sh[0], sh[1], mixed, init_dev, out_dev, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps; ++r)
+            launch_track(b->descs_dev, b->users_dev, b->S, sh[0], sh[1], mixed, init_dev, out_dev, s);
+        cudaEventRecord(e1, s);
+        cudaError_t es = cudaEventSynchronize(e1);
+        if (es != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(es, "autotune");
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (ms < best) {
+            best = ms;
+            bc = sh[0];
+            bt = sh[1];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->cluster = bc;
+    b->threads = bt;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    if (best_cluster) *best_cluster = bc;
+    if (best_threads) *best_threads = bt;
+    if (best_ms) *best_ms = best;
+    return GLT_OK;
+}
+
+}  // extern "C"

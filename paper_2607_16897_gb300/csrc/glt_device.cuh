@@ -1,0 +1,632 @@
+// Device-side building blocks of the tracker: per-stream descriptors, the
+// per-point linearisation (projection, bilinear gather of I and grad I,
+// residual, Huber weight, forward Jacobian, 44-term normal-equation
+// accumulation), the warp reduce-scatter, and the FP64 LM solver tail
+// (Cholesky 8x8, SE(3) exponential, pose composition).
+//
+// Method: GLidE-SLAM Sec. IV (Eqs. 1-5) in the forward form of Sec. IV-B
+// (Jacobian from the current image's gradient at the warped location), with
+// affine brightness, Huber weights and LM damping added by this library.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "glt.h"
+
+namespace glt {
+
+constexpr int kMaxLevels = GLT_MAX_LEVELS;
+constexpr int kNumH = 36;        // upper triangle of the 8x8 H
+constexpr int kIdxG = 36;        // g = J^T W r, 8 entries
+constexpr int kIdxE = 44;        // Huber energy
+constexpr int kIdxN = 45;        // valid sample count
+constexpr int kNumAcc = 46;
+constexpr int kAccPad = 48;      // padded for the 5-stage reduce-scatter
+
+// 8-pixel sparse pattern (offsets du_k of Eq. 2), level pixels.
+__host__ __device__ constexpr int pat_dx(int k) { return k == 1 ? -2 : k == 2 ? 2 : k == 5 ? -1 : k == 6 ? 1 : k == 7 ? -1 : 0; }
+__host__ __device__ constexpr int pat_dy(int k) { return k == 3 ? -2 : k == 4 ? 2 : (k == 5 || k == 6) ? -1 : k == 7 ? 1 : 0; }
+
+struct LevelDev {
+    const uint8_t* img;   // uint8 level, `pitch` bytes per row (pitch >= W + 8, multiple of 16)
+    const uint2* packed;  // GLT_MIXED: FP16 (I, gx, gy, 0) per pixel, W pixels per row
+    int W, H, pitch;
+};
+
+// One tracked stream as the kernels see it (device memory).
+struct StreamDesc {
+    LevelDev lv[kMaxLevels];
+    int L, N, Npad;
+    float fx, fy;          // level-0 focal lengths
+    float huber_k, zmin;
+    const float4* pt;      // (u0, v0, (u0-cx)/fx, (v0-cy)/fy)
+    const float2* dz;      // (depth, 1/depth)
+    const float* I0;       // [L][Npad][8]; I0[l][p][0] is NaN where the point is unusable
+    int max_iters[kMaxLevels];
+    int min_valid;
+    int max_trace;
+    double lambda0, lambda_up, lambda_down, eps_step, eps_cost, accept_step;
+    double* trace_cost;    // [max_trace] or null
+    int* trace_info;       // [max_trace] or null
+    int* trace_count;      // passes of the last track, or null
+};
+
+// The state one linearisation pass is evaluated at, in the form the FP32
+// gather uses: R - I and t rounded from the FP64 pose, e^a, b.
+struct PassParams {
+    float Rm[9];
+    float t[3];
+    float ea, b;
+    float scale;           // 2^-level
+    int level;
+    int done;
+};
+
+// ---------------------------------------------------------------------------
+// Per-point linearisation
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float u8f(uint32_t w, int byte) { return (float)((w >> (8 * byte)) & 0xffu); }
+
+struct PointGeom {
+    float al, be;          // bilinear weights' fractions (shared by all 8 samples)
+    int xb, yb;            // integer base of sample 0
+    float a0[3], a1[3];    // rows of d(pi)/d(x_c) * R (level intrinsics)
+    float xr[3];           // x_r
+};
+
+// Projects point p through the pass state. Returns false if the point is not
+// usable (invalid reference, behind zmin, or a pattern sample outside
+// 1 <= q < W-2, 1 <= q < H-2).
+//
+// Projection is evaluated relative to the reference pixel to keep FP32
+// accurate at any image width:  with m = ((u0-cx)/fx, (v0-cy)/fy, 1) and
+// D = (R - I) m + t / d,  x_c = d (m + D)  and
+// u - u0 = fx (D_x - m_x D_z) / (1 + D_z)   (exactly Eq. 1's pi(R x_r + t)).
+__device__ __forceinline__ bool project_point(const StreamDesc& D, const PassParams& P,
+                                              const LevelDev& lv, int p, PointGeom& G)
+{
+    const float4 q = D.pt[p];
+    const float2 dz = D.dz[p];
+    const float ub = q.z, vb = q.w, d = dz.x, rho = dz.y;
+    const float Dx = fmaf(P.Rm[0], ub, fmaf(P.Rm[1], vb, fmaf(P.t[0], rho, P.Rm[2])));
+    const float Dy = fmaf(P.Rm[3], ub, fmaf(P.Rm[4], vb, fmaf(P.t[1], rho, P.Rm[5])));
+    const float Dz = fmaf(P.Rm[6], ub, fmaf(P.Rm[7], vb, fmaf(P.t[2], rho, P.Rm[8])));
+    const float onez = 1.0f + Dz;
+    if (!(d * onez > D.zmin)) return false;
+    const float iz = 1.0f / onez;
+    const float du = D.fx * fmaf(-ub, Dz, Dx) * iz;
+    const float dv = D.fy * fmaf(-vb, Dz, Dy) * iz;
+    if (!(fabsf(du) < 1e6f && fabsf(dv) < 1e6f)) return false;
+    const float s = P.scale;
+    const float U = q.x * s, V = q.y * s;
+    const float Ui = floorf(U), Vi = floorf(V);
+    const float su = (U - Ui) + du * s;
+    const float sv = (V - Vi) + dv * s;
+    const float fu = floorf(su), fv = floorf(sv);
+    G.al = su - fu;
+    G.be = sv - fv;
+    G.xb = (int)Ui + (int)fu;
+    G.yb = (int)Vi + (int)fv;
+    if (G.xb < 3 || G.xb > lv.W - 5 || G.yb < 3 || G.yb > lv.H - 5) return false;
+    // d(pi)/d(x_c) R, with x_c / z_c = (m + D) / (1 + D_z) and 1/z_c = rho / (1 + D_z)
+    const float xn = (ub + Dx) * iz, yn = (vb + Dy) * iz;
+    const float fxl = D.fx * s * rho * iz, fyl = D.fy * s * rho * iz;
+    const float R0[3] = {1.0f + P.Rm[0], P.Rm[1], P.Rm[2]};
+    const float R1[3] = {P.Rm[3], 1.0f + P.Rm[4], P.Rm[5]};
+    const float R2[3] = {P.Rm[6], P.Rm[7], 1.0f + P.Rm[8]};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        G.a0[c] = fxl * fmaf(-xn, R2[c], R0[c]);
+        G.a1[c] = fyl * fmaf(-yn, R2[c], R1[c]);
+    }
+    G.xr[0] = d * ub;
+    G.xr[1] = d * vb;
+    G.xr[2] = d;
+    return true;
+}
+
+// Accumulates one residual sample into acc (upper triangle of w J J^T, w J r,
+// Huber energy, count).
+__device__ __forceinline__ void accumulate_sample(const PointGeom& G, float I, float gx, float gy,
+                                                  float i0, float ea, float b, float k,
+                                                  float* acc, float* res_out)
+{
+    float J[8];
+    const float Jt0 = fmaf(gx, G.a0[0], gy * G.a1[0]);
+    const float Jt1 = fmaf(gx, G.a0[1], gy * G.a1[1]);
+    const float Jt2 = fmaf(gx, G.a0[2], gy * G.a1[2]);
+    J[0] = Jt0;
+    J[1] = Jt1;
+    J[2] = Jt2;
+    // rotational columns: row vector (Jt) * (-[x_r]x) = x_r x Jt
+    J[3] = fmaf(G.xr[1], Jt2, -G.xr[2] * Jt1);
+    J[4] = fmaf(G.xr[2], Jt0, -G.xr[0] * Jt2);
+    J[5] = fmaf(G.xr[0], Jt1, -G.xr[1] * Jt0);
+    J[6] = -ea * i0;
+    J[7] = -1.0f;
+    const float r = fmaf(-ea, i0, I) - b;
+    const float ar = fabsf(r);
+    const float w = ar <= k ? 1.0f : k / ar;
+    const float rho = ar <= k ? 0.5f * r * r : k * (ar - 0.5f * k);
+    if (res_out) *res_out = r;
+    float wJ[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) wJ[i] = w * J[i];
+    int idx = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+#pragma unroll
+        for (int j = i; j < 8; ++j) {
+            acc[idx] = fmaf(wJ[i], J[j], acc[idx]);
+            ++idx;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[kIdxG + i] = fmaf(wJ[i], r, acc[kIdxG + i]);
+    acc[kIdxE] += rho;
+    acc[kIdxN] += 1.0f;
+}
+
+// Linearises map point p at the pass state into acc.  RES: also write the 8
+// residuals (NaN for an unusable point) to res[8p..8p+7].
+template <bool MIXED, bool RES>
+__device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassParams& P, int p,
+                                                float* acc, float* res)
+{
+    const LevelDev& lv = D.lv[P.level];
+    const float4* I0p = reinterpret_cast<const float4*>(D.I0 + ((size_t)P.level * D.Npad + p) * 8);
+    const float4 ia = I0p[0], ib = I0p[1];
+    PointGeom G;
+    bool ok = !isnan(ia.x) && project_point(D, P, lv, p, G);
+    if (!ok) {
+        if (RES) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) res[8 * p + k] = __int_as_float(0x7fc00000);
+        }
+        return;
+    }
+    const float i0[8] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
+    const float w00 = (1.0f - G.al) * (1.0f - G.be), w10 = G.al * (1.0f - G.be);
+    const float w01 = (1.0f - G.al) * G.be, w11 = G.al * G.be;
+    if (!MIXED) {
+        // 8x8 byte window, rows yb-3..yb+4, columns xb-3..xb+4: two aligned
+        // 8-byte loads per row, then a funnel shift to the window start.
+        const int xs = G.xb - 3;
+        const int a8 = xs & ~7;
+        const int sh = (xs - a8) * 8;
+        const uint8_t* base = lv.img + (size_t)(G.yb - 3) * lv.pitch + a8;
+        uint32_t rw[8][2];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const uint2* rp = reinterpret_cast<const uint2*>(base + (size_t)r * lv.pitch);
+            const uint2 w0 = __ldg(rp), w1 = __ldg(rp + 1);
+            if (sh < 32) {
+                rw[r][0] = __funnelshift_r(w0.x, w0.y, sh);
+                rw[r][1] = __funnelshift_r(w0.y, w1.x, sh);
+            } else {
+                rw[r][0] = __funnelshift_r(w0.y, w1.x, sh - 32);
+                rw[r][1] = __funnelshift_r(w1.x, w1.y, sh - 32);
+            }
+        }
+#define GLT_PX(r, c) u8f(rw[(r)][(c) >> 2], (c) & 3)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int r0 = pat_dy(k) + 3, c0 = pat_dx(k) + 3;
+            const float I00 = GLT_PX(r0, c0), I10 = GLT_PX(r0, c0 + 1);
+            const float I01 = GLT_PX(r0 + 1, c0), I11 = GLT_PX(r0 + 1, c0 + 1);
+            const float I = fmaf(w00, I00, fmaf(w10, I10, fmaf(w01, I01, w11 * I11)));
+            // central differences at the four taps (the 1/2 is applied after interpolation)
+            const float gx = 0.5f * fmaf(w00, I10 - GLT_PX(r0, c0 - 1),
+                                   fmaf(w10, GLT_PX(r0, c0 + 2) - I00,
+                                   fmaf(w01, I11 - GLT_PX(r0 + 1, c0 - 1),
+                                        w11 * (GLT_PX(r0 + 1, c0 + 2) - I01))));
+            const float gy = 0.5f * fmaf(w00, I01 - GLT_PX(r0 - 1, c0),
+                                   fmaf(w10, I11 - GLT_PX(r0 - 1, c0 + 1),
+                                   fmaf(w01, GLT_PX(r0 + 2, c0) - I00,
+                                        w11 * (GLT_PX(r0 + 2, c0 + 1) - I10))));
+            accumulate_sample(G, I, gx, gy, i0[k], P.ea, P.b, D.huber_k, acc,
+                              RES ? res + 8 * p + k : nullptr);
+        }
+#undef GLT_PX
+    } else {
+        const uint2* pk = lv.packed;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int x0 = G.xb + pat_dx(k), y0 = G.yb + pat_dy(k);
+            const uint2* t0 = pk + (size_t)y0 * lv.W + x0;
+            const uint2* t1 = t0 + lv.W;
+            const uint2 p00 = __ldg(t0), p10 = __ldg(t0 + 1), p01 = __ldg(t1), p11 = __ldg(t1 + 1);
+            const float2 a00 = __half22float2(*reinterpret_cast<const __half2*>(&p00.x));
+            const float2 a10 = __half22float2(*reinterpret_cast<const __half2*>(&p10.x));
+            const float2 a01 = __half22float2(*reinterpret_cast<const __half2*>(&p01.x));
+            const float2 a11 = __half22float2(*reinterpret_cast<const __half2*>(&p11.x));
+            const float y00 = __low2float(*reinterpret_cast<const __half2*>(&p00.y));
+            const float y10 = __low2float(*reinterpret_cast<const __half2*>(&p10.y));
+            const float y01 = __low2float(*reinterpret_cast<const __half2*>(&p01.y));
+            const float y11 = __low2float(*reinterpret_cast<const __half2*>(&p11.y));
+            const float I = fmaf(w00, a00.x, fmaf(w10, a10.x, fmaf(w01, a01.x, w11 * a11.x)));
+            const float gx = fmaf(w00, a00.y, fmaf(w10, a10.y, fmaf(w01, a01.y, w11 * a11.y)));
+            const float gy = fmaf(w00, y00, fmaf(w10, y10, fmaf(w01, y01, w11 * y11)));
+            accumulate_sample(G, I, gx, gy, i0[k], P.ea, P.b, D.huber_k, acc,
+                              RES ? res + 8 * p + k : nullptr);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------
+// Butterfly reduce-scatter of 48 values over a warp: 48 shuffles instead of
+// 5 x 48.  Afterwards lane L holds the warp sums of indices
+// base(L) + {0,1,2}, base = 24*b4 + 12*b3 + 6*b2 + 3*b1 (b_i = bit i of L).
+__device__ __forceinline__ int rs_base(int lane)
+{
+    return ((lane >> 4) & 1) * 24 + ((lane >> 3) & 1) * 12 + ((lane >> 2) & 1) * 6 + ((lane >> 1) & 1) * 3;
+}
+
+__device__ __forceinline__ void warp_reduce_scatter48(float (&v)[kAccPad], int lane)
+{
+    const unsigned full = 0xffffffffu;
+#define GLT_RS_STAGE(HALF, OFF)                                            \
+    {                                                                      \
+        const bool hi = (lane & (OFF)) != 0;                               \
+        _Pragma("unroll") for (int i = 0; i < (HALF); ++i) {               \
+            const float send = hi ? v[i] : v[i + (HALF)];                  \
+            const float keep = hi ? v[i + (HALF)] : v[i];                  \
+            v[i] = keep + __shfl_xor_sync(full, send, (OFF));              \
+        }                                                                  \
+    }
+    GLT_RS_STAGE(24, 16)
+    GLT_RS_STAGE(12, 8)
+    GLT_RS_STAGE(6, 4)
+    GLT_RS_STAGE(3, 2)
+#undef GLT_RS_STAGE
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] += __shfl_xor_sync(full, v[i], 1);
+}
+
+// Block reduction of the per-thread accumulators into out[0..kNumAcc).
+// KAHAN: compensated FP32 sum across warps, compensation in out_c.
+// Ends with __syncthreads().
+template <int THREADS, bool KAHAN>
+__device__ __forceinline__ void block_reduce(float (&acc)[kAccPad], float (*red)[kAccPad], float* out,
+                                             float* out_c)
+{
+    constexpr int NW = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    warp_reduce_scatter48(acc, lane);
+    if ((lane & 1) == 0) {
+        const int b = rs_base(lane);
+        red[warp][b + 0] = acc[0];
+        red[warp][b + 1] = acc[1];
+        red[warp][b + 2] = acc[2];
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumAcc) {
+        const int j = threadIdx.x;
+        float s = 0.0f, c = 0.0f;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            if (KAHAN) {
+                const float y = red[w][j] - c;
+                const float t = s + y;
+                c = (t - s) - y;
+                s = t;
+            } else {
+                s += red[w][j];
+            }
+        }
+        out[j] = s;
+        if (KAHAN) out_c[j] = -c;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 solver tail: SE(3) exponential, composition, 8x8 damped Cholesky
+// ---------------------------------------------------------------------------
+// exp of the twist xi = (v, w): R = I + A W + B W^2, t = (I + B W + C W^2) v
+// with A = sin th / th, B = (1 - cos th) / th^2, C = (th - sin th) / th^3.
+// Series of the same functions are used where the closed forms cancel.
+__device__ inline void se3_exp_d(const double* xi, double* T)
+{
+    const double w0 = xi[3], w1 = xi[4], w2 = xi[5];
+    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
+    const double th = sqrt(th2);
+    double A, B, C;
+    if (th < 1e-4) {
+        A = 1.0 - th2 * (1.0 / 6.0) + th2 * th2 * (1.0 / 120.0);
+        B = 0.5 - th2 * (1.0 / 24.0) + th2 * th2 * (1.0 / 720.0);
+    } else {
+        double sn, cs, sh, ch;
+        sincos(th, &sn, &cs);
+        sincos(0.5 * th, &sh, &ch);
+        A = sn / th;
+        B = 2.0 * sh * sh / th2;
+    }
+    if (th < 0.1) {
+        const double t4 = th2 * th2;
+        C = 1.0 / 6.0 - th2 * (1.0 / 120.0) + t4 * (1.0 / 5040.0) - t4 * th2 * (1.0 / 362880.0) +
+            t4 * t4 * (1.0 / 39916800.0);
+    } else {
+        C = (th - sin(th)) / (th2 * th);
+    }
+    // W = [w]x, W^2 = w w^T - th^2 I
+    const double W[9] = {0, -w2, w1, w2, 0, -w0, -w1, w0, 0};
+    const double ww[3] = {w0, w1, w2};
+    double Rm[9], V[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double W2 = ww[i] * ww[j] - (i == j ? th2 : 0.0);
+            const double I = i == j ? 1.0 : 0.0;
+            Rm[3 * i + j] = I + A * W[3 * i + j] + B * W2;
+            V[3 * i + j] = I + B * W[3 * i + j] + C * W2;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        T[4 * i + 0] = Rm[3 * i + 0];
+        T[4 * i + 1] = Rm[3 * i + 1];
+        T[4 * i + 2] = Rm[3 * i + 2];
+        T[4 * i + 3] = V[3 * i] * xi[0] + V[3 * i + 1] * xi[1] + V[3 * i + 2] * xi[2];
+    }
+}
+
+__device__ inline void se3_compose_d(const double* A, const double* B, double* C)
+{
+    double o[12];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            double s = c == 3 ? A[4 * r + 3] : 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s += A[4 * r + k] * B[4 * k + c];
+            o[4 * r + c] = s;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 12; ++i) C[i] = o[i];
+}
+
+// Solves (H + lambda diag(H)) delta = -g by Cholesky.  False if a pivot is not
+// positive (or below 1e-13 of its diagonal entry).
+__device__ inline bool damped_cholesky_solve(const double* H, const double* g, double lambda,
+                                             double* delta)
+{
+    double Lm[8][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const double ajj = H[9 * j] + lambda * H[9 * j];
+        double d = ajj;
+#pragma unroll
+        for (int k = 0; k < j; ++k) d -= Lm[j][k] * Lm[j][k];
+        if (!(d > 0.0) || !(d > 1e-13 * ajj)) return false;
+        const double ljj = sqrt(d);
+        Lm[j][j] = ljj;
+        const double inv = 1.0 / ljj;
+#pragma unroll
+        for (int i = j + 1; i < 8; ++i) {
+            double s = H[8 * i + j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= Lm[i][k] * Lm[j][k];
+            Lm[i][j] = s * inv;
+        }
+    }
+    double y[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        double s = -g[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) s -= Lm[i][k] * y[k];
+        y[i] = s / Lm[i][i];
+    }
+#pragma unroll
+    for (int i = 7; i >= 0; --i) {
+        double s = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 8; ++k) s -= Lm[k][i] * delta[k];
+        delta[i] = s / Lm[i][i];
+    }
+    return true;
+}
+
+// Pass parameters for state (T, a, b) on `level`.
+__device__ __host__ inline void make_pass_params(const double* T, double a, double b, int level,
+                                                 PassParams& P)
+{
+    P.Rm[0] = (float)(T[0] - 1.0);
+    P.Rm[1] = (float)T[1];
+    P.Rm[2] = (float)T[2];
+    P.Rm[3] = (float)T[4];
+    P.Rm[4] = (float)(T[5] - 1.0);
+    P.Rm[5] = (float)T[6];
+    P.Rm[6] = (float)T[8];
+    P.Rm[7] = (float)T[9];
+    P.Rm[8] = (float)(T[10] - 1.0);
+    P.t[0] = (float)T[3];
+    P.t[1] = (float)T[7];
+    P.t[2] = (float)T[11];
+    P.ea = expf((float)a);
+    P.b = (float)b;
+    P.level = level;
+    P.scale = ldexpf(1.0f, -level);
+    P.done = 0;
+}
+
+// LM state machine, replicated in every CTA of a stream's cluster (each CTA
+// runs it on bit-identical inputs, so all take the same decisions).
+enum { PH_START = 0, PH_CAND = 1 };
+
+struct Solver {
+    double T[12], a, b;       // accepted state
+    double Tc[12], ac, bc;    // candidate under evaluation
+    double H[64], g[8];       // normal equations at the accepted state
+    double cost, lambda, maxstep, res_cost;
+    int n, res_n, level, it, phase, status, passes;
+    int iters[kMaxLevels];
+};
+
+__device__ inline void unpack_normal(const double* tot, double* H, double* g)
+{
+    int idx = 0;
+    for (int i = 0; i < 8; ++i)
+        for (int j = i; j < 8; ++j) {
+            H[8 * i + j] = tot[idx];
+            H[8 * j + i] = tot[idx];
+            ++idx;
+        }
+    for (int i = 0; i < 8; ++i) g[i] = tot[kIdxG + i];
+}
+
+__device__ inline void solver_advance_level(const StreamDesc& D, Solver& S, PassParams& P)
+{
+    int l = S.level - 1;
+    while (l >= 0 && D.max_iters[l] <= 0) --l;
+    if (l < 0) {
+        P.done = 1;
+        return;
+    }
+    S.level = l;
+    S.phase = PH_START;
+    make_pass_params(S.T, S.a, S.b, l, P);
+}
+
+__device__ inline void solver_finish_level(Solver& S)
+{
+    S.iters[S.level] = S.it;
+    S.res_cost = S.cost;
+    S.res_n = S.n;
+}
+
+__device__ inline void solver_candidate(const StreamDesc& D, Solver& S, PassParams& P)
+{
+    double delta[8];
+    if (!damped_cholesky_solve(S.H, S.g, S.lambda, delta)) {
+        S.status |= GLT_TRACK_NOT_PD;
+        solver_finish_level(S);
+        solver_advance_level(D, S, P);
+        return;
+    }
+    double dT[12];
+    se3_exp_d(delta, dT);
+    se3_compose_d(S.T, dT, S.Tc);
+    S.ac = S.a + delta[6];
+    S.bc = S.b + delta[7];
+    double m = 0.0;
+    for (int i = 0; i < 6; ++i) m = fmax(m, fabs(delta[i]));
+    S.maxstep = m;
+    S.phase = PH_CAND;
+    make_pass_params(S.Tc, S.ac, S.bc, S.level, P);
+}
+
+__device__ inline void solver_init(const StreamDesc& D, const double* init, Solver& S, PassParams& P)
+{
+    for (int i = 0; i < 12; ++i) S.T[i] = init[i];
+    // project the initial rotation onto SO(3) (Gram-Schmidt on the rows) so a
+    // caller's accumulated rounding does not enter the solve
+    {
+        double* T = S.T;
+        const double n0 = sqrt(T[0] * T[0] + T[1] * T[1] + T[2] * T[2]);
+        for (int c = 0; c < 3; ++c) T[c] /= n0;
+        const double d = T[4] * T[0] + T[5] * T[1] + T[6] * T[2];
+        for (int c = 0; c < 3; ++c) T[4 + c] -= d * T[c];
+        const double n1 = sqrt(T[4] * T[4] + T[5] * T[5] + T[6] * T[6]);
+        for (int c = 0; c < 3; ++c) T[4 + c] /= n1;
+        T[8] = T[1] * T[6] - T[2] * T[5];
+        T[9] = T[2] * T[4] - T[0] * T[6];
+        T[10] = T[0] * T[5] - T[1] * T[4];
+    }
+    S.a = init[12];
+    S.b = init[13];
+    S.status = 0;
+    S.passes = 0;
+    S.it = 0;
+    S.n = 0;
+    S.res_n = 0;
+    S.cost = 0.0;
+    S.res_cost = __longlong_as_double(0x7ff8000000000000ll);
+    for (int l = 0; l < kMaxLevels; ++l) S.iters[l] = 0;
+    S.level = D.L;  // advance_level starts from L-1
+    P.done = 0;
+    solver_advance_level(D, S, P);
+}
+
+// One LM decision after a pass whose cluster-wide sums are `tot`.
+__device__ inline void solver_step(const StreamDesc& D, const double* tot, Solver& S, PassParams& P,
+                                   bool write_trace)
+{
+    const double E = tot[kIdxE];
+    const int n = (int)tot[kIdxN];
+    const bool enough = n >= D.min_valid && n > 0;
+    const double c = enough ? E / (double)n : __longlong_as_double(0x7ff0000000000000ll);
+    const int k = S.passes++;
+    if (S.phase == PH_START) {
+        if (write_trace && k < D.max_trace && D.trace_cost) {
+            D.trace_cost[k] = c;
+            D.trace_info[k] = S.level * 4;
+        }
+        if (!enough) {
+            S.status |= GLT_TRACK_TOO_FEW_POINTS;
+            solver_advance_level(D, S, P);
+            return;
+        }
+        unpack_normal(tot, S.H, S.g);
+        S.cost = c;
+        S.n = n;
+        S.lambda = D.lambda0;
+        S.it = 0;
+        solver_candidate(D, S, P);
+        return;
+    }
+    S.it++;
+    // take a candidate that lowers the cost, or a small (Gauss-Newton) step
+    const bool accepted = c < S.cost || (enough && S.maxstep < D.accept_step);
+    const bool flat = !accepted && (c - S.cost <= D.eps_cost * S.cost);
+    if (write_trace && k < D.max_trace && D.trace_cost) {
+        D.trace_cost[k] = c;
+        D.trace_info[k] = S.level * 4 + (accepted ? 2 : 0) + 1;
+    }
+    if (accepted) {
+        for (int i = 0; i < 12; ++i) S.T[i] = S.Tc[i];
+        S.a = S.ac;
+        S.b = S.bc;
+        unpack_normal(tot, S.H, S.g);
+        S.cost = c;
+        S.n = n;
+        S.lambda *= D.lambda_down;
+    } else {
+        S.lambda *= D.lambda_up;
+    }
+    if (S.it >= D.max_iters[S.level] || S.maxstep < D.eps_step || flat) {
+        solver_finish_level(S);
+        solver_advance_level(D, S, P);
+    } else {
+        solver_candidate(D, S, P);
+    }
+}
+
+__device__ inline void solver_write_result(const StreamDesc& D, const Solver& S, glt_result* out)
+{
+    if (D.trace_count) *D.trace_count = S.passes;
+    for (int i = 0; i < 12; ++i) out->T[i] = S.T[i];
+    out->a = S.a;
+    out->b = S.b;
+    out->cost = S.res_cost;
+    out->n_valid = S.res_n;
+    int tot = 0;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        out->iters[l] = S.iters[l];
+        tot += S.iters[l];
+    }
+    out->iters_total = tot;
+    out->passes = S.passes;
+    out->status = S.status;
+}
+
+}  // namespace glt

@@ -1,0 +1,125 @@
+// Host-side internals shared by the library's translation units: the tracker
+// and batch objects and the kernel launchers each .cu file provides.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "glt.h"
+#include "glt_device.cuh"
+
+namespace glt {
+
+// per-slot pyramid storage: one allocation, level l at off[l], row pitch pitch[l]
+struct Pyramid {
+    uint8_t* base = nullptr;
+    size_t bytes = 0;
+    size_t off[kMaxLevels] = {};
+    bool built = false;
+};
+
+struct PyrJob {             // one "level l-1 -> level l" downsampling job
+    const uint8_t* src;
+    uint8_t* dst;
+    int sW, sH, sp;
+    int dW, dH, dp;
+};
+
+struct CopyJob {            // one frame -> level-0 copy (batched form)
+    uint8_t* dst;
+    int W, H, dp;
+};
+
+struct PackJob {            // one level -> FP16 (I, gx, gy, 0) copy (mixed form)
+    const uint8_t* src;
+    uint2* dst;
+    int W, H, sp;
+};
+
+}  // namespace glt
+
+struct glt_tracker {
+    glt_config cfg;
+    int device = 0;
+    int L = 0;
+    int W[glt::kMaxLevels] = {}, H[glt::kMaxLevels] = {}, pitch[glt::kMaxLevels] = {};
+    glt::Pyramid pyr[2];
+    uint2* packed = nullptr;              // CUR FP16 levels (GLT_MIXED)
+    size_t poff[glt::kMaxLevels] = {};    // pixel offsets into `packed`
+    float* uvd_dev = nullptr;             // staging for host map points
+    float4* pt = nullptr;
+    float2* dz = nullptr;
+    float* I0 = nullptr;
+    int Npad = 0;
+    int N = 0;
+    bool have_points = false;
+    glt::StreamDesc desc_host{};
+    glt::StreamDesc* desc_dev = nullptr;
+    glt::StreamDesc** desc_ptr_dev = nullptr;  // device array {desc_dev}
+    int* user_dev = nullptr;                   // device {0}
+    int* trace_count = nullptr;
+    unsigned version = 0;                      // bumped by set_map_points
+    glt::PyrJob* jobs_dev = nullptr;      // [2 slots][L-1] downsampling jobs
+    glt::PackJob* pack_dev = nullptr;     // L packing jobs
+    double* init_dev = nullptr;           // 14 doubles
+    glt_result* result_dev = nullptr;
+    double* trace_cost = nullptr;
+    int* trace_info = nullptr;
+    int max_trace = 0;
+    // single-pass multi-block linearisation (debug / parity)
+    float* lin_partials = nullptr;
+    unsigned* lin_counter = nullptr;
+    double* lin_out = nullptr;
+    float* lin_res = nullptr;
+    int lin_blocks = 0;
+    // pinned host staging
+    double* h_init = nullptr;
+    glt_result* h_result = nullptr;
+    double* h_lin = nullptr;
+    int cluster = 1, threads = 256;
+};
+
+struct glt_batch {
+    std::vector<glt_tracker*> trk;        // caller order
+    std::vector<int> order;               // launch order (descending work)
+    int S = 0;
+    int precision = GLT_FP32;
+    glt::StreamDesc** descs_dev = nullptr; // launch order: each tracker's device descriptor
+    int* users_dev = nullptr;              // launch order -> caller index
+    glt::CopyJob* copy_dev = nullptr;     // caller order
+    glt::PyrJob* jobs_dev = nullptr;      // [L-1 rounds][S] caller order
+    glt::PackJob* pack_dev = nullptr;     // [Lmax][S]
+    int Lmax = 0;
+    int cluster = 2, threads = 256;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace glt {
+
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+// pyramid.cu
+cudaError_t launch_pyr_down(const PyrJob* jobs_dev, int njobs, int tiles_x, int tiles_y,
+                            cudaStream_t s);
+cudaError_t launch_copy_frames(const uint8_t* const* frames, const CopyJob* jobs, int njobs,
+                               int max_bytes, cudaStream_t s);
+cudaError_t launch_pack(const PackJob* jobs, int njobs, int max_pixels, cudaStream_t s);
+int pyr_tiles_x(int dW);
+int pyr_tiles_y(int dH);
+
+// points.cu
+cudaError_t launch_set_points(const glt_tracker* t, const float* uvd_dev, int n, cudaStream_t s);
+
+// track.cu
+cudaError_t launch_track(const StreamDesc* const* descs, const int* users, int S, int cluster,
+                         int threads, bool mixed, const double* init, glt_result* results,
+                         cudaStream_t s);
+cudaError_t launch_linearize(const glt_tracker* t, const PassParams& P, bool want_res,
+                             cudaStream_t s);
+bool track_shape_ok(int cluster, int threads, bool mixed);
+
+}  // namespace glt

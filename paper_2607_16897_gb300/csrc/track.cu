@@ -1,0 +1,230 @@
+// The persistent tracker kernel (whole coarse-to-fine LM in one launch, one
+// thread-block cluster per stream) and the single-pass multi-block
+// linearisation kernel.
+//
+// GLidE-SLAM Sec. IV-C "Track": per level and iteration, per-point residuals
+// and Jacobians, a tree reduction, a Cholesky solve and T <- T exp(delta),
+// all on the GPU.  Here the level x iteration loop stays inside one kernel:
+// each CTA of the cluster linearises a slice of the map points, the CTA sums
+// are exchanged through distributed shared memory, and every CTA runs the
+// (bit-identical) FP64 LM decision, so only one cluster barrier per pass is
+// needed.
+#include <cooperative_groups.h>
+
+#include "glt_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace glt {
+
+template <int THREADS, bool MIXED>
+__global__ void __launch_bounds__(THREADS) track_kernel(const StreamDesc* const* __restrict__ descs,
+                                                        const int* __restrict__ users,
+                                                        const double* __restrict__ init,
+                                                        glt_result* __restrict__ results)
+{
+    constexpr int NW = THREADS / 32;
+    __shared__ StreamDesc sD;
+    __shared__ PassParams P;
+    __shared__ Solver S;
+    __shared__ float red[NW][kAccPad];
+    __shared__ float part[2][kAccPad];
+    __shared__ float part_c[2][kAccPad];
+    __shared__ double tot[kAccPad];
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int stream = blockIdx.x / C;
+    const int tid = threadIdx.x;
+
+    const int user = users[stream];
+    {
+        const int* src = reinterpret_cast<const int*>(descs[stream]);
+        int* dst = reinterpret_cast<int*>(&sD);
+        for (int i = tid; i < (int)(sizeof(StreamDesc) / sizeof(int)); i += THREADS) dst[i] = src[i];
+    }
+    __syncthreads();
+    if (tid == 0) solver_init(sD, init + 14 * user, S, P);
+    __syncthreads();
+
+    int par = 0;
+    while (!P.done) {
+        float acc[kAccPad];
+#pragma unroll
+        for (int i = 0; i < kAccPad; ++i) acc[i] = 0.0f;
+        for (int p = rank * THREADS + tid; p < sD.N; p += C * THREADS)
+            linearize_point<MIXED, false>(sD, P, p, acc, nullptr);
+        block_reduce<THREADS, MIXED>(acc, red, part[par], part_c[par]);
+        if (C > 1) cluster.sync();
+        if (tid < kNumAcc) {
+            double s = 0.0;
+            for (int r = 0; r < C; ++r) {
+                const float* pr = C > 1 ? cluster.map_shared_rank(&part[par][0], r) : &part[par][0];
+                s += (double)pr[tid];
+                if (MIXED) {
+                    const float* cr = C > 1 ? cluster.map_shared_rank(&part_c[par][0], r) : &part_c[par][0];
+                    s += (double)cr[tid];
+                }
+            }
+            tot[tid] = s;
+        }
+        __syncthreads();
+        if (tid == 0) solver_step(sD, tot, S, P, rank == 0);
+        __syncthreads();
+        par ^= 1;
+    }
+    // peers may still read this CTA's partial sums: leave together
+    if (C > 1) cluster.sync();
+    if (rank == 0 && tid == 0) solver_write_result(sD, S, results + user);
+}
+
+// One linearisation pass over all points of one tracker, many blocks, with a
+// single-pass finish: each block writes its 46 sums, the last block to arrive
+// (ticket counter) adds the block sums in block order in FP64.
+template <int THREADS, bool MIXED>
+__global__ void __launch_bounds__(THREADS) linearize_kernel(const StreamDesc* __restrict__ desc,
+                                                            PassParams P,
+                                                            float* __restrict__ partials,
+                                                            unsigned* __restrict__ counter,
+                                                            double* __restrict__ out,
+                                                            float* __restrict__ res)
+{
+    constexpr int NW = THREADS / 32;
+    __shared__ float red[NW][kAccPad];
+    __shared__ float part[kAccPad];
+    __shared__ float part_c[kAccPad];
+    __shared__ int is_last;
+    const StreamDesc& D = *desc;
+    float acc[kAccPad];
+#pragma unroll
+    for (int i = 0; i < kAccPad; ++i) acc[i] = 0.0f;
+    const int p = blockIdx.x * THREADS + threadIdx.x;
+    if (p < D.N) {
+        if (res)
+            linearize_point<MIXED, true>(D, P, p, acc, res);
+        else
+            linearize_point<MIXED, false>(D, P, p, acc, nullptr);
+    }
+    block_reduce<THREADS, MIXED>(acc, red, part, part_c);
+    if (threadIdx.x < kNumAcc)
+        partials[(size_t)blockIdx.x * kAccPad + threadIdx.x] = part[threadIdx.x] + (MIXED ? part_c[threadIdx.x] : 0.0f);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        if (threadIdx.x < kNumAcc) {
+            double s = 0.0;
+            for (unsigned b = 0; b < gridDim.x; ++b)
+                s += (double)__ldcg(partials + (size_t)b * kAccPad + threadIdx.x);
+            out[threadIdx.x] = s;
+        }
+        if (threadIdx.x == 0) *counter = 0u;  // ready for the next launch
+    }
+}
+
+namespace {
+
+template <int THREADS, bool MIXED>
+cudaError_t launch_track_t(const StreamDesc* const* descs, const int* users, int S, int cluster,
+                           const double* init, glt_result* results, cudaStream_t s)
+{
+    auto kern = track_kernel<THREADS, MIXED>;
+    if (cluster > 8) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(S * cluster), 1, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, descs, users, init, results);
+}
+
+template <int THREADS, bool MIXED>
+bool shape_ok_t(int cluster)
+{
+    auto kern = track_kernel<THREADS, MIXED>;
+    if (cluster > 8 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cluster, 1, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n > 0;
+}
+
+}  // namespace
+
+bool track_shape_ok(int cluster, int threads, bool mixed)
+{
+    if (cluster < 1 || cluster > 16) return false;
+    switch (threads) {
+    case 128: return mixed ? shape_ok_t<128, true>(cluster) : shape_ok_t<128, false>(cluster);
+    case 256: return mixed ? shape_ok_t<256, true>(cluster) : shape_ok_t<256, false>(cluster);
+    case 512: return mixed ? shape_ok_t<512, true>(cluster) : shape_ok_t<512, false>(cluster);
+    default: return false;
+    }
+}
+
+cudaError_t launch_track(const StreamDesc* const* descs, const int* users, int S, int cluster,
+                         int threads, bool mixed, const double* init, glt_result* results,
+                         cudaStream_t s)
+{
+    switch (threads) {
+    case 128:
+        return mixed ? launch_track_t<128, true>(descs, users, S, cluster, init, results, s)
+                     : launch_track_t<128, false>(descs, users, S, cluster, init, results, s);
+    case 256:
+        return mixed ? launch_track_t<256, true>(descs, users, S, cluster, init, results, s)
+                     : launch_track_t<256, false>(descs, users, S, cluster, init, results, s);
+    case 512:
+        return mixed ? launch_track_t<512, true>(descs, users, S, cluster, init, results, s)
+                     : launch_track_t<512, false>(descs, users, S, cluster, init, results, s);
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_linearize(const glt_tracker* t, const PassParams& P, bool want_res,
+                             cudaStream_t s)
+{
+    constexpr int T = 128;
+    const int blocks = (t->N + T - 1) / T;
+    if (blocks <= 0 || blocks > t->lin_blocks) return cudaErrorInvalidValue;
+    float* res = want_res ? t->lin_res : nullptr;
+    if (t->cfg.precision == GLT_MIXED)
+        linearize_kernel<T, true><<<blocks, T, 0, s>>>(t->desc_dev, P, t->lin_partials,
+                                                       t->lin_counter, t->lin_out, res);
+    else
+        linearize_kernel<T, false><<<blocks, T, 0, s>>>(t->desc_dev, P, t->lin_partials,
+                                                        t->lin_counter, t->lin_out, res);
+    return cudaGetLastError();
+}
+
+}  // namespace glt

@@ -1,0 +1,65 @@
+"""The C-ABI library loads and exports every entry point include/glt.h
+declares, and the binding's structs match the C layout (no GPU needed)."""
+import ctypes
+import importlib.util
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "glt.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(glt_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    spec = importlib.util.spec_from_file_location(
+        "_glt_build", os.path.join(ROOT, "paper_2607_16897_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.build()
+
+
+def test_header_declares_the_api():
+    names = declared_functions()
+    for must in ("glt_create", "glt_build_pyramid", "glt_set_map_points", "glt_track_frame",
+                 "glt_debug_linearize", "glt_batch_track", "glt_batch_capture"):
+        assert must in names
+    assert len(names) >= 20
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header_and_layouts(lib_path):
+    import paper_2607_16897_gb300 as glt
+    assert set(glt.SIGNATURES) == set(declared_functions())
+    assert ctypes.sizeof(glt.glt_config) == 176
+    assert ctypes.sizeof(glt.glt_result) == 168
+    assert glt.RESULT_DTYPE.itemsize == glt.RESULT_BYTES
+    c = glt.default_config(640, 480, (525, 525, 320, 240))
+    assert c.levels == 4 and c.max_iters[0] == 10 and c.huber_k == 9.0
+
+
+def test_host_side_argument_checks(lib_path):
+    """Config validation happens before any device call, so it runs without a GPU."""
+    import paper_2607_16897_gb300 as glt
+    bad = [dict(levels=0), dict(levels=9), dict(huber_k=0.0), dict(max_points=0),
+           dict(precision=7), dict(cluster=17), dict(threads=100), dict(levels=7)]
+    for kw in bad:
+        c = glt.default_config(320, 240, (256, 256, 160, 120), **kw)
+        h = ctypes.c_void_p()
+        rc = glt.glt_create(ctypes.byref(c), ctypes.byref(h))
+        assert rc == glt.GLT_ERR_INVALID_ARG, kw
+        assert glt.glt_last_error()
+    assert glt.glt_build_pyramid(None, 0, None, 0, 0, None) == glt.GLT_ERR_INVALID_ARG
+    assert glt.glt_batch_create(None, 0, ctypes.byref(ctypes.c_void_p())) == glt.GLT_ERR_INVALID_ARG
