@@ -66,7 +66,8 @@ static void free_tracker(glt_tracker* t)
     cudaFree(t->pack_dev);
     cudaFree(t->init_dev);
     cudaFree(t->result_dev);
-    cudaFree(t->trace_cost);
+    cudaFree(t->trace_E);
+    cudaFree(t->trace_n);
     cudaFree(t->trace_info);
     cudaFree(t->lin_partials);
     cudaFree(t->lin_counter);
@@ -217,7 +218,8 @@ int glt_create(const glt_config* cfg, glt_tracker** out)
     int maxit = 0;
     for (int l = 0; l < t->L; ++l) maxit = std::max(maxit, cfg->max_iters[l]);
     t->max_trace = t->L * (1 + maxit);
-    ALLOC(dalloc(&t->trace_cost, (size_t)t->max_trace));
+    ALLOC(dalloc(&t->trace_E, (size_t)t->max_trace));
+    ALLOC(dalloc(&t->trace_n, (size_t)t->max_trace));
     ALLOC(dalloc(&t->trace_info, (size_t)t->max_trace));
     t->lin_blocks = (maxp + 127) / 128;
     ALLOC(dalloc(&t->lin_partials, (size_t)t->lin_blocks * kAccPad));
@@ -258,7 +260,8 @@ int glt_create(const glt_config* cfg, glt_tracker** out)
     D.eps_step = cfg->eps_step;
     D.eps_cost = cfg->eps_cost;
     D.accept_step = cfg->accept_step;
-    D.trace_cost = t->trace_cost;
+    D.trace_E = t->trace_E;
+    D.trace_n = t->trace_n;
     D.trace_info = t->trace_info;
     D.trace_count = t->trace_count;
     ALLOC(cudaMemcpy(t->desc_dev, &D, sizeof(D), cudaMemcpyHostToDevice));
@@ -460,9 +463,13 @@ int glt_get_trace(glt_tracker* t, double* cost, int* info, int max, int* count, 
     GLT_CHECK(cudaStreamSynchronize(s), "trace");
     int k = std::min(std::min(passes, t->max_trace), max);
     if (k > 0) {
-        GLT_CHECK(cudaMemcpyAsync(cost, t->trace_cost, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, s), "trace");
+        std::vector<int> nn(k);
+        GLT_CHECK(cudaMemcpyAsync(cost, t->trace_E, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, s), "trace");
+        GLT_CHECK(cudaMemcpyAsync(nn.data(), t->trace_n, (size_t)k * sizeof(int), cudaMemcpyDeviceToHost, s), "trace");
         GLT_CHECK(cudaMemcpyAsync(info, t->trace_info, (size_t)k * sizeof(int), cudaMemcpyDeviceToHost, s), "trace");
         GLT_CHECK(cudaStreamSynchronize(s), "trace");
+        for (int i = 0; i < k; ++i)
+            cost[i] = (nn[i] >= t->cfg.min_valid && nn[i] > 0) ? cost[i] / nn[i] : INFINITY;
     }
     *count = k;
     return GLT_OK;

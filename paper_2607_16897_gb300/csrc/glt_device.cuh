@@ -49,8 +49,9 @@ struct StreamDesc {
     int min_valid;
     int max_trace;
     double lambda0, lambda_up, lambda_down, eps_step, eps_cost, accept_step;
-    double* trace_cost;    // [max_trace] or null
-    int* trace_info;       // [max_trace] or null
+    double* trace_E;       // [max_trace] Huber energy of each pass, or null
+    int* trace_n;          // [max_trace] valid samples of each pass
+    int* trace_info;       // [max_trace] level * 4 + 2 * accepted + is_candidate
     int* trace_count;      // passes of the last track, or null
 };
 
@@ -326,117 +327,30 @@ __device__ __forceinline__ void block_reduce(float (&acc)[kAccPad], float (*red)
 }
 
 // ---------------------------------------------------------------------------
-// FP64 solver tail: SE(3) exponential, composition, 8x8 damped Cholesky
+// FP64 solver tail, run by one warp of every CTA
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate with long dependent
+// latencies (measured on the part: ~64 cycles per DFMA, ~420 per divide or
+// reciprocal, ~670 per square root, ~1700 per sincos), and this tail sits on
+// the critical path of every pass.  So it is laid out for latency:
+//  * the damped normal matrix is factored as L D L^T (no square roots), one
+//    row per lane, columns eliminated right-looking with warp shuffles;
+//  * pivot reciprocals are an FP32 seed refined by one Newton step in FP64
+//    (relative error ~4e-15);
+//  * the SE(3) exponential uses the power series of its coefficients in
+//    theta^2 below theta = 0.1 (sincos only beyond), each lane one element;
+//  * accept/reject compares E' n <= E n' instead of dividing.
 // ---------------------------------------------------------------------------
-// exp of the twist xi = (v, w): R = I + A W + B W^2, t = (I + B W + C W^2) v
-// with A = sin th / th, B = (1 - cos th) / th^2, C = (th - sin th) / th^3.
-// Series of the same functions are used where the closed forms cancel.
-__device__ inline void se3_exp_d(const double* xi, double* T)
+__device__ __forceinline__ double rcp_d(double d)
 {
-    const double w0 = xi[3], w1 = xi[4], w2 = xi[5];
-    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
-    const double th = sqrt(th2);
-    double A, B, C;
-    if (th < 1e-4) {
-        A = 1.0 - th2 * (1.0 / 6.0) + th2 * th2 * (1.0 / 120.0);
-        B = 0.5 - th2 * (1.0 / 24.0) + th2 * th2 * (1.0 / 720.0);
-    } else {
-        double sn, cs, sh, ch;
-        sincos(th, &sn, &cs);
-        sincos(0.5 * th, &sh, &ch);
-        A = sn / th;
-        B = 2.0 * sh * sh / th2;
-    }
-    if (th < 0.1) {
-        const double t4 = th2 * th2;
-        C = 1.0 / 6.0 - th2 * (1.0 / 120.0) + t4 * (1.0 / 5040.0) - t4 * th2 * (1.0 / 362880.0) +
-            t4 * t4 * (1.0 / 39916800.0);
-    } else {
-        C = (th - sin(th)) / (th2 * th);
-    }
-    // W = [w]x, W^2 = w w^T - th^2 I
-    const double W[9] = {0, -w2, w1, w2, 0, -w0, -w1, w0, 0};
-    const double ww[3] = {w0, w1, w2};
-    double Rm[9], V[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const double W2 = ww[i] * ww[j] - (i == j ? th2 : 0.0);
-            const double I = i == j ? 1.0 : 0.0;
-            Rm[3 * i + j] = I + A * W[3 * i + j] + B * W2;
-            V[3 * i + j] = I + B * W[3 * i + j] + C * W2;
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        T[4 * i + 0] = Rm[3 * i + 0];
-        T[4 * i + 1] = Rm[3 * i + 1];
-        T[4 * i + 2] = Rm[3 * i + 2];
-        T[4 * i + 3] = V[3 * i] * xi[0] + V[3 * i + 1] * xi[1] + V[3 * i + 2] * xi[2];
-    }
+    const double ad = fabs(d);
+    if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+    double r = (double)__frcp_rn((float)d);
+    const double e = fma(-d, r, 1.0);
+    return fma(r, e, r);
 }
 
-__device__ inline void se3_compose_d(const double* A, const double* B, double* C)
-{
-    double o[12];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            double s = c == 3 ? A[4 * r + 3] : 0.0;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) s += A[4 * r + k] * B[4 * k + c];
-            o[4 * r + c] = s;
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 12; ++i) C[i] = o[i];
-}
-
-// Solves (H + lambda diag(H)) delta = -g by Cholesky.  False if a pivot is not
-// positive (or below 1e-13 of its diagonal entry).
-__device__ inline bool damped_cholesky_solve(const double* H, const double* g, double lambda,
-                                             double* delta)
-{
-    double Lm[8][8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const double ajj = H[9 * j] + lambda * H[9 * j];
-        double d = ajj;
-#pragma unroll
-        for (int k = 0; k < j; ++k) d -= Lm[j][k] * Lm[j][k];
-        if (!(d > 0.0) || !(d > 1e-13 * ajj)) return false;
-        const double ljj = sqrt(d);
-        Lm[j][j] = ljj;
-        const double inv = 1.0 / ljj;
-#pragma unroll
-        for (int i = j + 1; i < 8; ++i) {
-            double s = H[8 * i + j];
-#pragma unroll
-            for (int k = 0; k < j; ++k) s -= Lm[i][k] * Lm[j][k];
-            Lm[i][j] = s * inv;
-        }
-    }
-    double y[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        double s = -g[i];
-#pragma unroll
-        for (int k = 0; k < i; ++k) s -= Lm[i][k] * y[k];
-        y[i] = s / Lm[i][i];
-    }
-#pragma unroll
-    for (int i = 7; i >= 0; --i) {
-        double s = y[i];
-#pragma unroll
-        for (int k = i + 1; k < 8; ++k) s -= Lm[k][i] * delta[k];
-        delta[i] = s / Lm[i][i];
-    }
-    return true;
-}
-
-// Pass parameters for state (T, a, b) on `level`.
+// Pass parameters for state (T, a, b) on `level` (single thread).
 __device__ __host__ inline void make_pass_params(const double* T, double a, double b, int level,
                                                  PassParams& P)
 {
@@ -459,6 +373,27 @@ __device__ __host__ inline void make_pass_params(const double* T, double a, doub
     P.done = 0;
 }
 
+// Same, one element per lane (lanes 0-13), for the pose in T (12 doubles).
+__device__ __forceinline__ void make_pass_params_warp(const double* T, double a, double b,
+                                                      int level, PassParams& P, int lane)
+{
+    if (lane < 12) {
+        const int r = lane >> 2, c = lane & 3;
+        const double v = T[lane] - ((c == r) ? 1.0 : 0.0);
+        if (c < 3)
+            P.Rm[3 * r + c] = (float)v;
+        else
+            P.t[r] = (float)v;
+    } else if (lane == 12) {
+        P.ea = expf((float)a);
+    } else if (lane == 13) {
+        P.b = (float)b;
+        P.level = level;
+        P.scale = ldexpf(1.0f, -level);
+        P.done = 0;
+    }
+}
+
 // LM state machine, replicated in every CTA of a stream's cluster (each CTA
 // runs it on bit-identical inputs, so all take the same decisions).
 enum { PH_START = 0, PH_CAND = 1 };
@@ -467,69 +402,18 @@ struct Solver {
     double T[12], a, b;       // accepted state
     double Tc[12], ac, bc;    // candidate under evaluation
     double H[64], g[8];       // normal equations at the accepted state
-    double cost, lambda, maxstep, res_cost;
-    int n, res_n, level, it, phase, status, passes;
+    double E, lambda, maxstep, res_E;
+    int n, res_n, level, it, phase, status, passes, done;
     int iters[kMaxLevels];
 };
 
-__device__ inline void unpack_normal(const double* tot, double* H, double* g)
-{
-    int idx = 0;
-    for (int i = 0; i < 8; ++i)
-        for (int j = i; j < 8; ++j) {
-            H[8 * i + j] = tot[idx];
-            H[8 * j + i] = tot[idx];
-            ++idx;
-        }
-    for (int i = 0; i < 8; ++i) g[i] = tot[kIdxG + i];
-}
+// Upper-triangle index of (i, j), i <= j, in the accumulator layout.
+__device__ __forceinline__ int upper_index(int i, int j) { return i * 8 - (i * (i - 1)) / 2 + (j - i); }
 
-__device__ inline void solver_advance_level(const StreamDesc& D, Solver& S, PassParams& P)
-{
-    int l = S.level - 1;
-    while (l >= 0 && D.max_iters[l] <= 0) --l;
-    if (l < 0) {
-        P.done = 1;
-        return;
-    }
-    S.level = l;
-    S.phase = PH_START;
-    make_pass_params(S.T, S.a, S.b, l, P);
-}
-
-__device__ inline void solver_finish_level(Solver& S)
-{
-    S.iters[S.level] = S.it;
-    S.res_cost = S.cost;
-    S.res_n = S.n;
-}
-
-__device__ inline void solver_candidate(const StreamDesc& D, Solver& S, PassParams& P)
-{
-    double delta[8];
-    if (!damped_cholesky_solve(S.H, S.g, S.lambda, delta)) {
-        S.status |= GLT_TRACK_NOT_PD;
-        solver_finish_level(S);
-        solver_advance_level(D, S, P);
-        return;
-    }
-    double dT[12];
-    se3_exp_d(delta, dT);
-    se3_compose_d(S.T, dT, S.Tc);
-    S.ac = S.a + delta[6];
-    S.bc = S.b + delta[7];
-    double m = 0.0;
-    for (int i = 0; i < 6; ++i) m = fmax(m, fabs(delta[i]));
-    S.maxstep = m;
-    S.phase = PH_CAND;
-    make_pass_params(S.Tc, S.ac, S.bc, S.level, P);
-}
-
+// Initial state (one thread): Gram-Schmidt the initial rotation, first level.
 __device__ inline void solver_init(const StreamDesc& D, const double* init, Solver& S, PassParams& P)
 {
     for (int i = 0; i < 12; ++i) S.T[i] = init[i];
-    // project the initial rotation onto SO(3) (Gram-Schmidt on the rows) so a
-    // caller's accumulated rounding does not enter the solve
     {
         double* T = S.T;
         const double n0 = sqrt(T[0] * T[0] + T[1] * T[1] + T[2] * T[2]);
@@ -548,67 +432,239 @@ __device__ inline void solver_init(const StreamDesc& D, const double* init, Solv
     S.passes = 0;
     S.it = 0;
     S.n = 0;
+    S.E = 0.0;
     S.res_n = 0;
-    S.cost = 0.0;
-    S.res_cost = __longlong_as_double(0x7ff8000000000000ll);
+    S.res_E = __longlong_as_double(0x7ff8000000000000ll);
+    S.done = 0;
     for (int l = 0; l < kMaxLevels; ++l) S.iters[l] = 0;
-    S.level = D.L;  // advance_level starts from L-1
-    P.done = 0;
-    solver_advance_level(D, S, P);
+    int l = D.L - 1;
+    while (l >= 0 && D.max_iters[l] <= 0) --l;
+    S.level = l;
+    S.phase = PH_START;
+    if (l < 0) {
+        S.done = 1;
+        P.done = 1;
+    } else {
+        make_pass_params(S.T, S.a, S.b, l, P);
+    }
 }
 
-// One LM decision after a pass whose cluster-wide sums are `tot`.
-__device__ inline void solver_step(const StreamDesc& D, const double* tot, Solver& S, PassParams& P,
-                                   bool write_trace)
+// One LM decision after a pass whose cluster-wide sums are `tot`; executed
+// by all 32 lanes of one warp with uniform control flow.
+__device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, Solver& S,
+                                        PassParams& P, int lane, bool write_trace)
 {
+    const unsigned full = 0xffffffffu;
+    const int row = lane & 7;
     const double E = tot[kIdxE];
     const int n = (int)tot[kIdxN];
     const bool enough = n >= D.min_valid && n > 0;
-    const double c = enough ? E / (double)n : __longlong_as_double(0x7ff0000000000000ll);
-    const int k = S.passes++;
-    if (S.phase == PH_START) {
-        if (write_trace && k < D.max_trace && D.trace_cost) {
-            D.trace_cost[k] = c;
-            D.trace_info[k] = S.level * 4;
-        }
+    const int level = S.level;
+    const int phase = S.phase;
+    int it = S.it;
+    double lambda = S.lambda;
+    int status = S.status;
+    bool load_normal = false, accept = false, finish = false, candidate = false;
+    if (phase == PH_START) {
         if (!enough) {
-            S.status |= GLT_TRACK_TOO_FEW_POINTS;
-            solver_advance_level(D, S, P);
-            return;
+            status |= GLT_TRACK_TOO_FEW_POINTS;
+        } else {
+            load_normal = true;
+            lambda = D.lambda0;
+            it = 0;
+            candidate = true;
         }
-        unpack_normal(tot, S.H, S.g);
-        S.cost = c;
-        S.n = n;
-        S.lambda = D.lambda0;
-        S.it = 0;
-        solver_candidate(D, S, P);
-        return;
-    }
-    S.it++;
-    // take a candidate that lowers the cost, or a small (Gauss-Newton) step
-    const bool accepted = c < S.cost || (enough && S.maxstep < D.accept_step);
-    const bool flat = !accepted && (c - S.cost <= D.eps_cost * S.cost);
-    if (write_trace && k < D.max_trace && D.trace_cost) {
-        D.trace_cost[k] = c;
-        D.trace_info[k] = S.level * 4 + (accepted ? 2 : 0) + 1;
-    }
-    if (accepted) {
-        for (int i = 0; i < 12; ++i) S.T[i] = S.Tc[i];
-        S.a = S.ac;
-        S.b = S.bc;
-        unpack_normal(tot, S.H, S.g);
-        S.cost = c;
-        S.n = n;
-        S.lambda *= D.lambda_down;
     } else {
-        S.lambda *= D.lambda_up;
+        ++it;
+        const double En = E * (double)S.n, Ecn = S.E * (double)n;
+        accept = enough && (En < Ecn || S.maxstep < D.accept_step);
+        const bool flat = !accept && enough && (En - Ecn <= D.eps_cost * Ecn);
+        lambda *= accept ? D.lambda_down : D.lambda_up;
+        load_normal = accept;
+        if (it >= D.max_iters[level] || S.maxstep < D.eps_step || flat)
+            finish = true;
+        else
+            candidate = true;
     }
-    if (S.it >= D.max_iters[S.level] || S.maxstep < D.eps_step || flat) {
-        solver_finish_level(S);
-        solver_advance_level(D, S, P);
-    } else {
-        solver_candidate(D, S, P);
+    if (write_trace && lane == 0 && D.trace_E && S.passes < D.max_trace) {
+        D.trace_E[S.passes] = E;
+        D.trace_n[S.passes] = n;
+        D.trace_info[S.passes] = level * 4 + (phase == PH_CAND ? 1 + (accept ? 2 : 0) : 0);
     }
+    __syncwarp();
+    // commit the pass outcome to the shared state
+    if (accept && lane < 12) S.T[lane] = S.Tc[lane];
+    if (load_normal) {
+        if (lane < 8) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                S.H[8 * lane + c] = tot[c >= lane ? upper_index(lane, c) : upper_index(c, lane)];
+            S.g[lane] = tot[kIdxG + lane];
+        }
+    }
+    if (lane == 0) {
+        S.passes += 1;
+        S.it = it;
+        S.lambda = lambda;
+        S.status = status;
+        if (accept) {
+            S.a = S.ac;
+            S.b = S.bc;
+        }
+        if (load_normal) {
+            S.E = E;
+            S.n = n;
+        }
+    }
+    __syncwarp();
+
+    bool next_level = (phase == PH_START && !enough) || finish;
+    if (candidate) {
+        // ---- (H + lambda diag H) delta = -g by L D L^T, lane `row` holds row `row`
+        double a[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a[c] = S.H[8 * row + c];
+        double a0 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c == row) {
+                a[c] = fma(lambda, a[c], a[c]);
+                a0 = a[c];
+            }
+        double y = -S.g[row];
+        double Lcol[8];
+        double dinv = 0.0;
+        bool ok = true;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) Lcol[c] = 0.0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const double d = __shfl_sync(full, a[j], j);
+            const double a0j = __shfl_sync(full, a0, j);
+            if (!(d > 0.0) || !(d > 1e-13 * a0j)) {
+                ok = false;
+                break;
+            }
+            const double r = rcp_d(d);
+            if (row == j) dinv = r;
+            const double lij = a[j] * r;
+#pragma unroll
+            for (int k = j + 1; k < 8; ++k) {
+                const double akj = __shfl_sync(full, a[j], k);
+                if (row > j) a[k] = fma(-lij, akj, a[k]);
+            }
+#pragma unroll
+            for (int k = j + 1; k < 8; ++k) {
+                const double lkj = __shfl_sync(full, lij, k);
+                if (row == j) Lcol[k] = lkj;
+            }
+            if (row > j) a[j] = lij;
+        }
+        if (!ok) {
+            if (lane == 0) S.status |= GLT_TRACK_NOT_PD;
+            finish = true;
+            next_level = true;
+        } else {
+            // forward (L y = -g), diagonal, backward (L^T x = D^-1 y)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const double yj = __shfl_sync(full, y, j);
+                if (row > j) y = fma(-a[j], yj, y);
+            }
+            double x = y * dinv;
+#pragma unroll
+            for (int j = 7; j >= 0; --j) {
+                const double xj = __shfl_sync(full, x, j);
+                if (row < j) x = fma(-Lcol[j], xj, x);
+            }
+            double dl[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) dl[c] = __shfl_sync(full, x, c);
+            // ---- exp(delta_xi): R = I + A W + B W^2, t = (I + B W + C W^2) v
+            const double w0 = dl[3], w1 = dl[4], w2 = dl[5];
+            const double th2 = fma(w0, w0, fma(w1, w1, w2 * w2));
+            double A, B, Cc;
+            if (th2 < 0.01) {
+                A = fma(fma(fma(fma(th2, 1.0 / 362880.0, -1.0 / 5040.0), th2, 1.0 / 120.0), th2, -1.0 / 6.0), th2, 1.0);
+                B = fma(fma(fma(fma(th2, 1.0 / 3628800.0, -1.0 / 40320.0), th2, 1.0 / 720.0), th2, -1.0 / 24.0), th2, 0.5);
+                Cc = fma(fma(fma(fma(th2, 1.0 / 39916800.0, -1.0 / 362880.0), th2, 1.0 / 5040.0), th2, -1.0 / 120.0), th2, 1.0 / 6.0);
+            } else {
+                const double th = sqrt(th2);
+                double sn, cs, sh, ch;
+                sincos(th, &sn, &cs);
+                sincos(0.5 * th, &sh, &ch);
+                A = sn / th;
+                B = 2.0 * sh * sh / th2;
+                Cc = (th - sn) / (th2 * th);
+            }
+            const double ww[3] = {w0, w1, w2};
+            const double W[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
+            double Em[12];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                double tr = 0.0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double W2 = fma(ww[r], ww[c], r == c ? -th2 : 0.0);
+                    const double I = r == c ? 1.0 : 0.0;
+                    Em[4 * r + c] = fma(A, W[3 * r + c], fma(B, W2, I));
+                    const double V = fma(B, W[3 * r + c], fma(Cc, W2, I));
+                    tr = fma(V, dl[c], tr);
+                }
+                Em[4 * r + 3] = tr;
+            }
+            // ---- candidate pose Tc = T exp(delta_xi), one element per lane
+            if (lane < 12) {
+                const int r = lane >> 2, c = lane & 3;
+                double e0 = 0, e1 = 0, e2 = 0;
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc)
+                    if (cc == c) {
+                        e0 = Em[cc];
+                        e1 = Em[4 + cc];
+                        e2 = Em[8 + cc];
+                    }
+                const double* Tr = S.T + 4 * r;
+                double v = fma(Tr[0], e0, fma(Tr[1], e1, Tr[2] * e2));
+                if (c == 3) v += Tr[3];
+                S.Tc[lane] = v;
+            }
+            double m = 0.0;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) m = fmax(m, fabs(dl[c]));
+            if (lane == 0) {
+                S.ac = S.a + dl[6];
+                S.bc = S.b + dl[7];
+                S.maxstep = m;
+                S.phase = PH_CAND;
+            }
+            __syncwarp();
+            make_pass_params_warp(S.Tc, S.a + dl[6], S.b + dl[7], level, P, lane);
+        }
+    }
+    if (finish && lane == 0) {
+        S.iters[level] = it;
+        S.res_E = S.E;
+        S.res_n = S.n;
+    }
+    __syncwarp();
+    if (next_level) {
+        int l = level - 1;
+        while (l >= 0 && D.max_iters[l] <= 0) --l;
+        if (l < 0) {
+            if (lane == 0) {
+                S.done = 1;
+                P.done = 1;
+            }
+        } else {
+            if (lane == 0) {
+                S.level = l;
+                S.phase = PH_START;
+            }
+            make_pass_params_warp(S.T, S.a, S.b, l, P, lane);
+        }
+    }
+    __syncwarp();
 }
 
 __device__ inline void solver_write_result(const StreamDesc& D, const Solver& S, glt_result* out)
@@ -617,7 +673,7 @@ __device__ inline void solver_write_result(const StreamDesc& D, const Solver& S,
     for (int i = 0; i < 12; ++i) out->T[i] = S.T[i];
     out->a = S.a;
     out->b = S.b;
-    out->cost = S.res_cost;
+    out->cost = S.res_n > 0 ? S.res_E / (double)S.res_n : S.res_E;
     out->n_valid = S.res_n;
     int tot = 0;
     for (int l = 0; l < kMaxLevels; ++l) {

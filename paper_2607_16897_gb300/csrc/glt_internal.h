@@ -65,7 +65,8 @@ struct glt_tracker {
     glt::PackJob* pack_dev = nullptr;     // L packing jobs
     double* init_dev = nullptr;           // 14 doubles
     glt_result* result_dev = nullptr;
-    double* trace_cost = nullptr;
+    double* trace_E = nullptr;
+    int* trace_n = nullptr;
     int* trace_info = nullptr;
     int max_trace = 0;
     // single-pass multi-block linearisation (debug / parity)

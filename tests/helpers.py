@@ -70,8 +70,11 @@ def compare_linearization(g, o, where=""):
     tol = G_TOL * np.linalg.norm(absg) + 3 * RES_FP32 * np.linalg.norm(quad)
     dg = np.linalg.norm(g["g"] - o["g"]) / np.linalg.norm(absg)
     assert np.linalg.norm(g["g"] - o["g"]) <= tol, f"{where}: g diff {dg} (res diff {d})"
+    # E = sum rho(r): same reading as g, d rho = w r dr adds in quadrature
+    wr = (o["w"][ov] * o["res"][ov]).ravel()
     dE = abs(g["E"] - o["E"]) / max(o["E"], 1e-30)
-    assert dE <= 1e-5, f"{where}: E diff {dE}"
+    assert abs(g["E"] - o["E"]) <= 1e-5 * o["E"] + 3 * RES_FP32 * np.sqrt((wr ** 2).sum()), \
+        f"{where}: E diff {dE}"
     return {"res": d, "H": dH, "g": dg, "E": dE}
 
 
