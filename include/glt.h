@@ -215,6 +215,34 @@ int glt_batch_autotune(glt_batch* batch, const double* init_dev, glt_result* out
 /* Sets the (cluster, threads) shape used by glt_batch_track / capture. */
 int glt_batch_set_shape(glt_batch* batch, int cluster, int threads);
 
+/* Allocation-free linearisation.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory where they
+ * call it -- code recorded into a CUDA graph by stream capture, real-time
+ * loops with a memory budget fixed at start-up, plugins whose host framework
+ * owns all device memory -- and who therefore cannot use glt_create.
+ * It runs one linearisation of Eqs. 3-5 (same arithmetic as
+ * glt_debug_linearize) on caller-owned DEVICE buffers: the REF and CUR images
+ * of pyramid level `level` (uint8, (width >> level) x (height >> level), row
+ * pitches in bytes >= the level width), n map points uvd_dev[n][3] =
+ * (u0, v0, depth) at level-0 pixels, level-0 intrinsics, the state (T
+ * host-side 3x4, a, b), Huber k and zmin; the reference patch is sampled on
+ * the fly.  It writes out_dev[46] (device doubles): the 36 upper-triangle
+ * entries of H row by row, g (8), the Huber energy E and the valid-sample
+ * count n.  Asynchronous on `stream`; allocates nothing.
+ * Scratch: a file-scope device array holding up to 512 block partial sums
+ * (n <= 65536 points; larger n returns GLT_ERR_CAPACITY), which every GPU
+ * that loads the library keeps until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  Every call shares the array
+ * and clears its ticket counter first, so calls that overlap on the GPU (on
+ * different streams, or concurrently from several host threads) race and
+ * must be serialised by the caller. */
+int glt_linearize_noalloc(const uint8_t* ref_dev, int ref_pitch, const uint8_t* cur_dev,
+                          int cur_pitch, int width, int height, int level, double fx, double fy,
+                          double cx, double cy, const float* uvd_dev, int n, const double T[12],
+                          double a, double b, double huber_k, double zmin, double* out_dev,
+                          void* stream);
+
 /* Thread-local message of the last error (never NULL). */
 const char* glt_last_error(void);
 

@@ -89,6 +89,8 @@ SIGNATURES = {
     "glt_batch_replay": (_i, [_vp, _vp]),
     "glt_batch_autotune": (_i, [_vp, _vp, _vp, _i, _P(_i), _P(_i), _P(ctypes.c_float), _vp]),
     "glt_batch_set_shape": (_i, [_vp, _i, _i]),
+    "glt_linearize_noalloc": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _d, _d, _d, _d, _vp, _i, _P(_d),
+                                   _d, _d, _d, _d, _vp, _vp]),
     "glt_last_error": (ctypes.c_char_p, []),
     "glt_version": (ctypes.c_char_p, []),
 }
