@@ -343,11 +343,30 @@ __device__ __forceinline__ void block_reduce(float (&acc)[kAccPad], float (*red)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double rcp_d(double d)
 {
+    // FP32 seed built from the bit pattern (no F2F conversions on the FP64
+    // pipe), then one Newton step in FP64: relative error < 1e-13.  Only for
+    // 1e-30 < |d| < 1e30, where the exponent fits FP32.
     const double ad = fabs(d);
     if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
-    double r = (double)__frcp_rn((float)d);
+    const int hi = __double2hiint(d);
+    const unsigned lo = (unsigned)__double2loint(d);
+    const int e32 = ((hi >> 20) & 0x7ff) - 896;
+    const unsigned fb = ((unsigned)hi & 0x80000000u) | ((unsigned)e32 << 23) |
+                        (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29);
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(fb)));
+    const unsigned rb = __float_as_uint(rf);
+    const int rhi = (int)((rb & 0x80000000u) | ((((rb >> 23) & 0xffu) + 896u) << 20) | ((rb >> 3) & 0xfffffu));
+    double r = __hiloint2double(rhi, (int)(rb << 29));
     const double e = fma(-d, r, 1.0);
     return fma(r, e, r);
+}
+
+// |x| compared through the bit pattern: for non-negative doubles the IEEE
+// ordering is the integer ordering of the bits (no FP64 instructions).
+__device__ __forceinline__ long long abs_bits(double x)
+{
+    return __double_as_longlong(x) & 0x7fffffffffffffffll;
 }
 
 // Pass parameters for state (T, a, b) on `level` (single thread).
@@ -402,7 +421,8 @@ struct Solver {
     double T[12], a, b;       // accepted state
     double Tc[12], ac, bc;    // candidate under evaluation
     double H[64], g[8];       // normal equations at the accepted state
-    double E, lambda, maxstep, res_E;
+    double E, nd, lambda, res_E;   // energy / samples (as double) at the accepted state
+    long long maxstep_bits;   // max |delta_xi| of the candidate, as abs_bits
     int n, res_n, level, it, phase, status, passes, done;
     int iters[kMaxLevels];
 };
@@ -432,7 +452,9 @@ __device__ inline void solver_init(const StreamDesc& D, const double* init, Solv
     S.passes = 0;
     S.it = 0;
     S.n = 0;
+    S.nd = 0.0;
     S.E = 0.0;
+    S.maxstep_bits = 0;
     S.res_n = 0;
     S.res_E = __longlong_as_double(0x7ff8000000000000ll);
     S.done = 0;
@@ -450,20 +472,23 @@ __device__ inline void solver_init(const StreamDesc& D, const double* init, Solv
 }
 
 // One LM decision after a pass whose cluster-wide sums are `tot`; executed
-// by all 32 lanes of one warp with uniform control flow.
+// by all 32 lanes of one warp with uniform control flow.  FP64 instructions
+// are kept to the minimum the method needs (each costs ~64 issue cycles).
 __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, Solver& S,
                                         PassParams& P, int lane, bool write_trace)
 {
     const unsigned full = 0xffffffffu;
     const int row = lane & 7;
     const double E = tot[kIdxE];
-    const int n = (int)tot[kIdxN];
+    const double nd = tot[kIdxN];           // exact integer count
+    const int n = (int)nd;
     const bool enough = n >= D.min_valid && n > 0;
     const int level = S.level;
     const int phase = S.phase;
     int it = S.it;
     double lambda = S.lambda;
     int status = S.status;
+    const long long step_bits = S.maxstep_bits;
     bool load_normal = false, accept = false, finish = false, candidate = false;
     if (phase == PH_START) {
         if (!enough) {
@@ -476,12 +501,15 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
         }
     } else {
         ++it;
-        const double En = E * (double)S.n, Ecn = S.E * (double)n;
-        accept = enough && (En < Ecn || S.maxstep < D.accept_step);
+        // c' < c  <=>  E' n < E n'  (both counts positive); flat: c' - c <= eps c
+        const double En = E * S.nd;
+        const double Ecn = S.E * nd;
+        const bool small = step_bits < abs_bits(D.accept_step);
+        accept = enough && (En < Ecn || small);
         const bool flat = !accept && enough && (En - Ecn <= D.eps_cost * Ecn);
         lambda *= accept ? D.lambda_down : D.lambda_up;
         load_normal = accept;
-        if (it >= D.max_iters[level] || S.maxstep < D.eps_step || flat)
+        if (it >= D.max_iters[level] || step_bits < abs_bits(D.eps_step) || flat)
             finish = true;
         else
             candidate = true;
@@ -494,13 +522,11 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
     __syncwarp();
     // commit the pass outcome to the shared state
     if (accept && lane < 12) S.T[lane] = S.Tc[lane];
-    if (load_normal) {
-        if (lane < 8) {
+    if (load_normal && lane < 8) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                S.H[8 * lane + c] = tot[c >= lane ? upper_index(lane, c) : upper_index(c, lane)];
-            S.g[lane] = tot[kIdxG + lane];
-        }
+        for (int c = 0; c < 8; ++c)
+            S.H[8 * lane + c] = tot[c >= lane ? upper_index(lane, c) : upper_index(c, lane)];
+        S.g[lane] = tot[kIdxG + lane];
     }
     if (lane == 0) {
         S.passes += 1;
@@ -513,6 +539,7 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
         }
         if (load_normal) {
             S.E = E;
+            S.nd = nd;
             S.n = n;
         }
     }
@@ -524,29 +551,27 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
         double a[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) a[c] = S.H[8 * row + c];
-        double a0 = 0.0;
+        double diag = 0.0;
 #pragma unroll
         for (int c = 0; c < 8; ++c)
-            if (c == row) {
-                a[c] = fma(lambda, a[c], a[c]);
-                a0 = a[c];
-            }
+            if (c == row) diag = a[c];
+        const double a0 = fma(lambda, diag, diag);   // damped diagonal
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c == row) a[c] = a0;
         double y = -S.g[row];
         double Lcol[8];
-        double dinv = 0.0;
-        bool ok = true;
+        double dinv = 0.0, dpiv = 0.0;
 #pragma unroll
         for (int c = 0; c < 8; ++c) Lcol[c] = 0.0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const double d = __shfl_sync(full, a[j], j);
-            const double a0j = __shfl_sync(full, a0, j);
-            if (!(d > 0.0) || !(d > 1e-13 * a0j)) {
-                ok = false;
-                break;
-            }
             const double r = rcp_d(d);
-            if (row == j) dinv = r;
+            if (row == j) {
+                dinv = r;
+                dpiv = d;
+            }
             const double lij = a[j] * r;
 #pragma unroll
             for (int k = j + 1; k < 8; ++k) {
@@ -560,6 +585,9 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
             }
             if (row > j) a[j] = lij;
         }
+        // pivots checked once, each lane its own: d > 0 and d > 1e-13 * damped diagonal
+        const bool piv_ok = dpiv > 1e-13 * a0 && dpiv > 0.0;
+        const bool ok = __all_sync(full, piv_ok || lane >= 8);
         if (!ok) {
             if (lane == 0) S.status |= GLT_TRACK_NOT_PD;
             finish = true;
@@ -580,11 +608,18 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
             double dl[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) dl[c] = __shfl_sync(full, x, c);
-            // ---- exp(delta_xi): R = I + A W + B W^2, t = (I + B W + C W^2) v
+            long long mbits = 0;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) mbits = max(mbits, abs_bits(dl[c]));
+            // ---- exp(delta_xi): R_e = I + A [w]x + B [w]x^2, t_e = v + B (w x v) + C w x (w x v)
             const double w0 = dl[3], w1 = dl[4], w2 = dl[5];
             const double th2 = fma(w0, w0, fma(w1, w1, w2 * w2));
             double A, B, Cc;
-            if (th2 < 0.01) {
+            if (th2 < 1e-4) {
+                A = fma(fma(th2, 1.0 / 120.0, -1.0 / 6.0), th2, 1.0);
+                B = fma(fma(th2, 1.0 / 720.0, -1.0 / 24.0), th2, 0.5);
+                Cc = fma(fma(th2, 1.0 / 5040.0, -1.0 / 120.0), th2, 1.0 / 6.0);
+            } else if (th2 < 0.01) {
                 A = fma(fma(fma(fma(th2, 1.0 / 362880.0, -1.0 / 5040.0), th2, 1.0 / 120.0), th2, -1.0 / 6.0), th2, 1.0);
                 B = fma(fma(fma(fma(th2, 1.0 / 3628800.0, -1.0 / 40320.0), th2, 1.0 / 720.0), th2, -1.0 / 24.0), th2, 0.5);
                 Cc = fma(fma(fma(fma(th2, 1.0 / 39916800.0, -1.0 / 362880.0), th2, 1.0 / 5040.0), th2, -1.0 / 120.0), th2, 1.0 / 6.0);
@@ -597,45 +632,41 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
                 B = 2.0 * sh * sh / th2;
                 Cc = (th - sn) / (th2 * th);
             }
-            const double ww[3] = {w0, w1, w2};
-            const double W[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
-            double Em[12];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                double tr = 0.0;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const double W2 = fma(ww[r], ww[c], r == c ? -th2 : 0.0);
-                    const double I = r == c ? 1.0 : 0.0;
-                    Em[4 * r + c] = fma(A, W[3 * r + c], fma(B, W2, I));
-                    const double V = fma(B, W[3 * r + c], fma(Cc, W2, I));
-                    tr = fma(V, dl[c], tr);
-                }
-                Em[4 * r + 3] = tr;
-            }
-            // ---- candidate pose Tc = T exp(delta_xi), one element per lane
+            const double v0 = dl[0], v1 = dl[1], v2 = dl[2];
+            const double c10 = fma(w1, v2, -w2 * v1), c11 = fma(w2, v0, -w0 * v2), c12 = fma(w0, v1, -w1 * v0);
+            const double c20 = fma(w1, c12, -w2 * c11), c21 = fma(w2, c10, -w0 * c12), c22 = fma(w0, c11, -w1 * c10);
+            const double te0 = fma(Cc, c20, fma(B, c10, v0));
+            const double te1 = fma(Cc, c21, fma(B, c11, v1));
+            const double te2 = fma(Cc, c22, fma(B, c12, v2));
+            // ---- Tc = T exp(delta_xi), one element (r, c) per lane:
+            // rotation  Rc_rc = R_rc + A (R_r x w)_c + B ((R_r . w) w_c - th2 R_rc)
+            // translation tc_r = R_r . t_e + t_r
             if (lane < 12) {
                 const int r = lane >> 2, c = lane & 3;
-                double e0 = 0, e1 = 0, e2 = 0;
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc)
-                    if (cc == c) {
-                        e0 = Em[cc];
-                        e1 = Em[4 + cc];
-                        e2 = Em[8 + cc];
-                    }
                 const double* Tr = S.T + 4 * r;
-                double v = fma(Tr[0], e0, fma(Tr[1], e1, Tr[2] * e2));
-                if (c == 3) v += Tr[3];
-                S.Tc[lane] = v;
+                const double R0 = Tr[0], R1 = Tr[1], R2 = Tr[2], t = Tr[3];
+                double out;
+                if (c == 3) {
+                    out = fma(R0, te0, fma(R1, te1, fma(R2, te2, t)));
+                } else {
+                    // (R_r x w)_c = R_{c+1} w_{c+2} - R_{c+2} w_{c+1} (indices mod 3)
+                    const double Ra = c == 0 ? R1 : (c == 1 ? R2 : R0);
+                    const double Rb = c == 0 ? R2 : (c == 1 ? R0 : R1);
+                    const double wa = c == 0 ? w1 : (c == 1 ? w2 : w0);
+                    const double wb = c == 0 ? w2 : (c == 1 ? w0 : w1);
+                    const double wc = c == 0 ? w0 : (c == 1 ? w1 : w2);
+                    const double Rc = c == 0 ? R0 : (c == 1 ? R1 : R2);
+                    const double q = fma(Ra, wb, -Rb * wa);
+                    const double pw = fma(R0, w0, fma(R1, w1, R2 * w2));
+                    const double t1 = fma(pw, wc, -th2 * Rc);
+                    out = fma(B, t1, fma(A, q, Rc));
+                }
+                S.Tc[lane] = out;
             }
-            double m = 0.0;
-#pragma unroll
-            for (int c = 0; c < 6; ++c) m = fmax(m, fabs(dl[c]));
             if (lane == 0) {
                 S.ac = S.a + dl[6];
                 S.bc = S.b + dl[7];
-                S.maxstep = m;
+                S.maxstep_bits = mbits;
                 S.phase = PH_CAND;
             }
             __syncwarp();

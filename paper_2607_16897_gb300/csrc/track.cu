@@ -58,29 +58,23 @@ __global__ void __launch_bounds__(THREADS) track_kernel(const StreamDesc* const*
         block_reduce<THREADS, MIXED>(acc, red, part[par], part_c[par]);
         if (C > 1) cluster.sync();
         if (tid < kNumAcc) {
-            // FP64 finish over the CTAs of the cluster: four interleaved
-            // partial sums keep the dependent FP64 add chain short
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            for (int r = 0; r < C; r += 4) {
-                double v[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    v[q] = 0.0;
-                    if (r + q < C) {
-                        const float* pr = C > 1 ? cluster.map_shared_rank(&part[par][0], r + q) : &part[par][0];
-                        v[q] = (double)pr[tid];
-                        if (MIXED) {
-                            const float* cr = C > 1 ? cluster.map_shared_rank(&part_c[par][0], r + q) : &part_c[par][0];
-                            v[q] += (double)cr[tid];
-                        }
-                    }
+            // finish over the CTAs of the cluster: a compensated FP32 sum
+            // (TwoSum, error-free per step) converted to FP64 once; the FP64
+            // pipe of this GPU is too slow to carry a chain of C adds
+            float hi = 0.0f, lo = 0.0f;
+            for (int r = 0; r < C; ++r) {
+                const float* pr = C > 1 ? cluster.map_shared_rank(&part[par][0], r) : &part[par][0];
+                float v = pr[tid];
+                if (MIXED) {
+                    const float* cr = C > 1 ? cluster.map_shared_rank(&part_c[par][0], r) : &part_c[par][0];
+                    lo += cr[tid];
                 }
-                s0 += v[0];
-                s1 += v[1];
-                s2 += v[2];
-                s3 += v[3];
+                const float s = hi + v;
+                const float bb = s - hi;
+                lo += (hi - (s - bb)) + (v - bb);
+                hi = s;
             }
-            tot[tid] = (s0 + s1) + (s2 + s3);
+            tot[tid] = (double)hi + (double)lo;
         }
         __syncthreads();
         if (tid < 32) solver_step_warp(sD, tot, S, P, tid, rank == 0);
