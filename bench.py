@@ -37,7 +37,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c4b"],
+                    help="c2: 640x480 single stream FP32 (default); c3: 64 streams of mixed "
+                         "sizes, batched; c4: 1280x720 mixed precision single stream; c4b: "
+                         "64 streams of c4, batched")
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="frames the oracle tracks for cpu_baseline (0 = auto, ~10-30 s)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -49,18 +52,19 @@ def parse():
 # workload
 # ---------------------------------------------------------------------------
 class Workload:
-    """C2: the frames, the reference keyframes and their map points."""
+    """One camera stream: its frames, reference keyframes and map points."""
 
-    def __init__(self, seed=1, frames=300, N=2000, W=640, H=480, f=525.0, L=4):
+    def __init__(self, seed=1, frames=300, N=2000, W=640, H=480, f=525.0, L=4, speed=0.5,
+                 ang=30.0, label="C2 single stream"):
         import synth
         self.cam = synth.camera_for(W, H, f)
-        self.seq = synth.sequence(seed, frames, self.cam, synth.ROOM_LARGE, 0.5, 30.0)
+        self.seq = synth.sequence(seed, frames, self.cam, synth.ROOM_LARGE, speed, ang)
         self.frames = [self.seq.frame(k)[0] for k in range(frames)]
         self.N, self.L = N, L
         self.refs = {}
-        self.name = (f"C2 single stream: {W}x{H} uint8, fx=fy={f:g}, {frames}-frame sequence "
-                     f"(0.5 m/s, 30 deg/s), N={N} points, L={L}, Huber 9, <=10 LM iters/level, "
-                     f"const-velocity init, reference every 8 frames")
+        self.name = (f"{label}: {W}x{H} uint8, fx=fy={f:g}, {frames}-frame sequence "
+                     f"({speed:g} m/s, {ang:g} deg/s), N={N} points, L={L}, Huber 9, "
+                     f"<=10 LM iters/level, const-velocity init, reference every 8 frames")
 
     def ref_points(self, r):
         import synth
@@ -254,23 +258,40 @@ def oracle_track_sequence(wl, frames, inits=None):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, same workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = Workload()
-    W = args.warmup
-    K = args.steps
-    t, res, _ = oracle_track_sequence(wl, min(len(wl.frames) - 1, W + K))
-    # time only the K frames after the warm-up ones: re-run them is wasteful,
-    # so time per frame is taken over the whole bounded run
-    n = min(len(wl.frames) - 1, W + K)
-    fps = n / t
+    W, K = args.warmup, args.steps
+    if args.workload in ("c3", "c4b"):
+        import concurrent.futures
+        wls = batch_workloads(args.workload, rank)
+        F = len(wls[0].frames)
+        n = min(F - 1, W + K)
+        workers = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
+            list(ex.map(lambda w: oracle_track_sequence(w, n), wls))
+        t = time.perf_counter() - t0
+        frames = n * len(wls)
+        name = f"{args.workload.upper()} batched, {len(wls)} streams"
+        sample = f"frames 1..{n} of each of the {len(wls)} streams, one host thread per stream"
+        cores = workers
+    else:
+        wl = single_workload(args.workload, rank)
+        n = min(len(wl.frames) - 1, W + K)
+        t, _, _ = oracle_track_sequence(wl, n)
+        frames = n
+        name = wl.name
+        sample = f"frames 1..{n} of the sequence, pyramid + track per frame"
+        cores = 1
+    fps = frames / t
     line = {"metric": "frames tracked/s", "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
-            "steps": K, "warmup": W, "ms_per_step": 1000.0 * t / n, "higher_is_better": True,
+            "steps": K, "warmup": W, "ms_per_step": 1000.0 * t / frames, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference", "config": {"workload": wl.name},
-            "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{n} frames of the sequence, pyramid + track per frame"},
+            "impl": "reference", "config": {"workload": name},
+            "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -291,11 +312,12 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    wl = Workload(seed=1 + rank)      # replicas: one independent stream per GPU
+    wl = single_workload(args.workload, rank)   # replicas: one independent stream per GPU
+    precision = "mixed" if args.workload == "c4" else "fp32"
     Wd, Hd, L, N = wl.cam.W, wl.cam.H, wl.L, wl.N
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
-    trk = glt.Tracker(Wd, Hd, wl.cam.K, levels=L, max_points=N)
+    trk = glt.Tracker(Wd, Hd, wl.cam.K, levels=L, max_points=N, precision=precision)
     frames_dev = torch.from_numpy(np.stack(wl.frames)).to(f"cuda:{local}")
     frames_pin = torch.from_numpy(np.stack(wl.frames)).pin_memory()
     init_dev = torch.zeros(14, dtype=torch.float64, device=f"cuda:{local}")
@@ -417,7 +439,9 @@ def run_ours(args):
         line = {"metric": "frames tracked/s", "value": value, "unit": "frames/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1000.0 * dev_s / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f16 storage / f32 math" if precision == "mixed" else "f32",
+                "data": "synthetic",
                 "config": {"workload": wl.name, "global_batch": world, "streams_per_gpu": 1,
                            "parallelism": f"replicas x{world}",
                            "l2": "flushed between steps (256 MB write, outside the step events)",
@@ -498,10 +522,296 @@ def run_cpu_baseline(args, wl, rec):
     return cpu, parity
 
 
+def single_workload(kind, rank=0):
+    if kind == "c4":
+        return Workload(seed=2000 + rank, frames=300, N=8000, W=1280, H=720, f=1050.0, L=5,
+                        speed=1.0, ang=60.0, label="C4 mixed precision, single stream")
+    return Workload(seed=1 + rank)
+
+
+def batch_workloads(kind, rank=0, nstreams=64, frames=24):
+    """C3: 64 streams, sizes uniform over {320x240, 640x480, 752x480, 1280x720}
+    (f = 0.8 W), N uniform in [300, 4000], L = 4.  C4b: 64 streams of the C4
+    configuration (1280x720, N = 8000, L = 5, 1 m/s, 60 deg/s)."""
+    rng = np.random.default_rng(1000 + rank)
+    sizes = [(320, 240), (640, 480), (752, 480), (1280, 720)]
+    wls = []
+    for s in range(nstreams):
+        if kind == "c4b":
+            wls.append(Workload(seed=2000 + s + 100000 * rank, frames=frames, N=8000, W=1280, H=720,
+                                f=1050.0, L=5, speed=1.0, ang=60.0, label="C4b stream"))
+        else:
+            W, H = sizes[int(rng.integers(4))]
+            N = int(rng.integers(300, 4001))
+            wls.append(Workload(seed=1000 + s + 100000 * rank, frames=frames, N=N, W=W, H=H,
+                                f=0.8 * W, L=4, label="C3 stream"))
+    return wls
+
+
+def run_batch(args):
+    """Batched form: every stream's next frame tracked by one graph replay
+    (pyramids of all streams + one persistent track launch)."""
+    import torch
+    import paper_2607_16897_gb300 as glt
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wls = batch_workloads(args.workload, rank)
+    precision = "mixed" if args.workload == "c4b" else "fp32"
+    S = len(wls)
+    F = len(wls[0].frames)
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    trks = [glt.Tracker(w.cam.W, w.cam.H, w.cam.K, levels=w.L, max_points=w.N, precision=precision)
+            for w in wls]
+    batch = glt.Batch(trks)
+    frames_dev = [torch.from_numpy(np.stack(w.frames)).to(dev) for w in wls]
+    frames_pin = [torch.from_numpy(np.stack(w.frames)).pin_memory() for w in wls]
+    slots = [torch.empty((w.cam.H, w.cam.W), dtype=torch.uint8, device=dev) for w in wls]
+    ptr_dev = torch.zeros(S, dtype=torch.int64, device=dev)
+    ptr_pin = torch.zeros(S, dtype=torch.int64).pin_memory()
+    init_dev = torch.zeros((S, 14), dtype=torch.float64, device=dev)
+    init_pin = torch.zeros((S, 14), dtype=torch.float64).pin_memory()
+    out_dev = torch.zeros(S * glt.RESULT_BYTES, dtype=torch.uint8, device=dev)
+    out_pin = torch.zeros(S * glt.RESULT_BYTES, dtype=torch.uint8).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    uvd_dev = {}
+
+    def refresh(s, r, host=False):
+        t = trks[s]
+        if host:
+            t.build_pyramid(glt.GLT_REF, wls[s].frames[r], stream=sh)
+            t.set_map_points(wls[s].ref_points(r), stream=sh)
+        else:
+            key = (s, r)
+            if key not in uvd_dev:
+                uvd_dev[key] = torch.from_numpy(wls[s].ref_points(r)).to(dev)
+            t.build_pyramid(glt.GLT_REF, frames_dev[s][r], stream=sh)
+            t.set_map_points(uvd_dev[key], stream=sh)
+
+    # every stream starts on its frame 0 as reference
+    drvs = [SequenceDriver(w) for w in wls]
+    for s in range(S):
+        drvs[s].refresh(0)
+        refresh(s, 0)
+    torch.cuda.synchronize()
+
+    def prepare(k, use_slots):
+        for s in range(S):
+            T_init, ab = drvs[s].init_for(k), drvs[s].ab_init()
+            init_pin[s] = torch.from_numpy(np.concatenate([T_init.ravel(), list(ab)]))
+            ptr_pin[s] = slots[s].data_ptr() if use_slots else frames_dev[s][k].data_ptr()
+
+    def finish(k, record, refresh_host=False):
+        res = glt.parse_results(out_pin.numpy())
+        n_ref = 0
+        for s in range(S):
+            if record is not None:
+                record.append((s, k, drvs[s].r, init_pin[s].numpy().copy(), res[s]))
+            drvs[s].record(k, res[s])
+            if k + 1 < F and drvs[s].refresh(k):
+                refresh(s, k, host=refresh_host)
+                n_ref += 1
+        return res, n_ref
+
+    # autotune the tile shape on frame 1, then capture the step
+    prepare(1, False)
+    with torch.cuda.stream(stream):
+        ptr_dev.copy_(ptr_pin, non_blocking=True)
+        init_dev.copy_(init_pin, non_blocking=True)
+        batch.build_pyramid(ptr_dev, stream=sh)
+    stream.synchronize()
+    shape = batch.autotune(init_dev, out_dev, reps=3, stream=sh)
+    batch.capture(ptr_dev, init_dev, out_dev, stream)
+
+    def run_steps(nsteps, timed, record, e2e=False):
+        for d in drvs:
+            d.__init__(d.wl)
+        for s in range(S):
+            drvs[s].refresh(0)
+            refresh(s, 0, host=e2e)
+        stream.synchronize()
+        k = 0
+        dev_ms, n_ref_total = [], 0
+        h2d = d2h = 0
+        for i in range(nsteps):
+            k += 1
+            if k >= F:
+                k = 1
+                for d in drvs:
+                    d.__init__(d.wl)
+                for s in range(S):
+                    drvs[s].refresh(0)
+                    refresh(s, 0, host=e2e)
+            prepare(k, e2e)
+            with torch.cuda.stream(stream):
+                if e2e:
+                    for s in range(S):
+                        slots[s].copy_(frames_pin[s][k], non_blocking=True)
+                        h2d += slots[s].numel()
+                    h2d += init_pin.numel() * 8
+                else:
+                    flush.zero_()
+                ptr_dev.copy_(ptr_pin, non_blocking=True)
+                init_dev.copy_(init_pin, non_blocking=True)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                batch.replay(stream=sh)
+                e1.record(stream)
+                out_pin.copy_(out_dev, non_blocking=True)
+                d2h += out_pin.numel()
+            stream.synchronize()
+            if timed:
+                dev_ms.append(e0.elapsed_time(e1))
+            _, nr = finish(k, record, refresh_host=e2e)
+            n_ref_total += nr
+        return dev_ms, n_ref_total, h2d, d2h
+
+    run_steps(max(args.warmup, 3), False, None)
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    rec = []
+    t0 = time.perf_counter()
+    dev_ms, n_ref, _, _ = run_steps(args.steps, True, rec)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    dev_s = sum(dev_ms) / 1000.0
+    if dist:
+        t = torch.tensor([dev_s, t_wall], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_s, t_wall = float(t[0]), float(t[1])
+    frames_done = world * S * args.steps
+    value = frames_done / dev_s
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        _, _, h2d, d2h = run_steps(args.steps, False, None, e2e=True)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t1
+        e2e = {"value": S * args.steps / te, "unit": "frames/s",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "note": "every step copies all streams' frames from pinned host memory, replays the "
+                       "graph, reads all results back; reference refreshes through the C ABI with "
+                       "host buffers"}
+    cpu = parity = None
+    if rank == 0 and not args.no_cpu:
+        cpu, parity = batch_cpu_baseline(wls, rec)
+    # roofline of the persistent tracker (the graph's dominant kernel)
+    samples = sum(r[4]["passes"] * 8 * wls[r[0]].N for r in rec) / args.steps
+    achieved = FLOPS_PER_SAMPLE * samples / (dev_s / args.steps) / 1e12
+    peaks, src = measured_peaks()
+    peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    gt = [pose_error(wls[s], k, r, res["T"]) for (s, k, r, _, res) in rec]
+    accuracy = {"median_rot_deg": float(np.rad2deg(np.median([e[0] for e in gt]))),
+                "median_trans_mm": float(1000 * np.median([e[1] for e in gt])),
+                "p99_trans_mm": float(1000 * np.percentile([e[1] for e in gt], 99)),
+                "status_nonzero": int(sum(1 for r in rec if r[4]["status"]))}
+    if rank == 0:
+        L = max(w.L for w in wls)
+        line = {"metric": "frames tracked/s", "value": value, "unit": "frames/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1000.0 * dev_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f16 storage / f32 math" if precision == "mixed" else "f32",
+                "data": "synthetic",
+                "config": {"workload": (f"{args.workload.upper()} batched: {S} streams in one graph "
+                                        f"replay (pyramids + one persistent track launch); "
+                                        + ("1280x720, N=8000, L=5, 1 m/s, 60 deg/s"
+                                           if args.workload == "c4b" else
+                                           "sizes uniform over 320x240/640x480/752x480/1280x720, "
+                                           "N uniform 300-4000, L=4")
+                                        + f", {F}-frame sequences, reference every 8 frames"),
+                           "global_batch": world * S, "streams_per_gpu": S,
+                           "parallelism": f"replicas x{world}",
+                           "autotuned_shape": {"cluster": shape[0], "threads": shape[1],
+                                               "ms": shape[2]},
+                           "l2": "flushed between steps (256 MB write, outside the step events)",
+                           "timing": "sum of per-step CUDA-event times around the graph replay"},
+                "breakdown_ms": {"replay": statistics.mean(dev_ms),
+                                 "wall_per_step": 1000.0 * t_wall / args.steps},
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "traffic": None, "kernel": "track_kernel",
+                             "peak_source": f"FP32 FMA peak from unit counts at "
+                                            f"{peaks.get('sm_max_mhz', 2070.0):g} MHz ({src} clock)",
+                             "samples_per_step": samples},
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": args.steps * (L + 1 + (1 if precision == "mixed" else 0))
+                                + n_ref * L,
+                "parity_vs_oracle": parity, "accuracy_vs_truth": accuracy}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def batch_cpu_baseline(wls, rec, frames_per_stream=8):
+    """The oracle on the first frames of every stream, one host thread per
+    stream over all cores, with the GPU run's initial states and references."""
+    import concurrent.futures
+    S = len(wls)
+    per = {}
+    for (s, k, r, init, res) in rec:
+        if k <= frames_per_stream and (s, k) not in per:
+            per[(s, k)] = (r, init[:12].reshape(3, 4), (float(init[12]), float(init[13])), res)
+
+    def one(s):
+        ks = [k for k in range(1, frames_per_stream + 1) if (s, k) in per]
+        inits = {k: per[(s, k)][:3] for k in ks}
+        t, out, _ = oracle_track_sequence(wls[s], len(ks), inits=inits)
+        diffs = []
+        for k in ks:
+            gr = per[(s, k)][3]
+            g = gr["T"]
+            o = out[k]["T"]
+            dR = g[:, :3].T @ o[:, :3]
+            sn = 0.5 * np.linalg.norm([dR[2, 1] - dR[1, 2], dR[0, 2] - dR[2, 0], dR[1, 0] - dR[0, 1]])
+            diffs.append((float(np.arctan2(sn, 0.5 * (np.trace(dR) - 1))),
+                          float(np.linalg.norm(g[:, 3] - o[:, 3])),
+                          {"stream": s, "frame": k, "size": [wls[s].cam.W, wls[s].cam.H],
+                           "N": wls[s].N, "gpu_iters": gr["iters"][:wls[s].L],
+                           "oracle_iters": out[k]["iters"], "gpu_status": gr["status"],
+                           "oracle_status": out[k]["status"], "gpu_cost": gr["cost"],
+                           "oracle_cost": out[k]["cost"]}))
+        return len(ks), diffs
+
+    workers = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
+        outs = list(ex.map(one, range(S)))
+    t = time.perf_counter() - t0
+    n = sum(o[0] for o in outs)
+    diffs = [d for o in outs for d in o[1]]
+    cpu = {"value": n / t, "unit": "frames/s", "cores": workers, "kind": "oracle",
+           "sample": f"frames 1..{frames_per_stream} of each of the {S} streams (FP64 C oracle, one "
+                     f"host thread per stream, same initial states and references as the GPU run)"}
+    worst = sorted(diffs, key=lambda d: -d[1])[:3]
+    parity = {"frames": n, "max_rot_rad": max(d[0] for d in diffs),
+              "max_trans_m": max(d[1] for d in diffs),
+              "within_tolerance": int(sum(1 for d in diffs if d[0] <= 1e-5 and d[1] <= 1e-5)),
+              "worst": [dict(w[2], rot_rad=w[0], trans_m=w[1]) for w in worst],
+              "tolerance": {"rot_rad": 1e-5, "trans_m": 1e-5}}
+    return cpu, parity
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload in ("c3", "c4b"):
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -1,0 +1,121 @@
+"""Batched form: streams of different sizes, point counts and level counts
+tracked in one persistent launch (and one CUDA-graph replay) must each agree
+with the FP64 oracle run on the same stream alone (pose within 1e-5 rad /
+1e-5 m)."""
+import numpy as np
+import pytest
+
+from helpers import A_TOL, B_TOL, ROT_TOL, TRANS_TOL, pose_diff
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [  # (W, H, f, N, L)
+    (320, 240, 256.0, 300, 4),
+    (640, 480, 525.0, 2000, 4),
+    (752, 480, 601.6, 1000, 3),
+    (1280, 720, 1024.0, 4000, 4),
+    (320, 240, 256.0, 1, 3),      # too few samples on every level
+    (640, 480, 512.0, 37, 4),     # ragged: fewer points than one warp
+]
+
+
+@pytest.fixture(scope="module")
+def glt():
+    import paper_2607_16897_gb300 as g
+    return g
+
+
+def make_streams(syn, orc, glt, precision):
+    import torch
+    streams = []
+    for i, (W, H, f, N, L) in enumerate(SPECS):
+        cam = syn.camera_for(W, H, f)
+        seq = syn.sequence(500 + i, 6, cam, syn.ROOM_LARGE, 0.5, 30.0)
+        ref, uvd = syn.reference_points(seq, 0, max(N, 1), 0.5, 8.0)
+        uvd = uvd[:N]
+        cur, _ = seq.frame(3)
+        trk = glt.Tracker(W, H, cam.K, levels=L, max_points=max(N, 1), precision=precision)
+        trk.build_pyramid(glt.GLT_REF, ref)
+        trk.set_map_points(uvd)
+        o = orc.OracleTracker(W, H, cam.K, levels=L)
+        o.build_pyramid(0, ref)
+        o.set_map_points(uvd)
+        o.build_pyramid(1, cur)
+        T_init = syn.relative(seq.T_wc[0], seq.T_wc[2])   # previous frame's true pose
+        streams.append(dict(trk=trk, orc=o, cur=torch.from_numpy(cur).cuda(), T_init=T_init))
+    return streams
+
+
+def run_batch(glt, streams, shape=None, graph=False):
+    import torch
+    S = len(streams)
+    batch = glt.Batch([s["trk"] for s in streams])
+    if shape:
+        batch.set_shape(*shape)
+    ptrs = torch.tensor([s["cur"].data_ptr() for s in streams], dtype=torch.int64).cuda()
+    init = torch.tensor(np.stack([np.concatenate([s["T_init"].ravel(), [0.0, 0.0]])
+                                  for s in streams]), dtype=torch.float64).cuda()
+    out = torch.zeros(S * glt.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    if graph:
+        st = torch.cuda.Stream()
+        batch.capture(ptrs, init, out, st)
+        batch.replay(stream=st)
+        st.synchronize()
+    else:
+        batch.build_pyramid(ptrs)
+        batch.track(init, out)
+        torch.cuda.synchronize()
+    res = glt.parse_results(out)
+    batch.close()
+    return res
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_batch_matches_oracle_per_stream(glt, orc, syn, precision):
+    streams = make_streams(syn, orc, glt, precision)
+    res = run_batch(glt, streams)
+    for i, (s, g) in enumerate(zip(streams, res)):
+        o = s["orc"].track_frame(s["T_init"])
+        ang, dt = pose_diff(g["T"], o["T"])
+        assert ang <= ROT_TOL and dt <= TRANS_TOL, (i, ang, dt)
+        assert abs(g["a"] - o["a"]) <= A_TOL and abs(g["b"] - o["b"]) <= B_TOL, i
+        assert g["status"] == o["status"], i
+        assert g["iters"][:len(o["iters"])] == o["iters"] or abs(g["passes"] - o["passes"]) <= 3
+    assert res[4]["status"] & glt.GLT_TRACK_TOO_FEW_POINTS
+    for s in streams:
+        s["trk"].close()
+
+
+def test_graph_replay_equals_direct_launch_and_shapes(glt, orc, syn):
+    streams = make_streams(syn, orc, glt, "fp32")
+    direct = run_batch(glt, streams, shape=(2, 256))
+    graph = run_batch(glt, streams, shape=(2, 256), graph=True)
+    for d, g in zip(direct, graph):
+        assert np.array_equal(d["T"], g["T"]) and d["passes"] == g["passes"]
+    # other shapes agree with the oracle too
+    for shape in [(1, 128), (4, 256), (8, 128)]:
+        res = run_batch(glt, streams, shape=shape)
+        for s, g in zip(streams, res):
+            o = s["orc"].track_frame(s["T_init"])
+            ang, dt = pose_diff(g["T"], o["T"])
+            assert ang <= ROT_TOL and dt <= TRANS_TOL, (shape, ang, dt)
+    for s in streams:
+        s["trk"].close()
+
+
+def test_autotune_picks_a_valid_shape(glt, orc, syn):
+    import torch
+    streams = make_streams(syn, orc, glt, "fp32")
+    batch = glt.Batch([s["trk"] for s in streams])
+    ptrs = torch.tensor([s["cur"].data_ptr() for s in streams], dtype=torch.int64).cuda()
+    init = torch.tensor(np.stack([np.concatenate([s["T_init"].ravel(), [0.0, 0.0]])
+                                  for s in streams]), dtype=torch.float64).cuda()
+    out = torch.zeros(len(streams) * glt.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    batch.build_pyramid(ptrs)
+    c, t, ms = batch.autotune(init, out, reps=2)
+    assert c in (1, 2, 4, 8) and t in (128, 256, 512) and ms > 0
+    with pytest.raises(glt.GltError):
+        batch.set_shape(3, 100)
+    batch.close()
+    for s in streams:
+        s["trk"].close()
