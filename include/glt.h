@@ -109,8 +109,8 @@ typedef struct glt_result {
 } glt_result;
 
 /* Fills `cfg` with the defaults: 4 levels, 10 iterations per level, Huber 9,
- * lambda0 1e-4 (x4 up, x0.5 down), eps_step 1e-6, eps_cost 1e-4,
- * accept_step 1e-4, min_valid 16, zmin 1e-3, FP32, automatic cluster/threads,
+ * lambda0 1e-4 (x4 up, x0.5 down), eps_step 1e-6, eps_cost 0 (off),
+ * accept_step 1e-3, min_valid 16, zmin 1e-3, FP32, automatic cluster/threads,
  * max_points 4096. */
 void glt_default_config(glt_config* cfg, int width, int height, double fx, double fy,
                         double cx, double cy);

@@ -235,7 +235,7 @@ def linearize(img_l, K0, level, x_r, I0_l, valid_l, T, a, b, huber_k=9.0, zmin=1
 # configuration and tracking
 # --------------------------------------------------------------------------
 DEFAULT_CONFIG = dict(levels=4, max_iters=[10] * 8, huber_k=9.0, lambda0=1e-4, lambda_up=4.0,
-                      lambda_down=0.5, eps_step=1e-6, eps_cost=1e-4, accept_step=1e-4,
+                      lambda_down=0.5, eps_step=1e-6, eps_cost=0.0, accept_step=1e-3,
                       min_valid=16, zmin=1e-3)
 
 

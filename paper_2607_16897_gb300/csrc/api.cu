@@ -151,8 +151,8 @@ void glt_default_config(glt_config* c, int width, int height, double fx, double 
     c->lambda_up = 4.0;
     c->lambda_down = 0.5;
     c->eps_step = 1e-6;
-    c->eps_cost = 1e-4;
-    c->accept_step = 1e-4;
+    c->eps_cost = 0.0;
+    c->accept_step = 1e-3;
     c->min_valid = 16;
     c->zmin = 1e-3;
     c->precision = GLT_FP32;
