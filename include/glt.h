@@ -71,6 +71,7 @@ extern "C" {
 
 typedef struct glt_tracker glt_tracker;
 typedef struct glt_batch glt_batch;
+typedef struct glt_nn glt_nn;
 
 typedef struct glt_config {
     int width, height;          /* level-0 frame size in pixels (>= 16 each) */
@@ -242,6 +243,76 @@ int glt_linearize_noalloc(const uint8_t* ref_dev, int ref_pitch, const uint8_t* 
                           double cx, double cy, const float* uvd_dev, int n, const double T[12],
                           double a, double b, double huber_k, double zmin, double* out_dev,
                           void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned initial-pose proposal.  The paper has no counterpart: it seeds each
+ * frame with a constant-velocity guess only.  This optional stage maps the
+ * coarsest-level residual image of a stream (current minus reference at the
+ * identity warp, 40 x 30, divided by 64) and the stream's previous inter-frame
+ * motion (a 6-vector: log of that motion divided by 0.02) to an increment of
+ * the initial state, which then starts the same LM solve.
+ * Network: 3 x (conv 3x3, stride 2, zero padding 1, ReLU) with 16, 32, 64
+ * channels -> flatten (1280) ++ motion (6) -> fc 128 + ReLU -> fc 8.
+ * The 8 outputs y give delta = (0.01 y[0..6], y[7]) and the proposal
+ * T' = T_init exp(delta[0..5]), a' = a + delta[6], b' = b + delta[7].
+ * Parameters are one flat FP32 array of GLT_NN_PARAMS values: conv1.w
+ * [16,1,3,3], conv1.b [16], conv2.w [32,16,3,3], conv2.b [32], conv3.w
+ * [64,32,3,3], conv3.b [64], fc1.w [128,1286], fc1.b [128], fc2.w [8,128],
+ * fc2.b [8], each row-major.  The kernels use BF16 copies of the weights
+ * (rounded to nearest even from the FP32 master copy), FP32 activations and
+ * FP32 accumulation in a fixed order (results are deterministic).
+ * Inputs x are [B][1200] (row-major 30 x 40 images), motions m [B][6],
+ * outputs and targets [B][8], all FP32 DEVICE arrays.
+ * A network object is not thread-safe; work on it is ordered on the stream
+ * passed to each call, and it must not be used on two streams at once.
+ * ------------------------------------------------------------------------- */
+#define GLT_NN_PARAMS 189064
+#define GLT_NN_INPUT 1200
+#define GLT_NN_MOTION 6
+#define GLT_NN_OUTPUT 8
+
+/* Allocates a network for batches of up to max_batch (1..65536) samples:
+ * FP32 master weights, BF16 copy, Adam moments, activations.  Weights are
+ * uninitialised until glt_nn_set_params.  Errors: INVALID_ARG, CUDA. */
+int glt_nn_create(int max_batch, glt_nn** out);
+void glt_nn_destroy(glt_nn* nn);
+
+/* Copies `count` (= GLT_NN_PARAMS) FP32 host values into the master weights,
+ * refreshes the BF16 copy and resets the Adam state.  Synchronous. */
+int glt_nn_set_params(glt_nn* nn, const float* params_host, int count);
+
+/* Copies the FP32 master weights to host memory.  Synchronous. */
+int glt_nn_get_params(glt_nn* nn, float* params_host, int count);
+
+/* Inference: y_dev[B][8] = network(x_dev, m_dev).  Asynchronous. */
+int glt_nn_forward(glt_nn* nn, const float* x_dev, const float* m_dev, float* y_dev, int B,
+                   void* stream);
+
+/* Loss L = 0.5/B sum_b ||y_b - t_b||^2 and its gradient with respect to every
+ * parameter (with the BF16 weights used in the forward and backward passes),
+ * written to host grad_host[GLT_NN_PARAMS] and *loss_host (may be NULL).
+ * Synchronous.  Changes no weights. */
+int glt_nn_gradient(glt_nn* nn, const float* x_dev, const float* m_dev, const float* t_dev, int B,
+                    float* grad_host, float* loss_host, void* stream);
+
+/* One training step: forward, backward, Adam (beta1 0.9, beta2 0.999,
+ * eps 1e-8, bias-corrected, learning rate lr > 0) on the FP32 master weights,
+ * BF16 refresh.  The pre-update loss goes to the device float *loss_dev (may
+ * be NULL).  Asynchronous. */
+int glt_nn_train_step(glt_nn* nn, const float* x_dev, const float* m_dev, const float* t_dev,
+                      int B, float lr, float* loss_dev, void* stream);
+
+/* Attaches `nn` (or detaches it, nn = NULL) as the proposal stage of the
+ * batch: from then on glt_batch_track and glt_batch_capture first build each
+ * stream's residual image from its REF and CUR coarsest levels, run the
+ * network on all S streams with the motions motion_dev[S][6] (a DEVICE array
+ * read at run time) and start every stream's LM from the proposed state
+ * instead of init_dev.  Every tracker of the batch needs a 40 x 30 coarsest
+ * level (640 x 480 with 5 levels, 320 x 240 with 4).  The batch references
+ * the network, which must outlive it and must not be trained while the batch
+ * uses it.  Invalidates a captured graph.  The autotuner ignores the stage.
+ * Errors: INVALID_ARG (size, max_batch < S), CUDA. */
+int glt_batch_set_proposal(glt_batch* batch, glt_nn* nn, const float* motion_dev);
 
 /* Thread-local message of the last error (never NULL). */
 const char* glt_last_error(void);

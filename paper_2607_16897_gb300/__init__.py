@@ -29,6 +29,10 @@ GLT_TRACK_NOT_PD = 2
 GLT_REF, GLT_CUR = 0, 1
 GLT_FP32, GLT_MIXED = 0, 1
 MAX_LEVELS = 8
+GLT_NN_PARAMS = 189064
+GLT_NN_INPUT = 1200
+GLT_NN_MOTION = 6
+GLT_NN_OUTPUT = 8
 
 
 class glt_config(ctypes.Structure):
@@ -91,6 +95,14 @@ SIGNATURES = {
     "glt_batch_set_shape": (_i, [_vp, _i, _i]),
     "glt_linearize_noalloc": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _d, _d, _d, _d, _vp, _i, _P(_d),
                                    _d, _d, _d, _d, _vp, _vp]),
+    "glt_nn_create": (_i, [_i, _P(_vp)]),
+    "glt_nn_destroy": (None, [_vp]),
+    "glt_nn_set_params": (_i, [_vp, _P(ctypes.c_float), _i]),
+    "glt_nn_get_params": (_i, [_vp, _P(ctypes.c_float), _i]),
+    "glt_nn_forward": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
+    "glt_nn_gradient": (_i, [_vp, _vp, _vp, _vp, _i, _P(ctypes.c_float), _P(ctypes.c_float), _vp]),
+    "glt_nn_train_step": (_i, [_vp, _vp, _vp, _vp, _i, ctypes.c_float, _vp, _vp]),
+    "glt_batch_set_proposal": (_i, [_vp, _vp, _vp]),
     "glt_last_error": (ctypes.c_char_p, []),
     "glt_version": (ctypes.c_char_p, []),
 }
@@ -323,6 +335,67 @@ class Batch:
                                        ctypes.byref(c), ctypes.byref(t), ctypes.byref(ms),
                                        _stream_handle(stream)), "glt_batch_autotune")
         return c.value, t.value, ms.value
+
+    def set_proposal(self, nn, motion_dev):
+        """Attach a proposal network (``NN``) with per-stream motions
+        motion_dev [S, 6] (float32, device); ``nn=None`` detaches it."""
+        self._nn = nn
+        self._motion = motion_dev
+        _check(_lib.glt_batch_set_proposal(self.handle, nn.handle if nn is not None else None,
+                                           _dptr(motion_dev) if nn is not None else None),
+               "glt_batch_set_proposal")
+
+
+class NN:
+    """Learned initial-pose proposal network (glt_nn_*): FP32 device arrays
+    x [B, 1200], m [B, 6], y / t [B, 8]."""
+
+    def __init__(self, max_batch, params=None):
+        h = ctypes.c_void_p()
+        _check(_lib.glt_nn_create(int(max_batch), ctypes.byref(h)), "glt_nn_create")
+        self.handle = h
+        self.max_batch = int(max_batch)
+        if params is not None:
+            self.set_params(params)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.glt_nn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(_lib.glt_nn_set_params(self.handle, p.ctypes.data_as(_P(ctypes.c_float)), p.size),
+               "glt_nn_set_params")
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(GLT_NN_PARAMS, np.float32)
+        _check(_lib.glt_nn_get_params(self.handle, p.ctypes.data_as(_P(ctypes.c_float)), p.size),
+               "glt_nn_get_params")
+        return p
+
+    def forward(self, x_dev, m_dev, y_dev, B, stream=None):
+        _check(_lib.glt_nn_forward(self.handle, _dptr(x_dev), _dptr(m_dev), _dptr(y_dev), int(B),
+                                   _stream_handle(stream)), "glt_nn_forward")
+
+    def gradient(self, x_dev, m_dev, t_dev, B, stream=None):
+        g = np.zeros(GLT_NN_PARAMS, np.float32)
+        loss = ctypes.c_float()
+        _check(_lib.glt_nn_gradient(self.handle, _dptr(x_dev), _dptr(m_dev), _dptr(t_dev), int(B),
+                                    g.ctypes.data_as(_P(ctypes.c_float)), ctypes.byref(loss),
+                                    _stream_handle(stream)), "glt_nn_gradient")
+        return g, loss.value
+
+    def train_step(self, x_dev, m_dev, t_dev, B, lr, loss_dev=None, stream=None):
+        _check(_lib.glt_nn_train_step(self.handle, _dptr(x_dev), _dptr(m_dev), _dptr(t_dev), int(B),
+                                      float(lr), _dptr(loss_dev) if loss_dev is not None else None,
+                                      _stream_handle(stream)), "glt_nn_train_step")
 
 
 def version() -> str:

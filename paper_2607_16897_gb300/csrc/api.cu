@@ -488,6 +488,9 @@ static void free_batch(glt_batch* b)
     cudaFree(b->copy_dev);
     cudaFree(b->jobs_dev);
     cudaFree(b->pack_dev);
+    cudaFree(b->prop_jobs);
+    cudaFree(b->prop_x);
+    cudaFree(b->prop_init);
     delete b;
 }
 
@@ -628,9 +631,13 @@ int glt_batch_track(glt_batch* b, const double* init_dev, glt_result* out_dev, v
     int rc = batch_prereq(b);
     if (rc != GLT_OK) return rc;
     if (!init_dev || !out_dev) return invalid("NULL argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (b->nn) {
+        GLT_CHECK(launch_proposal(b, init_dev, s), "proposal kernels");
+        init_dev = b->prop_init;
+    }
     GLT_CHECK(launch_track(b->descs_dev, b->users_dev, b->S, b->cluster, b->threads,
-                           b->precision == GLT_MIXED, init_dev, out_dev,
-                           reinterpret_cast<cudaStream_t>(stream)),
+                           b->precision == GLT_MIXED, init_dev, out_dev, s),
               "batch track kernel");
     return GLT_OK;
 }
@@ -653,8 +660,14 @@ int glt_batch_capture(glt_batch* b, const uint8_t* const* frames_dev, const doub
     }
     GLT_CHECK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
     int r1 = batch_pyramid(b, frames_dev, s);
-    cudaError_t e1 = launch_track(b->descs_dev, b->users_dev, b->S, b->cluster, b->threads,
-                                  b->precision == GLT_MIXED, init_dev, out_dev, s);
+    cudaError_t e1 = cudaSuccess;
+    if (b->nn) {
+        e1 = launch_proposal(b, init_dev, s);
+        init_dev = b->prop_init;
+    }
+    if (e1 == cudaSuccess)
+        e1 = launch_track(b->descs_dev, b->users_dev, b->S, b->cluster, b->threads,
+                          b->precision == GLT_MIXED, init_dev, out_dev, s);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
     if (r1 != GLT_OK) {

@@ -32,6 +32,12 @@ struct CopyJob {            // one frame -> level-0 copy (batched form)
     int W, H, dp;
 };
 
+struct PropJob {            // coarsest levels (40 x 30) of one stream, for the proposal input
+    const uint8_t* ref;
+    const uint8_t* cur;
+    int pitch;
+};
+
 struct PackJob {            // one level -> FP16 (I, gx, gy, 0) copy (mixed form)
     const uint8_t* src;
     uint2* dst;
@@ -96,11 +102,20 @@ struct glt_batch {
     int cluster = 2, threads = 256;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // learned initial-pose proposal (optional)
+    glt_nn* nn = nullptr;
+    const float* motion_dev = nullptr;
+    glt::PropJob* prop_jobs = nullptr;
+    float* prop_x = nullptr;
+    double* prop_init = nullptr;
 };
 
 namespace glt {
 
 void set_error(const std::string& msg);
+int invalid_arg_msg(const char* msg);
+cudaError_t nn_forward(glt_nn* n, const float* x, const float* mo, int B, cudaStream_t s);
+cudaError_t launch_proposal(glt_batch* b, const double* init_dev, cudaStream_t s);
 int cuda_fail(cudaError_t e, const char* what);
 
 // pyramid.cu

@@ -1,0 +1,558 @@
+// Learned initial-pose proposal: a 3 x (conv 3x3 stride 2 pad 1 + ReLU) +
+// 2-layer MLP network (189064 parameters) mapping the coarsest-level residual
+// image (1 x 30 x 40) and the previous inter-frame motion (6) to an 8-vector
+// increment of the initial state.  Hand-written training and inference
+// kernels: BF16 weights (rounded from FP32 master weights after every Adam
+// step), FP32 activations and accumulation, deterministic reductions (fixed
+// summation order, no atomics).
+//
+// Flat parameter layout: conv1.w [16,1,3,3], conv1.b [16], conv2.w [32,16,3,3],
+// conv2.b [32], conv3.w [64,32,3,3], conv3.b [64], fc1.w [128,1286],
+// fc1.b [128], fc2.w [8,128], fc2.b [8], row-major, in that order.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "glt_internal.h"
+
+namespace glt {
+namespace nn {
+
+constexpr int kIn = 1200, kMotion = 6, kOut = 8, kFlat = 1280, kF = 1286, kHid = 128;
+struct Layer {
+    int w, b;  // offsets of weight and bias in the flat layout
+};
+constexpr Layer kC1 = {0, 144}, kC2 = {160, 4768}, kC3 = {4800, 23232}, kF1 = {23296, 187904},
+                kF2 = {188032, 189056};
+constexpr int kParams = 189064;
+
+__device__ __forceinline__ float wv(const __nv_bfloat16* w, int i) { return __bfloat162float(w[i]); }
+
+// out[b,o,i,j] = bias_o + sum_{c,di,dj} w[o,c,di,dj] in[b,c,2i+di-1,2j+dj-1]; stores the
+// pre-activation z and a = max(z, 0).
+__global__ void conv_fwd(const float* __restrict__ in, const __nv_bfloat16* __restrict__ w, int woff,
+                         int boff, int B, int C, int H, int W, int O, float* __restrict__ z,
+                         float* __restrict__ a)
+{
+    const int Ho = (H + 1) / 2, Wo = (W + 1) / 2;
+    const int n = B * O * Ho * Wo;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int j = t % Wo, i = (t / Wo) % Ho, o = (t / (Wo * Ho)) % O, b = t / (Wo * Ho * O);
+        float s = wv(w, boff + o);
+        for (int c = 0; c < C; ++c) {
+            const float* x = in + ((size_t)(b * C + c) * H) * W;
+            const int wb = woff + (o * C + c) * 9;
+#pragma unroll
+            for (int di = 0; di < 3; ++di) {
+                const int r = 2 * i + di - 1;
+                if (r < 0 || r >= H) continue;
+#pragma unroll
+                for (int dj = 0; dj < 3; ++dj) {
+                    const int q = 2 * j + dj - 1;
+                    if (q < 0 || q >= W) continue;
+                    s = fmaf(wv(w, wb + di * 3 + dj), x[r * W + q], s);
+                }
+            }
+        }
+        z[t] = s;
+        a[t] = fmaxf(s, 0.0f);
+    }
+}
+
+// out[b,o] = bias_o + sum_i w[o,i] in[b,i], in = (in0[b, 0:n0], in1[b, 0:n1]);
+// one warp per output, lanes stride over i, fixed-order shuffle reduction.
+__global__ void fc_fwd(const float* __restrict__ in0, int n0, const float* __restrict__ in1, int n1,
+                       const __nv_bfloat16* __restrict__ w, int woff, int boff, int B, int O,
+                       float* __restrict__ z, float* __restrict__ a, int relu)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= B * O) return;
+    const int b = warp / O, o = warp % O;
+    const int n = n0 + n1;
+    const __nv_bfloat16* wr = w + woff + (size_t)o * n;
+    float s = 0.0f;
+    for (int i = lane; i < n; i += 32) {
+        const float x = i < n0 ? in0[(size_t)b * n0 + i] : in1[(size_t)b * n1 + (i - n0)];
+        s = fmaf(wv(wr, i), x, s);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+        s += wv(w, boff + o);
+        z[warp] = s;
+        a[warp] = relu ? fmaxf(s, 0.0f) : s;
+    }
+}
+
+// dy = (y - t) / B and loss = 0.5 * sum (y - t)^2 / B (one block).
+__global__ void loss_grad(const float* __restrict__ y, const float* __restrict__ t, int B,
+                          float* __restrict__ dy, float* __restrict__ loss)
+{
+    __shared__ float red[256];
+    float s = 0.0f;
+    const int n = B * kOut;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float d = y[i] - t[i];
+        dy[i] = d / (float)B;
+        s = fmaf(d, d, s);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && loss) *loss = 0.5f * red[0] / (float)B;
+}
+
+// fully connected backward: dW[o,i] = sum_b dz[b,o] in[b,i] (one thread per
+// weight), db[o] = sum_b dz[b,o].
+__global__ void fc_bwd_w(const float* __restrict__ dz, const float* __restrict__ in0, int n0,
+                         const float* __restrict__ in1, int n1, int B, int O,
+                         float* __restrict__ grad, int woff, int boff)
+{
+    const int n = n0 + n1;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < O * n) {
+        const int o = t / n, i = t % n;
+        float s = 0.0f;
+        for (int b = 0; b < B; ++b) {
+            const float x = i < n0 ? in0[(size_t)b * n0 + i] : in1[(size_t)b * n1 + (i - n0)];
+            s = fmaf(dz[b * O + o], x, s);
+        }
+        grad[woff + t] = s;
+    } else if (t < O * n + O) {
+        const int o = t - O * n;
+        float s = 0.0f;
+        for (int b = 0; b < B; ++b) s += dz[b * O + o];
+        grad[boff + o] = s;
+    }
+}
+
+// input gradient of a fully connected layer, times the ReLU mask of the
+// input's pre-activation: din[b,i] = (sum_o w[o,i] dz[b,o]) * (zin[b,i] > 0), i < nout.
+__global__ void fc_bwd_in(const float* __restrict__ dz, const __nv_bfloat16* __restrict__ w, int woff,
+                          int n, int B, int O, int nout, const float* __restrict__ zin,
+                          float* __restrict__ din)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B * nout) return;
+    const int b = t / nout, i = t % nout;
+    float s = 0.0f;
+    for (int o = 0; o < O; ++o) s = fmaf(wv(w, woff + (size_t)o * n + i), dz[b * O + o], s);
+    din[t] = zin[t] > 0.0f ? s : 0.0f;
+}
+
+// conv weight and bias gradients: one block per weight (or bias), strided
+// loop over (b, i, j) and a fixed-order block reduction.
+__global__ void conv_bwd_w(const float* __restrict__ dz, const float* __restrict__ in, int B, int C,
+                           int H, int W, int O, float* __restrict__ grad, int woff, int boff)
+{
+    __shared__ float red[128];
+    const int Ho = (H + 1) / 2, Wo = (W + 1) / 2;
+    const int nw = O * C * 9;
+    const int k = blockIdx.x;
+    float s = 0.0f;
+    const int n = B * Ho * Wo;
+    if (k < nw) {
+        const int o = k / (C * 9), c = (k / 9) % C, di = (k % 9) / 3, dj = k % 3;
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            const int j = t % Wo, i = (t / Wo) % Ho, b = t / (Wo * Ho);
+            const int r = 2 * i + di - 1, q = 2 * j + dj - 1;
+            if (r >= 0 && r < H && q >= 0 && q < W)
+                s = fmaf(dz[((size_t)(b * O + o) * Ho + i) * Wo + j], in[((size_t)(b * C + c) * H + r) * W + q], s);
+        }
+    } else {
+        const int o = k - nw;
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            const int j = t % Wo, i = (t / Wo) % Ho, b = t / (Wo * Ho);
+            s += dz[((size_t)(b * O + o) * Ho + i) * Wo + j];
+        }
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = 64; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) grad[k < nw ? woff + k : boff + (k - nw)] = red[0];
+}
+
+// conv input gradient times the input pre-activation's ReLU mask.
+__global__ void conv_bwd_in(const float* __restrict__ dz, const __nv_bfloat16* __restrict__ w, int woff,
+                            int B, int C, int H, int W, int O, const float* __restrict__ zin,
+                            float* __restrict__ din)
+{
+    const int Ho = (H + 1) / 2, Wo = (W + 1) / 2;
+    const int n = B * C * H * W;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int x = t % W, y = (t / W) % H, c = (t / (W * H)) % C, b = t / (W * H * C);
+        float s = 0.0f;
+        for (int o = 0; o < O; ++o) {
+#pragma unroll
+            for (int di = 0; di < 3; ++di) {
+                const int r2 = y + 1 - di;
+                if (r2 < 0 || (r2 & 1) || (r2 >> 1) >= Ho) continue;
+#pragma unroll
+                for (int dj = 0; dj < 3; ++dj) {
+                    const int q2 = x + 1 - dj;
+                    if (q2 < 0 || (q2 & 1) || (q2 >> 1) >= Wo) continue;
+                    s = fmaf(wv(w, woff + (o * C + c) * 9 + di * 3 + dj),
+                             dz[((size_t)(b * O + o) * Ho + (r2 >> 1)) * Wo + (q2 >> 1)], s);
+                }
+            }
+        }
+        din[t] = zin[t] > 0.0f ? s : 0.0f;
+    }
+}
+
+// Adam (Kingma and Ba) on the FP32 master weights, then the BF16 copy.
+__global__ void adam(float* __restrict__ w, __nv_bfloat16* __restrict__ wbf, const float* __restrict__ g,
+                     float* __restrict__ m, float* __restrict__ v, int n, float lr, float b1, float b2,
+                     float eps, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
+    const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    w[i] = wi;
+    wbf[i] = __float2bfloat16_rn(wi);
+}
+
+__global__ void to_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict__ wbf, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) wbf[i] = __float2bfloat16_rn(w[i]);
+}
+
+}  // namespace nn
+}  // namespace glt
+
+struct glt_nn {
+    int max_batch = 0;
+    int step = 0;
+    float* w = nullptr;               // FP32 master
+    __nv_bfloat16* wbf = nullptr;     // BF16 copy used by the kernels
+    float* g = nullptr;
+    float* m = nullptr;
+    float* v = nullptr;
+    float *z1, *a1, *z2, *a2, *z3, *a3, *z4, *h, *y, *dy, *dh, *d3, *d2, *d1;
+    float* loss = nullptr;
+};
+
+using namespace glt;
+using namespace glt::nn;
+
+namespace {
+
+int nn_alloc(glt_nn* n)
+{
+    const int B = n->max_batch;
+    auto al = [](float** p, size_t count) {
+        return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(float));
+    };
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = al(&n->w, kParams);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&n->wbf), kParams * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = al(&n->g, kParams);
+    if (e == cudaSuccess) e = al(&n->m, kParams);
+    if (e == cudaSuccess) e = al(&n->v, kParams);
+    if (e == cudaSuccess) e = al(&n->z1, (size_t)B * 16 * 15 * 20);
+    if (e == cudaSuccess) e = al(&n->a1, (size_t)B * 16 * 15 * 20);
+    if (e == cudaSuccess) e = al(&n->z2, (size_t)B * 32 * 8 * 10);
+    if (e == cudaSuccess) e = al(&n->a2, (size_t)B * 32 * 8 * 10);
+    if (e == cudaSuccess) e = al(&n->z3, (size_t)B * kFlat);
+    if (e == cudaSuccess) e = al(&n->a3, (size_t)B * kFlat);
+    if (e == cudaSuccess) e = al(&n->z4, (size_t)B * kHid);
+    if (e == cudaSuccess) e = al(&n->h, (size_t)B * kHid);
+    if (e == cudaSuccess) e = al(&n->y, (size_t)B * kOut);
+    if (e == cudaSuccess) e = al(&n->dy, (size_t)B * kOut);
+    if (e == cudaSuccess) e = al(&n->dh, (size_t)B * kHid);
+    if (e == cudaSuccess) e = al(&n->d3, (size_t)B * kFlat);
+    if (e == cudaSuccess) e = al(&n->d2, (size_t)B * 32 * 8 * 10);
+    if (e == cudaSuccess) e = al(&n->d1, (size_t)B * 16 * 15 * 20);
+    if (e == cudaSuccess) e = al(&n->loss, 1);
+    if (e == cudaSuccess) e = cudaMemset(n->m, 0, kParams * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(n->v, 0, kParams * sizeof(float));
+    return e == cudaSuccess ? GLT_OK : cuda_fail(e, "proposal network allocation");
+}
+
+void nn_free(glt_nn* n)
+{
+    if (!n) return;
+    for (float* p : {n->w, n->g, n->m, n->v, n->z1, n->a1, n->z2, n->a2, n->z3, n->a3, n->z4, n->h,
+                     n->y, n->dy, n->dh, n->d3, n->d2, n->d1, n->loss})
+        cudaFree(p);
+    cudaFree(n->wbf);
+    delete n;
+}
+
+int grid_for(int n, int t) { return (n + t - 1) / t; }
+
+}  // namespace
+
+cudaError_t glt::nn_forward(glt_nn* n, const float* x, const float* mo, int B, cudaStream_t s)
+{
+    conv_fwd<<<grid_for(B * 16 * 15 * 20, 128), 128, 0, s>>>(x, n->wbf, kC1.w, kC1.b, B, 1, 30, 40, 16, n->z1, n->a1);
+    conv_fwd<<<grid_for(B * 32 * 8 * 10, 128), 128, 0, s>>>(n->a1, n->wbf, kC2.w, kC2.b, B, 16, 15, 20, 32, n->z2, n->a2);
+    conv_fwd<<<grid_for(B * kFlat, 128), 128, 0, s>>>(n->a2, n->wbf, kC3.w, kC3.b, B, 32, 8, 10, 64, n->z3, n->a3);
+    fc_fwd<<<grid_for(B * kHid * 32, 256), 256, 0, s>>>(n->a3, kFlat, mo, kMotion, n->wbf, kF1.w, kF1.b, B, kHid, n->z4, n->h, 1);
+    fc_fwd<<<grid_for(B * kOut * 32, 256), 256, 0, s>>>(n->h, kHid, nullptr, 0, n->wbf, kF2.w, kF2.b, B, kOut, n->y, n->y, 0);
+    return cudaGetLastError();
+}
+
+namespace {
+
+cudaError_t nn_backward(glt_nn* n, const float* x, const float* mo, const float* t, int B, cudaStream_t s)
+{
+    loss_grad<<<1, 256, 0, s>>>(n->y, t, B, n->dy, n->loss);
+    fc_bwd_w<<<grid_for(kOut * kHid + kOut, 256), 256, 0, s>>>(n->dy, n->h, kHid, nullptr, 0, B, kOut, n->g, kF2.w, kF2.b);
+    fc_bwd_in<<<grid_for(B * kHid, 256), 256, 0, s>>>(n->dy, n->wbf, kF2.w, kHid, B, kOut, kHid, n->z4, n->dh);
+    fc_bwd_w<<<grid_for(kHid * kF + kHid, 256), 256, 0, s>>>(n->dh, n->a3, kFlat, mo, kMotion, B, kHid, n->g, kF1.w, kF1.b);
+    fc_bwd_in<<<grid_for(B * kFlat, 256), 256, 0, s>>>(n->dh, n->wbf, kF1.w, kF, B, kHid, kFlat, n->z3, n->d3);
+    conv_bwd_w<<<64 * 32 * 9 + 64, 128, 0, s>>>(n->d3, n->a2, B, 32, 8, 10, 64, n->g, kC3.w, kC3.b);
+    conv_bwd_in<<<grid_for(B * 32 * 8 * 10, 128), 128, 0, s>>>(n->d3, n->wbf, kC3.w, B, 32, 8, 10, 64, n->z2, n->d2);
+    conv_bwd_w<<<32 * 16 * 9 + 32, 128, 0, s>>>(n->d2, n->a1, B, 16, 15, 20, 32, n->g, kC2.w, kC2.b);
+    conv_bwd_in<<<grid_for(B * 16 * 15 * 20, 128), 128, 0, s>>>(n->d2, n->wbf, kC2.w, B, 16, 15, 20, 32, n->z1, n->d1);
+    conv_bwd_w<<<16 * 1 * 9 + 16, 128, 0, s>>>(n->d1, x, B, 1, 30, 40, 16, n->g, kC1.w, kC1.b);
+    return cudaGetLastError();
+}
+
+int check_batch(const glt_nn* n, int B)
+{
+    if (!n) return invalid_arg_msg("network is NULL");
+    if (B < 1 || B > n->max_batch) return invalid_arg_msg("batch size outside [1, max_batch]");
+    return GLT_OK;
+}
+
+}  // namespace
+
+int glt::invalid_arg_msg(const char* msg)
+{
+    set_error(msg);
+    return GLT_ERR_INVALID_ARG;
+}
+
+// ---------------------------------------------------------------------------
+// Proposal stage of the batched tracker
+// ---------------------------------------------------------------------------
+namespace glt {
+namespace nn {
+
+// network input: the coarsest-level residual image at identity warp,
+// (I_cur - I_ref) / 64, 30 x 40 per stream
+__global__ void residual_images(const PropJob* __restrict__ jobs, float* __restrict__ x, int S)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= S * kIn) return;
+    const int s = t / kIn, p = t % kIn;
+    const int r = p / 40, c = p % 40;
+    const PropJob J = jobs[s];
+    x[t] = ((float)J.cur[r * J.pitch + c] - (float)J.ref[r * J.pitch + c]) * (1.0f / 64.0f);
+}
+
+// one thread per stream: T <- T exp(d_xi), a += d_a, b += d_b, where the
+// increment is the network output scaled by (0.01 x 7, 1.0); FP64 exponential
+// (closed form, Taylor series below theta^2 = 0.01) and composition.
+__global__ void compose_init(const double* __restrict__ in, const float* __restrict__ y,
+                             double* __restrict__ out, int S)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const double* T = in + 14 * s;
+    double d[8];
+    for (int k = 0; k < 8; ++k) d[k] = (double)y[8 * s + k] * (k < 7 ? 0.01 : 1.0);
+    const double w0 = d[3], w1 = d[4], w2 = d[5];
+    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
+    double A, B, C;
+    if (th2 < 0.01) {
+        A = 1.0 + th2 * (-1.0 / 6.0 + th2 * (1.0 / 120.0 + th2 * (-1.0 / 5040.0 + th2 / 362880.0)));
+        B = 0.5 + th2 * (-1.0 / 24.0 + th2 * (1.0 / 720.0 + th2 * (-1.0 / 40320.0 + th2 / 3628800.0)));
+        C = 1.0 / 6.0 + th2 * (-1.0 / 120.0 + th2 * (1.0 / 5040.0 + th2 * (-1.0 / 362880.0 + th2 / 39916800.0)));
+    } else {
+        const double th = sqrt(th2);
+        const double sh = sin(0.5 * th);
+        A = sin(th) / th;
+        B = 2.0 * sh * sh / th2;
+        C = (th - sin(th)) / (th2 * th);
+    }
+    const double Wm[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
+    const double ww[3] = {w0, w1, w2};
+    double E[12];
+    for (int r = 0; r < 3; ++r) {
+        double tr = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const double W2 = ww[r] * ww[c] - (r == c ? th2 : 0.0);
+            const double I = r == c ? 1.0 : 0.0;
+            E[4 * r + c] = I + A * Wm[3 * r + c] + B * W2;
+            tr += (I + B * Wm[3 * r + c] + C * W2) * d[c];
+        }
+        E[4 * r + 3] = tr;
+    }
+    double* O = out + 14 * s;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 4; ++c) {
+            double v = c == 3 ? T[4 * r + 3] : 0.0;
+            for (int k = 0; k < 3; ++k) v += T[4 * r + k] * E[4 * k + c];
+            O[4 * r + c] = v;
+        }
+    O[12] = T[12] + d[6];
+    O[13] = T[13] + d[7];
+}
+
+}  // namespace nn
+
+cudaError_t launch_proposal(glt_batch* b, const double* init_dev, cudaStream_t s)
+{
+    const int S = b->S;
+    nn::residual_images<<<(S * nn::kIn + 255) / 256, 256, 0, s>>>(b->prop_jobs, b->prop_x, S);
+    cudaError_t e = nn_forward(b->nn, b->prop_x, b->motion_dev, S, s);
+    if (e != cudaSuccess) return e;
+    nn::compose_init<<<(S + 127) / 128, 128, 0, s>>>(init_dev, b->nn->y, b->prop_init, S);
+    return cudaGetLastError();
+}
+
+}  // namespace glt
+
+extern "C" {
+
+int glt_batch_set_proposal(glt_batch* b, glt_nn* n, const float* motion_dev)
+{
+    if (!b) return invalid_arg_msg("batch is NULL");
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    if (!n) {
+        b->nn = nullptr;
+        b->motion_dev = nullptr;
+        return GLT_OK;
+    }
+    if (!motion_dev) return invalid_arg_msg("motion_dev is NULL");
+    if (n->max_batch < b->S) return invalid_arg_msg("network max_batch is smaller than the batch");
+    std::vector<PropJob> jobs(b->S);
+    for (int i = 0; i < b->S; ++i) {
+        glt_tracker* t = b->trk[i];
+        const int l = t->L - 1;
+        if (t->W[l] != 40 || t->H[l] != 30)
+            return invalid_arg_msg("the proposal needs every stream's coarsest level to be 40 x 30");
+        jobs[i].ref = t->pyr[GLT_REF].base + t->pyr[GLT_REF].off[l];
+        jobs[i].cur = t->pyr[GLT_CUR].base + t->pyr[GLT_CUR].off[l];
+        jobs[i].pitch = t->pitch[l];
+    }
+    cudaError_t e = cudaSuccess;
+    if (!b->prop_jobs) {
+        e = cudaMalloc(reinterpret_cast<void**>(&b->prop_jobs), b->S * sizeof(PropJob));
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->prop_x), (size_t)b->S * kIn * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->prop_init), (size_t)b->S * 14 * sizeof(double));
+        if (e != cudaSuccess) return cuda_fail(e, "proposal buffers");
+    }
+    e = cudaMemcpy(b->prop_jobs, jobs.data(), b->S * sizeof(PropJob), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "proposal jobs");
+    b->nn = n;
+    b->motion_dev = motion_dev;
+    return GLT_OK;
+}
+
+int glt_nn_create(int max_batch, glt_nn** out)
+{
+    if (!out) return invalid_arg_msg("out is NULL");
+    *out = nullptr;
+    if (max_batch < 1 || max_batch > 65536) return invalid_arg_msg("max_batch must be in [1, 65536]");
+    glt_nn* n = new glt_nn();
+    n->max_batch = max_batch;
+    int rc = nn_alloc(n);
+    if (rc != GLT_OK) {
+        nn_free(n);
+        return rc;
+    }
+    *out = n;
+    return GLT_OK;
+}
+
+void glt_nn_destroy(glt_nn* n) { nn_free(n); }
+
+int glt_nn_set_params(glt_nn* n, const float* host, int count)
+{
+    if (!n || !host) return invalid_arg_msg("NULL argument");
+    if (count != kParams) return invalid_arg_msg("count must equal GLT_NN_PARAMS");
+    cudaError_t e = cudaMemcpy(n->w, host, kParams * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(n->m, 0, kParams * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(n->v, 0, kParams * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(e, "glt_nn_set_params");
+    to_bf16<<<grid_for(kParams, 256), 256>>>(n->w, n->wbf, kParams);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "glt_nn_set_params");
+    n->step = 0;
+    return GLT_OK;
+}
+
+int glt_nn_get_params(glt_nn* n, float* host, int count)
+{
+    if (!n || !host) return invalid_arg_msg("NULL argument");
+    if (count != kParams) return invalid_arg_msg("count must equal GLT_NN_PARAMS");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(host, n->w, kParams * sizeof(float), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? GLT_OK : cuda_fail(e, "glt_nn_get_params");
+}
+
+int glt_nn_forward(glt_nn* n, const float* x_dev, const float* m_dev, float* y_dev, int B, void* stream)
+{
+    int rc = check_batch(n, B);
+    if (rc != GLT_OK) return rc;
+    if (!x_dev || !m_dev || !y_dev) return invalid_arg_msg("NULL argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = nn_forward(n, x_dev, m_dev, B, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y_dev, n->y, (size_t)B * kOut * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? GLT_OK : cuda_fail(e, "glt_nn_forward");
+}
+
+int glt_nn_gradient(glt_nn* n, const float* x_dev, const float* m_dev, const float* t_dev, int B,
+                    float* grad_host, float* loss_host, void* stream)
+{
+    int rc = check_batch(n, B);
+    if (rc != GLT_OK) return rc;
+    if (!x_dev || !m_dev || !t_dev || !grad_host) return invalid_arg_msg("NULL argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = nn_forward(n, x_dev, m_dev, B, s);
+    if (e == cudaSuccess) e = nn_backward(n, x_dev, m_dev, t_dev, B, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(grad_host, n->g, kParams * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && loss_host) e = cudaMemcpyAsync(loss_host, n->loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? GLT_OK : cuda_fail(e, "glt_nn_gradient");
+}
+
+int glt_nn_train_step(glt_nn* n, const float* x_dev, const float* m_dev, const float* t_dev, int B,
+                      float lr, float* loss_dev, void* stream)
+{
+    int rc = check_batch(n, B);
+    if (rc != GLT_OK) return rc;
+    if (!x_dev || !m_dev || !t_dev) return invalid_arg_msg("NULL argument");
+    if (!(lr > 0.0f)) return invalid_arg_msg("lr must be > 0");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = nn_forward(n, x_dev, m_dev, B, s);
+    if (e == cudaSuccess) e = nn_backward(n, x_dev, m_dev, t_dev, B, s);
+    if (e != cudaSuccess) return cuda_fail(e, "glt_nn_train_step");
+    n->step += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    const float c1 = (float)(1.0 / (1.0 - std::pow(b1, n->step)));
+    const float c2 = (float)(1.0 / (1.0 - std::pow(b2, n->step)));
+    adam<<<grid_for(kParams, 256), 256, 0, s>>>(n->w, n->wbf, n->g, n->m, n->v, kParams, lr, (float)b1,
+                                                (float)b2, 1e-8f, c1, c2);
+    if (loss_dev) e = cudaMemcpyAsync(loss_dev, n->loss, sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? GLT_OK : cuda_fail(e, "glt_nn_train_step");
+}
+
+}  // extern "C"

@@ -1,0 +1,223 @@
+"""Learned initial-pose proposal: the hand-written forward, backward and Adam
+kernels against the FP64 oracle network (oracle/nn.py) evaluated with the same
+BF16-rounded weights, training on the GPU, and the proposal stage of the
+batched tracker against an FP64 composition of the oracle network's output.
+
+Tolerances: outputs within 1e-4 (relative to max(1, |y|)); per-layer gradient
+norms within 1e-3 relative (FP32 sums over up to 1286 products and 256 batch
+rows against FP64); one Adam update within 1e-3 of the learning rate."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def glt():
+    import paper_2607_16897_gb300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def onn():
+    from oracle import nn
+    return nn
+
+
+def make_params(onn, seed):
+    rng = np.random.default_rng(seed)
+    p = onn.init_params(seed)
+    for name, shape in onn.SHAPES:
+        if name.endswith(".b"):
+            p[name] = rng.normal(0.0, 0.05, size=shape)
+    return onn.flatten(p).astype(np.float32)
+
+
+def make_inputs(B, seed):
+    rng = np.random.default_rng(seed)
+    # residual images: integer gray differences / 64, as the proposal stage forms them
+    x = (rng.integers(-48, 49, size=(B, 1200)) / 64.0).astype(np.float32)
+    m = rng.normal(size=(B, 6)).astype(np.float32)
+    t = rng.normal(size=(B, 8)).astype(np.float32)
+    return x, m, t
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("B", [1, 7, 256])
+def test_forward_matches_oracle(glt, onn, B):
+    import torch
+    w = make_params(onn, 3)
+    x, m, _ = make_inputs(B, 10 + B)
+    net = glt.NN(256, w)
+    y = torch.zeros(B, 8, device="cuda")
+    net.forward(dev(x), dev(m), y, B)
+    torch.cuda.synchronize()
+    yo, _ = onn.forward(onn.unflatten(onn.to_bf16(w)), x.reshape(B, 1, 30, 40), m)
+    err = np.abs(y.cpu().numpy() - yo).max()
+    assert err <= 1e-4 * max(1.0, np.abs(yo).max()), err
+    net.close()
+
+
+def test_gradient_matches_oracle(glt, onn):
+    B = 64
+    w = make_params(onn, 5)
+    x, m, t = make_inputs(B, 21)
+    net = glt.NN(B, w)
+    g, loss = net.gradient(dev(x), dev(m), dev(t), B)
+    p = onn.unflatten(onn.to_bf16(w))
+    y, cache = onn.forward(p, x.reshape(B, 1, 30, 40), m)
+    go, _, _ = onn.backward(p, cache, y, t)
+    assert abs(loss - onn.loss(y, t)) <= 1e-5 * onn.loss(y, t)
+    gg = onn.unflatten(g.astype(np.float64))
+    for name, _ in onn.SHAPES:
+        ref = np.linalg.norm(go[name])
+        assert ref > 0, name
+        rel = np.linalg.norm(gg[name] - go[name]) / ref
+        assert rel <= 1e-3, (name, rel)
+    # a plausible slip (one layer's gradient transposed or dropped) is far outside
+    assert np.linalg.norm(gg["fc2.b"] - go["fc2.b"]) < 0.1 * np.linalg.norm(go["fc2.b"])
+    net.close()
+
+
+def test_gradient_is_deterministic(glt, onn):
+    B = 256
+    w = make_params(onn, 6)
+    x, m, t = make_inputs(B, 22)
+    net = glt.NN(B, w)
+    g1, l1 = net.gradient(dev(x), dev(m), dev(t), B)
+    g2, l2 = net.gradient(dev(x), dev(m), dev(t), B)
+    assert np.array_equal(g1, g2) and l1 == l2
+    net.close()
+
+
+def test_adam_steps_match_oracle(glt, onn):
+    """Two Adam steps on the GPU against the oracle's Adam fed the GPU
+    gradients (which the gradient test pins separately)."""
+    import torch
+    B, lr = 32, 1e-3
+    w0 = make_params(onn, 7)
+    x, m, t = make_inputs(B, 23)
+    xd, md, td = dev(x), dev(m), dev(t)
+    net = glt.NN(B, w0)
+    g0, _ = net.gradient(xd, md, td, B)
+    loss = torch.zeros(1, device="cuda")
+    net.train_step(xd, md, td, B, lr, loss)
+    g1, _ = net.gradient(xd, md, td, B)
+    net.train_step(xd, md, td, B, lr, loss)
+    w2 = net.get_params()
+    p = onn.unflatten(w0.astype(np.float64))
+    state = {}
+    p = onn.adam_step(p, onn.unflatten(g0.astype(np.float64)), state, lr=lr)
+    p = onn.adam_step(p, onn.unflatten(g1.astype(np.float64)), state, lr=lr)
+    ref = onn.flatten(p)
+    moved = np.abs(ref - w0) > 0.5 * lr
+    assert moved.mean() > 0.3          # Adam moves most weights by about lr per step
+    err = np.abs(w2.astype(np.float64) - ref).max()
+    assert err <= 1e-3 * lr, err
+    net.close()
+
+
+def test_training_reduces_loss(glt, onn):
+    """Regression onto a fixed random teacher network: 300 Adam steps on the
+    GPU cut the loss by more than half."""
+    import torch
+    B = 256
+    x, m, _ = make_inputs(B, 24)
+    teacher = make_params(onn, 8)
+    yt, _ = onn.forward(onn.unflatten(onn.to_bf16(teacher)), x.reshape(B, 1, 30, 40), m)
+    yt = yt.astype(np.float32)
+    net = glt.NN(B, make_params(onn, 9))
+    xd, md, td = dev(x), dev(m), dev(yt)
+    losses = torch.zeros(300, device="cuda")
+    for k in range(300):
+        net.train_step(xd, md, td, B, 1e-3, losses[k:k + 1])
+    ls = losses.cpu().numpy()
+    assert np.all(np.isfinite(ls))
+    assert ls[-10:].mean() < 0.5 * ls[:3].mean(), (ls[:3], ls[-10:])
+    net.close()
+
+
+def test_nn_argument_errors(glt, onn):
+    import torch
+    net = glt.NN(4)
+    with pytest.raises(glt.GltError):
+        net.set_params(np.zeros(10, np.float32))
+    x = torch.zeros(8, 1200, device="cuda")
+    m = torch.zeros(8, 6, device="cuda")
+    y = torch.zeros(8, 8, device="cuda")
+    with pytest.raises(glt.GltError):
+        net.forward(x, m, y, 8)                # batch above max_batch
+    with pytest.raises(glt.GltError):
+        net.forward(x, m, y, 0)
+    with pytest.raises(glt.GltError):
+        glt.NN(0)
+    net.close()
+
+
+def test_proposal_stage_composes_network_output(glt, onn, orc, syn):
+    """With every level's iteration budget at zero the batched tracker returns
+    its initial state, so the output is the proposal itself:
+    T_init exp(0.01 y[0:6]), a + 0.01 y[6], b + y[7] with y the network on the
+    coarsest-level residual image (cur - ref) / 64 and the stream's motion."""
+    import torch
+    specs = [(640, 480, 525.0, 5), (320, 240, 256.0, 4), (640, 480, 600.0, 5)]
+    w = make_params(onn, 11)
+    net = glt.NN(8, w)
+    trks, curs, xs, inits = [], [], [], []
+    rng = np.random.default_rng(4)
+    for i, (W, H, f, L) in enumerate(specs):
+        cam = syn.camera_for(W, H, f)
+        seq = syn.sequence(700 + i, 6, cam, syn.ROOM_LARGE, 1.0, 45.0)
+        ref, uvd = syn.reference_points(seq, 0, 300, 0.5, 8.0)
+        cur, _ = seq.frame(4)
+        trk = glt.Tracker(W, H, cam.K, levels=L, max_points=300, max_iters=[0] * 8)
+        trk.build_pyramid(glt.GLT_REF, ref)
+        trk.set_map_points(uvd)
+        trks.append(trk)
+        curs.append(torch.from_numpy(cur).cuda())
+        xs.append((orc.pyramid(cur, L)[-1].astype(np.float64)
+                   - orc.pyramid(ref, L)[-1].astype(np.float64)) / 64.0)
+        T = syn.relative(seq.T_wc[0], seq.T_wc[3])
+        inits.append(np.concatenate([T.ravel(), rng.normal(0, 0.05, 1), rng.normal(0, 3, 1)]))
+    S = len(specs)
+    motion = rng.normal(size=(S, 6)).astype(np.float32)
+    batch = glt.Batch(trks)
+    md = dev(motion)
+    batch.set_proposal(net, md)
+    ptrs = torch.tensor([c.data_ptr() for c in curs], dtype=torch.int64).cuda()
+    init = torch.tensor(np.stack(inits), dtype=torch.float64).cuda()
+    out = torch.zeros(S * glt.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.Stream()
+    batch.capture(ptrs, init, out, st)
+    batch.replay(stream=st)
+    st.synchronize()
+    res = glt.parse_results(out)
+    y, _ = onn.forward(onn.unflatten(onn.to_bf16(w)), np.stack(xs)[:, None], motion)
+    for s in range(S):
+        d = y[s] * np.array([0.01] * 7 + [1.0])
+        Te = orc.se3_mul(inits[s][:12].reshape(3, 4), orc.se3_exp(d[:6]))
+        assert np.abs(res[s]["T"] - Te).max() <= 1e-6, s
+        assert abs(res[s]["a"] - (inits[s][12] + d[6])) <= 1e-6
+        assert abs(res[s]["b"] - (inits[s][13] + d[7])) <= 1e-4
+    # detaching restores the plain initial state
+    batch.set_proposal(None, None)
+    batch.build_pyramid(ptrs)
+    batch.track(init, out)
+    torch.cuda.synchronize()
+    for s, r in enumerate(glt.parse_results(out)):
+        assert np.abs(r["T"] - inits[s][:12].reshape(3, 4)).max() <= 1e-12
+    # a stream whose coarsest level is not 40 x 30 is refused
+    t2 = glt.Tracker(640, 480, syn.camera_for(640, 480, 525.0).K, levels=4, max_points=10)
+    b2 = glt.Batch([t2])
+    with pytest.raises(glt.GltError):
+        b2.set_proposal(net, md)
+    b2.close()
+    t2.close()
+    batch.close()
+    for t in trks:
+        t.close()
+    net.close()
