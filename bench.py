@@ -37,10 +37,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c4b"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c4b", "c5"],
                     help="c2: 640x480 single stream FP32 (default); c3: 64 streams of mixed "
                          "sizes, batched; c4: 1280x720 mixed precision single stream; c4b: "
-                         "64 streams of c4, batched")
+                         "64 streams of c4, batched; c5: 256 streams of 640x480 with the "
+                         "learned proposal, against the plain form on the same streams")
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="frames the oracle tracks for cpu_baseline (0 = auto, ~10-30 s)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -55,11 +56,13 @@ class Workload:
     """One camera stream: its frames, reference keyframes and map points."""
 
     def __init__(self, seed=1, frames=300, N=2000, W=640, H=480, f=525.0, L=4, speed=0.5,
-                 ang=30.0, label="C2 single stream"):
+                 ang=30.0, label="C2 single stream", render=True):
         import synth
         self.cam = synth.camera_for(W, H, f)
         self.seq = synth.sequence(seed, frames, self.cam, synth.ROOM_LARGE, speed, ang)
-        self.frames = [self.seq.frame(k)[0] for k in range(frames)]
+        self.job = (seed, frames, W, H, f)
+        self.speed, self.ang = speed, ang
+        self.frames = [self.seq.frame(k)[0] for k in range(frames)] if render else None
         self.N, self.L = N, L
         self.refs = {}
         self.name = (f"{label}: {W}x{H} uint8, fx=fy={f:g}, {frames}-frame sequence "
@@ -225,10 +228,12 @@ def fp32_peak_tflops(sm_mhz):
 # ---------------------------------------------------------------------------
 # oracle timing (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_track_sequence(wl, frames, inits=None):
+def oracle_track_sequence(wl, frames, inits=None, proposal=None, motions=None):
     """Tracks frames 1..frames with the FP64 oracle; returns (seconds spent in
-    pyramid+track, results, inits used).  inits: optional {k: (r, T_init)} to
-    replay exactly the GPU's initial states and references."""
+    pyramid+track, results, inits used).  inits: optional {k: (r, T_init, ab)}
+    to replay exactly the GPU's initial states and references.  proposal:
+    optional oracle network parameters (BF16-rounded, FP64) applied to each
+    initial state, with motions[k] the network's motion input."""
     import oracle
     K = wl.cam.K
     trk = oracle.OracleTracker(wl.cam.W, wl.cam.H, K, levels=wl.L)
@@ -236,6 +241,7 @@ def oracle_track_sequence(wl, frames, inits=None):
     t_track = 0.0
     out, used = {}, {}
     cur_ref = None
+    ref_coarse = None
     for k in range(1, frames + 1):
         if inits is not None:
             r, T_init, ab = inits[k]
@@ -245,9 +251,22 @@ def oracle_track_sequence(wl, frames, inits=None):
         if r != cur_ref:
             trk.build_pyramid(0, wl.frames[r])
             trk.set_map_points(wl.ref_points(r))
+            if proposal is not None:
+                ref_coarse = oracle.pyramid(wl.frames[r], wl.L)[-1].astype(np.float64)
             cur_ref = r
         t0 = time.perf_counter()
         trk.build_pyramid(1, wl.frames[k])
+        if proposal is not None:
+            from oracle import nn as onn
+            from paper_2607_16897_gb300.proposal import OUT_SCALE
+            from paper_2607_16897_gb300.proposal import motion_feature
+            mk = motions[k] if motions is not None else motion_feature(drv.Tw.get(k - 1),
+                                                                      drv.Tw.get(k - 2))
+            x = (oracle.pyramid(wl.frames[k], wl.L)[-1].astype(np.float64) - ref_coarse) / 64.0
+            y, _ = onn.forward(proposal, x[None, None], np.asarray(mk, np.float64)[None])
+            d = y[0] * OUT_SCALE
+            T_init = oracle.se3_mul(T_init, oracle.se3_exp(d[:6]))
+            ab = (ab[0] + d[6], ab[1] + d[7])
         res = trk.track_frame(T_init, ab)
         t_track += time.perf_counter() - t0
         out[k] = res
@@ -263,15 +282,23 @@ def run_reference(args):
     if rank != 0:
         return
     W, K = args.warmup, args.steps
-    if args.workload in ("c3", "c4b"):
+    if args.workload in ("c3", "c4b", "c5"):
         import concurrent.futures
-        wls = batch_workloads(args.workload, rank)
+        from paper_2607_16897_gb300 import proposal as prop
+        pool = prop.render_pool()
+        wls = batch_workloads(args.workload, rank, pool=pool)
+        pool.close()
+        pool.join()
+        pw = None
+        if args.workload == "c5":
+            from oracle import nn as onn
+            pw = onn.unflatten(onn.to_bf16(prop.load_weights()))
         F = len(wls[0].frames)
         n = min(F - 1, W + K)
         workers = os.cpu_count() or 1
         t0 = time.perf_counter()
         with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
-            list(ex.map(lambda w: oracle_track_sequence(w, n), wls))
+            list(ex.map(lambda w: oracle_track_sequence(w, n, proposal=pw), wls))
         t = time.perf_counter() - t0
         frames = n * len(wls)
         name = f"{args.workload.upper()} batched, {len(wls)} streams"
@@ -529,42 +556,70 @@ def single_workload(kind, rank=0):
     return Workload(seed=1 + rank)
 
 
-def batch_workloads(kind, rank=0, nstreams=64, frames=24):
+def batch_workloads(kind, rank=0, nstreams=None, frames=24, pool=None):
     """C3: 64 streams, sizes uniform over {320x240, 640x480, 752x480, 1280x720}
     (f = 0.8 W), N uniform in [300, 4000], L = 4.  C4b: 64 streams of the C4
-    configuration (1280x720, N = 8000, L = 5, 1 m/s, 60 deg/s)."""
+    configuration (1280x720, N = 8000, L = 5, 1 m/s, 60 deg/s).  C5: 256
+    streams of 640x480 (f = 525), N = 2000, L = 5 (40 x 30 coarsest level),
+    held-out seeds 5000..5255 with the proposal's training motion range (mean
+    speed 0.5-2 m/s, 30-90 deg/s per stream).  With a process pool the
+    frames and the references at multiples of 8 are rendered in parallel."""
+    from paper_2607_16897_gb300 import proposal as prop
     rng = np.random.default_rng(1000 + rank)
     sizes = [(320, 240), (640, 480), (752, 480), (1280, 720)]
+    nstreams = nstreams or (256 if kind == "c5" else 64)
     wls = []
     for s in range(nstreams):
         if kind == "c4b":
             wls.append(Workload(seed=2000 + s + 100000 * rank, frames=frames, N=8000, W=1280, H=720,
-                                f=1050.0, L=5, speed=1.0, ang=60.0, label="C4b stream"))
+                                f=1050.0, L=5, speed=1.0, ang=60.0, label="C4b stream",
+                                render=pool is None))
+        elif kind == "c5":
+            seed = prop.TEST_SEED0 + s + 100000 * rank
+            v, w = prop.stream_motion(seed)
+            wls.append(Workload(seed=seed, frames=frames, N=2000, W=640, H=480, f=525.0, L=5,
+                                speed=v, ang=w, label="C5 stream", render=pool is None))
         else:
             W, H = sizes[int(rng.integers(4))]
             N = int(rng.integers(300, 4001))
             wls.append(Workload(seed=1000 + s + 100000 * rank, frames=frames, N=N, W=W, H=H,
-                                f=0.8 * W, L=4, label="C3 stream"))
+                                f=0.8 * W, L=4, label="C3 stream", render=pool is None))
+    if pool is not None:
+        jobs = [w.job + (k, 0, w.speed, w.ang) for w in wls for k in range(frames)]
+        imgs = pool.map(prop._render_job, jobs, chunksize=8)
+        for i, w in enumerate(wls):
+            w.frames = [imgs[i * frames + k][0] for k in range(frames)]
+        refs = [(i, r) for i in range(len(wls)) for r in range(0, frames - 1, 8)]
+        pts = pool.map(prop._render_job, [wls[i].job + (r, wls[i].N, wls[i].speed, wls[i].ang)
+                                          for i, r in refs], chunksize=4)
+        for (i, r), (_, uvd) in zip(refs, pts):
+            wls[i].refs[r] = uvd
     return wls
 
 
 def run_batch(args):
     """Batched form: every stream's next frame tracked by one graph replay
-    (pyramids of all streams + one persistent track launch)."""
+    (pyramids of all streams + one persistent track launch).  C5 runs the same
+    streams twice, plain and with the learned proposal stage in the graph."""
     import torch
     import paper_2607_16897_gb300 as glt
+    from paper_2607_16897_gb300 import proposal as prop
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    pool = prop.render_pool()          # spawned before the first CUDA call
+    wls = batch_workloads(args.workload, rank, pool=pool)
+    pool.close()
+    pool.join()
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    wls = batch_workloads(args.workload, rank)
     precision = "mixed" if args.workload == "c4b" else "fp32"
+    use_prop = args.workload == "c5"
     S = len(wls)
     F = len(wls[0].frames)
     stream = torch.cuda.Stream()
@@ -579,9 +634,12 @@ def run_batch(args):
     ptr_pin = torch.zeros(S, dtype=torch.int64).pin_memory()
     init_dev = torch.zeros((S, 14), dtype=torch.float64, device=dev)
     init_pin = torch.zeros((S, 14), dtype=torch.float64).pin_memory()
+    motion_dev = torch.zeros((S, 6), dtype=torch.float32, device=dev)
+    motion_pin = torch.zeros((S, 6), dtype=torch.float32).pin_memory()
     out_dev = torch.zeros(S * glt.RESULT_BYTES, dtype=torch.uint8, device=dev)
     out_pin = torch.zeros(S * glt.RESULT_BYTES, dtype=torch.uint8).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    net = glt.NN(S, prop.load_weights()) if use_prop else None
     uvd_dev = {}
 
     def refresh(s, r, host=False):
@@ -596,17 +654,21 @@ def run_batch(args):
             t.build_pyramid(glt.GLT_REF, frames_dev[s][r], stream=sh)
             t.set_map_points(uvd_dev[key], stream=sh)
 
-    # every stream starts on its frame 0 as reference
     drvs = [SequenceDriver(w) for w in wls]
-    for s in range(S):
-        drvs[s].refresh(0)
-        refresh(s, 0)
-    torch.cuda.synchronize()
+
+    def restart(host=False):
+        for d in drvs:
+            d.__init__(d.wl)
+        for s in range(S):
+            drvs[s].refresh(0)
+            refresh(s, 0, host=host)
 
     def prepare(k, use_slots):
         for s in range(S):
-            T_init, ab = drvs[s].init_for(k), drvs[s].ab_init()
+            d = drvs[s]
+            T_init, ab = d.init_for(k), d.ab_init()
             init_pin[s] = torch.from_numpy(np.concatenate([T_init.ravel(), list(ab)]))
+            motion_pin[s] = torch.from_numpy(prop.motion_feature(d.Tw.get(k - 1), d.Tw.get(k - 2)))
             ptr_pin[s] = slots[s].data_ptr() if use_slots else frames_dev[s][k].data_ptr()
 
     def finish(k, record, refresh_host=False):
@@ -614,29 +676,16 @@ def run_batch(args):
         n_ref = 0
         for s in range(S):
             if record is not None:
-                record.append((s, k, drvs[s].r, init_pin[s].numpy().copy(), res[s]))
+                record.append((s, k, drvs[s].r, init_pin[s].numpy().copy(), res[s],
+                               motion_pin[s].numpy().copy()))
             drvs[s].record(k, res[s])
             if k + 1 < F and drvs[s].refresh(k):
                 refresh(s, k, host=refresh_host)
                 n_ref += 1
         return res, n_ref
 
-    # autotune the tile shape on frame 1, then capture the step
-    prepare(1, False)
-    with torch.cuda.stream(stream):
-        ptr_dev.copy_(ptr_pin, non_blocking=True)
-        init_dev.copy_(init_pin, non_blocking=True)
-        batch.build_pyramid(ptr_dev, stream=sh)
-    stream.synchronize()
-    shape = batch.autotune(init_dev, out_dev, reps=3, stream=sh)
-    batch.capture(ptr_dev, init_dev, out_dev, stream)
-
     def run_steps(nsteps, timed, record, e2e=False):
-        for d in drvs:
-            d.__init__(d.wl)
-        for s in range(S):
-            drvs[s].refresh(0)
-            refresh(s, 0, host=e2e)
+        restart(host=e2e)
         stream.synchronize()
         k = 0
         dev_ms, n_ref_total = [], 0
@@ -645,22 +694,19 @@ def run_batch(args):
             k += 1
             if k >= F:
                 k = 1
-                for d in drvs:
-                    d.__init__(d.wl)
-                for s in range(S):
-                    drvs[s].refresh(0)
-                    refresh(s, 0, host=e2e)
+                restart(host=e2e)
             prepare(k, e2e)
             with torch.cuda.stream(stream):
                 if e2e:
                     for s in range(S):
                         slots[s].copy_(frames_pin[s][k], non_blocking=True)
                         h2d += slots[s].numel()
-                    h2d += init_pin.numel() * 8
+                    h2d += init_pin.numel() * 8 + (motion_pin.numel() * 4 if use_prop else 0)
                 else:
                     flush.zero_()
                 ptr_dev.copy_(ptr_pin, non_blocking=True)
                 init_dev.copy_(init_pin, non_blocking=True)
+                motion_dev.copy_(motion_pin, non_blocking=True)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -675,25 +721,53 @@ def run_batch(args):
             n_ref_total += nr
         return dev_ms, n_ref_total, h2d, d2h
 
-    run_steps(max(args.warmup, 3), False, None)
-    if dist:
-        dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    torch.cuda.synchronize()
-    rec = []
-    t0 = time.perf_counter()
-    dev_ms, n_ref, _, _ = run_steps(args.steps, True, rec)
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter() - t0
-    clk = clocks.stop()
-    dev_s = sum(dev_ms) / 1000.0
-    if dist:
-        t = torch.tensor([dev_s, t_wall], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s, t_wall = float(t[0]), float(t[1])
-    frames_done = world * S * args.steps
-    value = frames_done / dev_s
+    # every stream starts on its frame 0 as reference; autotune the tile shape
+    # on frame 1 (plain form)
+    restart()
+    prepare(1, False)
+    with torch.cuda.stream(stream):
+        ptr_dev.copy_(ptr_pin, non_blocking=True)
+        init_dev.copy_(init_pin, non_blocking=True)
+        batch.build_pyramid(ptr_dev, stream=sh)
+    stream.synchronize()
+    shape = batch.autotune(init_dev, out_dev, reps=3, stream=sh)
+
+    def measure(form):
+        """Captures the step graph of `form` ("plain" / "proposal") and times it."""
+        batch.set_proposal(net if form == "proposal" else None, motion_dev if form == "proposal" else None)
+        batch.capture(ptr_dev, init_dev, out_dev, stream)
+        run_steps(max(args.warmup, 3), False, None)
+        if dist:
+            dist.barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        torch.cuda.synchronize()
+        rec = []
+        t0 = time.perf_counter()
+        dev_ms, n_ref, _, _ = run_steps(args.steps, True, rec)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t0
+        clk = clocks.stop()
+        dev_s = sum(dev_ms) / 1000.0
+        if dist:
+            t = torch.tensor([dev_s, t_wall], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dev_s, t_wall = float(t[0]), float(t[1])
+        gt = [pose_error(wls[r[0]], r[1], r[2], r[4]["T"]) for r in rec]
+        acc = {"median_rot_deg": float(np.rad2deg(np.median([e[0] for e in gt]))),
+               "median_trans_mm": float(1000 * np.median([e[1] for e in gt])),
+               "p99_trans_mm": float(1000 * np.percentile([e[1] for e in gt], 99)),
+               "status_nonzero": int(sum(1 for r in rec if r[4]["status"])),
+               "rejected_frames": int(sum(d.rejected for d in drvs))}
+        return dict(dev_ms=dev_ms, dev_s=dev_s, t_wall=t_wall, clk=clk, rec=rec, n_ref=n_ref,
+                    value=world * S * args.steps / dev_s, accuracy=acc,
+                    iters_per_frame=float(np.mean([r[4]["iters_total"] for r in rec])),
+                    passes_per_frame=float(np.mean([r[4]["passes"] for r in rec])))
+
+    forms = ["plain", "proposal"] if use_prop else ["plain"]
+    runs = {f: measure(f) for f in forms}
+    head = runs[forms[-1]]
+    value, dev_s, dev_ms, rec = head["value"], head["dev_s"], head["dev_ms"], head["rec"]
     e2e = None
     if not args.no_e2e:
         torch.cuda.synchronize()
@@ -708,19 +782,27 @@ def run_batch(args):
                        "host buffers"}
     cpu = parity = None
     if rank == 0 and not args.no_cpu:
-        cpu, parity = batch_cpu_baseline(wls, rec)
+        pw = None
+        if use_prop:
+            from oracle import nn as onn
+            pw = onn.unflatten(onn.to_bf16(prop.load_weights()))
+        cpu, parity = batch_cpu_baseline(wls, rec, proposal=pw)
     # roofline of the persistent tracker (the graph's dominant kernel)
     samples = sum(r[4]["passes"] * 8 * wls[r[0]].N for r in rec) / args.steps
     achieved = FLOPS_PER_SAMPLE * samples / (dev_s / args.steps) / 1e12
     peaks, src = measured_peaks()
     peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
-    gt = [pose_error(wls[s], k, r, res["T"]) for (s, k, r, _, res) in rec]
-    accuracy = {"median_rot_deg": float(np.rad2deg(np.median([e[0] for e in gt]))),
-                "median_trans_mm": float(1000 * np.median([e[1] for e in gt])),
-                "p99_trans_mm": float(1000 * np.percentile([e[1] for e in gt], 99)),
-                "status_nonzero": int(sum(1 for r in rec if r[4]["status"]))}
     if rank == 0:
         L = max(w.L for w in wls)
+        if args.workload == "c4b":
+            desc = "1280x720, N=8000, L=5, 1 m/s, 60 deg/s"
+        elif use_prop:
+            desc = ("640x480 (f=525), N=2000, L=5, held-out seeds 5000-5255, mean speed 0.5-2 m/s "
+                    "and 30-90 deg/s per stream; learned proposal (3 conv + 2 fc, BF16 weights) "
+                    "in the graph ahead of the track launch")
+        else:
+            desc = "sizes uniform over 320x240/640x480/752x480/1280x720, N uniform 300-4000, L=4"
+        launches = L + 1 + (1 if precision == "mixed" else 0) + (7 if use_prop else 0)
         line = {"metric": "frames tracked/s", "value": value, "unit": "frames/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1000.0 * dev_s / args.steps, "higher_is_better": True,
@@ -728,11 +810,7 @@ def run_batch(args):
                 "dtype": "f16 storage / f32 math" if precision == "mixed" else "f32",
                 "data": "synthetic",
                 "config": {"workload": (f"{args.workload.upper()} batched: {S} streams in one graph "
-                                        f"replay (pyramids + one persistent track launch); "
-                                        + ("1280x720, N=8000, L=5, 1 m/s, 60 deg/s"
-                                           if args.workload == "c4b" else
-                                           "sizes uniform over 320x240/640x480/752x480/1280x720, "
-                                           "N uniform 300-4000, L=4")
+                                        f"replay (pyramids + one persistent track launch); " + desc
                                         + f", {F}-frame sequences, reference every 8 frames"),
                            "global_batch": world * S, "streams_per_gpu": S,
                            "parallelism": f"replicas x{world}",
@@ -741,36 +819,61 @@ def run_batch(args):
                            "l2": "flushed between steps (256 MB write, outside the step events)",
                            "timing": "sum of per-step CUDA-event times around the graph replay"},
                 "breakdown_ms": {"replay": statistics.mean(dev_ms),
-                                 "wall_per_step": 1000.0 * t_wall / args.steps},
+                                 "wall_per_step": 1000.0 * head["t_wall"] / args.steps},
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak, "traffic": None, "kernel": "track_kernel",
                              "peak_source": f"FP32 FMA peak from unit counts at "
                                             f"{peaks.get('sm_max_mhz', 2070.0):g} MHz ({src} clock)",
                              "samples_per_step": samples},
-                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": args.steps * (L + 1 + (1 if precision == "mixed" else 0))
-                                + n_ref * L,
-                "parity_vs_oracle": parity, "accuracy_vs_truth": accuracy}
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": head["clk"],
+                "gpu_launches": args.steps * launches + head["n_ref"] * L,
+                "parity_vs_oracle": parity, "accuracy_vs_truth": head["accuracy"],
+                "iters_per_frame": head["iters_per_frame"],
+                "passes_per_frame": head["passes_per_frame"]}
+        if use_prop:
+            pl = runs["plain"]
+            agree = []
+            for a, b in zip(pl["rec"], head["rec"]):
+                if a[:3] == b[:3]:
+                    dR = a[4]["T"][:, :3].T @ b[4]["T"][:, :3]
+                    agree.append((np.arccos(np.clip(0.5 * (np.trace(dR) - 1), -1, 1)),
+                                  np.linalg.norm(a[4]["T"][:, 3] - b[4]["T"][:, 3])))
+            line["plain_same_streams"] = {
+                "value": pl["value"], "unit": "frames/s", "ms_per_step": 1000.0 * pl["dev_s"] / args.steps,
+                "iters_per_frame": pl["iters_per_frame"], "passes_per_frame": pl["passes_per_frame"],
+                "accuracy_vs_truth": pl["accuracy"], "clocks": pl["clk"]}
+            line["proposal_gain"] = {
+                "iters_saved_per_frame": pl["iters_per_frame"] - head["iters_per_frame"],
+                "passes_saved_per_frame": pl["passes_per_frame"] - head["passes_per_frame"],
+                "speedup": value / pl["value"],
+                "frames_compared": len(agree),
+                "final_pose_agreement_with_plain": {
+                    "within_1e-5": int(sum(1 for a in agree if a[0] <= 1e-5 and a[1] <= 1e-5)),
+                    "median_rot_rad": float(np.median([a[0] for a in agree])) if agree else None,
+                    "median_trans_m": float(np.median([a[1] for a in agree])) if agree else None}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
 
 
-def batch_cpu_baseline(wls, rec, frames_per_stream=8):
+def batch_cpu_baseline(wls, rec, frames_per_stream=8, proposal=None):
     """The oracle on the first frames of every stream, one host thread per
-    stream over all cores, with the GPU run's initial states and references."""
+    stream over all cores, with the GPU run's initial states, references and
+    (with `proposal`, the oracle network's parameters) motion inputs."""
     import concurrent.futures
     S = len(wls)
     per = {}
-    for (s, k, r, init, res) in rec:
+    for (s, k, r, init, res, mot) in rec:
         if k <= frames_per_stream and (s, k) not in per:
-            per[(s, k)] = (r, init[:12].reshape(3, 4), (float(init[12]), float(init[13])), res)
+            per[(s, k)] = (r, init[:12].reshape(3, 4), (float(init[12]), float(init[13])), res, mot)
 
     def one(s):
         ks = [k for k in range(1, frames_per_stream + 1) if (s, k) in per]
         inits = {k: per[(s, k)][:3] for k in ks}
-        t, out, _ = oracle_track_sequence(wls[s], len(ks), inits=inits)
+        motions = {k: per[(s, k)][4] for k in ks}
+        t, out, _ = oracle_track_sequence(wls[s], len(ks), inits=inits, proposal=proposal,
+                                          motions=motions)
         diffs = []
         for k in ks:
             gr = per[(s, k)][3]
@@ -810,7 +913,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload in ("c3", "c4b"):
+    elif args.workload in ("c3", "c4b", "c5"):
         run_batch(args)
     else:
         run_ours(args)

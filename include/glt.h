@@ -84,7 +84,9 @@ typedef struct glt_config {
     double lambda0;             /* initial LM damping of diag(H) at each level start */
     double lambda_up;           /* damping factor after a rejected candidate */
     double lambda_down;         /* damping factor after an accepted candidate */
-    double eps_step;            /* stop a level once max |delta_xi| < eps_step */
+    double eps_step;            /* stop the finest level once max |delta_xi| < eps_step */
+    double eps_step_coarse;     /* ... and every coarser level once max |delta_xi| <
+                                   eps_step_coarse */
     double eps_cost;            /* ... or once a rejected candidate raised the cost by
                                    no more than eps_cost * cost */
     double accept_step;         /* candidates with max |delta_xi| < accept_step are taken
@@ -110,7 +112,8 @@ typedef struct glt_result {
 } glt_result;
 
 /* Fills `cfg` with the defaults: 4 levels, 10 iterations per level, Huber 9,
- * lambda0 1e-4 (x4 up, x0.5 down), eps_step 1e-6, eps_cost 0 (off),
+ * lambda0 1e-4 (x4 up, x0.5 down), eps_step 1e-6 (finest level),
+ * eps_step_coarse 3e-4 (coarser levels), eps_cost 0 (off),
  * accept_step 1e-3, min_valid 16, zmin 1e-3, FP32, automatic cluster/threads,
  * max_points 4096. */
 void glt_default_config(glt_config* cfg, int width, int height, double fx, double fy,

@@ -63,7 +63,8 @@ class _Config(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("max_iters", ctypes.c_int * 8),
                 ("huber_k", ctypes.c_double), ("lambda0", ctypes.c_double),
                 ("lambda_up", ctypes.c_double), ("lambda_down", ctypes.c_double),
-                ("eps_step", ctypes.c_double), ("eps_cost", ctypes.c_double),
+                ("eps_step", ctypes.c_double), ("eps_step_coarse", ctypes.c_double),
+                ("eps_cost", ctypes.c_double),
                 ("accept_step", ctypes.c_double), ("min_valid", ctypes.c_int),
                 ("zmin", ctypes.c_double)]
 
@@ -235,7 +236,7 @@ def linearize(img_l, K0, level, x_r, I0_l, valid_l, T, a, b, huber_k=9.0, zmin=1
 # configuration and tracking
 # --------------------------------------------------------------------------
 DEFAULT_CONFIG = dict(levels=4, max_iters=[10] * 8, huber_k=9.0, lambda0=1e-4, lambda_up=4.0,
-                      lambda_down=0.5, eps_step=1e-6, eps_cost=0.0, accept_step=1e-3,
+                      lambda_down=0.5, eps_step=1e-6, eps_step_coarse=3e-4, eps_cost=0.0, accept_step=1e-3,
                       min_valid=16, zmin=1e-3)
 
 
@@ -257,6 +258,7 @@ def _cconfig(c: dict) -> _Config:
     cc.lambda_up = float(c["lambda_up"])
     cc.lambda_down = float(c["lambda_down"])
     cc.eps_step = float(c["eps_step"])
+    cc.eps_step_coarse = float(c["eps_step_coarse"])
     cc.eps_cost = float(c["eps_cost"])
     cc.accept_step = float(c["accept_step"])
     cc.min_valid = int(c["min_valid"])

@@ -359,8 +359,8 @@ void orc_linearize(const double* img, int W, int H, orc_cam K0, int level, const
  * if its rotational/translational part is below accept_step (small steps are
  * Gauss-Newton steps, as in the paper; the safeguard only screens large
  * ones).  A level stops after max_iters candidates, once a step is
- * below eps_step, or when a rejected candidate raised the cost by no more
- * than eps_cost * cost.
+ * below eps_step (eps_step_coarse on the levels above the finest), or when a
+ * rejected candidate raised the cost by no more than eps_cost * cost.
  * ------------------------------------------------------------------------ */
 static int cholesky_solve8(const double A[64], const double g[8], double delta[8])
 {
@@ -493,7 +493,7 @@ void orc_track(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
             } else {
                 lambda *= cfg->lambda_up;
             }
-            if (m < cfg->eps_step || flat) break;
+            if (m < (l > 0 ? cfg->eps_step_coarse : cfg->eps_step) || flat) break;
         }
         out->iters[l] = it;
         out->iters_total += it;

@@ -39,6 +39,7 @@ typedef struct {
     double huber_k;
     double lambda0, lambda_up, lambda_down;
     double eps_step;
+    double eps_step_coarse;
     double eps_cost;
     double accept_step;
     int min_valid;

@@ -42,6 +42,7 @@ class glt_config(ctypes.Structure):
                 ("max_iters", ctypes.c_int * MAX_LEVELS), ("huber_k", ctypes.c_double),
                 ("lambda0", ctypes.c_double), ("lambda_up", ctypes.c_double),
                 ("lambda_down", ctypes.c_double), ("eps_step", ctypes.c_double),
+                ("eps_step_coarse", ctypes.c_double),
                 ("eps_cost", ctypes.c_double), ("accept_step", ctypes.c_double),
                 ("min_valid", ctypes.c_int),
                 ("zmin", ctypes.c_double), ("precision", ctypes.c_int), ("cluster", ctypes.c_int),

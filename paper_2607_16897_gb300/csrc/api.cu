@@ -96,8 +96,9 @@ static int check_config(const glt_config* c)
     if (!(c->huber_k > 0) || !std::isfinite(c->huber_k)) return invalid("huber_k must be > 0");
     if (!(c->lambda0 > 0) || !(c->lambda_up >= 1) || !(c->lambda_down > 0) || !(c->lambda_down <= 1))
         return invalid("LM damping factors out of range");
-    if (!(c->eps_step >= 0) || !(c->eps_cost >= 0) || !(c->accept_step >= 0))
-        return invalid("eps_step / eps_cost / accept_step must be >= 0");
+    if (!(c->eps_step >= 0) || !(c->eps_step_coarse >= 0) || !(c->eps_cost >= 0) ||
+        !(c->accept_step >= 0))
+        return invalid("eps_step / eps_step_coarse / eps_cost / accept_step must be >= 0");
     if (c->min_valid < 1) return invalid("min_valid must be >= 1");
     if (!(c->zmin > 0)) return invalid("zmin must be > 0");
     if (c->precision != GLT_FP32 && c->precision != GLT_MIXED) return invalid("unknown precision");
@@ -151,6 +152,7 @@ void glt_default_config(glt_config* c, int width, int height, double fx, double 
     c->lambda_up = 4.0;
     c->lambda_down = 0.5;
     c->eps_step = 1e-6;
+    c->eps_step_coarse = 3e-4;
     c->eps_cost = 0.0;
     c->accept_step = 1e-3;
     c->min_valid = 16;
@@ -258,6 +260,7 @@ int glt_create(const glt_config* cfg, glt_tracker** out)
     D.lambda_up = cfg->lambda_up;
     D.lambda_down = cfg->lambda_down;
     D.eps_step = cfg->eps_step;
+    D.eps_step_coarse = cfg->eps_step_coarse;
     D.eps_cost = cfg->eps_cost;
     D.accept_step = cfg->accept_step;
     D.trace_E = t->trace_E;

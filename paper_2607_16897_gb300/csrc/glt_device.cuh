@@ -48,7 +48,7 @@ struct StreamDesc {
     int max_iters[kMaxLevels];
     int min_valid;
     int max_trace;
-    double lambda0, lambda_up, lambda_down, eps_step, eps_cost, accept_step;
+    double lambda0, lambda_up, lambda_down, eps_step, eps_step_coarse, eps_cost, accept_step;
     double* trace_E;       // [max_trace] Huber energy of each pass, or null
     int* trace_n;          // [max_trace] valid samples of each pass
     int* trace_info;       // [max_trace] level * 4 + 2 * accepted + is_candidate
@@ -509,7 +509,8 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
         const bool flat = !accept && enough && (En - Ecn <= D.eps_cost * Ecn);
         lambda *= accept ? D.lambda_down : D.lambda_up;
         load_normal = accept;
-        if (it >= D.max_iters[level] || step_bits < abs_bits(D.eps_step) || flat)
+        if (it >= D.max_iters[level] ||
+            step_bits < abs_bits(level > 0 ? D.eps_step_coarse : D.eps_step) || flat)
             finish = true;
         else
             candidate = true;

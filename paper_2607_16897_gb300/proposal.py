@@ -119,21 +119,24 @@ def stream_motion(seed: int):
 _SEQ_CACHE = {}
 
 
-def _sequence(seed, frames, W, H, f):
+def _sequence(seed, frames, W, H, f, speed=None, ang=None):
     import synth
-    key = (seed, frames, W, H, f)
+    key = (seed, frames, W, H, f, speed, ang)
     if key not in _SEQ_CACHE:
-        speed, ang = stream_motion(seed)
+        if speed is None:
+            speed, ang = stream_motion(seed)
         cam = synth.camera_for(W, H, f)
         _SEQ_CACHE[key] = synth.sequence(seed, frames, cam, synth.ROOM_LARGE, speed, ang)
     return _SEQ_CACHE[key]
 
 
 def _render_job(job):
-    """(seed, frames, W, H, f, k, N) -> (frame k, map points if N > 0)."""
+    """(seed, frames, W, H, f, k, N[, speed, ang]) -> (frame k, map points if
+    N > 0); speed and ang default to ``stream_motion(seed)``."""
     import synth
-    seed, frames, W, H, f, k, N = job
-    seq = _sequence(seed, frames, W, H, f)
+    seed, frames, W, H, f, k, N = job[:7]
+    speed, ang = (job[7], job[8]) if len(job) > 7 else (None, None)
+    seq = _sequence(seed, frames, W, H, f, speed, ang)
     if N > 0:
         img, uvd = synth.reference_points(seq, k, N, 0.5, 8.0)
         return img, uvd
@@ -228,7 +231,8 @@ def generate(seeds, frames=224, W=640, H=480, f=525.0, N=2000, L=5, interval=8, 
                 dropped += 1
             Tw[i][k] = orthonormalised(pose_mul(T_conv, Tw[i][ref_k[i]]))
             ab[i] = ab_conv
-            Tw[i].pop(k - 3, None)
+            if k - 3 != ref_k[i]:
+                Tw[i].pop(k - 3, None)
         if log and (k % 32 == 1 or k == frames - 1):
             log(f"frame {k}/{frames}: {len(ts)} pairs, {dropped} dropped, {time.time() - t0:.0f} s")
     batch.close()

@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(lib_path):
 def test_binding_covers_header_and_layouts(lib_path):
     import paper_2607_16897_gb300 as glt
     assert set(glt.SIGNATURES) == set(declared_functions())
-    assert ctypes.sizeof(glt.glt_config) == 176
+    assert ctypes.sizeof(glt.glt_config) == 184
     assert ctypes.sizeof(glt.glt_result) == 168
     assert glt.RESULT_DTYPE.itemsize == glt.RESULT_BYTES
     c = glt.default_config(640, 480, (525, 525, 320, 240))

@@ -27,8 +27,10 @@ def pose_err(syn, T, Tt):
 
 
 def test_pure_affine_change_is_recovered_exactly(orc, syn):
+    # every level run to eps_step: the stop rule looks at the pose part of the
+    # step only, so a coarse-level stop can leave b some 1e-7 gray short
     p = syn.pair_c1(1, sigma=2.0)
-    tr = tracker_for(orc, p)
+    tr = tracker_for(orc, p, eps_step_coarse=1e-6)
     a, b = 0.05, 3.0
     cur = [np.exp(a) * lv.astype(np.float64) + b for lv in tr.pyr[0]]
     res = orc.track(cur, p.cam.K, tr.x_r, tr.I0, tr.valid, tr.cfg, I34, 0.0, 0.0)
@@ -199,3 +201,30 @@ def test_initial_rotation_is_reorthonormalised(orc, syn):
     G[:, :3] = np.stack([q0, q1, np.cross(q0, q1)])
     r2 = tr.track_frame(G)
     np.testing.assert_allclose(r["T"], r2["T"], atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [3, 8])
+def test_coarse_level_stop_rule_keeps_the_fixed_point(orc, syn, seed):
+    """Levels above the finest stop once a candidate step is below
+    eps_step_coarse (trace: every earlier candidate of such a level is at or
+    above it), and the final state equals the one of a schedule that runs
+    every level to eps_step: the coarse levels only have to bring the state
+    into the finest level's basin, where Gauss-Newton has one fixed point."""
+    p = syn.pair_c1(seed, sigma=2.0)
+    tracker = tracker_for(orc, p)
+    res = tracker.track_frame(I34)
+    eps_c = tracker.cfg["eps_step_coarse"]
+    assert eps_c > tracker.cfg["eps_step"]
+    tr = res["trace"]
+    for lvl in (2, 1):
+        steps = [e["step"] for e in tr if e["candidate"] and e["level"] == lvl]
+        assert steps and all(s >= eps_c for s in steps[:-1])
+        assert steps[-1] < eps_c or len(steps) == tracker.cfg["max_iters"][lvl]
+    fine = orc.OracleTracker(p.cam.W, p.cam.H, p.cam.K, levels=3, eps_step_coarse=1e-6)
+    fine.build_pyramid(0, p.ref)
+    fine.set_map_points(p.uvd)
+    fine.build_pyramid(1, p.cur)
+    ref = fine.track_frame(I34)
+    assert res["passes"] < ref["passes"]
+    assert np.linalg.norm(res["T"][:, 3] - ref["T"][:, 3]) < 1e-6
+    assert np.abs(res["T"][:, :3] - ref["T"][:, :3]).max() < 1e-6
