@@ -492,7 +492,6 @@ static void free_batch(glt_batch* b)
     cudaFree(b->jobs_dev);
     cudaFree(b->pack_dev);
     cudaFree(b->prop_jobs);
-    cudaFree(b->prop_x);
     cudaFree(b->prop_init);
     delete b;
 }

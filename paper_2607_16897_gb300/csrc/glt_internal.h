@@ -106,7 +106,6 @@ struct glt_batch {
     glt_nn* nn = nullptr;
     const float* motion_dev = nullptr;
     glt::PropJob* prop_jobs = nullptr;
-    float* prop_x = nullptr;
     double* prop_init = nullptr;
 };
 

@@ -175,7 +175,7 @@ def generate(seeds, frames=224, W=640, H=480, f=525.0, N=2000, L=5, interval=8, 
     ptrs = torch.tensor([c.data_ptr() for c in cur], dtype=torch.int64, device="cuda")
     init = torch.zeros((S, 14), dtype=torch.float64, device="cuda")
     out = torch.zeros(S * RESULT_BYTES, dtype=torch.uint8, device="cuda")
-    xs, ms, ts = [], [], []
+    xs, ms, ts, seq_of = [], [], [], []
     Tw = [dict() for _ in seeds]       # world->camera estimates per frame
     ab = [(0.0, 0.0)] * S
     ref_k = [0] * S
@@ -227,6 +227,7 @@ def generate(seeds, frames=224, W=640, H=480, f=525.0, N=2000, L=5, interval=8, 
                 xs.append(((coarse - ref_coarse[i]) / 64.0).ravel())
                 ms.append(mot[i])
                 ts.append(target(T_init[i], ab_init[i], T_conv, ab_conv))
+                seq_of.append(i)
             else:
                 dropped += 1
             Tw[i][k] = orthonormalised(pose_mul(T_conv, Tw[i][ref_k[i]]))
@@ -242,7 +243,8 @@ def generate(seeds, frames=224, W=640, H=480, f=525.0, N=2000, L=5, interval=8, 
         pool.close()
         pool.join()
     return dict(x=np.stack(xs).astype(np.float32), m=np.stack(ms).astype(np.float32),
-                t=np.stack(ts).astype(np.float32), dropped=dropped)
+                t=np.stack(ts).astype(np.float32), seq=np.array(seq_of, np.int32), S=S,
+                dropped=dropped)
 
 
 # ---------------------------------------------------------------------------
@@ -266,52 +268,160 @@ def init_params(seed=0) -> np.ndarray:
     return w
 
 
-def train(data, epochs=30, batch=256, lr=1e-3, val_frac=0.1, seed=0, log=print):
+def train(data, epochs=20, batch=256, lr=3e-4, val_frac=0.1, eval_every=50, seed=0, log=print):
     """Adam on the GPU with the library's training kernels; returns (params,
-    history).  The last `val_frac` of the pairs are held out for validation."""
+    summary).  The pairs of the last `val_frac` of the sequences are held out;
+    the parameters with the lowest held-out loss (evaluated every
+    `eval_every` steps) are returned."""
     import torch
     from . import NN
-    x, m, t = data["x"], data["m"], data["t"]
-    P = len(t)
-    nval = max(1, int(val_frac * P))
-    ntr = P - nval
-    xd = torch.from_numpy(x).cuda()
-    md = torch.from_numpy(m).cuda()
-    td = torch.from_numpy(t).cuda()
+    x, m, t, seq = data["x"], data["m"], data["t"], data["seq"]
+    cut = int(round((1.0 - val_frac) * data["S"]))
+    tr_idx = np.nonzero(seq < cut)[0]
+    va_idx = np.nonzero(seq >= cut)[0]
+    ntr, nval = len(tr_idx), len(va_idx)
+    xd = torch.from_numpy(x[tr_idx]).cuda()
+    md = torch.from_numpy(m[tr_idx]).cuda()
+    td = torch.from_numpy(t[tr_idx]).cuda()
+    xv = torch.from_numpy(x[va_idx]).cuda()
+    mv = torch.from_numpy(m[va_idx]).cuda()
+    tv = torch.from_numpy(t[va_idx]).cuda()
     net = NN(max(batch, nval), init_params(seed))
     rng = np.random.default_rng(seed)
     steps = ntr // batch
     loss_dev = torch.zeros(steps, device="cuda")
     yv = torch.zeros((nval, 8), device="cuda")
+    base = float(0.5 * np.mean(np.sum(t[va_idx] ** 2, axis=1)))
+
+    def val_loss():
+        net.forward(xv, mv, yv, nval)
+        torch.cuda.synchronize()
+        return float(0.5 * torch.mean(torch.sum((yv - tv) ** 2, dim=1)))
+
+    best, best_w, best_at = val_loss(), net.get_params(), 0
     hist = []
-    base = float(0.5 * np.mean(np.sum(t[ntr:] ** 2, axis=1)))
     for ep in range(epochs):
         perm = torch.from_numpy(rng.permutation(ntr)).cuda()
-        lr_ep = lr * (0.1 if ep >= int(0.8 * epochs) else 1.0)
         for s in range(steps):
             idx = perm[s * batch:(s + 1) * batch]
             net.train_step(xd[idx].contiguous(), md[idx].contiguous(), td[idx].contiguous(), batch,
-                           lr_ep, loss_dev[s:s + 1])
-        net.forward(xd[ntr:].contiguous(), md[ntr:].contiguous(), yv, nval)
-        torch.cuda.synchronize()
-        vl = float(0.5 * torch.mean(torch.sum((yv - td[ntr:]) ** 2, dim=1)))
+                           lr, loss_dev[s:s + 1])
+            if (s + 1) % eval_every == 0 or s == steps - 1:
+                vl = val_loss()
+                if vl < best:
+                    best, best_w, best_at = vl, net.get_params(), ep * steps + s + 1
         tl = float(loss_dev.mean())
         hist.append((tl, vl))
         if log:
-            log(f"epoch {ep}: train {tl:.4f} val {vl:.4f} (zero-proposal val {base:.4f})")
-    w = net.get_params()
+            log(f"epoch {ep}: train {tl:.4f} val {vl:.4f} best {best:.4f} at step {best_at} "
+                f"(zero proposal {base:.4f})")
     net.close()
-    return w, dict(history=hist, zero_val=base, pairs=P, val_pairs=nval)
+    return best_w, dict(history=hist, zero_val=base, best_val=best, best_step=best_at,
+                        train_pairs=ntr, val_pairs=nval, val_sequences=data["S"] - cut)
+
+
+def evaluate(weights, seeds, frames=16, W=640, H=480, f=525.0, N=2000, L=5, interval=8,
+             pool=None):
+    """Paired comparison on the given sequences: every frame is tracked from
+    the same constant-velocity start (the plain form's sequence driver) by the
+    plain tracker, by the tracker behind the proposal stage, and by the
+    proposal stage alone (no LM iterations), so the returned statistics isolate
+    what the proposal changes: the distance of its start from the converged
+    state against that of the constant-velocity start (|log(T0^-1 T)| of the
+    pose part, in units of 0.01), the linearisation passes, and the agreement
+    of the final poses."""
+    import torch
+    from . import GLT_REF, NN, Batch, Tracker, RESULT_BYTES, parse_results
+    import synth
+
+    seeds = list(seeds)
+    S = len(seeds)
+    own_pool = pool is None
+    if own_pool:
+        pool = render_pool()
+    cam = synth.camera_for(W, H, f)
+    seqs = [_sequence(s, frames, W, H, f) for s in seeds]
+    forms = {"plain": {}, "proposal": {}, "init": {"max_iters": [0] * 8}}
+    trk = {k: [Tracker(W, H, cam.K, levels=L, max_points=N, **kw) for _ in seeds]
+           for k, kw in forms.items()}
+    batches = {k: Batch(trk[k]) for k in forms}
+    net = NN(S, weights)
+    motion = torch.zeros((S, 6), dtype=torch.float32, device="cuda")
+    batches["proposal"].set_proposal(net, motion)
+    batches["init"].set_proposal(net, motion)
+    cur = [torch.empty((H, W), dtype=torch.uint8, device="cuda") for _ in seeds]
+    ptrs = torch.tensor([c.data_ptr() for c in cur], dtype=torch.int64, device="cuda")
+    init = torch.zeros((S, 14), dtype=torch.float64, device="cuda")
+    out = torch.zeros(S * RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    Tw = [dict() for _ in seeds]
+    ab = [(0.0, 0.0)] * S
+    ref_k = [0] * S
+    rows = []
+    for k in range(frames):
+        is_ref = k % interval == 0
+        rendered = pool.map(_render_job, [(s, frames, W, H, f, k, N if is_ref else 0) for s in seeds])
+        if is_ref:
+            for i, (img, uvd) in enumerate(rendered):
+                for form in forms:
+                    trk[form][i].build_pyramid(GLT_REF, img)
+                    trk[form][i].set_map_points(uvd)
+                ref_k[i] = k
+                Tw[i][k] = pose_inv(seqs[i].T_wc[k])
+                ab[i] = (0.0, 0.0)
+            continue
+        starts, mot = [], []
+        for i in range(S):
+            Tp, Tpp = Tw[i][k - 1], Tw[i].get(k - 2)
+            M = pose_mul(Tp, pose_inv(Tpp)) if Tpp is not None else np.hstack([np.eye(3), np.zeros((3, 1))])
+            starts.append(np.concatenate([pose_mul(pose_mul(M, Tp), pose_inv(Tw[i][ref_k[i]])).ravel(),
+                                          list(ab[i])]))
+            mot.append(motion_feature(Tp, Tpp))
+            cur[i].copy_(torch.from_numpy(rendered[i][0]))
+        init.copy_(torch.from_numpy(np.stack(starts)))
+        motion.copy_(torch.from_numpy(np.stack(mot)))
+        res = {}
+        for form in forms:
+            batches[form].build_pyramid(ptrs)
+            batches[form].track(init, out)
+            torch.cuda.synchronize()
+            res[form] = parse_results(out)
+        for i in range(S):
+            rp, rq, r0 = res["plain"][i], res["proposal"][i], res["init"][i]
+            T_conv = rp["T"]
+            e_cv = np.linalg.norm(se3_log(pose_mul(pose_inv(starts[i][:12].reshape(3, 4)), T_conv)))
+            e_nn = np.linalg.norm(se3_log(pose_mul(pose_inv(r0["T"]), T_conv)))
+            dR = rp["T"][:, :3].T @ rq["T"][:, :3]
+            ang = float(np.arccos(np.clip(0.5 * (np.trace(dR) - 1.0), -1.0, 1.0)))
+            rows.append((e_cv / 0.01, e_nn / 0.01, rp["passes"], rq["passes"], ang,
+                         float(np.linalg.norm(rp["T"][:, 3] - rq["T"][:, 3]))))
+            Tw[i][k] = orthonormalised(pose_mul(T_conv, Tw[i][ref_k[i]]))
+            ab[i] = (rp["a"], rp["b"])
+            if k - 3 != ref_k[i]:
+                Tw[i].pop(k - 3, None)
+    for form in forms:
+        batches[form].close()
+        for t in trk[form]:
+            t.close()
+    net.close()
+    if own_pool:
+        pool.close()
+        pool.join()
+    a = np.array(rows)
+    return dict(frames=len(a), cv_start_err=float(a[:, 0].mean()), proposal_start_err=float(a[:, 1].mean()),
+                proposal_closer=float((a[:, 1] < a[:, 0]).mean()),
+                passes_plain=float(a[:, 2].mean()), passes_proposal=float(a[:, 3].mean()),
+                agree_1e5=float(((a[:, 4] <= 1e-5) & (a[:, 5] <= 1e-5)).mean()),
+                max_rot_diff=float(a[:, 4].max()), max_trans_diff=float(a[:, 5].max()))
 
 
 def main(argv=None):
     import argparse
     import json
     ap = argparse.ArgumentParser(description="generate the proposal training set and train it")
-    ap.add_argument("--sequences", type=int, default=256)
-    ap.add_argument("--frames", type=int, default=224)
-    ap.add_argument("--epochs", type=int, default=30)
-    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--sequences", type=int, default=1024)
+    ap.add_argument("--frames", type=int, default=56)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--lr", type=float, default=3e-4)
     ap.add_argument("--out", default=WEIGHTS_PATH)
     ap.add_argument("--log", default=None, help="JSON summary file")
     a = ap.parse_args(argv)
