@@ -353,13 +353,77 @@ namespace nn {
 //   conv1 -> conv2 -> conv3 (ReLU) -> fc1 (ReLU) on [flatten, motion] -> fc2,
 //   then T' = T exp(0.01 y[0:6]), a' = a + 0.01 y[6], b' = b + y[7] in FP64.
 // Conv inputs are stored with a one-pixel zero border, so every 3x3 window is
-// read without bounds tests, and each thread produces KO output channels of
-// one output pixel (the window is loaded once per input channel).  The sum
-// order per output (bias, then channel, row, column) is that of conv_fwd.
-constexpr int kPropThreads = 256;
+// read without bounds tests.  conv1 gives each thread 4 output channels of one
+// pixel; conv2 and conv3 run as small GEMMs (output pixels x channels, K =
+// input channel x tap) with register tiles of PT pixels x 4 channels and the
+// layer's weights staged once per block in shared memory as BF16, transposed
+// to [K][O] so a tile's 4 weights are one 8-byte load.  The sum order per
+// output (bias, then channel, row, column) is that of conv_fwd.
+constexpr int kPropThreads = 512;
 constexpr int kXp = 32 * 42, kA1p = 16 * 17 * 22, kA2p = 32 * 10 * 12;
+constexpr int kW2 = 144 * 32, kW3 = 288 * 64;       // BF16 weights, [K][O]
 constexpr int kPropSmemFloats = kXp + kA1p + kA2p + (kF + 2) + kHid + kOut;
-constexpr size_t kPropSmemBytes = kPropSmemFloats * sizeof(float);
+constexpr size_t kPropSmemBytes = kPropSmemFloats * sizeof(float) + (kW2 + kW3) * sizeof(__nv_bfloat16);
+
+// GEMM form of a stride-2 3x3 conv on a zero-bordered input: thread t < tasks
+// computes PT consecutive output pixels (row-major) x 4 channels.
+template <int C, int H, int W, int O, int PT, bool PADOUT>
+__device__ __forceinline__ void conv_gemm(const float* __restrict__ in, const __nv_bfloat16* __restrict__ wt,
+                                          const __nv_bfloat16* __restrict__ w, int boff,
+                                          float* __restrict__ out)
+{
+    constexpr int Ho = (H + 1) / 2, Wo = (W + 1) / 2, Wp = W + 2, plane = (H + 2) * (W + 2);
+    constexpr int PG = Ho * Wo / PT, tasks = PG * (O / 4);
+    static_assert(Ho * Wo % PT == 0, "pixel tiles must cover the output");
+    const int t = threadIdx.x;
+    if (t >= tasks) return;
+    const int pg = t % PG, cg = t / PG;
+    int base[PT];
+#pragma unroll
+    for (int u = 0; u < PT; ++u) {
+        const int p = pg * PT + u;
+        base[u] = 2 * (p / Wo) * Wp + 2 * (p % Wo);
+    }
+    float acc[PT][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float b = __bfloat162float(__ldg(w + boff + cg * 4 + k));
+#pragma unroll
+        for (int u = 0; u < PT; ++u) acc[u][k] = b;
+    }
+    for (int c = 0; c < C; ++c) {
+        const float* xc = in + c * plane;
+        const __nv_bfloat16* wc = wt + (c * 9) * O + cg * 4;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const uint2 raw = *reinterpret_cast<const uint2*>(wc + q * O);
+            const float2 w01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.x));
+            const float2 w23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.y));
+            const int off = (q / 3) * Wp + (q % 3);
+#pragma unroll
+            for (int u = 0; u < PT; ++u) {
+                const float a = xc[base[u] + off];
+                acc[u][0] = fmaf(w01.x, a, acc[u][0]);
+                acc[u][1] = fmaf(w01.y, a, acc[u][1]);
+                acc[u][2] = fmaf(w23.x, a, acc[u][2]);
+                acc[u][3] = fmaf(w23.y, a, acc[u][3]);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < PT; ++u) {
+        const int p = pg * PT + u, i = p / Wo, j = p % Wo;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int o = cg * 4 + k;
+            const float r = fmaxf(acc[u][k], 0.0f);
+            if (PADOUT)
+                out[o * (Ho + 2) * (Wo + 2) + (i + 1) * (Wo + 2) + (j + 1)] = r;
+            else
+                out[(o * Ho + i) * Wo + j] = r;
+        }
+    }
+}
 
 __device__ __forceinline__ float2 wv2(const __nv_bfloat16* w, int i)
 {
@@ -418,9 +482,32 @@ proposal_kernel(const PropJob* __restrict__ jobs, const float* __restrict__ moti
     float* f = a2 + kA2p;
     float* h = f + (kF + 2);
     float* y = h + kHid;
+    __nv_bfloat16* w2t = reinterpret_cast<__nv_bfloat16*>(y + kOut);
+    __nv_bfloat16* w3t = w2t + kW2;
     const int s = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int q = tid; q < kXp + kA1p + kA2p; q += kPropThreads) sm[q] = 0.0f;
+    // conv2 / conv3 weights -> [K][O] (K = c * 9 + tap), read as 16-byte
+    // vectors (both layers start on a 16-byte boundary of the flat layout)
+    {
+        const uint4* g2 = reinterpret_cast<const uint4*>(w + kC2.w);
+        const uint4* g3 = reinterpret_cast<const uint4*>(w + kC3.w);
+        for (int v = tid; v < (kW2 + kW3) / 8; v += kPropThreads) {
+            const bool l2 = v < kW2 / 8;
+            const uint4 raw = __ldg(l2 ? g2 + v : g3 + (v - kW2 / 8));
+            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&raw);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (l2) {
+                    const int q = 8 * v + u;
+                    w2t[(q % 144) * 32 + q / 144] = e[u];
+                } else {
+                    const int q = 8 * (v - kW2 / 8) + u;
+                    w3t[(q % 288) * 64 + q / 288] = e[u];
+                }
+            }
+        }
+    }
     __syncthreads();
     const PropJob J = jobs[s];
     for (int p = tid; p < kIn; p += kPropThreads) {
@@ -432,13 +519,14 @@ proposal_kernel(const PropJob* __restrict__ jobs, const float* __restrict__ moti
     __syncthreads();
     conv_block<1, 30, 40, 16, 4, true>(xp, w, kC1.w, kC1.b, a1);
     __syncthreads();
-    conv_block<16, 15, 20, 32, 4, true>(a1, w, kC2.w, kC2.b, a2);
+    conv_gemm<16, 15, 20, 32, 4, true>(a1, w2t, w, kC2.b, a2);
     __syncthreads();
-    conv_block<32, 8, 10, 64, 2, false>(a2, w, kC3.w, kC3.b, f);
+    conv_gemm<32, 8, 10, 64, 2, false>(a2, w3t, w, kC3.b, f);
     __syncthreads();
     // fc1: each warp takes 4 output rows at a time, BF16 pairs along the rows
     for (int o0 = warp * 4; o0 < kHid; o0 += 4 * (kPropThreads / 32)) {
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 4
         for (int i = 2 * lane; i < kF; i += 64) {
             const float f0 = f[i], f1 = f[i + 1];
 #pragma unroll
