@@ -313,6 +313,18 @@ int glt_build_pyramid(glt_tracker* t, int slot, const uint8_t* img, int pitch_by
     if (pitch_bytes < t->cfg.width) return invalid("pitch_bytes < width");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Pyramid& P = t->pyr[slot];
+    if (is_device && t->L > 1) {
+        // level 1 straight from the caller's frame; its tiles write level 0
+        for (int l = 1; l < t->L; ++l)
+            GLT_CHECK(launch_pyr_down(t->jobs_dev + slot * GLT_MAX_LEVELS + (l - 1), 1,
+                                      pyr_tiles_x(t->W[l]), pyr_tiles_y(t->H[l]), s, nullptr,
+                                      l == 1 ? img : nullptr, l == 1 ? pitch_bytes : 0),
+                      "pyramid kernel");
+        if (slot == GLT_CUR && t->packed)
+            GLT_CHECK(launch_pack(t->pack_dev, t->L, t->W[0] * t->H[0], s), "pack kernel");
+        P.built = true;
+        return GLT_OK;
+    }
     GLT_CHECK(cudaMemcpy2DAsync(P.base + P.off[0], (size_t)t->pitch[0], img, (size_t)pitch_bytes,
                                 (size_t)t->W[0], (size_t)t->H[0],
                                 is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
@@ -600,10 +612,15 @@ static int batch_pyramid(glt_batch* b, const uint8_t* const* frames_dev, cudaStr
             maxh[l] = std::max(maxh[l], t->H[l]);
         }
     }
-    GLT_CHECK(launch_copy_frames(frames_dev, b->copy_dev, b->S, maxbytes, s), "batch copy kernel");
+    // level 1 reads the frames and writes level 0; streams with one level
+    // only need the copy
+    bool single_level = false;
+    for (glt_tracker* t : b->trk) single_level |= t->L == 1;
+    if (single_level || b->Lmax == 1)
+        GLT_CHECK(launch_copy_frames(frames_dev, b->copy_dev, b->S, maxbytes, s), "batch copy kernel");
     for (int l = 1; l < b->Lmax; ++l)
         GLT_CHECK(launch_pyr_down(b->jobs_dev + (size_t)(l - 1) * b->S, b->S, pyr_tiles_x(maxw[l]),
-                                  pyr_tiles_y(maxh[l]), s),
+                                  pyr_tiles_y(maxh[l]), s, (l == 1 && !single_level) ? frames_dev : nullptr),
                   "batch pyramid kernel");
     if (b->precision == GLT_MIXED)
         GLT_CHECK(launch_pack(b->pack_dev, b->Lmax * b->S, maxpix, s), "batch pack kernel");

@@ -119,7 +119,8 @@ int cuda_fail(cudaError_t e, const char* what);
 
 // pyramid.cu
 cudaError_t launch_pyr_down(const PyrJob* jobs_dev, int njobs, int tiles_x, int tiles_y,
-                            cudaStream_t s);
+                            cudaStream_t s, const uint8_t* const* frames = nullptr,
+                            const uint8_t* src = nullptr, int sp = 0);
 cudaError_t launch_copy_frames(const uint8_t* const* frames, const CopyJob* jobs, int njobs,
                                int max_bytes, cudaStream_t s);
 cudaError_t launch_pack(const PackJob* jobs, int njobs, int max_pixels, cudaStream_t s);

@@ -8,7 +8,8 @@
 // 4-byte loads, runs the vertical pass into a 16-bit buffer and the horizontal
 // pass, and stores 4 output bytes per thread.
 // Jobs (one per stream) index blockIdx.z, so a whole batch of streams builds a
-// level in one launch.
+// level in one launch.  Level 1 reads the caller's frame and writes the
+// level-0 copy from its staged windows, so a frame is read from HBM once.
 #include "glt_internal.h"
 
 namespace glt {
@@ -24,35 +25,90 @@ constexpr int PYR_THREADS = 256;
 int pyr_tiles_x(int dW) { return (dW + TW - 1) / TW; }
 int pyr_tiles_y(int dH) { return (dH + TH - 1) / TH; }
 
-__global__ void __launch_bounds__(PYR_THREADS) pyr_down_kernel(const PyrJob* __restrict__ jobs)
+// One 64 x 16 output tile of J's level.  COHERENT selects L2 loads
+// (ld.global.cg) for a source level written earlier in the same launch; a
+// source that is read-only for the launch goes through the read-only cache.
+template <bool COHERENT>
+__device__ __forceinline__ uint32_t ld_word(const uint8_t* p)
 {
-    __shared__ uint8_t in[IH][IW];
-    __shared__ uint16_t vs[TH][IW];
-    const PyrJob J = jobs[blockIdx.z];
-    const int ox0 = blockIdx.x * TW, oy0 = blockIdx.y * TH;
-    if (ox0 >= J.dW || oy0 >= J.dH) return;
+    return COHERENT ? __ldcg(reinterpret_cast<const unsigned int*>(p))
+                    : __ldg(reinterpret_cast<const unsigned int*>(p));
+}
+template <bool COHERENT>
+__device__ __forceinline__ uint8_t ld_byte(const uint8_t* p)
+{
+    return COHERENT ? __ldcg(p) : __ldg(p);
+}
+
+// If copy0 is set (level 1 built straight from the source frame), the tile
+// also writes its share of the level-0 copy (pitch cp) from the staged window:
+// source rows [2 oy0, 2 oy0 + 2 TH) and columns [2 ox0, 2 ox0 + 2 TW), extended
+// to the frame's last row / column on the last tile row / column, so the
+// tiles partition level 0.
+template <bool COHERENT>
+__device__ __forceinline__ void pyr_tile(const PyrJob& J, int ox0, int oy0, uint8_t (*in)[IW],
+                                         uint16_t (*vs)[IW], uint8_t* copy0 = nullptr, int cp = 0)
+{
     const int ix0 = 2 * ox0 - 4, iy0 = 2 * oy0 - 2;
     // stage the input window (clamp-to-edge); 4-byte loads when the whole
     // window row lies inside the image and is aligned, bytes otherwise
     const bool interior_x = ix0 >= 0 && ix0 + IW <= J.sW && ((J.sp & 3) == 0) &&
                             ((reinterpret_cast<uintptr_t>(J.src) & 3) == 0);
+    // all of a thread's loads are issued before any store, so the window
+    // costs about one memory round trip instead of one per loop iteration
     if (interior_x) {
-        constexpr int WPR = IW / 4;
-        for (int i = threadIdx.x; i < IH * WPR; i += PYR_THREADS) {
-            const int r = i / WPR, c = i % WPR;
-            const int gy = min(max(iy0 + r, 0), J.sH - 1);
-            const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(J.src + (size_t)gy * J.sp + ix0) + c);
-            *reinterpret_cast<uint32_t*>(&in[r][4 * c]) = w;
+        constexpr int WPR = IW / 4, NW = IH * WPR, PER = (NW + PYR_THREADS - 1) / PYR_THREADS;
+        uint32_t v[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = threadIdx.x + k * PYR_THREADS;
+            if (i < NW) {
+                const int r = i / WPR, c = i % WPR;
+                const int gy = min(max(iy0 + r, 0), J.sH - 1);
+                v[k] = ld_word<COHERENT>(J.src + (size_t)gy * J.sp + ix0 + 4 * c);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = threadIdx.x + k * PYR_THREADS;
+            if (i < NW) *reinterpret_cast<uint32_t*>(&in[i / WPR][4 * (i % WPR)]) = v[k];
         }
     } else {
-        for (int i = threadIdx.x; i < IH * IW; i += PYR_THREADS) {
-            const int r = i / IW, c = i % IW;
-            const int gy = min(max(iy0 + r, 0), J.sH - 1);
-            const int gx = min(max(ix0 + c, 0), J.sW - 1);
-            in[r][c] = __ldg(J.src + (size_t)gy * J.sp + gx);
+        constexpr int NB = IH * IW, PER = (NB + PYR_THREADS - 1) / PYR_THREADS;
+        uint8_t v[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = threadIdx.x + k * PYR_THREADS;
+            if (i < NB) {
+                const int r = i / IW, c = i % IW;
+                const int gy = min(max(iy0 + r, 0), J.sH - 1);
+                const int gx = min(max(ix0 + c, 0), J.sW - 1);
+                v[k] = ld_byte<COHERENT>(J.src + (size_t)gy * J.sp + gx);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = threadIdx.x + k * PYR_THREADS;
+            if (i < NB) in[i / IW][i % IW] = v[k];
         }
     }
     __syncthreads();
+    if (copy0) {
+        const int y0 = 2 * oy0, y1 = oy0 + TH >= J.dH ? J.sH : 2 * oy0 + 2 * TH;
+        const int x0 = 2 * ox0, x1 = ox0 + TW >= J.dW ? J.sW : 2 * ox0 + 2 * TW;
+        const int nw = (x1 - x0) >> 2;          // whole 4-byte words (x0 is a multiple of 128)
+        const int tail = (x1 - x0) & 3;
+        const int per_row = nw + tail;
+        for (int i = threadIdx.x; i < (y1 - y0) * per_row; i += PYR_THREADS) {
+            const int r = i / per_row, k = i % per_row;
+            uint8_t* drow = copy0 + (size_t)(y0 + r) * cp + x0;
+            const uint8_t* srow = &in[r + 2][4];  // staged column 4 is source column x0
+            if (k < nw)
+                reinterpret_cast<uint32_t*>(drow)[k] = *reinterpret_cast<const uint32_t*>(srow + 4 * k);
+            else
+                drow[4 * nw + (k - nw)] = srow[4 * nw + (k - nw)];
+        }
+    }
     // vertical 5-tap pass on every staged column
     for (int i = threadIdx.x; i < TH * IW; i += PYR_THREADS) {
         const int y = i / IW, c = i % IW;
@@ -80,13 +136,38 @@ __global__ void __launch_bounds__(PYR_THREADS) pyr_down_kernel(const PyrJob* __r
             for (int k = 0; k < 4 && gx + k < J.dW; ++k) dst[k] = (uint8_t)(packed >> (8 * k));
         }
     }
+    __syncthreads();   // the staging buffers are reused by the next tile
+}
+
+// One level of S streams (blockIdx.z = stream).  For level 1 the source can
+// be the caller's frame instead of the level-0 buffer: `frames` (a device table
+// of S contiguous frames, pitch = width) or `src` / `sp` (one stream); the
+// tiles then also write the level-0 copy into the job's source buffer.
+__global__ void __launch_bounds__(PYR_THREADS) pyr_down_kernel(const PyrJob* __restrict__ jobs,
+                                                               const uint8_t* const* __restrict__ frames,
+                                                               const uint8_t* __restrict__ src, int sp)
+{
+    __shared__ __align__(16) uint8_t in[IH][IW];
+    __shared__ __align__(16) uint16_t vs[TH][IW];
+    PyrJob J = jobs[blockIdx.z];
+    const int ox0 = blockIdx.x * TW, oy0 = blockIdx.y * TH;
+    if (ox0 >= J.dW || oy0 >= J.dH) return;
+    if (frames || src) {
+        uint8_t* level0 = const_cast<uint8_t*>(J.src);
+        const int p0 = J.sp;
+        J.src = frames ? frames[blockIdx.z] : src;
+        J.sp = frames ? J.sW : sp;
+        pyr_tile<false>(J, ox0, oy0, in, vs, level0, p0);
+    } else {
+        pyr_tile<false>(J, ox0, oy0, in, vs);
+    }
 }
 
 cudaError_t launch_pyr_down(const PyrJob* jobs_dev, int njobs, int tiles_x, int tiles_y,
-                            cudaStream_t s)
+                            cudaStream_t s, const uint8_t* const* frames, const uint8_t* src, int sp)
 {
     dim3 grid((unsigned)tiles_x, (unsigned)tiles_y, (unsigned)njobs);
-    pyr_down_kernel<<<grid, PYR_THREADS, 0, s>>>(jobs_dev);
+    pyr_down_kernel<<<grid, PYR_THREADS, 0, s>>>(jobs_dev, frames, src, sp);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,14 @@ def test_pyramid_rendered_and_pitched_input(glt, orc, syn):
     ref = orc.pyramid(p.cur, 3)
     for l in range(3):
         np.testing.assert_array_equal(trk.get_pyramid(glt.GLT_CUR, l), ref[l])
+    # a source pointer that is not 4-byte aligned (one byte into the rows)
+    padded[:, 1:W + 1] = p.ref
+    dev = torch.from_numpy(padded).cuda()
+    rc = glt.glt_build_pyramid(trk.handle, glt.GLT_CUR, dev.data_ptr() + 1, W + 37, 1,
+                               torch.cuda.current_stream().cuda_stream)
+    assert rc == glt.GLT_OK
+    for l, lv in enumerate(orc.pyramid(p.ref, 3)):
+        np.testing.assert_array_equal(trk.get_pyramid(glt.GLT_CUR, l), lv)
     assert glt.glt_build_pyramid(trk.handle, 5, dev.data_ptr(), W, 1, None) == glt.GLT_ERR_INVALID_ARG
     assert glt.glt_build_pyramid(trk.handle, 0, dev.data_ptr(), W - 1, 1, None) == glt.GLT_ERR_INVALID_ARG
     trk.close()
