@@ -345,12 +345,13 @@ __device__ __forceinline__ double rcp_d(double d)
 {
     // FP32 seed built from the bit pattern (no F2F conversions on the FP64
     // pipe), then one Newton step in FP64: relative error < 1e-13.  Only for
-    // 1e-30 < |d| < 1e30, where the exponent fits FP32.
-    const double ad = fabs(d);
-    if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+    // 2^-100 <= |d| < 2^100 (exponent tested as an integer), where the
+    // exponent fits FP32; zero, infinities, NaN and the rest divide.
     const int hi = __double2hiint(d);
     const unsigned lo = (unsigned)__double2loint(d);
-    const int e32 = ((hi >> 20) & 0x7ff) - 896;
+    const int ebits = (hi >> 20) & 0x7ff;
+    if (ebits < 1023 - 100 || ebits >= 1023 + 100) return 1.0 / d;
+    const int e32 = ebits - 896;
     const unsigned fb = ((unsigned)hi & 0x80000000u) | ((unsigned)e32 << 23) |
                         (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29);
     float rf;
@@ -506,7 +507,8 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
         const double Ecn = S.E * nd;
         const bool small = step_bits < abs_bits(D.accept_step);
         accept = enough && (En < Ecn || small);
-        const bool flat = !accept && enough && (En - Ecn <= D.eps_cost * Ecn);
+        const bool flat = !accept && enough && __double_as_longlong(D.eps_cost) != 0 &&
+                          (En - Ecn <= D.eps_cost * Ecn);   // off (no FP64 work) when eps_cost = 0
         lambda *= accept ? D.lambda_down : D.lambda_up;
         load_normal = accept;
         if (it >= D.max_iters[level] ||
@@ -548,61 +550,72 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
 
     bool next_level = (phase == PH_START && !enough) || finish;
     if (candidate) {
-        // ---- (H + lambda diag H) delta = -g by L D L^T, lane `row` holds row `row`
-        double a[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) a[c] = S.H[8 * row + c];
-        double diag = 0.0;
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-            if (c == row) diag = a[c];
-        const double a0 = fma(lambda, diag, diag);   // damped diagonal
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-            if (c == row) a[c] = a0;
-        double y = -S.g[row];
-        double Lcol[8];
-        double dinv = 0.0, dpiv = 0.0;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) Lcol[c] = 0.0;
+        // ---- (H + lambda diag H) delta = -g by L D L^T, right-looking, one
+        // matrix entry per lane: lanes 0-27 hold the strictly lower entries
+        // (i, k), i > k, column by column; lanes 0-7 also hold the diagonal
+        // entry of row `lane`.  Each column costs one reciprocal, one scale
+        // and two FMAs per warp (trailing entries and diagonal) instead of
+        // one FMA per trailing column.
+        const int ek = lane < 7 ? 0 : lane < 13 ? 1 : lane < 18 ? 2 : lane < 22 ? 3 : lane < 25 ? 4
+                     : lane < 27 ? 5 : lane < 28 ? 6 : 7;
+        const int ei = lane < 28 ? lane - (ek * 7 - (ek * (ek - 1)) / 2) + ek + 1 : 8;
+        double e = lane < 28 ? S.H[8 * ei + ek] : 0.0;
+        const double diag = S.H[8 * row + row];
+        const double a0 = fma(lambda, diag, diag);   // damped diagonal (lanes 0-7)
+        double dg = a0;
+        double dinv = 0.0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const double d = __shfl_sync(full, a[j], j);
+            const double d = __shfl_sync(full, dg, j);
             const double r = rcp_d(d);
-            if (row == j) {
-                dinv = r;
-                dpiv = d;
+            if (lane == j) dinv = r;
+            if (j < 7) {
+                const double l = e * r;                         // l_ij on the lanes of column j
+                const int cj = j * 7 - (j * (j - 1)) / 2 - j - 1;   // lane of (i, j) is cj + i
+                const bool trail = lane < 28 && ek > j;        // entry (i, k), k > j: -= l_ij a_kj
+                const bool drow = lane > j && lane < 8;          // diagonal d_i, i > j: -= l_ij a_ij
+                const double li = __shfl_sync(full, l, cj + (trail ? ei : j + 1));
+                const double ak = __shfl_sync(full, e, cj + (trail ? ek : j + 1));
+                const double ld = __shfl_sync(full, l, cj + (drow ? lane : j + 1));
+                const double ad = __shfl_sync(full, e, cj + (drow ? lane : j + 1));
+                if (trail) e = fma(-li, ak, e);
+                if (drow) dg = fma(-ld, ad, dg);
+                if (lane < 28 && ek == j) e = l;
             }
-            const double lij = a[j] * r;
-#pragma unroll
-            for (int k = j + 1; k < 8; ++k) {
-                const double akj = __shfl_sync(full, a[j], k);
-                if (row > j) a[k] = fma(-lij, akj, a[k]);
-            }
-#pragma unroll
-            for (int k = j + 1; k < 8; ++k) {
-                const double lkj = __shfl_sync(full, lij, k);
-                if (row == j) Lcol[k] = lkj;
-            }
-            if (row > j) a[j] = lij;
         }
         // pivots checked once, each lane its own: d > 0 and d > 1e-13 * damped diagonal
-        const bool piv_ok = dpiv > 1e-13 * a0 && dpiv > 0.0;
+        const bool piv_ok = dg > 1e-13 * a0 && dg > 0.0;
         const bool ok = __all_sync(full, piv_ok || lane >= 8);
         if (!ok) {
             if (lane == 0) S.status |= GLT_TRACK_NOT_PD;
             finish = true;
             next_level = true;
         } else {
-            // forward (L y = -g), diagonal, backward (L^T x = D^-1 y)
+            // row `row` of L (entries left of the diagonal) and column `row`
+            // (entries below it) gathered into the row's lane
+            double Lrow[8], Lcol[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int c = 0; c < 7; ++c) {
+                const int cc = c * 7 - (c * (c - 1)) / 2 - c - 1;
+                const double v = __shfl_sync(full, e, cc + (row > c ? row : c + 1));
+                Lrow[c] = row > c ? v : 0.0;
+            }
+#pragma unroll
+            for (int i = 1; i < 8; ++i) {
+                const int cr = row * 7 - (row * (row - 1)) / 2 - row - 1;
+                const double v = __shfl_sync(full, e, row < i ? cr + i : 0);
+                Lcol[i] = row < i ? v : 0.0;
+            }
+            // forward (L y = -g), diagonal, backward (L^T x = D^-1 y)
+            double y = -S.g[row];
+#pragma unroll
+            for (int j = 0; j < 7; ++j) {
                 const double yj = __shfl_sync(full, y, j);
-                if (row > j) y = fma(-a[j], yj, y);
+                if (row > j) y = fma(-Lrow[j], yj, y);
             }
             double x = y * dinv;
 #pragma unroll
-            for (int j = 7; j >= 0; --j) {
+            for (int j = 7; j >= 1; --j) {
                 const double xj = __shfl_sync(full, x, j);
                 if (row < j) x = fma(-Lcol[j], xj, x);
             }
