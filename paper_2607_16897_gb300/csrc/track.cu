@@ -17,8 +17,14 @@ namespace cg = cooperative_groups;
 
 namespace glt {
 
+constexpr int kMaxCluster = 16;   // largest cluster a stream may use (config.cluster)
+
+// The 128-thread shape is capped at 128 registers so four CTAs fit on an SM
+// (batches of many small clusters); the wider shapes keep the registers the
+// compiler wants (a single stream's latency).
+
 template <int THREADS, bool MIXED>
-__global__ void __launch_bounds__(THREADS) track_kernel(const StreamDesc* const* __restrict__ descs,
+__global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(const StreamDesc* const* __restrict__ descs,
                                                         const int* __restrict__ users,
                                                         const double* __restrict__ init,
                                                         glt_result* __restrict__ results)
@@ -61,18 +67,26 @@ __global__ void __launch_bounds__(THREADS) track_kernel(const StreamDesc* const*
             // finish over the CTAs of the cluster: a compensated FP32 sum
             // (TwoSum, error-free per step) converted to FP64 once; the FP64
             // pipe of this GPU is too slow to carry a chain of C adds
-            float hi = 0.0f, lo = 0.0f;
-            for (int r = 0; r < C; ++r) {
-                const float* pr = C > 1 ? cluster.map_shared_rank(&part[par][0], r) : &part[par][0];
-                float v = pr[tid];
-                if (MIXED) {
-                    const float* cr = C > 1 ? cluster.map_shared_rank(&part_c[par][0], r) : &part_c[par][0];
-                    lo += cr[tid];
+            // (all remote loads are issued before the first add: one
+            // distributed-shared-memory round trip instead of C)
+            float v[kMaxCluster], vc[kMaxCluster];
+#pragma unroll
+            for (int r = 0; r < kMaxCluster; ++r) {
+                if (r < C) {
+                    v[r] = C > 1 ? cluster.map_shared_rank(&part[par][0], r)[tid] : part[par][tid];
+                    if (MIXED) vc[r] = C > 1 ? cluster.map_shared_rank(&part_c[par][0], r)[tid] : part_c[par][tid];
                 }
-                const float s = hi + v;
-                const float bb = s - hi;
-                lo += (hi - (s - bb)) + (v - bb);
-                hi = s;
+            }
+            float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+            for (int r = 0; r < kMaxCluster; ++r) {
+                if (r < C) {
+                    if (MIXED) lo += vc[r];
+                    const float s = hi + v[r];
+                    const float bb = s - hi;
+                    lo += (hi - (s - bb)) + (v[r] - bb);
+                    hi = s;
+                }
             }
             tot[tid] = (double)hi + (double)lo;
         }
