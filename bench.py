@@ -28,6 +28,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLOPS_PER_SAMPLE = 160      # algorithmic FP32 flops per residual sample per pass
+# DRAM bytes (read + write) per track_kernel launch, measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
+# launch as in the timed steps) on the workload named by the key; a value is
+# removed whenever the kernel changes after it was taken.
+TRACK_TRAFFIC = {"c2": 782336, "c3": 55356160}
 I34 = np.hstack([np.eye(3), np.zeros((3, 1))])
 
 
@@ -44,6 +49,9 @@ def parse():
                          "learned proposal, against the plain form on the same streams")
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="frames the oracle tracks for cpu_baseline (0 = auto, ~10-30 s)")
+    ap.add_argument("--shape", default=None,
+                    help="batched forms: fixed tile shape 'cluster,threads' instead of the "
+                         "autotuner's pick (profiling runs, where the tuner's timings are distorted)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -457,7 +465,8 @@ def run_ours(args):
     peaks, src = measured_peaks()
     peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "kernel": "track_kernel",
+            "frac": achieved / peak, "traffic": TRACK_TRAFFIC.get(args.workload),
+            "kernel": "track_kernel",
             "peak_source": f"FP32 FMA peak from unit counts (152 SMs x 128 lanes x 2) at "
                            f"{peaks.get('sm_max_mhz', 2070.0):g} MHz ({src} clock)",
             "launch_ms": statistics.mean(trk_ms), "passes_per_launch": statistics.mean(passes),
@@ -730,7 +739,12 @@ def run_batch(args):
         init_dev.copy_(init_pin, non_blocking=True)
         batch.build_pyramid(ptr_dev, stream=sh)
     stream.synchronize()
-    shape = batch.autotune(init_dev, out_dev, reps=3, stream=sh)
+    if args.shape:
+        c, t = (int(v) for v in args.shape.split(","))
+        batch.set_shape(c, t)
+        shape = (c, t, None)
+    else:
+        shape = batch.autotune(init_dev, out_dev, reps=3, stream=sh)
 
     def measure(form):
         """Captures the step graph of `form` ("plain" / "proposal") and times it."""
@@ -821,7 +835,8 @@ def run_batch(args):
                 "breakdown_ms": {"replay": statistics.mean(dev_ms),
                                  "wall_per_step": 1000.0 * head["t_wall"] / args.steps},
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                             "frac": achieved / peak, "traffic": None, "kernel": "track_kernel",
+                             "frac": achieved / peak, "traffic": TRACK_TRAFFIC.get(args.workload),
+                             "kernel": "track_kernel",
                              "peak_source": f"FP32 FMA peak from unit counts at "
                                             f"{peaks.get('sm_max_mhz', 2070.0):g} MHz ({src} clock)",
                              "samples_per_step": samples},
