@@ -455,8 +455,10 @@ def run_ours(args):
     # oracle on a bounded sample, same initial states and references
     cpu = None
     parity = None
+    lin_err = None
     if rank == 0 and not args.no_cpu:
         cpu, parity = run_cpu_baseline(args, wl, rec)
+        lin_err = linearization_error(glt, wl, rec[-1], precision)
 
     # roofline of the dominant kernel (the persistent tracker)
     mean_trk = statistics.mean(trk_ms) / 1000.0
@@ -488,7 +490,8 @@ def run_ours(args):
                                  "wall_per_step": 1000.0 * t_wall / args.steps},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": args.steps * L + n_ref * L,
-                "parity_vs_oracle": parity, "accuracy_vs_truth": accuracy}
+                "parity_vs_oracle": parity, "accuracy_vs_truth": accuracy,
+                "linearization_error_vs_oracle": lin_err}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -556,6 +559,34 @@ def run_cpu_baseline(args, wl, rec):
     parity = {"frames": n, "max_rot_rad": max(rot), "max_trans_m": max(trans),
               "tolerance": {"rot_rad": 1e-5, "trans_m": 1e-5}}
     return cpu, parity
+
+
+def linearization_error(glt, wl, rec_entry, precision):
+    """H, g and E of one linearisation on every level, GPU (this precision)
+    against the FP64 oracle, at the initial state of the given frame:
+    |dH|_F / |H|_F, |dg| / |g|, |dE| / E, and whether the sample counts match."""
+    import oracle
+    k, r, T_init, ab, _ = rec_entry
+    trk = glt.Tracker(wl.cam.W, wl.cam.H, wl.cam.K, levels=wl.L, max_points=wl.N, precision=precision)
+    trk.build_pyramid(glt.GLT_REF, wl.frames[r])
+    trk.set_map_points(wl.ref_points(r))
+    trk.build_pyramid(glt.GLT_CUR, wl.frames[k])
+    o = oracle.OracleTracker(wl.cam.W, wl.cam.H, wl.cam.K, levels=wl.L)
+    o.build_pyramid(0, wl.frames[r])
+    o.set_map_points(wl.ref_points(r))
+    o.build_pyramid(1, wl.frames[k])
+    out = {"frame": k, "state": "constant-velocity initial state", "levels": []}
+    for l in range(wl.L):
+        gd = trk.debug_linearize(l, T_init, ab[0], ab[1], want_res=False)
+        od = o.debug_linearize(l, T_init, ab[0], ab[1], per_sample=False)
+        out["levels"].append({
+            "level": l,
+            "H_rel": float(np.linalg.norm(gd["H"] - od["H"]) / np.linalg.norm(od["H"])),
+            "g_rel": float(np.linalg.norm(gd["g"] - od["g"]) / np.linalg.norm(od["g"])),
+            "E_rel": float(abs(gd["E"] - od["E"]) / od["E"]),
+            "n_equal": bool(gd["n"] == od["n"])})
+    trk.close()
+    return out
 
 
 def single_workload(kind, rank=0):
