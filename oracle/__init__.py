@@ -66,7 +66,7 @@ class _Config(ctypes.Structure):
                 ("eps_step", ctypes.c_double), ("eps_step_coarse", ctypes.c_double),
                 ("eps_cost", ctypes.c_double),
                 ("accept_step", ctypes.c_double), ("min_valid", ctypes.c_int),
-                ("zmin", ctypes.c_double)]
+                ("zmin", ctypes.c_double), ("ic", ctypes.c_int)]
 
 
 class _Result(ctypes.Structure):
@@ -95,9 +95,15 @@ def _load():
                                           dp, dp, dp, ip, dp, dp, dp, u8p]
             lib.orc_track.argtypes = [dp, i, i, _Cam, dp, dp, u8p, i, P(_Config), dp, d, d,
                                       P(_Result), dp, ip, dp, i]
+            lib.orc_ic_jacobian.argtypes = [dp, i, i, _Cam, i, dp, fp, u8p, i, dp]
+            lib.orc_linearize2.argtypes = [dp, i, i, _Cam, i, dp, dp, u8p, dp, i, dp, d, d, d, d,
+                                           dp, dp, dp, ip, dp, dp, dp, u8p]
+            lib.orc_track2.argtypes = [dp, i, i, _Cam, dp, dp, u8p, dp, i, P(_Config), dp, d, d,
+                                       P(_Result), dp, ip, dp, i]
             for fn in (lib.orc_pyr_down, lib.orc_build_pyramid, lib.orc_se3_exp, lib.orc_se3_log,
                        lib.orc_se3_mul, lib.orc_backproject, lib.orc_ref_patch,
-                       lib.orc_linearize, lib.orc_track):
+                       lib.orc_linearize, lib.orc_track, lib.orc_ic_jacobian,
+                       lib.orc_linearize2, lib.orc_track2):
                 fn.restype = None
             _lib = lib
     return _lib
@@ -199,8 +205,24 @@ def ref_patch(img_l, level: int, uvd):
     return I0, valid
 
 
+def ic_jacobian(ref_l, K0, level, x_r, uvd, valid_l):
+    """Inverse-compositional cache of one level: [N, 8, 6] reference-side
+    pose Jacobian rows (zero for unusable points)."""
+    img = _f64(ref_l)
+    H, W = img.shape
+    x_r = _f64(x_r)
+    N = x_r.shape[0]
+    uvd = np.ascontiguousarray(uvd, np.float32).reshape(-1, 3)
+    valid_l = np.ascontiguousarray(valid_l, np.uint8)
+    out = np.zeros(N * 48)
+    _load().orc_ic_jacobian(_p(img, ctypes.c_double), W, H, _cam(K0), int(level),
+                            _p(x_r, ctypes.c_double), _p(uvd, ctypes.c_float),
+                            _p(valid_l, ctypes.c_uint8), N, _p(out, ctypes.c_double))
+    return out.reshape(N, 8, 6)
+
+
 def linearize(img_l, K0, level, x_r, I0_l, valid_l, T, a, b, huber_k=9.0, zmin=1e-3,
-              per_sample=True):
+              per_sample=True, Jic=None):
     img = _f64(img_l)
     H, W = img.shape
     x_r = _f64(x_r)
@@ -218,9 +240,11 @@ def linearize(img_l, K0, level, x_r, I0_l, valid_l, T, a, b, huber_k=9.0, zmin=1
         jac = np.zeros(N * 64)
         wts = np.zeros(N * 8)
         pv = np.zeros(N, np.uint8)
-    _load().orc_linearize(_p(img, ctypes.c_double), W, H, _cam(K0), int(level),
+    Jic = None if Jic is None else _f64(Jic).reshape(N * 48)
+    _load().orc_linearize2(_p(img, ctypes.c_double), W, H, _cam(K0), int(level),
                           _p(x_r, ctypes.c_double), _p(I0_l, ctypes.c_double),
-                          _p(valid_l, ctypes.c_uint8), N, _p(T, ctypes.c_double), float(a),
+                          _p(valid_l, ctypes.c_uint8), _p(Jic, ctypes.c_double), N,
+                          _p(T, ctypes.c_double), float(a),
                           float(b), float(huber_k), float(zmin), _p(Hm, ctypes.c_double),
                           _p(g, ctypes.c_double), ctypes.byref(E), ctypes.byref(n),
                           _p(res, ctypes.c_double), _p(jac, ctypes.c_double),
@@ -237,7 +261,7 @@ def linearize(img_l, K0, level, x_r, I0_l, valid_l, T, a, b, huber_k=9.0, zmin=1
 # --------------------------------------------------------------------------
 DEFAULT_CONFIG = dict(levels=4, max_iters=[10] * 8, huber_k=9.0, lambda0=1e-4, lambda_up=4.0,
                       lambda_down=0.5, eps_step=1e-6, eps_step_coarse=3e-4, eps_cost=0.0, accept_step=1e-3,
-                      min_valid=16, zmin=1e-3)
+                      min_valid=16, zmin=1e-3, jacobian="forward")
 
 
 def make_config(**kw) -> dict:
@@ -263,11 +287,13 @@ def _cconfig(c: dict) -> _Config:
     cc.accept_step = float(c["accept_step"])
     cc.min_valid = int(c["min_valid"])
     cc.zmin = float(c["zmin"])
+    cc.ic = {"forward": 0, "ic": 1}[c["jacobian"]]
     return cc
 
 
-def track(cur_levels, K0, x_r, I0, valid, cfg: dict, T_init, a0=0.0, b0=0.0) -> dict:
-    """cur_levels: list of level images; I0 [L, N, 8]; valid [L, N]."""
+def track(cur_levels, K0, x_r, I0, valid, cfg: dict, T_init, a0=0.0, b0=0.0, Jic=None) -> dict:
+    """cur_levels: list of level images; I0 [L, N, 8]; valid [L, N]; Jic
+    [L, N, 8, 6] (inverse-compositional cache, needed when cfg jacobian = ic)."""
     L = int(cfg["levels"])
     H0, W0 = np.asarray(cur_levels[0]).shape
     flat = np.concatenate([_f64(cur_levels[l]).ravel() for l in range(L)])
@@ -282,8 +308,12 @@ def track(cur_levels, K0, x_r, I0, valid, cfg: dict, T_init, a0=0.0, b0=0.0) -> 
     tc = np.zeros(max(mt, 1))
     ti = np.zeros(max(mt, 1), np.int32)
     ts = np.zeros(max(mt, 1))
-    _load().orc_track(_p(flat, ctypes.c_double), W0, H0, _cam(K0), _p(x_r, ctypes.c_double),
-                      _p(I0, ctypes.c_double), _p(valid, ctypes.c_uint8), N, ctypes.byref(cc),
+    if cfg["jacobian"] == "ic" and Jic is None:
+        raise ValueError("the inverse-compositional solve needs its Jacobian cache")
+    Jic = None if Jic is None else _f64(Jic).reshape(L * N * 48)
+    _load().orc_track2(_p(flat, ctypes.c_double), W0, H0, _cam(K0), _p(x_r, ctypes.c_double),
+                      _p(I0, ctypes.c_double), _p(valid, ctypes.c_uint8), _p(Jic, ctypes.c_double),
+                      N, ctypes.byref(cc),
                       _p(T, ctypes.c_double), float(a0), float(b0), ctypes.byref(r),
                       _p(tc, ctypes.c_double), _p(ti, ctypes.c_int), _p(ts, ctypes.c_double), mt)
     n = min(r.passes, mt)
@@ -309,6 +339,7 @@ class OracleTracker:
         self.x_r = None
         self.I0 = None
         self.valid = None
+        self.Jic = None
 
     def build_pyramid(self, slot: int, img) -> None:
         img = np.ascontiguousarray(img, np.uint8)
@@ -326,12 +357,16 @@ class OracleTracker:
         self.valid = np.zeros((self.L, N), np.uint8)
         for l in range(self.L):
             self.I0[l], self.valid[l] = ref_patch(self.pyr[self.REF][l], l, uvd)
+        self.Jic = None
+        if self.cfg["jacobian"] == "ic":
+            self.Jic = np.stack([ic_jacobian(self.pyr[self.REF][l], self.K, l, self.x_r, uvd,
+                                             self.valid[l]) for l in range(self.L)])
 
     def debug_linearize(self, level, T, a, b, per_sample=True):
         return linearize(self.pyr[self.CUR][level], self.K, level, self.x_r, self.I0[level],
                          self.valid[level], T, a, b, self.cfg["huber_k"], self.cfg["zmin"],
-                         per_sample)
+                         per_sample, Jic=None if self.Jic is None else self.Jic[level])
 
     def track_frame(self, T_init, ab_init=(0.0, 0.0)) -> dict:
         return track(self.pyr[self.CUR], self.K, self.x_r, self.I0, self.valid, self.cfg,
-                     T_init, float(ab_init[0]), float(ab_init[1]))
+                     T_init, float(ab_init[0]), float(ab_init[1]), Jic=self.Jic)

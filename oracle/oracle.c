@@ -265,13 +265,64 @@ void orc_ref_patch(const double* img, int W, int H, int level, const float* uvd,
 }
 
 /* ------------------------------------------------------------------------
+ * Inverse-compositional cache (Sec. IV-B: J_ik = grad I0(u_i^0 + du_k)
+ * dpi/dx dx/ddelta with x = T0 P_i, i.e. evaluated on the reference side;
+ * Sec. IV-C "Precompute IC": computed once per reference and level).
+ * ------------------------------------------------------------------------ */
+void orc_ic_jacobian(const double* ref, int W, int H, orc_cam K0, int level, const double* x_r,
+                     const float* uvd, const uint8_t* valid_ref, int N, double* Jic)
+{
+    double s = ldexp(1.0, -level);
+    double fx = K0.fx * s, fy = K0.fy * s;
+    (void)H;
+    for (int i = 0; i < N; ++i) {
+        double* Ji = Jic + (size_t)i * 48;
+        memset(Ji, 0, 48 * sizeof(double));
+        if (!valid_ref[i]) continue;
+        const double* X = x_r + 3 * i;
+        /* dpi/dx at x_r and [I | -[x_r]x] */
+        double dpi[6] = {fx / X[2], 0, -fx * X[0] / (X[2] * X[2]),
+                         0, fy / X[2], -fy * X[1] / (X[2] * X[2])};
+        double Xh[9];
+        hat(X, Xh);
+        double Jg[12];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 6; ++c) {
+                double acc = 0;
+                for (int k = 0; k < 3; ++k) {
+                    double m = c < 3 ? (k == c ? 1.0 : 0.0) : -Xh[3 * k + (c - 3)];
+                    acc += dpi[3 * r + k] * m;
+                }
+                Jg[6 * r + c] = acc;
+            }
+        double u = uvd[3 * i] * s, v = uvd[3 * i + 1] * s;
+        for (int k = 0; k < 8; ++k) {
+            double gx, gy;
+            bilinear_grad(ref, W, u + orc_pattern_dx[k], v + orc_pattern_dy[k], &gx, &gy);
+            for (int c = 0; c < 6; ++c) Ji[6 * k + c] = gx * Jg[c] + gy * Jg[6 + c];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------
  * Linearisation (Sec. IV-A Eqs. 1-5; forward form of Sec. IV-B: J uses the
- * current image's gradient at the warped location).
+ * current image's gradient at the warped location; with Jic, the
+ * inverse-compositional form: J uses the cached reference-side rows).
  * ------------------------------------------------------------------------ */
 void orc_linearize(const double* img, int W, int H, orc_cam K0, int level, const double* x_r,
                    const double* I0, const uint8_t* valid_ref, int N, const double T[12],
                    double a, double b, double huber_k, double zmin, double* Hout, double* g,
                    double* E, int* n, double* res, double* jac, double* wts, uint8_t* pvalid)
+{
+    orc_linearize2(img, W, H, K0, level, x_r, I0, valid_ref, NULL, N, T, a, b, huber_k, zmin,
+                   Hout, g, E, n, res, jac, wts, pvalid);
+}
+
+void orc_linearize2(const double* img, int W, int H, orc_cam K0, int level, const double* x_r,
+                    const double* I0, const uint8_t* valid_ref, const double* Jic, int N,
+                    const double T[12], double a, double b, double huber_k, double zmin,
+                    double* Hout, double* g, double* E, int* n, double* res, double* jac,
+                    double* wts, uint8_t* pvalid)
 {
     double s = ldexp(1.0, -level);
     double fx = K0.fx * s, fy = K0.fy * s, cx = K0.cx * s, cy = K0.cy * s;
@@ -334,7 +385,10 @@ void orc_linearize(const double* img, int W, int H, orc_cam K0, int level, const
             double w = ar <= huber_k ? 1.0 : huber_k / ar;
             double rho = ar <= huber_k ? 0.5 * r * r : huber_k * ar - 0.5 * huber_k * huber_k;
             double J[8];
-            for (int c = 0; c < 6; ++c) J[c] = gx * Jg[c] + gy * Jg[6 + c];
+            if (Jic)
+                for (int c = 0; c < 6; ++c) J[c] = ea * Jic[(size_t)i * 48 + 6 * k + c];
+            else
+                for (int c = 0; c < 6; ++c) J[c] = gx * Jg[c] + gy * Jg[6 + c];
             J[6] = -ea * i0;
             J[7] = -1.0;
             for (int p = 0; p < 8; ++p) {
@@ -406,6 +460,16 @@ void orc_track(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
                const double T_init[12], double a0, double b0, orc_result* out,
                double* trace_cost, int* trace_info, double* trace_step, int max_trace)
 {
+    orc_track2(cur, W0, H0, K0, x_r, I0, valid, NULL, N, cfg, T_init, a0, b0, out, trace_cost,
+               trace_info, trace_step, max_trace);
+}
+
+void orc_track2(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
+                const double* I0, const uint8_t* valid, const double* Jic, int N,
+                const orc_config* cfg, const double T_init[12], double a0, double b0,
+                orc_result* out, double* trace_cost, int* trace_info, double* trace_step,
+                int max_trace)
+{
     int L = cfg->levels;
     size_t off[8];
     int Ws[8], Hs[8];
@@ -446,8 +510,9 @@ void orc_track(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
         const double* img = cur + off[l];
         const double* I0l = I0 + (size_t)l * N * 8;
         const uint8_t* vl = valid + (size_t)l * N;
-        orc_linearize(img, Ws[l], Hs[l], K0, l, x_r, I0l, vl, N, T, a, b, cfg->huber_k,
-                      cfg->zmin, Hm, g, &E, &n, NULL, NULL, NULL, NULL);
+        const double* Jl = (cfg->ic && Jic) ? Jic + (size_t)l * N * 48 : NULL;
+        orc_linearize2(img, Ws[l], Hs[l], K0, l, x_r, I0l, vl, Jl, N, T, a, b, cfg->huber_k,
+                       cfg->zmin, Hm, g, &E, &n, NULL, NULL, NULL, NULL);
         int enough = n >= cfg->min_valid && n > 0;
         trace_pass(out, trace_cost, trace_info, trace_step, max_trace, enough ? E / n : INFINITY,
                    l, 0, 0, 0.0);
@@ -472,8 +537,8 @@ void orc_track(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
             double an = a + delta[6], bn = b + delta[7];
             double Hn[64], gn[8], En;
             int nn;
-            orc_linearize(img, Ws[l], Hs[l], K0, l, x_r, I0l, vl, N, Tn, an, bn, cfg->huber_k,
-                          cfg->zmin, Hn, gn, &En, &nn, NULL, NULL, NULL, NULL);
+            orc_linearize2(img, Ws[l], Hs[l], K0, l, x_r, I0l, vl, Jl, N, Tn, an, bn,
+                           cfg->huber_k, cfg->zmin, Hn, gn, &En, &nn, NULL, NULL, NULL, NULL);
             ++it;
             double m = 0;
             for (int d = 0; d < 6; ++d) m = fmax(m, fabs(delta[d]));

@@ -44,6 +44,7 @@ typedef struct {
     double accept_step;
     int min_valid;
     double zmin;
+    int ic; /* 0: forward Jacobian (current image), 1: inverse-compositional (reference side) */
 } orc_config;
 
 typedef struct {
@@ -90,6 +91,23 @@ void orc_linearize(const double* img, int W, int H, orc_cam K0, int level, const
                    double a, double b, double huber_k, double zmin, double* Hout, double* g,
                    double* E, int* n, double* res, double* jac, double* wts, uint8_t* pvalid);
 
+/* Inverse-compositional cache (Sec. IV-B, the IC Jacobian equation; Sec. IV-C
+ * "Precompute IC") on level l of the REFERENCE image: for every point and
+ * pattern sample k, J_ic[(8 i + k) * 6 + c] = grad I0(u0_l + du_k) dpi/dx(x_r)
+ * [I | -[x_r]x], the pose Jacobian evaluated on the reference side (at the
+ * identity pose).  Rows of points with valid_ref[i] = 0 are zero. */
+void orc_ic_jacobian(const double* ref, int W, int H, orc_cam K0, int level, const double* x_r,
+                     const float* uvd, const uint8_t* valid_ref, int N, double* Jic);
+
+/* As orc_linearize; with Jic non-NULL the pose columns of each Jacobian row
+ * are e^a J_ic (the template approximation of the current-side Jacobian: the
+ * current image's gradient is not used), the affine columns unchanged. */
+void orc_linearize2(const double* img, int W, int H, orc_cam K0, int level, const double* x_r,
+                    const double* I0, const uint8_t* valid_ref, const double* Jic, int N,
+                    const double T[12], double a, double b, double huber_k, double zmin,
+                    double* Hout, double* g, double* E, int* n, double* res, double* jac,
+                    double* wts, uint8_t* pvalid);
+
 /* Coarse-to-fine LM (Sec. IV-A and the accept/reject schedule of this
  * library).  cur: concatenated double pyramid of the current frame
  * (level-0 first, unpadded, dims from W0, H0).  I0: [L][N][8], valid: [L][N].
@@ -101,6 +119,13 @@ void orc_track(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
                const double* I0, const uint8_t* valid, int N, const orc_config* cfg,
                const double T_init[12], double a0, double b0, orc_result* out,
                double* trace_cost, int* trace_info, double* trace_step, int max_trace);
+/* As orc_track; with cfg->ic set, Jic is the [L][N*8*6] inverse-compositional
+ * cache of orc_ic_jacobian, used by every linearisation of the solve. */
+void orc_track2(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
+                const double* I0, const uint8_t* valid, const double* Jic, int N,
+                const orc_config* cfg, const double T_init[12], double a0, double b0,
+                orc_result* out, double* trace_cost, int* trace_info, double* trace_step,
+                int max_trace);
 
 #ifdef __cplusplus
 }
