@@ -69,6 +69,10 @@ extern "C" {
 #define GLT_FP32 0  /* uint8 levels, FP32 residuals/Jacobians/sums, FP64 solve */
 #define GLT_MIXED 1 /* FP16 (I, gx, gy) levels, FP32 math, Kahan FP32 block sums, FP64 solve */
 
+/* Jacobian forms (Sec. IV-B) */
+#define GLT_FORWARD 0 /* current image's gradient at the warped location, every pass */
+#define GLT_IC 1      /* inverse compositional: reference-side rows cached per reference */
+
 typedef struct glt_tracker glt_tracker;
 typedef struct glt_batch glt_batch;
 typedef struct glt_nn glt_nn;
@@ -97,6 +101,14 @@ typedef struct glt_config {
     int precision;              /* GLT_FP32 or GLT_MIXED */
     int cluster;                /* CTAs cooperating on one stream (1..16, 0 = auto) */
     int threads;                /* threads per CTA (128, 256 or 512; 0 = auto) */
+    int jacobian;               /* GLT_FORWARD or GLT_IC.  GLT_IC (Sec. IV-B, IV-C
+                                   "Precompute IC"): glt_set_map_points also caches
+                                   the reference gradient at every pattern sample of
+                                   every level, and each pass uses the rows
+                                   e^a grad I0(u0_l + du_k) dpi/dx(x_r) [I | -[x_r]x]
+                                   instead of the current image's gradient (the
+                                   inverse-compositional template approximation;
+                                   T <- T exp(delta) as in the paper) */
 } glt_config;
 
 typedef struct glt_result {
@@ -115,7 +127,7 @@ typedef struct glt_result {
  * lambda0 1e-4 (x4 up, x0.5 down), eps_step 1e-6 (finest level),
  * eps_step_coarse 3e-4 (coarser levels), eps_cost 0 (off),
  * accept_step 1e-3, min_valid 16, zmin 1e-3, FP32, automatic cluster/threads,
- * max_points 4096. */
+ * max_points 4096, GLT_FORWARD. */
 void glt_default_config(glt_config* cfg, int width, int height, double fx, double fy,
                         double cx, double cy);
 

@@ -28,6 +28,7 @@ GLT_TRACK_TOO_FEW_POINTS = 1
 GLT_TRACK_NOT_PD = 2
 GLT_REF, GLT_CUR = 0, 1
 GLT_FP32, GLT_MIXED = 0, 1
+GLT_FORWARD, GLT_IC = 0, 1
 MAX_LEVELS = 8
 GLT_NN_PARAMS = 189064
 GLT_NN_INPUT = 1200
@@ -46,7 +47,7 @@ class glt_config(ctypes.Structure):
                 ("eps_cost", ctypes.c_double), ("accept_step", ctypes.c_double),
                 ("min_valid", ctypes.c_int),
                 ("zmin", ctypes.c_double), ("precision", ctypes.c_int), ("cluster", ctypes.c_int),
-                ("threads", ctypes.c_int)]
+                ("threads", ctypes.c_int), ("jacobian", ctypes.c_int)]
 
 
 class glt_result(ctypes.Structure):
@@ -164,6 +165,8 @@ def default_config(width, height, K, **kw) -> glt_config:
                 c.max_iters[i] = int(v[i])
         elif k == "precision" and isinstance(v, str):
             c.precision = {"fp32": GLT_FP32, "mixed": GLT_MIXED}[v]
+        elif k == "jacobian" and isinstance(v, str):
+            c.jacobian = {"forward": GLT_FORWARD, "ic": GLT_IC}[v]
         else:
             if not hasattr(c, k):
                 raise KeyError(k)

@@ -58,6 +58,7 @@ static void free_tracker(glt_tracker* t)
     cudaFree(t->pt);
     cudaFree(t->dz);
     cudaFree(t->I0);
+    cudaFree(t->G0);
     cudaFree(t->desc_dev);
     cudaFree(t->desc_ptr_dev);
     cudaFree(t->user_dev);
@@ -105,6 +106,8 @@ static int check_config(const glt_config* c)
     if (c->cluster < 0 || c->cluster > 16) return invalid("cluster must be in [0, 16]");
     if (c->threads != 0 && c->threads != 128 && c->threads != 256 && c->threads != 512)
         return invalid("threads must be 0, 128, 256 or 512");
+    if (c->jacobian != GLT_FORWARD && c->jacobian != GLT_IC)
+        return invalid("jacobian must be GLT_FORWARD or GLT_IC");
     return GLT_OK;
 }
 
@@ -160,6 +163,7 @@ void glt_default_config(glt_config* c, int width, int height, double fx, double 
     c->precision = GLT_FP32;
     c->cluster = 0;
     c->threads = 0;
+    c->jacobian = GLT_FORWARD;
 }
 
 int glt_create(const glt_config* cfg, glt_tracker** out)
@@ -209,6 +213,7 @@ int glt_create(const glt_config* cfg, glt_tracker** out)
     ALLOC(dalloc(&t->pt, (size_t)t->Npad));
     ALLOC(dalloc(&t->dz, (size_t)t->Npad));
     ALLOC(dalloc(&t->I0, (size_t)t->L * t->Npad * 8));
+    if (cfg->jacobian == GLT_IC) ALLOC(dalloc(&t->G0, (size_t)t->L * t->Npad * 8));
     ALLOC(dalloc(&t->desc_dev, 1));
     ALLOC(dalloc(&t->desc_ptr_dev, 1));
     ALLOC(dalloc(&t->user_dev, 1));
@@ -253,6 +258,7 @@ int glt_create(const glt_config* cfg, glt_tracker** out)
     D.pt = t->pt;
     D.dz = t->dz;
     D.I0 = t->I0;
+    D.G0 = t->G0;
     for (int l = 0; l < GLT_MAX_LEVELS; ++l) D.max_iters[l] = l < t->L ? cfg->max_iters[l] : 0;
     D.min_valid = cfg->min_valid;
     D.max_trace = t->max_trace;

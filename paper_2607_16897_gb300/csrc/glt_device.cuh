@@ -45,6 +45,7 @@ struct StreamDesc {
     const float4* pt;      // (u0, v0, (u0-cx)/fx, (v0-cy)/fy)
     const float2* dz;      // (depth, 1/depth)
     const float* I0;       // [L][Npad][8]; I0[l][p][0] is NaN where the point is unusable
+    const float2* G0;      // GLT_IC: reference gradient (gx, gy) [L][Npad][8], else null
     int max_iters[kMaxLevels];
     int min_valid;
     int max_trace;
@@ -190,6 +191,25 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
         return;
     }
     const float i0[8] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
+    // inverse-compositional form: geometric rows at the reference point
+    // (identity pose) and the cached reference gradients times e^a
+    const bool ic = D.G0 != nullptr;
+    float4 g0[4];
+    if (ic) {
+        const float4 q = D.pt[p];
+        const float rho = D.dz[p].y;
+        const float fxl = D.fx * P.scale * rho, fyl = D.fy * P.scale * rho;
+        G.a0[0] = fxl;
+        G.a0[1] = 0.0f;
+        G.a0[2] = -fxl * q.z;
+        G.a1[0] = 0.0f;
+        G.a1[1] = fyl;
+        G.a1[2] = -fyl * q.w;
+        const float4* gp = reinterpret_cast<const float4*>(D.G0 + ((size_t)P.level * D.Npad + p) * 8);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) g0[k] = gp[k];
+    }
+#define GLT_G0(k, c) (((k) & 1) ? ((c) ? g0[(k) >> 1].w : g0[(k) >> 1].z) : ((c) ? g0[(k) >> 1].y : g0[(k) >> 1].x))
     const float w00 = (1.0f - G.al) * (1.0f - G.be), w10 = G.al * (1.0f - G.be);
     const float w01 = (1.0f - G.al) * G.be, w11 = G.al * G.be;
     if (!MIXED) {
@@ -219,15 +239,21 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
             const float I00 = GLT_PX(r0, c0), I10 = GLT_PX(r0, c0 + 1);
             const float I01 = GLT_PX(r0 + 1, c0), I11 = GLT_PX(r0 + 1, c0 + 1);
             const float I = fmaf(w00, I00, fmaf(w10, I10, fmaf(w01, I01, w11 * I11)));
-            // central differences at the four taps (the 1/2 is applied after interpolation)
-            const float gx = 0.5f * fmaf(w00, I10 - GLT_PX(r0, c0 - 1),
-                                   fmaf(w10, GLT_PX(r0, c0 + 2) - I00,
-                                   fmaf(w01, I11 - GLT_PX(r0 + 1, c0 - 1),
-                                        w11 * (GLT_PX(r0 + 1, c0 + 2) - I01))));
-            const float gy = 0.5f * fmaf(w00, I01 - GLT_PX(r0 - 1, c0),
-                                   fmaf(w10, I11 - GLT_PX(r0 - 1, c0 + 1),
-                                   fmaf(w01, GLT_PX(r0 + 2, c0) - I00,
-                                        w11 * (GLT_PX(r0 + 2, c0 + 1) - I10))));
+            float gx, gy;
+            if (ic) {
+                gx = P.ea * GLT_G0(k, 0);
+                gy = P.ea * GLT_G0(k, 1);
+            } else {
+                // central differences at the four taps (the 1/2 is applied after interpolation)
+                gx = 0.5f * fmaf(w00, I10 - GLT_PX(r0, c0 - 1),
+                            fmaf(w10, GLT_PX(r0, c0 + 2) - I00,
+                            fmaf(w01, I11 - GLT_PX(r0 + 1, c0 - 1),
+                                 w11 * (GLT_PX(r0 + 1, c0 + 2) - I01))));
+                gy = 0.5f * fmaf(w00, I01 - GLT_PX(r0 - 1, c0),
+                            fmaf(w10, I11 - GLT_PX(r0 - 1, c0 + 1),
+                            fmaf(w01, GLT_PX(r0 + 2, c0) - I00,
+                                 w11 * (GLT_PX(r0 + 2, c0 + 1) - I10))));
+            }
             accumulate_sample(G, I, gx, gy, i0[k], P.ea, P.b, D.huber_k, acc,
                               RES ? res + 8 * p + k : nullptr);
         }
@@ -249,12 +275,13 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
             const float y01 = __low2float(*reinterpret_cast<const __half2*>(&p01.y));
             const float y11 = __low2float(*reinterpret_cast<const __half2*>(&p11.y));
             const float I = fmaf(w00, a00.x, fmaf(w10, a10.x, fmaf(w01, a01.x, w11 * a11.x)));
-            const float gx = fmaf(w00, a00.y, fmaf(w10, a10.y, fmaf(w01, a01.y, w11 * a11.y)));
-            const float gy = fmaf(w00, y00, fmaf(w10, y10, fmaf(w01, y01, w11 * y11)));
+            const float gx = ic ? P.ea * GLT_G0(k, 0) : fmaf(w00, a00.y, fmaf(w10, a10.y, fmaf(w01, a01.y, w11 * a11.y)));
+            const float gy = ic ? P.ea * GLT_G0(k, 1) : fmaf(w00, y00, fmaf(w10, y10, fmaf(w01, y01, w11 * y11)));
             accumulate_sample(G, I, gx, gy, i0[k], P.ea, P.b, D.huber_k, acc,
                               RES ? res + 8 * p + k : nullptr);
         }
     }
+#undef GLT_G0
 }
 
 // ---------------------------------------------------------------------------

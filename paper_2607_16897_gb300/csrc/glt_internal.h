@@ -58,6 +58,7 @@ struct glt_tracker {
     float4* pt = nullptr;
     float2* dz = nullptr;
     float* I0 = nullptr;
+    float2* G0 = nullptr;                 // GLT_IC reference gradients [L][Npad][8]
     int Npad = 0;
     int N = 0;
     bool have_points = false;

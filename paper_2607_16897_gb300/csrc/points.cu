@@ -1,6 +1,8 @@
-// Map-point upload (GLidE-SLAM Sec. IV-C "Precompute", the part the forward
-// form needs): back-project each point and sample its reference patch I0 at
-// the 8 pattern offsets on every REF level (Eq. 2's I0(u_i^0 + du_k)).
+// Map-point upload (GLidE-SLAM Sec. IV-C "Precompute"): back-project each
+// point and sample its reference patch I0 at the 8 pattern offsets on every
+// REF level (Eq. 2's I0(u_i^0 + du_k)); in the inverse-compositional form
+// also the reference gradient there (the image part of the cached Jacobian
+// rows of Sec. IV-B; the geometric part at x_r follows from the point).
 #include "glt_internal.h"
 
 namespace glt {
@@ -16,7 +18,7 @@ struct RefLevels {
 __global__ void set_points_kernel(const StreamDesc* __restrict__ desc, RefLevels ref,
                                   const float* __restrict__ uvd, float cx, float cy,
                                   float4* __restrict__ pt, float2* __restrict__ dz,
-                                  float* __restrict__ I0)
+                                  float* __restrict__ I0, float2* __restrict__ G0)
 {
     const StreamDesc& D = *desc;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -37,6 +39,11 @@ __global__ void set_points_kernel(const StreamDesc* __restrict__ desc, RefLevels
             const float nan = __int_as_float(0x7fc00000);
             out[0] = make_float4(nan, 0.f, 0.f, 0.f);
             out[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (G0) {
+                float4* g = reinterpret_cast<float4*>(G0 + ((size_t)l * D.Npad + p) * 8);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) g[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
             continue;
         }
         const float al = U - fu, be = V - fv;
@@ -51,6 +58,27 @@ __global__ void set_points_kernel(const StreamDesc* __restrict__ desc, RefLevels
         }
         out[0] = make_float4(v[0], v[1], v[2], v[3]);
         out[1] = make_float4(v[4], v[5], v[6], v[7]);
+        if (G0) {
+            // central differences at the four taps, bilinear weights, then the 1/2
+            float gg[16];
+            const int P = lv.pitch;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint8_t* t = img + (size_t)(yb + pat_dy(k)) * P + (xb + pat_dx(k));
+                const float I00 = t[0], I10 = t[1], I01 = t[P], I11 = t[P + 1];
+                gg[2 * k] = 0.5f * fmaf(w00, I10 - (float)t[-1],
+                                   fmaf(w10, (float)t[2] - I00,
+                                   fmaf(w01, I11 - (float)t[P - 1],
+                                        w11 * ((float)t[P + 2] - I01))));
+                gg[2 * k + 1] = 0.5f * fmaf(w00, I01 - (float)t[-P],
+                                       fmaf(w10, I11 - (float)t[1 - P],
+                                       fmaf(w01, (float)t[2 * P] - I00,
+                                            w11 * ((float)t[2 * P + 1] - I10))));
+            }
+            float4* g = reinterpret_cast<float4*>(G0 + ((size_t)l * D.Npad + p) * 8);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) g[k] = make_float4(gg[4 * k], gg[4 * k + 1], gg[4 * k + 2], gg[4 * k + 3]);
+        }
     }
 }
 
@@ -62,7 +90,7 @@ cudaError_t launch_set_points(const glt_tracker* t, const float* uvd_dev, int n,
     RefLevels ref{};
     for (int l = 0; l < t->L; ++l) ref.img[l] = t->pyr[GLT_REF].base + t->pyr[GLT_REF].off[l];
     set_points_kernel<<<blocks, threads, 0, s>>>(t->desc_dev, ref, uvd_dev, (float)t->cfg.cx,
-                                                 (float)t->cfg.cy, t->pt, t->dz, t->I0);
+                                                 (float)t->cfg.cy, t->pt, t->dz, t->I0, t->G0);
     return cudaGetLastError();
 }
 

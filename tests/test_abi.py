@@ -54,7 +54,8 @@ def test_host_side_argument_checks(lib_path):
     """Config validation happens before any device call, so it runs without a GPU."""
     import paper_2607_16897_gb300 as glt
     bad = [dict(levels=0), dict(levels=9), dict(huber_k=0.0), dict(max_points=0),
-           dict(precision=7), dict(cluster=17), dict(threads=100), dict(levels=7)]
+           dict(precision=7), dict(cluster=17), dict(threads=100), dict(levels=7),
+           dict(jacobian=3)]
     for kw in bad:
         c = glt.default_config(320, 240, (256, 256, 160, 120), **kw)
         h = ctypes.c_void_p()
