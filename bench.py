@@ -49,6 +49,9 @@ def parse():
                          "learned proposal, against the plain form on the same streams")
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="frames the oracle tracks for cpu_baseline (0 = auto, ~10-30 s)")
+    ap.add_argument("--jacobian", default="forward", choices=["forward", "ic"],
+                    help="Jacobian form: forward (current image, default) or ic "
+                         "(inverse compositional, reference-side rows cached per reference)")
     ap.add_argument("--shape", default=None,
                     help="batched forms: fixed tile shape 'cluster,threads' instead of the "
                          "autotuner's pick (profiling runs, where the tuner's timings are distorted)")
@@ -73,6 +76,7 @@ class Workload:
         self.frames = [self.seq.frame(k)[0] for k in range(frames)] if render else None
         self.N, self.L = N, L
         self.refs = {}
+        self.jacobian = "forward"
         self.name = (f"{label}: {W}x{H} uint8, fx=fy={f:g}, {frames}-frame sequence "
                      f"({speed:g} m/s, {ang:g} deg/s), N={N} points, L={L}, Huber 9, "
                      f"<=10 LM iters/level, const-velocity init, reference every 8 frames")
@@ -244,7 +248,7 @@ def oracle_track_sequence(wl, frames, inits=None, proposal=None, motions=None):
     initial state, with motions[k] the network's motion input."""
     import oracle
     K = wl.cam.K
-    trk = oracle.OracleTracker(wl.cam.W, wl.cam.H, K, levels=wl.L)
+    trk = oracle.OracleTracker(wl.cam.W, wl.cam.H, K, levels=wl.L, jacobian=wl.jacobian)
     drv = SequenceDriver(wl)
     t_track = 0.0
     out, used = {}, {}
@@ -297,6 +301,8 @@ def run_reference(args):
         wls = batch_workloads(args.workload, rank, pool=pool)
         pool.close()
         pool.join()
+        for w in wls:
+            w.jacobian = args.jacobian
         pw = None
         if args.workload == "c5":
             from oracle import nn as onn
@@ -314,6 +320,7 @@ def run_reference(args):
         cores = workers
     else:
         wl = single_workload(args.workload, rank)
+        wl.jacobian = args.jacobian
         n = min(len(wl.frames) - 1, W + K)
         t, _, _ = oracle_track_sequence(wl, n)
         frames = n
@@ -324,7 +331,7 @@ def run_reference(args):
     line = {"metric": "frames tracked/s", "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
             "steps": K, "warmup": W, "ms_per_step": 1000.0 * t / frames, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference", "config": {"workload": name},
+            "impl": "reference", "config": {"workload": name, "jacobian": args.jacobian},
             "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0,
@@ -348,11 +355,13 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     wl = single_workload(args.workload, rank)   # replicas: one independent stream per GPU
+    wl.jacobian = args.jacobian
     precision = "mixed" if args.workload == "c4" else "fp32"
     Wd, Hd, L, N = wl.cam.W, wl.cam.H, wl.L, wl.N
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
-    trk = glt.Tracker(Wd, Hd, wl.cam.K, levels=L, max_points=N, precision=precision)
+    trk = glt.Tracker(Wd, Hd, wl.cam.K, levels=L, max_points=N, precision=precision,
+                      jacobian=wl.jacobian)
     frames_dev = torch.from_numpy(np.stack(wl.frames)).to(f"cuda:{local}")
     frames_pin = torch.from_numpy(np.stack(wl.frames)).pin_memory()
     init_dev = torch.zeros(14, dtype=torch.float64, device=f"cuda:{local}")
@@ -480,7 +489,8 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f16 storage / f32 math" if precision == "mixed" else "f32",
                 "data": "synthetic",
-                "config": {"workload": wl.name, "global_batch": world, "streams_per_gpu": 1,
+                "config": {"workload": wl.name, "jacobian": args.jacobian, "global_batch": world,
+                           "streams_per_gpu": 1,
                            "parallelism": f"replicas x{world}",
                            "l2": "flushed between steps (256 MB write, outside the step events)",
                            "timing": "sum of per-step CUDA-event times (pyramid + track)"},
@@ -567,11 +577,12 @@ def linearization_error(glt, wl, rec_entry, precision):
     |dH|_F / |H|_F, |dg| / |g|, |dE| / E, and whether the sample counts match."""
     import oracle
     k, r, T_init, ab, _ = rec_entry
-    trk = glt.Tracker(wl.cam.W, wl.cam.H, wl.cam.K, levels=wl.L, max_points=wl.N, precision=precision)
+    trk = glt.Tracker(wl.cam.W, wl.cam.H, wl.cam.K, levels=wl.L, max_points=wl.N, precision=precision,
+                      jacobian=wl.jacobian)
     trk.build_pyramid(glt.GLT_REF, wl.frames[r])
     trk.set_map_points(wl.ref_points(r))
     trk.build_pyramid(glt.GLT_CUR, wl.frames[k])
-    o = oracle.OracleTracker(wl.cam.W, wl.cam.H, wl.cam.K, levels=wl.L)
+    o = oracle.OracleTracker(wl.cam.W, wl.cam.H, wl.cam.K, levels=wl.L, jacobian=wl.jacobian)
     o.build_pyramid(0, wl.frames[r])
     o.set_map_points(wl.ref_points(r))
     o.build_pyramid(1, wl.frames[k])
@@ -652,6 +663,8 @@ def run_batch(args):
     wls = batch_workloads(args.workload, rank, pool=pool)
     pool.close()
     pool.join()
+    for w in wls:
+        w.jacobian = args.jacobian
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
     dist = None
@@ -664,8 +677,8 @@ def run_batch(args):
     F = len(wls[0].frames)
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
-    trks = [glt.Tracker(w.cam.W, w.cam.H, w.cam.K, levels=w.L, max_points=w.N, precision=precision)
-            for w in wls]
+    trks = [glt.Tracker(w.cam.W, w.cam.H, w.cam.K, levels=w.L, max_points=w.N, precision=precision,
+                        jacobian=w.jacobian) for w in wls]
     batch = glt.Batch(trks)
     frames_dev = [torch.from_numpy(np.stack(w.frames)).to(dev) for w in wls]
     frames_pin = [torch.from_numpy(np.stack(w.frames)).pin_memory() for w in wls]
@@ -857,6 +870,7 @@ def run_batch(args):
                 "config": {"workload": (f"{args.workload.upper()} batched: {S} streams in one graph "
                                         f"replay (pyramids + one persistent track launch); " + desc
                                         + f", {F}-frame sequences, reference every 8 frames"),
+                           "jacobian": args.jacobian,
                            "global_batch": world * S, "streams_per_gpu": S,
                            "parallelism": f"replicas x{world}",
                            "autotuned_shape": {"cluster": shape[0], "threads": shape[1],
