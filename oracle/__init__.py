@@ -66,7 +66,8 @@ class _Config(ctypes.Structure):
                 ("eps_step", ctypes.c_double), ("eps_step_coarse", ctypes.c_double),
                 ("eps_cost", ctypes.c_double),
                 ("accept_step", ctypes.c_double), ("min_valid", ctypes.c_int),
-                ("zmin", ctypes.c_double), ("ic", ctypes.c_int)]
+                ("zmin", ctypes.c_double), ("ic", ctypes.c_int), ("pattern", ctypes.c_int),
+                ("affine", ctypes.c_int)]
 
 
 class _Result(ctypes.Structure):
@@ -95,9 +96,13 @@ def _load():
                                           dp, dp, dp, ip, dp, dp, dp, u8p]
             lib.orc_track.argtypes = [dp, i, i, _Cam, dp, dp, u8p, i, P(_Config), dp, d, d,
                                       P(_Result), dp, ip, dp, i]
-            lib.orc_ic_jacobian.argtypes = [dp, i, i, _Cam, i, dp, fp, u8p, i, dp]
-            lib.orc_linearize2.argtypes = [dp, i, i, _Cam, i, dp, dp, u8p, dp, i, dp, d, d, d, d,
-                                           dp, dp, dp, ip, dp, dp, dp, u8p]
+            lib.orc_ic_jacobian.argtypes = [dp, i, i, _Cam, i, dp, fp, u8p, i, i, dp]
+            lib.orc_linearize2.argtypes = [dp, i, i, _Cam, i, dp, dp, u8p, dp, i, i, dp, d, d, d,
+                                           d, dp, dp, dp, ip, dp, dp, dp, u8p]
+            lib.orc_ref_patch2.argtypes = [dp, i, i, i, fp, i, i, dp, u8p]
+            lib.orc_pattern.argtypes = [i, ip, ip]
+            lib.orc_pattern.restype = i
+            lib.orc_ref_patch2.restype = None
             lib.orc_track2.argtypes = [dp, i, i, _Cam, dp, dp, u8p, dp, i, P(_Config), dp, d, d,
                                        P(_Result), dp, ip, dp, i]
             for fn in (lib.orc_pyr_down, lib.orc_build_pyramid, lib.orc_se3_exp, lib.orc_se3_log,
@@ -191,22 +196,33 @@ def backproject(K, uvd) -> np.ndarray:
     return x
 
 
-def ref_patch(img_l, level: int, uvd):
-    """I0 [N, 8] and validity [N] of one level.  img_l: the level image (any
-    real dtype, converted exactly to double)."""
+def pattern_offsets(pattern: int = 0):
+    """(dx, dy) of the pattern's samples: 0 = the 8-pixel pattern, odd p = p x p."""
+    dx = np.zeros(121, np.int32)
+    dy = np.zeros(121, np.int32)
+    K = _load().orc_pattern(int(pattern), _p(dx, ctypes.c_int), _p(dy, ctypes.c_int))
+    if K == 0:
+        raise ValueError(f"unknown pattern {pattern}")
+    return dx[:K].copy(), dy[:K].copy()
+
+
+def ref_patch(img_l, level: int, uvd, pattern: int = 0):
+    """I0 [N, K] and validity [N] of one level (K samples of the pattern).
+    img_l: the level image (any real dtype, converted exactly to double)."""
     img = _f64(img_l)
     H, W = img.shape
     uvd = np.ascontiguousarray(uvd, np.float32).reshape(-1, 3)
     N = uvd.shape[0]
-    I0 = np.zeros((N, 8))
+    K = len(pattern_offsets(pattern)[0])
+    I0 = np.zeros((N, K))
     valid = np.zeros(N, np.uint8)
-    _load().orc_ref_patch(_p(img, ctypes.c_double), W, H, level, _p(uvd, ctypes.c_float), N,
-                          _p(I0, ctypes.c_double), _p(valid, ctypes.c_uint8))
+    _load().orc_ref_patch2(_p(img, ctypes.c_double), W, H, level, _p(uvd, ctypes.c_float), N,
+                           int(pattern), _p(I0, ctypes.c_double), _p(valid, ctypes.c_uint8))
     return I0, valid
 
 
-def ic_jacobian(ref_l, K0, level, x_r, uvd, valid_l):
-    """Inverse-compositional cache of one level: [N, 8, 6] reference-side
+def ic_jacobian(ref_l, K0, level, x_r, uvd, valid_l, pattern: int = 0):
+    """Inverse-compositional cache of one level: [N, K, 6] reference-side
     pose Jacobian rows (zero for unusable points)."""
     img = _f64(ref_l)
     H, W = img.shape
@@ -214,20 +230,22 @@ def ic_jacobian(ref_l, K0, level, x_r, uvd, valid_l):
     N = x_r.shape[0]
     uvd = np.ascontiguousarray(uvd, np.float32).reshape(-1, 3)
     valid_l = np.ascontiguousarray(valid_l, np.uint8)
-    out = np.zeros(N * 48)
+    K = len(pattern_offsets(pattern)[0])
+    out = np.zeros(N * K * 6)
     _load().orc_ic_jacobian(_p(img, ctypes.c_double), W, H, _cam(K0), int(level),
                             _p(x_r, ctypes.c_double), _p(uvd, ctypes.c_float),
-                            _p(valid_l, ctypes.c_uint8), N, _p(out, ctypes.c_double))
-    return out.reshape(N, 8, 6)
+                            _p(valid_l, ctypes.c_uint8), N, int(pattern), _p(out, ctypes.c_double))
+    return out.reshape(N, K, 6)
 
 
 def linearize(img_l, K0, level, x_r, I0_l, valid_l, T, a, b, huber_k=9.0, zmin=1e-3,
-              per_sample=True, Jic=None):
+              per_sample=True, Jic=None, pattern=0):
     img = _f64(img_l)
     H, W = img.shape
     x_r = _f64(x_r)
     N = x_r.shape[0]
-    I0_l = _f64(I0_l)
+    K = len(pattern_offsets(pattern)[0])
+    I0_l = _f64(I0_l).reshape(N * K)
     valid_l = np.ascontiguousarray(valid_l, np.uint8)
     T = _f64(T).reshape(12)
     Hm = np.zeros(64)
@@ -236,22 +254,22 @@ def linearize(img_l, K0, level, x_r, I0_l, valid_l, T, a, b, huber_k=9.0, zmin=1
     n = ctypes.c_int()
     res = jac = wts = pv = None
     if per_sample:
-        res = np.zeros(N * 8)
-        jac = np.zeros(N * 64)
-        wts = np.zeros(N * 8)
+        res = np.zeros(N * K)
+        jac = np.zeros(N * K * 8)
+        wts = np.zeros(N * K)
         pv = np.zeros(N, np.uint8)
-    Jic = None if Jic is None else _f64(Jic).reshape(N * 48)
+    Jic = None if Jic is None else _f64(Jic).reshape(N * K * 6)
     _load().orc_linearize2(_p(img, ctypes.c_double), W, H, _cam(K0), int(level),
                           _p(x_r, ctypes.c_double), _p(I0_l, ctypes.c_double),
                           _p(valid_l, ctypes.c_uint8), _p(Jic, ctypes.c_double), N,
-                          _p(T, ctypes.c_double), float(a),
+                          int(pattern), _p(T, ctypes.c_double), float(a),
                           float(b), float(huber_k), float(zmin), _p(Hm, ctypes.c_double),
                           _p(g, ctypes.c_double), ctypes.byref(E), ctypes.byref(n),
                           _p(res, ctypes.c_double), _p(jac, ctypes.c_double),
                           _p(wts, ctypes.c_double), _p(pv, ctypes.c_uint8))
     out = {"H": Hm.reshape(8, 8), "g": g, "E": E.value, "n": n.value}
     if per_sample:
-        out.update(res=res.reshape(N, 8), J=jac.reshape(N, 8, 8), w=wts.reshape(N, 8),
+        out.update(res=res.reshape(N, K), J=jac.reshape(N, K, 8), w=wts.reshape(N, K),
                    point_valid=pv.astype(bool))
     return out
 
@@ -261,7 +279,7 @@ def linearize(img_l, K0, level, x_r, I0_l, valid_l, T, a, b, huber_k=9.0, zmin=1
 # --------------------------------------------------------------------------
 DEFAULT_CONFIG = dict(levels=4, max_iters=[10] * 8, huber_k=9.0, lambda0=1e-4, lambda_up=4.0,
                       lambda_down=0.5, eps_step=1e-6, eps_step_coarse=3e-4, eps_cost=0.0, accept_step=1e-3,
-                      min_valid=16, zmin=1e-3, jacobian="forward")
+                      min_valid=16, zmin=1e-3, jacobian="forward", pattern=0, affine=True)
 
 
 def make_config(**kw) -> dict:
@@ -288,6 +306,8 @@ def _cconfig(c: dict) -> _Config:
     cc.min_valid = int(c["min_valid"])
     cc.zmin = float(c["zmin"])
     cc.ic = {"forward": 0, "ic": 1}[c["jacobian"]]
+    cc.pattern = int(c["pattern"])
+    cc.affine = 1 if c["affine"] else 0
     return cc
 
 
@@ -299,7 +319,8 @@ def track(cur_levels, K0, x_r, I0, valid, cfg: dict, T_init, a0=0.0, b0=0.0, Jic
     flat = np.concatenate([_f64(cur_levels[l]).ravel() for l in range(L)])
     x_r = _f64(x_r)
     N = x_r.shape[0]
-    I0 = _f64(I0).reshape(L, N, 8)
+    K = len(pattern_offsets(cfg["pattern"])[0])
+    I0 = _f64(I0).reshape(L, N, K)
     valid = np.ascontiguousarray(valid, np.uint8).reshape(L, N)
     T = _f64(T_init).reshape(12)
     cc = _cconfig(cfg)
@@ -310,7 +331,7 @@ def track(cur_levels, K0, x_r, I0, valid, cfg: dict, T_init, a0=0.0, b0=0.0, Jic
     ts = np.zeros(max(mt, 1))
     if cfg["jacobian"] == "ic" and Jic is None:
         raise ValueError("the inverse-compositional solve needs its Jacobian cache")
-    Jic = None if Jic is None else _f64(Jic).reshape(L * N * 48)
+    Jic = None if Jic is None else _f64(Jic).reshape(L * N * K * 6)
     _load().orc_track2(_p(flat, ctypes.c_double), W0, H0, _cam(K0), _p(x_r, ctypes.c_double),
                       _p(I0, ctypes.c_double), _p(valid, ctypes.c_uint8), _p(Jic, ctypes.c_double),
                       N, ctypes.byref(cc),
@@ -353,19 +374,22 @@ class OracleTracker:
         self.uvd = uvd
         self.x_r = backproject(self.K, uvd)
         N = uvd.shape[0]
-        self.I0 = np.zeros((self.L, N, 8))
+        pat = self.cfg["pattern"]
+        K = len(pattern_offsets(pat)[0])
+        self.I0 = np.zeros((self.L, N, K))
         self.valid = np.zeros((self.L, N), np.uint8)
         for l in range(self.L):
-            self.I0[l], self.valid[l] = ref_patch(self.pyr[self.REF][l], l, uvd)
+            self.I0[l], self.valid[l] = ref_patch(self.pyr[self.REF][l], l, uvd, pat)
         self.Jic = None
         if self.cfg["jacobian"] == "ic":
             self.Jic = np.stack([ic_jacobian(self.pyr[self.REF][l], self.K, l, self.x_r, uvd,
-                                             self.valid[l]) for l in range(self.L)])
+                                             self.valid[l], pat) for l in range(self.L)])
 
     def debug_linearize(self, level, T, a, b, per_sample=True):
         return linearize(self.pyr[self.CUR][level], self.K, level, self.x_r, self.I0[level],
                          self.valid[level], T, a, b, self.cfg["huber_k"], self.cfg["zmin"],
-                         per_sample, Jic=None if self.Jic is None else self.Jic[level])
+                         per_sample, Jic=None if self.Jic is None else self.Jic[level],
+                         pattern=self.cfg["pattern"])
 
     def track_frame(self, T_init, ab_init=(0.0, 0.0)) -> dict:
         return track(self.pyr[self.CUR], self.K, self.x_r, self.I0, self.valid, self.cfg,

@@ -28,6 +28,26 @@ const int orc_pattern_dy[8] = {0, 0, 0, -2, 2, -1, -1, 1};
  * each direction, clamp-to-edge borders, even-sample decimation, exact
  * integer sum with round-half-up: p_l(x,y) = (sum w_i w_j p(2x+i, 2y+j) + 128) >> 8.
  * ------------------------------------------------------------------------ */
+int orc_pattern(int pattern, int* dx, int* dy)
+{
+    if (pattern == 0) {
+        for (int k = 0; k < 8; ++k) {
+            dx[k] = orc_pattern_dx[k];
+            dy[k] = orc_pattern_dy[k];
+        }
+        return 8;
+    }
+    if (pattern < 3 || pattern > 11 || (pattern & 1) == 0) return 0;
+    int h = (pattern - 1) / 2, K = 0;
+    for (int j = -h; j <= h; ++j)
+        for (int i = -h; i <= h; ++i) {
+            dx[K] = i;
+            dy[K] = j;
+            ++K;
+        }
+    return K;
+}
+
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 void orc_pyr_down(const uint8_t* src, int W, int H, int pitch, uint8_t* dst)
@@ -252,15 +272,22 @@ static void bilinear_grad(const double* img, int W, double qx, double qy, double
 void orc_ref_patch(const double* img, int W, int H, int level, const float* uvd, int N,
                    double* I0, uint8_t* valid)
 {
+    orc_ref_patch2(img, W, H, level, uvd, N, 0, I0, valid);
+}
+
+void orc_ref_patch2(const double* img, int W, int H, int level, const float* uvd, int N,
+                    int pattern, double* I0, uint8_t* valid)
+{
+    int dx[121], dy[121];
+    int K = orc_pattern(pattern, dx, dy);
     double s = ldexp(1.0, -level);
     for (int i = 0; i < N; ++i) {
         double u = uvd[3 * i] * s, v = uvd[3 * i + 1] * s;
         int ok = uvd[3 * i + 2] > 0; /* a map point needs a positive depth */
-        for (int k = 0; k < 8 && ok; ++k)
-            ok = sample_inside(u + orc_pattern_dx[k], v + orc_pattern_dy[k], W, H);
+        for (int k = 0; k < K && ok; ++k) ok = sample_inside(u + dx[k], v + dy[k], W, H);
         valid[i] = (uint8_t)ok;
-        for (int k = 0; k < 8; ++k)
-            I0[8 * i + k] = ok ? bilinear(img, W, u + orc_pattern_dx[k], v + orc_pattern_dy[k]) : 0.0;
+        for (int k = 0; k < K; ++k)
+            I0[(size_t)K * i + k] = ok ? bilinear(img, W, u + dx[k], v + dy[k]) : 0.0;
     }
 }
 
@@ -270,14 +297,16 @@ void orc_ref_patch(const double* img, int W, int H, int level, const float* uvd,
  * Sec. IV-C "Precompute IC": computed once per reference and level).
  * ------------------------------------------------------------------------ */
 void orc_ic_jacobian(const double* ref, int W, int H, orc_cam K0, int level, const double* x_r,
-                     const float* uvd, const uint8_t* valid_ref, int N, double* Jic)
+                     const float* uvd, const uint8_t* valid_ref, int N, int pattern, double* Jic)
 {
+    int dx[121], dy[121];
+    int K = orc_pattern(pattern, dx, dy);
     double s = ldexp(1.0, -level);
     double fx = K0.fx * s, fy = K0.fy * s;
     (void)H;
     for (int i = 0; i < N; ++i) {
-        double* Ji = Jic + (size_t)i * 48;
-        memset(Ji, 0, 48 * sizeof(double));
+        double* Ji = Jic + (size_t)i * K * 6;
+        memset(Ji, 0, (size_t)K * 6 * sizeof(double));
         if (!valid_ref[i]) continue;
         const double* X = x_r + 3 * i;
         /* dpi/dx at x_r and [I | -[x_r]x] */
@@ -296,9 +325,9 @@ void orc_ic_jacobian(const double* ref, int W, int H, orc_cam K0, int level, con
                 Jg[6 * r + c] = acc;
             }
         double u = uvd[3 * i] * s, v = uvd[3 * i + 1] * s;
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < K; ++k) {
             double gx, gy;
-            bilinear_grad(ref, W, u + orc_pattern_dx[k], v + orc_pattern_dy[k], &gx, &gy);
+            bilinear_grad(ref, W, u + dx[k], v + dy[k], &gx, &gy);
             for (int c = 0; c < 6; ++c) Ji[6 * k + c] = gx * Jg[c] + gy * Jg[6 + c];
         }
     }
@@ -314,16 +343,18 @@ void orc_linearize(const double* img, int W, int H, orc_cam K0, int level, const
                    double a, double b, double huber_k, double zmin, double* Hout, double* g,
                    double* E, int* n, double* res, double* jac, double* wts, uint8_t* pvalid)
 {
-    orc_linearize2(img, W, H, K0, level, x_r, I0, valid_ref, NULL, N, T, a, b, huber_k, zmin,
+    orc_linearize2(img, W, H, K0, level, x_r, I0, valid_ref, NULL, N, 0, T, a, b, huber_k, zmin,
                    Hout, g, E, n, res, jac, wts, pvalid);
 }
 
 void orc_linearize2(const double* img, int W, int H, orc_cam K0, int level, const double* x_r,
                     const double* I0, const uint8_t* valid_ref, const double* Jic, int N,
-                    const double T[12], double a, double b, double huber_k, double zmin,
-                    double* Hout, double* g, double* E, int* n, double* res, double* jac,
-                    double* wts, uint8_t* pvalid)
+                    int pattern, const double T[12], double a, double b, double huber_k,
+                    double zmin, double* Hout, double* g, double* E, int* n, double* res,
+                    double* jac, double* wts, uint8_t* pvalid)
 {
+    int pdx[121], pdy[121];
+    int K = orc_pattern(pattern, pdx, pdy);
     double s = ldexp(1.0, -level);
     double fx = K0.fx * s, fy = K0.fy * s, cx = K0.cx * s, cy = K0.cy * s;
     double R[9] = {T[0], T[1], T[2], T[4], T[5], T[6], T[8], T[9], T[10]};
@@ -336,9 +367,9 @@ void orc_linearize2(const double* img, int W, int H, orc_cam K0, int level, cons
     for (int i = 0; i < N; ++i) {
         const double* X = x_r + 3 * i;
         if (res)
-            for (int k = 0; k < 8; ++k) res[8 * i + k] = NAN;
-        if (jac) memset(jac + 64 * (size_t)i, 0, 64 * sizeof(double));
-        if (wts) memset(wts + 8 * (size_t)i, 0, 8 * sizeof(double));
+            for (int k = 0; k < K; ++k) res[(size_t)K * i + k] = NAN;
+        if (jac) memset(jac + (size_t)K * 8 * i, 0, (size_t)K * 8 * sizeof(double));
+        if (wts) memset(wts + (size_t)K * i, 0, (size_t)K * sizeof(double));
         if (pvalid) pvalid[i] = 0;
         if (!valid_ref[i]) continue;
         /* x_c = R x_r + t; pi(x_c) with level intrinsics (Eq. 1) */
@@ -348,7 +379,7 @@ void orc_linearize2(const double* img, int W, int H, orc_cam K0, int level, cons
         double u = fx * xc[0] / xc[2] + cx;
         double v = fy * xc[1] / xc[2] + cy;
         int ok = 1;
-        for (int k = 0; k < 8 && ok; ++k) ok = sample_inside(u + orc_pattern_dx[k], v + orc_pattern_dy[k], W, H);
+        for (int k = 0; k < K && ok; ++k) ok = sample_inside(u + pdx[k], v + pdy[k], W, H);
         if (!ok) continue;
         if (pvalid) pvalid[i] = 1;
         /* geometric Jacobian d u / d delta_xi = dpi/dx_c * R [I | -[x_r]x]
@@ -373,12 +404,12 @@ void orc_linearize2(const double* img, int W, int H, orc_cam K0, int level, cons
                 for (int k = 0; k < 3; ++k) acc += dpi[3 * r + k] * M[6 * k + c];
                 Jg[6 * r + c] = acc;
             }
-        for (int k = 0; k < 8; ++k) {
-            double qx = u + orc_pattern_dx[k], qy = v + orc_pattern_dy[k];
+        for (int k = 0; k < K; ++k) {
+            double qx = u + pdx[k], qy = v + pdy[k];
             double I = bilinear(img, W, qx, qy);
             double gx, gy;
             bilinear_grad(img, W, qx, qy, &gx, &gy);
-            double i0 = I0[8 * i + k];
+            double i0 = I0[(size_t)K * i + k];
             double r = I - ea * i0 - b;
             /* Huber weight and energy (k = huber_k) */
             double ar = fabs(r);
@@ -386,7 +417,7 @@ void orc_linearize2(const double* img, int W, int H, orc_cam K0, int level, cons
             double rho = ar <= huber_k ? 0.5 * r * r : huber_k * ar - 0.5 * huber_k * huber_k;
             double J[8];
             if (Jic)
-                for (int c = 0; c < 6; ++c) J[c] = ea * Jic[(size_t)i * 48 + 6 * k + c];
+                for (int c = 0; c < 6; ++c) J[c] = ea * Jic[((size_t)K * i + k) * 6 + c];
             else
                 for (int c = 0; c < 6; ++c) J[c] = gx * Jg[c] + gy * Jg[6 + c];
             J[6] = -ea * i0;
@@ -397,9 +428,9 @@ void orc_linearize2(const double* img, int W, int H, orc_cam K0, int level, cons
             }
             *E += rho;
             *n += 1;
-            if (res) res[8 * i + k] = r;
-            if (jac) memcpy(jac + 64 * (size_t)i + 8 * k, J, sizeof(J));
-            if (wts) wts[8 * i + k] = w;
+            if (res) res[(size_t)K * i + k] = r;
+            if (jac) memcpy(jac + ((size_t)K * i + k) * 8, J, sizeof(J));
+            if (wts) wts[(size_t)K * i + k] = w;
         }
     }
 }
@@ -460,7 +491,10 @@ void orc_track(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
                const double T_init[12], double a0, double b0, orc_result* out,
                double* trace_cost, int* trace_info, double* trace_step, int max_trace)
 {
-    orc_track2(cur, W0, H0, K0, x_r, I0, valid, NULL, N, cfg, T_init, a0, b0, out, trace_cost,
+    orc_config c = *cfg;
+    c.pattern = 0;
+    c.ic = 0;
+    orc_track2(cur, W0, H0, K0, x_r, I0, valid, NULL, N, &c, T_init, a0, b0, out, trace_cost,
                trace_info, trace_step, max_trace);
 }
 
@@ -505,14 +539,16 @@ void orc_track2(const double* cur, int W0, int H0, orc_cam K0, const double* x_r
     out->cost = NAN;
     double Hm[64], g[8], E;
     int n;
+    int pdx[121], pdy[121];
+    const int K = orc_pattern(cfg->pattern, pdx, pdy);
     for (int l = L - 1; l >= 0; --l) {
         if (cfg->max_iters[l] <= 0) continue;
         const double* img = cur + off[l];
-        const double* I0l = I0 + (size_t)l * N * 8;
+        const double* I0l = I0 + (size_t)l * N * K;
         const uint8_t* vl = valid + (size_t)l * N;
-        const double* Jl = (cfg->ic && Jic) ? Jic + (size_t)l * N * 48 : NULL;
-        orc_linearize2(img, Ws[l], Hs[l], K0, l, x_r, I0l, vl, Jl, N, T, a, b, cfg->huber_k,
-                       cfg->zmin, Hm, g, &E, &n, NULL, NULL, NULL, NULL);
+        const double* Jl = (cfg->ic && Jic) ? Jic + (size_t)l * N * K * 6 : NULL;
+        orc_linearize2(img, Ws[l], Hs[l], K0, l, x_r, I0l, vl, Jl, N, cfg->pattern, T, a, b,
+                       cfg->huber_k, cfg->zmin, Hm, g, &E, &n, NULL, NULL, NULL, NULL);
         int enough = n >= cfg->min_valid && n > 0;
         trace_pass(out, trace_cost, trace_info, trace_step, max_trace, enough ? E / n : INFINITY,
                    l, 0, 0, 0.0);
@@ -524,10 +560,21 @@ void orc_track2(const double* cur, int W0, int H0, orc_cam K0, const double* x_r
         double lambda = cfg->lambda0;
         int it = 0;
         while (it < cfg->max_iters[l]) {
-            double A[64], delta[8];
+            double A[64], delta[8], gs[8];
             memcpy(A, Hm, sizeof(A));
-            for (int d = 0; d < 8; ++d) A[8 * d + d] += lambda * Hm[8 * d + d];
-            if (!cholesky_solve8(A, g, delta)) {
+            memcpy(gs, g, sizeof(gs));
+            if (!cfg->affine) {
+                /* (a, b) held fixed: the affine rows and columns become the
+                 * identity and their right-hand side zero, so da = db = 0 and
+                 * the pose block is solved alone */
+                for (int r = 6; r < 8; ++r) {
+                    for (int c = 0; c < 8; ++c) A[8 * r + c] = A[8 * c + r] = 0.0;
+                    A[8 * r + r] = 1.0;
+                    gs[r] = 0.0;
+                }
+            }
+            for (int d = 0; d < 8; ++d) A[8 * d + d] += lambda * A[8 * d + d];
+            if (!cholesky_solve8(A, gs, delta)) {
                 out->status |= ORC_NOT_PD;
                 break;
             }
@@ -537,8 +584,8 @@ void orc_track2(const double* cur, int W0, int H0, orc_cam K0, const double* x_r
             double an = a + delta[6], bn = b + delta[7];
             double Hn[64], gn[8], En;
             int nn;
-            orc_linearize2(img, Ws[l], Hs[l], K0, l, x_r, I0l, vl, Jl, N, Tn, an, bn,
-                           cfg->huber_k, cfg->zmin, Hn, gn, &En, &nn, NULL, NULL, NULL, NULL);
+            orc_linearize2(img, Ws[l], Hs[l], K0, l, x_r, I0l, vl, Jl, N, cfg->pattern, Tn, an,
+                           bn, cfg->huber_k, cfg->zmin, Hn, gn, &En, &nn, NULL, NULL, NULL, NULL);
             ++it;
             double m = 0;
             for (int d = 0; d < 6; ++d) m = fmax(m, fabs(delta[d]));

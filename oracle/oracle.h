@@ -45,6 +45,8 @@ typedef struct {
     int min_valid;
     double zmin;
     int ic; /* 0: forward Jacobian (current image), 1: inverse-compositional (reference side) */
+    int pattern; /* 0: the 8-pixel sparse pattern; odd p (3..11): the paper's p x p patch */
+    int affine;  /* 1: estimate (a, b); 0: keep them at their initial values (the paper's form) */
 } orc_config;
 
 typedef struct {
@@ -62,6 +64,15 @@ enum { ORC_TOO_FEW_POINTS = 1, ORC_NOT_PD = 2 };
 /* the 8-pixel sparse pattern, offsets in level pixels */
 extern const int orc_pattern_dx[8];
 extern const int orc_pattern_dy[8];
+
+/* Sample offsets of a pattern (0: the 8-pixel pattern; odd p: the p x p patch
+ * of Sec. IV-A, row by row from (-(p-1)/2, -(p-1)/2)).  Returns the number of
+ * samples K (at most 121), or 0 for an unknown pattern. */
+int orc_pattern(int pattern, int* dx, int* dy);
+
+/* As orc_ref_patch for any pattern: I0[N*K]. */
+void orc_ref_patch2(const double* img, int W, int H, int level, const float* uvd, int N,
+                    int pattern, double* I0, uint8_t* valid);
 
 /* Pyramid (Sec. IV-C "Image pyramids"): one level down. dst is
  * (W/2) x (H/2), row-major contiguous. */
@@ -95,18 +106,20 @@ void orc_linearize(const double* img, int W, int H, orc_cam K0, int level, const
  * "Precompute IC") on level l of the REFERENCE image: for every point and
  * pattern sample k, J_ic[(8 i + k) * 6 + c] = grad I0(u0_l + du_k) dpi/dx(x_r)
  * [I | -[x_r]x], the pose Jacobian evaluated on the reference side (at the
- * identity pose).  Rows of points with valid_ref[i] = 0 are zero. */
+ * identity pose).  Rows of points with valid_ref[i] = 0 are zero.  Layout
+ * [N][K][6] for the pattern's K samples. */
 void orc_ic_jacobian(const double* ref, int W, int H, orc_cam K0, int level, const double* x_r,
-                     const float* uvd, const uint8_t* valid_ref, int N, double* Jic);
+                     const float* uvd, const uint8_t* valid_ref, int N, int pattern, double* Jic);
 
-/* As orc_linearize; with Jic non-NULL the pose columns of each Jacobian row
+/* As orc_linearize for any pattern (I0[N*K], per-sample outputs with K
+ * samples per point); with Jic non-NULL the pose columns of each Jacobian row
  * are e^a J_ic (the template approximation of the current-side Jacobian: the
  * current image's gradient is not used), the affine columns unchanged. */
 void orc_linearize2(const double* img, int W, int H, orc_cam K0, int level, const double* x_r,
                     const double* I0, const uint8_t* valid_ref, const double* Jic, int N,
-                    const double T[12], double a, double b, double huber_k, double zmin,
-                    double* Hout, double* g, double* E, int* n, double* res, double* jac,
-                    double* wts, uint8_t* pvalid);
+                    int pattern, const double T[12], double a, double b, double huber_k,
+                    double zmin, double* Hout, double* g, double* E, int* n, double* res,
+                    double* jac, double* wts, uint8_t* pvalid);
 
 /* Coarse-to-fine LM (Sec. IV-A and the accept/reject schedule of this
  * library).  cur: concatenated double pyramid of the current frame
@@ -119,8 +132,9 @@ void orc_track(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
                const double* I0, const uint8_t* valid, int N, const orc_config* cfg,
                const double T_init[12], double a0, double b0, orc_result* out,
                double* trace_cost, int* trace_info, double* trace_step, int max_trace);
-/* As orc_track; with cfg->ic set, Jic is the [L][N*8*6] inverse-compositional
- * cache of orc_ic_jacobian, used by every linearisation of the solve. */
+/* As orc_track with cfg->pattern (I0 [L][N][K]) and cfg->affine; with cfg->ic
+ * set, Jic is the [L][N*K*6] inverse-compositional cache of orc_ic_jacobian,
+ * used by every linearisation of the solve. */
 void orc_track2(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
                 const double* I0, const uint8_t* valid, const double* Jic, int N,
                 const orc_config* cfg, const double T_init[12], double a0, double b0,
