@@ -85,7 +85,8 @@ typedef struct glt_config {
     int max_points;             /* capacity of glt_set_map_points */
     int max_iters[GLT_MAX_LEVELS]; /* LM candidate evaluations per level (0 skips a level) */
     double huber_k;             /* Huber threshold in gray levels (weight k/|r| beyond it) */
-    double lambda0;             /* initial LM damping of diag(H) at each level start */
+    double lambda0;             /* initial LM damping of diag(H) at each level start
+                                   (>= 0; 0 with accept_step huge is plain Gauss-Newton) */
     double lambda_up;           /* damping factor after a rejected candidate */
     double lambda_down;         /* damping factor after an accepted candidate */
     double eps_step;            /* stop the finest level once max |delta_xi| < eps_step */
@@ -109,6 +110,12 @@ typedef struct glt_config {
                                    instead of the current image's gradient (the
                                    inverse-compositional template approximation;
                                    T <- T exp(delta) as in the paper) */
+    int pattern;                /* 0: the 8-pixel sparse pattern; odd p in 3..11: the
+                                   paper's p x p patch (Sec. IV-A; 7 x 7 and 11 x 11 in
+                                   Sec. V), samples row by row from (-(p-1)/2, -(p-1)/2);
+                                   p x p needs precision GLT_FP32 */
+    int affine;                 /* 1: estimate (a, b); 0: keep the initial (a, b) (the
+                                   paper estimates no brightness change) */
 } glt_config;
 
 typedef struct glt_result {
@@ -127,7 +134,11 @@ typedef struct glt_result {
  * lambda0 1e-4 (x4 up, x0.5 down), eps_step 1e-6 (finest level),
  * eps_step_coarse 3e-4 (coarser levels), eps_cost 0 (off),
  * accept_step 1e-3, min_valid 16, zmin 1e-3, FP32, automatic cluster/threads,
- * max_points 4096, GLT_FORWARD. */
+ * max_points 4096, GLT_FORWARD, the 8-pixel pattern, affine estimated.
+ * The paper's configuration is levels 6, pattern 7 (or 11), affine 0,
+ * jacobian GLT_IC, huber_k very large (no robust weights), lambda0 0,
+ * accept_step very large and eps_step = eps_step_coarse = 0 (plain
+ * Gauss-Newton with a fixed number of iterations per level). */
 void glt_default_config(glt_config* cfg, int width, int height, double fx, double fy,
                         double cx, double cy);
 
@@ -176,7 +187,8 @@ int glt_track_frame_async(glt_tracker* trk, const double* init_dev, glt_result* 
  * the full symmetric H (64 doubles, row-major), g = J^T W r (8; the paper's
  * right-hand side b of Eq. 5 is -g), the Huber energy E and the number of
  * valid samples n, all written to host memory; if `res` is not NULL it gets
- * the N*8 FP32 residuals (NaN for samples of unused points).  Synchronous.
+ * the N*K FP32 residuals, K samples of the pattern per point (8, or p*p),
+ * NaN for samples of unused points.  Synchronous.
  * Uses a multi-block kernel with a single-pass last-block finish. */
 int glt_debug_linearize(glt_tracker* trk, int level, const double T[12], double a, double b,
                         double H[64], double g[8], double* E, int* n, float* res,

@@ -47,7 +47,8 @@ class glt_config(ctypes.Structure):
                 ("eps_cost", ctypes.c_double), ("accept_step", ctypes.c_double),
                 ("min_valid", ctypes.c_int),
                 ("zmin", ctypes.c_double), ("precision", ctypes.c_int), ("cluster", ctypes.c_int),
-                ("threads", ctypes.c_int), ("jacobian", ctypes.c_int)]
+                ("threads", ctypes.c_int), ("jacobian", ctypes.c_int), ("pattern", ctypes.c_int),
+                ("affine", ctypes.c_int)]
 
 
 class glt_result(ctypes.Structure):
@@ -261,7 +262,8 @@ class Tracker:
         g = np.zeros(8)
         E = ctypes.c_double()
         n = ctypes.c_int()
-        res = np.zeros(max(self.N, 1) * 8, np.float32) if want_res else None
+        K = 8 if self.cfg.pattern == 0 else self.cfg.pattern ** 2
+        res = np.zeros(max(self.N, 1) * K, np.float32) if want_res else None
         _check(_lib.glt_debug_linearize(self.handle, int(level), T.ctypes.data_as(_P(_d)),
                                         float(a), float(b), H.ctypes.data_as(_P(_d)),
                                         g.ctypes.data_as(_P(_d)), ctypes.byref(E),
@@ -270,7 +272,7 @@ class Tracker:
                                         _stream_handle(stream)), "glt_debug_linearize")
         out = {"H": H.reshape(8, 8), "g": g, "E": E.value, "n": n.value}
         if want_res:
-            out["res"] = res[:self.N * 8].reshape(self.N, 8)
+            out["res"] = res[:self.N * K].reshape(self.N, K)
         return out
 
     def get_pyramid(self, slot, level, stream=None) -> np.ndarray:

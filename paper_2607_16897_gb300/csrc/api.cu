@@ -95,7 +95,7 @@ static int check_config(const glt_config* c)
     for (int l = 0; l < c->levels; ++l)
         if (c->max_iters[l] < 0 || c->max_iters[l] > 1000) return invalid("max_iters must be in [0, 1000]");
     if (!(c->huber_k > 0) || !std::isfinite(c->huber_k)) return invalid("huber_k must be > 0");
-    if (!(c->lambda0 > 0) || !(c->lambda_up >= 1) || !(c->lambda_down > 0) || !(c->lambda_down <= 1))
+    if (!(c->lambda0 >= 0) || !std::isfinite(c->lambda0) || !(c->lambda_up >= 1) || !(c->lambda_down > 0) || !(c->lambda_down <= 1))
         return invalid("LM damping factors out of range");
     if (!(c->eps_step >= 0) || !(c->eps_step_coarse >= 0) || !(c->eps_cost >= 0) ||
         !(c->accept_step >= 0))
@@ -108,6 +108,11 @@ static int check_config(const glt_config* c)
         return invalid("threads must be 0, 128, 256 or 512");
     if (c->jacobian != GLT_FORWARD && c->jacobian != GLT_IC)
         return invalid("jacobian must be GLT_FORWARD or GLT_IC");
+    if (c->pattern != 0 && (c->pattern < 3 || c->pattern > 11 || (c->pattern & 1) == 0))
+        return invalid("pattern must be 0 (8-pixel) or an odd patch size 3..11");
+    if (c->pattern != 0 && c->precision != GLT_FP32)
+        return invalid("p x p patches need precision GLT_FP32");
+    if (c->affine != 0 && c->affine != 1) return invalid("affine must be 0 or 1");
     return GLT_OK;
 }
 
@@ -164,6 +169,8 @@ void glt_default_config(glt_config* c, int width, int height, double fx, double 
     c->cluster = 0;
     c->threads = 0;
     c->jacobian = GLT_FORWARD;
+    c->pattern = 0;
+    c->affine = 1;
 }
 
 int glt_create(const glt_config* cfg, glt_tracker** out)
@@ -212,8 +219,9 @@ int glt_create(const glt_config* cfg, glt_tracker** out)
     ALLOC(dalloc(&t->uvd_dev, (size_t)maxp * 3));
     ALLOC(dalloc(&t->pt, (size_t)t->Npad));
     ALLOC(dalloc(&t->dz, (size_t)t->Npad));
-    ALLOC(dalloc(&t->I0, (size_t)t->L * t->Npad * 8));
-    if (cfg->jacobian == GLT_IC) ALLOC(dalloc(&t->G0, (size_t)t->L * t->Npad * 8));
+    t->K = cfg->pattern == 0 ? 8 : cfg->pattern * cfg->pattern;
+    ALLOC(dalloc(&t->I0, (size_t)t->L * t->Npad * t->K));
+    if (cfg->jacobian == GLT_IC) ALLOC(dalloc(&t->G0, (size_t)t->L * t->Npad * t->K));
     ALLOC(dalloc(&t->desc_dev, 1));
     ALLOC(dalloc(&t->desc_ptr_dev, 1));
     ALLOC(dalloc(&t->user_dev, 1));
@@ -233,7 +241,7 @@ int glt_create(const glt_config* cfg, glt_tracker** out)
     ALLOC(dalloc(&t->lin_counter, 1));
     ALLOC(cudaMemset(t->lin_counter, 0, sizeof(unsigned)));
     ALLOC(dalloc(&t->lin_out, (size_t)kAccPad));
-    ALLOC(dalloc(&t->lin_res, (size_t)maxp * 8));
+    ALLOC(dalloc(&t->lin_res, (size_t)maxp * t->K));
     ALLOC(cudaMallocHost(reinterpret_cast<void**>(&t->h_init), 14 * sizeof(double)));
     ALLOC(cudaMallocHost(reinterpret_cast<void**>(&t->h_result), sizeof(glt_result)));
     ALLOC(cudaMallocHost(reinterpret_cast<void**>(&t->h_lin), kAccPad * sizeof(double)));
@@ -259,6 +267,9 @@ int glt_create(const glt_config* cfg, glt_tracker** out)
     D.dz = t->dz;
     D.I0 = t->I0;
     D.G0 = t->G0;
+    D.pattern = cfg->pattern;
+    D.K = t->K;
+    D.affine = cfg->affine;
     for (int l = 0; l < GLT_MAX_LEVELS; ++l) D.max_iters[l] = l < t->L ? cfg->max_iters[l] : 0;
     D.min_valid = cfg->min_valid;
     D.max_trace = t->max_trace;
@@ -445,7 +456,7 @@ int glt_debug_linearize(glt_tracker* t, int level, const double T[12], double a,
     GLT_CHECK(cudaMemcpyAsync(t->h_lin, t->lin_out, kAccPad * sizeof(double), cudaMemcpyDeviceToHost, s),
               "linearize download");
     if (res)
-        GLT_CHECK(cudaMemcpyAsync(res, t->lin_res, (size_t)t->N * 8 * sizeof(float), cudaMemcpyDeviceToHost, s),
+        GLT_CHECK(cudaMemcpyAsync(res, t->lin_res, (size_t)t->N * t->K * sizeof(float), cudaMemcpyDeviceToHost, s),
                   "residual download");
     GLT_CHECK(cudaStreamSynchronize(s), "linearize");
     int idx = 0;

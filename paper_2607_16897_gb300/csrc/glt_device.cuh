@@ -44,8 +44,10 @@ struct StreamDesc {
     float huber_k, zmin;
     const float4* pt;      // (u0, v0, (u0-cx)/fx, (v0-cy)/fy)
     const float2* dz;      // (depth, 1/depth)
-    const float* I0;       // [L][Npad][8]; I0[l][p][0] is NaN where the point is unusable
-    const float2* G0;      // GLT_IC: reference gradient (gx, gy) [L][Npad][8], else null
+    const float* I0;       // [L][Npad][K]; I0[l][p][0] is NaN where the point is unusable
+    const float2* G0;      // GLT_IC: reference gradient (gx, gy) [L][Npad][K], else null
+    int pattern, K;        // 0 and 8: the 8-pixel pattern; p and p*p: the p x p patch
+    int affine;            // 0: (a, b) held at their initial values
     int max_iters[kMaxLevels];
     int min_valid;
     int max_trace;
@@ -112,7 +114,8 @@ __device__ __forceinline__ bool project_point(const StreamDesc& D, const PassPar
     G.be = sv - fv;
     G.xb = (int)Ui + (int)fu;
     G.yb = (int)Vi + (int)fv;
-    if (G.xb < 3 || G.xb > lv.W - 5 || G.yb < 3 || G.yb > lv.H - 5) return false;
+    const int h = D.pattern ? (D.pattern - 1) / 2 : 2;   // half extent of the pattern
+    if (G.xb < 1 + h || G.xb > lv.W - 3 - h || G.yb < 1 + h || G.yb > lv.H - 3 - h) return false;
     // d(pi)/d(x_c) R, with x_c / z_c = (m + D) / (1 + D_z) and 1/z_c = rho / (1 + D_z)
     const float xn = (ub + Dx) * iz, yn = (vb + Dy) * iz;
     const float fxl = D.fx * s * rho * iz, fyl = D.fy * s * rho * iz;
@@ -172,22 +175,80 @@ __device__ __forceinline__ void accumulate_sample(const PointGeom& G, float I, f
     acc[kIdxN] += 1.0f;
 }
 
-// Linearises map point p at the pass state into acc.  RES: also write the 8
-// residuals (NaN for an unusable point) to res[8p..8p+7].
+// The p x p patch (the paper's Sec. IV-A patch): K = p*p samples read one by
+// one (four taps, plus the gradient taps in the forward form) through the
+// read-only cache; FP32 levels only.
+static __device__ __noinline__ void linearize_square(const StreamDesc& D, const PassParams& P, int p,
+                                              PointGeom& G, float* acc, float* res)
+{
+    const LevelDev& lv = D.lv[P.level];
+    const int K = D.K, h = (D.pattern - 1) / 2, S = lv.pitch;
+    const bool ic = D.G0 != nullptr;
+    if (ic) {
+        const float4 q = D.pt[p];
+        const float rho = D.dz[p].y;
+        const float fxl = D.fx * P.scale * rho, fyl = D.fy * P.scale * rho;
+        G.a0[0] = fxl;
+        G.a0[1] = 0.0f;
+        G.a0[2] = -fxl * q.z;
+        G.a1[0] = 0.0f;
+        G.a1[1] = fyl;
+        G.a1[2] = -fyl * q.w;
+    }
+    const float w00 = (1.0f - G.al) * (1.0f - G.be), w10 = G.al * (1.0f - G.be);
+    const float w01 = (1.0f - G.al) * G.be, w11 = G.al * G.be;
+    const float* I0p = D.I0 + ((size_t)P.level * D.Npad + p) * K;
+    const float2* G0p = ic ? D.G0 + ((size_t)P.level * D.Npad + p) * K : nullptr;
+    for (int k = 0; k < K; ++k) {
+        const int dx = k % D.pattern - h, dy = k / D.pattern - h;
+        const uint8_t* t = lv.img + (size_t)(G.yb + dy) * S + (G.xb + dx);
+        const float I00 = __ldg(t), I10 = __ldg(t + 1), I01 = __ldg(t + S), I11 = __ldg(t + S + 1);
+        const float I = fmaf(w00, I00, fmaf(w10, I10, fmaf(w01, I01, w11 * I11)));
+        float gx, gy;
+        if (ic) {
+            const float2 g0 = G0p[k];
+            gx = P.ea * g0.x;
+            gy = P.ea * g0.y;
+        } else {
+            gx = 0.5f * fmaf(w00, I10 - (float)__ldg(t - 1),
+                        fmaf(w10, (float)__ldg(t + 2) - I00,
+                        fmaf(w01, I11 - (float)__ldg(t + S - 1),
+                             w11 * ((float)__ldg(t + S + 2) - I01))));
+            gy = 0.5f * fmaf(w00, I01 - (float)__ldg(t - S),
+                        fmaf(w10, I11 - (float)__ldg(t - S + 1),
+                        fmaf(w01, (float)__ldg(t + 2 * S) - I00,
+                             w11 * ((float)__ldg(t + 2 * S + 1) - I10))));
+        }
+        accumulate_sample(G, I, gx, gy, I0p[k], P.ea, P.b, D.huber_k, acc, res ? res + (size_t)K * p + k : nullptr);
+    }
+}
+
+// Linearises map point p at the pass state into acc.  RES: also write the K
+// residuals (NaN for an unusable point) to res[Kp..Kp+K-1].
 template <bool MIXED, bool RES>
 __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassParams& P, int p,
                                                 float* acc, float* res)
 {
     const LevelDev& lv = D.lv[P.level];
-    const float4* I0p = reinterpret_cast<const float4*>(D.I0 + ((size_t)P.level * D.Npad + p) * 8);
-    const float4 ia = I0p[0], ib = I0p[1];
+    const float* I0b = D.I0 + ((size_t)P.level * D.Npad + p) * D.K;
+    float4 ia = make_float4(0.f, 0.f, 0.f, 0.f), ib = ia;
+    if (D.pattern) {
+        ia.x = I0b[0];              // the p x p path reads its samples itself
+    } else {
+        const float4* I0p = reinterpret_cast<const float4*>(I0b);   // K = 8: 32-byte rows
+        ia = I0p[0];
+        ib = I0p[1];
+    }
     PointGeom G;
     bool ok = !isnan(ia.x) && project_point(D, P, lv, p, G);
     if (!ok) {
         if (RES) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) res[8 * p + k] = __int_as_float(0x7fc00000);
+            for (int k = 0; k < D.K; ++k) res[(size_t)D.K * p + k] = __int_as_float(0x7fc00000);
         }
+        return;
+    }
+    if (D.pattern) {
+        linearize_square(D, P, p, G, acc, RES ? res : nullptr);
         return;
     }
     const float i0[8] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
@@ -553,10 +614,16 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
     // commit the pass outcome to the shared state
     if (accept && lane < 12) S.T[lane] = S.Tc[lane];
     if (load_normal && lane < 8) {
+        // with (a, b) held fixed their rows and columns become the identity and
+        // their right-hand side zero, so the solve gives da = db = 0
+        const bool fixed_ab = !D.affine;
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-            S.H[8 * lane + c] = tot[c >= lane ? upper_index(lane, c) : upper_index(c, lane)];
-        S.g[lane] = tot[kIdxG + lane];
+        for (int c = 0; c < 8; ++c) {
+            double v = tot[c >= lane ? upper_index(lane, c) : upper_index(c, lane)];
+            if (fixed_ab && (lane >= 6 || c >= 6)) v = lane == c ? 1.0 : 0.0;
+            S.H[8 * lane + c] = v;
+        }
+        S.g[lane] = (fixed_ab && lane >= 6) ? 0.0 : tot[kIdxG + lane];
     }
     if (lane == 0) {
         S.passes += 1;

@@ -58,7 +58,8 @@ struct glt_tracker {
     float4* pt = nullptr;
     float2* dz = nullptr;
     float* I0 = nullptr;
-    float2* G0 = nullptr;                 // GLT_IC reference gradients [L][Npad][8]
+    float2* G0 = nullptr;                 // GLT_IC reference gradients [L][Npad][K]
+    int K = 8;                            // samples per point of the pattern
     int Npad = 0;
     int N = 0;
     bool have_points = false;

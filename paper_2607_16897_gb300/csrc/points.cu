@@ -28,21 +28,20 @@ __global__ void set_points_kernel(const StreamDesc* __restrict__ desc, RefLevels
                         fabsf(u0) < 1e7f && fabsf(v0) < 1e7f;
     pt[p] = make_float4(u0, v0, (u0 - cx) / D.fx, (v0 - cy) / D.fy);
     dz[p] = make_float2(d, 1.0f / d);
+    const int K = D.K, h = D.pattern ? (D.pattern - 1) / 2 : 2;
     for (int l = 0; l < D.L; ++l) {
-        float4* out = reinterpret_cast<float4*>(I0 + ((size_t)l * D.Npad + p) * 8);
+        float* out = I0 + ((size_t)l * D.Npad + p) * K;
+        float2* gout = G0 ? G0 + ((size_t)l * D.Npad + p) * K : nullptr;
         const LevelDev& lv = D.lv[l];
         const float s = ldexpf(1.0f, -l);
         const float U = u0 * s, V = v0 * s;
         const float fu = floorf(U), fv = floorf(V);
         const int xb = finite ? (int)fu : -1000, yb = finite ? (int)fv : -1000;
-        if (!finite || xb < 3 || xb > lv.W - 5 || yb < 3 || yb > lv.H - 5) {
-            const float nan = __int_as_float(0x7fc00000);
-            out[0] = make_float4(nan, 0.f, 0.f, 0.f);
-            out[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (G0) {
-                float4* g = reinterpret_cast<float4*>(G0 + ((size_t)l * D.Npad + p) * 8);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) g[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        // every sample q = (U + dx, V + dy) must satisfy 1 <= q < W-2, 1 <= q < H-2
+        if (!finite || xb < 1 + h || xb > lv.W - 3 - h || yb < 1 + h || yb > lv.H - 3 - h) {
+            for (int k = 0; k < K; ++k) {
+                out[k] = k == 0 ? __int_as_float(0x7fc00000) : 0.0f;
+                if (gout) gout[k] = make_float2(0.0f, 0.0f);
             }
             continue;
         }
@@ -50,34 +49,25 @@ __global__ void set_points_kernel(const StreamDesc* __restrict__ desc, RefLevels
         const float w00 = (1.0f - al) * (1.0f - be), w10 = al * (1.0f - be);
         const float w01 = (1.0f - al) * be, w11 = al * be;
         const uint8_t* img = ref.img[l];
-        float v[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const uint8_t* t = img + (size_t)(yb + pat_dy(k)) * lv.pitch + (xb + pat_dx(k));
-            v[k] = fmaf(w00, (float)t[0], fmaf(w10, (float)t[1], fmaf(w01, (float)t[lv.pitch], w11 * (float)t[lv.pitch + 1])));
-        }
-        out[0] = make_float4(v[0], v[1], v[2], v[3]);
-        out[1] = make_float4(v[4], v[5], v[6], v[7]);
-        if (G0) {
-            // central differences at the four taps, bilinear weights, then the 1/2
-            float gg[16];
-            const int P = lv.pitch;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const uint8_t* t = img + (size_t)(yb + pat_dy(k)) * P + (xb + pat_dx(k));
-                const float I00 = t[0], I10 = t[1], I01 = t[P], I11 = t[P + 1];
-                gg[2 * k] = 0.5f * fmaf(w00, I10 - (float)t[-1],
-                                   fmaf(w10, (float)t[2] - I00,
-                                   fmaf(w01, I11 - (float)t[P - 1],
-                                        w11 * ((float)t[P + 2] - I01))));
-                gg[2 * k + 1] = 0.5f * fmaf(w00, I01 - (float)t[-P],
-                                       fmaf(w10, I11 - (float)t[1 - P],
-                                       fmaf(w01, (float)t[2 * P] - I00,
-                                            w11 * ((float)t[2 * P + 1] - I10))));
+        const int P = lv.pitch;
+        for (int k = 0; k < K; ++k) {
+            const int dx = D.pattern ? k % D.pattern - h : pat_dx(k);
+            const int dy = D.pattern ? k / D.pattern - h : pat_dy(k);
+            const uint8_t* t = img + (size_t)(yb + dy) * P + (xb + dx);
+            const float I00 = t[0], I10 = t[1], I01 = t[P], I11 = t[P + 1];
+            out[k] = fmaf(w00, I00, fmaf(w10, I10, fmaf(w01, I01, w11 * I11)));
+            if (gout) {
+                // central differences at the four taps, bilinear weights, then the 1/2
+                const float gx = 0.5f * fmaf(w00, I10 - (float)t[-1],
+                                        fmaf(w10, (float)t[2] - I00,
+                                        fmaf(w01, I11 - (float)t[P - 1],
+                                             w11 * ((float)t[P + 2] - I01))));
+                const float gy = 0.5f * fmaf(w00, I01 - (float)t[-P],
+                                        fmaf(w10, I11 - (float)t[1 - P],
+                                        fmaf(w01, (float)t[2 * P] - I00,
+                                             w11 * ((float)t[2 * P + 1] - I10))));
+                gout[k] = make_float2(gx, gy);
             }
-            float4* g = reinterpret_cast<float4*>(G0 + ((size_t)l * D.Npad + p) * 8);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) g[k] = make_float4(gg[4 * k], gg[4 * k + 1], gg[4 * k + 2], gg[4 * k + 3]);
         }
     }
 }
