@@ -42,14 +42,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c4b", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c4b", "c5", "c2p", "c2e"],
                     help="c2: 640x480 single stream FP32 (default); c3: 64 streams of mixed "
                          "sizes, batched; c4: 1280x720 mixed precision single stream; c4b: "
                          "64 streams of c4, batched; c5: 256 streams of 640x480 with the "
-                         "learned proposal, against the plain form on the same streams")
+                         "learned proposal, against the plain form on the same streams; c2p / "
+                         "c2e: single stream in the paper's configuration (7x7 / 11x11 patches, "
+                         "IC Jacobians, 6 levels, fixed-count Gauss-Newton, no affine, no Huber) "
+                         "at 640x480 / 752x480")
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="frames the oracle tracks for cpu_baseline (0 = auto, ~10-30 s)")
-    ap.add_argument("--jacobian", default="forward", choices=["forward", "ic"],
+    ap.add_argument("--jacobian", default=None, choices=["forward", "ic"],
                     help="Jacobian form: forward (current image, default) or ic "
                          "(inverse compositional, reference-side rows cached per reference)")
     ap.add_argument("--shape", default=None,
@@ -67,19 +70,28 @@ class Workload:
     """One camera stream: its frames, reference keyframes and map points."""
 
     def __init__(self, seed=1, frames=300, N=2000, W=640, H=480, f=525.0, L=4, speed=0.5,
-                 ang=30.0, label="C2 single stream", render=True):
+                 ang=30.0, label="C2 single stream", render=True, exposure=True, solver=None,
+                 jacobian="forward", max_cost=2.5):
         import synth
         self.cam = synth.camera_for(W, H, f)
-        self.seq = synth.sequence(seed, frames, self.cam, synth.ROOM_LARGE, speed, ang)
+        rng_ab = {} if exposure else dict(a_range=(0.0, 0.0), b_range=(0.0, 0.0))
+        self.seq = synth.sequence(seed, frames, self.cam, synth.ROOM_LARGE, speed, ang, **rng_ab)
+        self.solver = dict(solver or {})    # tracker configuration overrides
+        self.max_cost = max_cost
         self.job = (seed, frames, W, H, f)
         self.speed, self.ang = speed, ang
         self.frames = [self.seq.frame(k)[0] for k in range(frames)] if render else None
         self.N, self.L = N, L
         self.refs = {}
-        self.jacobian = "forward"
-        self.name = (f"{label}: {W}x{H} uint8, fx=fy={f:g}, {frames}-frame sequence "
-                     f"({speed:g} m/s, {ang:g} deg/s), N={N} points, L={L}, Huber 9, "
-                     f"<=10 LM iters/level, const-velocity init, reference every 8 frames")
+        self.jacobian = jacobian
+        if solver:
+            self.name = (f"{label}: {W}x{H} uint8, fx=fy={f:g}, {frames}-frame sequence "
+                         f"({speed:g} m/s, {ang:g} deg/s, no exposure change), N={N} points, "
+                         f"L={L}, const-velocity init, reference every 8 frames")
+        else:
+            self.name = (f"{label}: {W}x{H} uint8, fx=fy={f:g}, {frames}-frame sequence "
+                         f"({speed:g} m/s, {ang:g} deg/s), N={N} points, L={L}, Huber 9, "
+                         f"<=10 LM iters/level, const-velocity init, reference every 8 frames")
 
     def ref_points(self, r):
         import synth
@@ -122,10 +134,10 @@ class SequenceDriver:
     the last reference, is handed to the indirect pipeline, which here is the
     renderer's true pose and depth: that frame becomes the new reference."""
 
-    def __init__(self, wl: Workload, interval=8, max_cost=2.5):
+    def __init__(self, wl: Workload, interval=8, max_cost=None):
         self.wl = wl
         self.interval = interval
-        self.max_cost = max_cost
+        self.max_cost = wl.max_cost if max_cost is None else max_cost
         self.rejected = 0
         self.r = 0
         self.since = 0
@@ -248,7 +260,7 @@ def oracle_track_sequence(wl, frames, inits=None, proposal=None, motions=None):
     initial state, with motions[k] the network's motion input."""
     import oracle
     K = wl.cam.K
-    trk = oracle.OracleTracker(wl.cam.W, wl.cam.H, K, levels=wl.L, jacobian=wl.jacobian)
+    trk = oracle.OracleTracker(wl.cam.W, wl.cam.H, K, levels=wl.L, jacobian=wl.jacobian, **wl.solver)
     drv = SequenceDriver(wl)
     t_track = 0.0
     out, used = {}, {}
@@ -302,7 +314,8 @@ def run_reference(args):
         pool.close()
         pool.join()
         for w in wls:
-            w.jacobian = args.jacobian
+            if args.jacobian:
+                w.jacobian = args.jacobian
         pw = None
         if args.workload == "c5":
             from oracle import nn as onn
@@ -318,20 +331,23 @@ def run_reference(args):
         name = f"{args.workload.upper()} batched, {len(wls)} streams"
         sample = f"frames 1..{n} of each of the {len(wls)} streams, one host thread per stream"
         cores = workers
+        jac = wls[0].jacobian
     else:
         wl = single_workload(args.workload, rank)
-        wl.jacobian = args.jacobian
+        if args.jacobian:
+            wl.jacobian = args.jacobian
         n = min(len(wl.frames) - 1, W + K)
         t, _, _ = oracle_track_sequence(wl, n)
         frames = n
         name = wl.name
         sample = f"frames 1..{n} of the sequence, pyramid + track per frame"
         cores = 1
+        jac = wl.jacobian
     fps = frames / t
     line = {"metric": "frames tracked/s", "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
             "steps": K, "warmup": W, "ms_per_step": 1000.0 * t / frames, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference", "config": {"workload": name, "jacobian": args.jacobian},
+            "impl": "reference", "config": {"workload": name, "jacobian": jac},
             "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0,
@@ -355,13 +371,14 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     wl = single_workload(args.workload, rank)   # replicas: one independent stream per GPU
-    wl.jacobian = args.jacobian
+    if args.jacobian:
+        wl.jacobian = args.jacobian
     precision = "mixed" if args.workload == "c4" else "fp32"
     Wd, Hd, L, N = wl.cam.W, wl.cam.H, wl.L, wl.N
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
     trk = glt.Tracker(Wd, Hd, wl.cam.K, levels=L, max_points=N, precision=precision,
-                      jacobian=wl.jacobian)
+                      jacobian=wl.jacobian, **wl.solver)
     frames_dev = torch.from_numpy(np.stack(wl.frames)).to(f"cuda:{local}")
     frames_pin = torch.from_numpy(np.stack(wl.frames)).pin_memory()
     init_dev = torch.zeros(14, dtype=torch.float64, device=f"cuda:{local}")
@@ -489,7 +506,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f16 storage / f32 math" if precision == "mixed" else "f32",
                 "data": "synthetic",
-                "config": {"workload": wl.name, "jacobian": args.jacobian, "global_batch": world,
+                "config": {"workload": wl.name, "jacobian": wl.jacobian, "global_batch": world,
                            "streams_per_gpu": 1,
                            "parallelism": f"replicas x{world}",
                            "l2": "flushed between steps (256 MB write, outside the step events)",
@@ -578,11 +595,12 @@ def linearization_error(glt, wl, rec_entry, precision):
     import oracle
     k, r, T_init, ab, _ = rec_entry
     trk = glt.Tracker(wl.cam.W, wl.cam.H, wl.cam.K, levels=wl.L, max_points=wl.N, precision=precision,
-                      jacobian=wl.jacobian)
+                      jacobian=wl.jacobian, **wl.solver)
     trk.build_pyramid(glt.GLT_REF, wl.frames[r])
     trk.set_map_points(wl.ref_points(r))
     trk.build_pyramid(glt.GLT_CUR, wl.frames[k])
-    o = oracle.OracleTracker(wl.cam.W, wl.cam.H, wl.cam.K, levels=wl.L, jacobian=wl.jacobian)
+    o = oracle.OracleTracker(wl.cam.W, wl.cam.H, wl.cam.K, levels=wl.L, jacobian=wl.jacobian,
+                             **wl.solver)
     o.build_pyramid(0, wl.frames[r])
     o.set_map_points(wl.ref_points(r))
     o.build_pyramid(1, wl.frames[k])
@@ -600,7 +618,25 @@ def linearization_error(glt, wl, rec_entry, precision):
     return out
 
 
+# the paper's configuration: p x p patches, IC Jacobians, plain Gauss-Newton
+# with 10 iterations on each of 6 levels, no affine brightness, no Huber weights
+PAPER_SOLVER = dict(affine=False, lambda0=0.0, accept_step=1e30, eps_step=0.0,
+                    eps_step_coarse=0.0, huber_k=1e30)
+
+
 def single_workload(kind, rank=0):
+    if kind == "c2p":
+        return Workload(seed=1 + rank, frames=300, N=2000, W=640, H=480, f=525.0, L=6,
+                        exposure=False, solver=dict(PAPER_SOLVER, pattern=7), jacobian="ic",
+                        max_cost=50.0,
+                        label="C2 in the paper's configuration (TUM-like, 7x7 patches, IC, "
+                              "6 levels, 10 GN iterations per level, no affine, no Huber)")
+    if kind == "c2e":
+        return Workload(seed=1 + rank, frames=300, N=2000, W=752, H=480, f=458.0, L=6,
+                        exposure=False, solver=dict(PAPER_SOLVER, pattern=11), jacobian="ic",
+                        max_cost=50.0,
+                        label="752x480 in the paper's configuration (EuRoC-like, 11x11 patches, "
+                              "IC, 6 levels, 10 GN iterations per level, no affine, no Huber)")
     if kind == "c4":
         return Workload(seed=2000 + rank, frames=300, N=8000, W=1280, H=720, f=1050.0, L=5,
                         speed=1.0, ang=60.0, label="C4 mixed precision, single stream")
@@ -664,7 +700,8 @@ def run_batch(args):
     pool.close()
     pool.join()
     for w in wls:
-        w.jacobian = args.jacobian
+        if args.jacobian:
+            w.jacobian = args.jacobian
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
     dist = None
@@ -678,7 +715,7 @@ def run_batch(args):
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
     trks = [glt.Tracker(w.cam.W, w.cam.H, w.cam.K, levels=w.L, max_points=w.N, precision=precision,
-                        jacobian=w.jacobian) for w in wls]
+                        jacobian=w.jacobian, **w.solver) for w in wls]
     batch = glt.Batch(trks)
     frames_dev = [torch.from_numpy(np.stack(w.frames)).to(dev) for w in wls]
     frames_pin = [torch.from_numpy(np.stack(w.frames)).pin_memory() for w in wls]
@@ -870,7 +907,7 @@ def run_batch(args):
                 "config": {"workload": (f"{args.workload.upper()} batched: {S} streams in one graph "
                                         f"replay (pyramids + one persistent track launch); " + desc
                                         + f", {F}-frame sequences, reference every 8 frames"),
-                           "jacobian": args.jacobian,
+                           "jacobian": wls[0].jacobian,
                            "global_batch": world * S, "streams_per_gpu": S,
                            "parallelism": f"replicas x{world}",
                            "autotuned_shape": {"cluster": shape[0], "threads": shape[1],

@@ -119,14 +119,14 @@ static int check_config(const glt_config* c)
 // CTAs per stream for n points when the caller left it to the library.
 static void resolve_shape(glt_tracker* t)
 {
-    const bool mixed = t->cfg.precision == GLT_MIXED;
+    const int variant = track_variant(t->cfg);
     int threads = t->cfg.threads ? t->cfg.threads : 256;
     int cluster = t->cfg.cluster;
     if (cluster == 0) {
         cluster = (t->N + threads - 1) / threads;
         cluster = std::min(16, std::max(1, cluster));
     }
-    while (cluster > 1 && !track_shape_ok(cluster, threads, mixed)) cluster = cluster > 8 ? 8 : cluster - 1;
+    while (cluster > 1 && !track_shape_ok(cluster, threads, variant)) cluster = cluster > 8 ? 8 : cluster - 1;
     t->cluster = cluster;
     t->threads = threads;
 }
@@ -406,7 +406,7 @@ int glt_track_frame_async(glt_tracker* t, const double* init_dev, glt_result* ou
     if (!init_dev || !out_dev) return invalid("init_dev / out_dev is NULL");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     GLT_CHECK(launch_track(t->desc_ptr_dev, t->user_dev, 1, t->cluster, t->threads,
-                           t->cfg.precision == GLT_MIXED, init_dev, out_dev, s),
+                           track_variant(t->cfg), init_dev, out_dev, s),
               "track kernel");
     return GLT_OK;
 }
@@ -425,7 +425,7 @@ int glt_track_frame(glt_tracker* t, const double T_init[12], const double ab_ini
     GLT_CHECK(cudaMemcpyAsync(t->init_dev, t->h_init, 14 * sizeof(double), cudaMemcpyHostToDevice, s),
               "init upload");
     GLT_CHECK(launch_track(t->desc_ptr_dev, t->user_dev, 1, t->cluster, t->threads,
-                           t->cfg.precision == GLT_MIXED, t->init_dev, t->result_dev, s),
+                           track_variant(t->cfg), t->init_dev, t->result_dev, s),
               "track kernel");
     GLT_CHECK(cudaMemcpyAsync(t->h_result, t->result_dev, sizeof(glt_result), cudaMemcpyDeviceToHost, s),
               "result download");
@@ -611,7 +611,14 @@ int glt_batch_create(glt_tracker* const* trackers, int S, glt_batch** out)
 #undef BALLOC
     b->cluster = 2;
     b->threads = 256;
-    if (!track_shape_ok(b->cluster, b->threads, prec == GLT_MIXED)) b->cluster = 1;
+    // one kernel variant for the whole batch: the most general one any stream needs
+    b->variant = 0;
+    for (int i = 0; i < S; ++i) {
+        const int v = track_variant(trackers[i]->cfg);
+        if (v == 1 || v == 2) b->variant = v;
+        else if (v == 3 && b->variant == 0) b->variant = 3;
+    }
+    if (!track_shape_ok(b->cluster, b->threads, b->variant)) b->cluster = 1;
     *out = b;
     return GLT_OK;
 }
@@ -673,7 +680,7 @@ int glt_batch_track(glt_batch* b, const double* init_dev, glt_result* out_dev, v
         init_dev = b->prop_init;
     }
     GLT_CHECK(launch_track(b->descs_dev, b->users_dev, b->S, b->cluster, b->threads,
-                           b->precision == GLT_MIXED, init_dev, out_dev, s),
+                           b->variant, init_dev, out_dev, s),
               "batch track kernel");
     return GLT_OK;
 }
@@ -703,7 +710,7 @@ int glt_batch_capture(glt_batch* b, const uint8_t* const* frames_dev, const doub
     }
     if (e1 == cudaSuccess)
         e1 = launch_track(b->descs_dev, b->users_dev, b->S, b->cluster, b->threads,
-                          b->precision == GLT_MIXED, init_dev, out_dev, s);
+                          b->variant, init_dev, out_dev, s);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
     if (r1 != GLT_OK) {
@@ -730,7 +737,7 @@ int glt_batch_replay(glt_batch* b, void* stream)
 int glt_batch_set_shape(glt_batch* b, int cluster, int threads)
 {
     if (!b) return invalid("batch is NULL");
-    if (!track_shape_ok(cluster, threads, b->precision == GLT_MIXED)) return invalid("shape cannot launch");
+    if (!track_shape_ok(cluster, threads, b->variant)) return invalid("shape cannot launch");
     b->cluster = cluster;
     b->threads = threads;
     return GLT_OK;
@@ -750,17 +757,17 @@ int glt_batch_autotune(glt_batch* b, const double* init_dev, glt_result* out_dev
     GLT_CHECK(cudaEventCreate(&e1), "event");
     float best = 1e30f;
     int bc = b->cluster, bt = b->threads;
-    const bool mixed = b->precision == GLT_MIXED;
+    const int variant = b->variant;
     for (auto& sh : shapes) {
-        if (!track_shape_ok(sh[0], sh[1], mixed)) continue;
-        cudaError_t e = launch_track(b->descs_dev, b->users_dev, b->S, sh[0], sh[1], mixed, init_dev, out_dev, s);
+        if (!track_shape_ok(sh[0], sh[1], variant)) continue;
+        cudaError_t e = launch_track(b->descs_dev, b->users_dev, b->S, sh[0], sh[1], variant, init_dev, out_dev, s);
         if (e != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
         cudaEventRecord(e0, s);
         for (int r = 0; r < reps; ++r)
-            launch_track(b->descs_dev, b->users_dev, b->S, sh[0], sh[1], mixed, init_dev, out_dev, s);
+            launch_track(b->descs_dev, b->users_dev, b->S, sh[0], sh[1], variant, init_dev, out_dev, s);
         cudaEventRecord(e1, s);
         cudaError_t es = cudaEventSynchronize(e1);
         if (es != cudaSuccess) {

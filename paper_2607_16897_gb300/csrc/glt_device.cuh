@@ -89,6 +89,7 @@ struct PointGeom {
 // accurate at any image width:  with m = ((u0-cx)/fx, (v0-cy)/fy, 1) and
 // D = (R - I) m + t / d,  x_c = d (m + D)  and
 // u - u0 = fx (D_x - m_x D_z) / (1 + D_z)   (exactly Eq. 1's pi(R x_r + t)).
+template <bool SQUARE = false>
 __device__ __forceinline__ bool project_point(const StreamDesc& D, const PassParams& P,
                                               const LevelDev& lv, int p, PointGeom& G)
 {
@@ -114,7 +115,7 @@ __device__ __forceinline__ bool project_point(const StreamDesc& D, const PassPar
     G.be = sv - fv;
     G.xb = (int)Ui + (int)fu;
     G.yb = (int)Vi + (int)fv;
-    const int h = D.pattern ? (D.pattern - 1) / 2 : 2;   // half extent of the pattern
+    const int h = (SQUARE && D.pattern) ? (D.pattern - 1) / 2 : 2;   // half extent of the pattern
     if (G.xb < 1 + h || G.xb > lv.W - 3 - h || G.yb < 1 + h || G.yb > lv.H - 3 - h) return false;
     // d(pi)/d(x_c) R, with x_c / z_c = (m + D) / (1 + D_z) and 1/z_c = rho / (1 + D_z)
     const float xn = (ub + Dx) * iz, yn = (vb + Dy) * iz;
@@ -177,8 +178,9 @@ __device__ __forceinline__ void accumulate_sample(const PointGeom& G, float I, f
 
 // The p x p patch (the paper's Sec. IV-A patch): K = p*p samples read one by
 // one (four taps, plus the gradient taps in the forward form) through the
-// read-only cache; FP32 levels only.
-static __device__ __noinline__ void linearize_square(const StreamDesc& D, const PassParams& P, int p,
+// read-only cache; FP32 levels only.  Inlined so the accumulators stay in
+// registers.
+__device__ __forceinline__ void linearize_square(const StreamDesc& D, const PassParams& P, int p,
                                               PointGeom& G, float* acc, float* res)
 {
     const LevelDev& lv = D.lv[P.level];
@@ -225,7 +227,9 @@ static __device__ __noinline__ void linearize_square(const StreamDesc& D, const 
 
 // Linearises map point p at the pass state into acc.  RES: also write the K
 // residuals (NaN for an unusable point) to res[Kp..Kp+K-1].
-template <bool MIXED, bool RES>
+// SQUARE: the p x p path is compiled in; IC: the inverse-compositional rows
+// are compiled in (both decided per stream at run time when compiled in).
+template <bool MIXED, bool RES, bool SQUARE = false, bool IC = true>
 __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassParams& P, int p,
                                                 float* acc, float* res)
 {
@@ -240,22 +244,22 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
         ib = I0p[1];
     }
     PointGeom G;
-    bool ok = !isnan(ia.x) && project_point(D, P, lv, p, G);
+    bool ok = !isnan(ia.x) && project_point<SQUARE>(D, P, lv, p, G);
     if (!ok) {
         if (RES) {
             for (int k = 0; k < D.K; ++k) res[(size_t)D.K * p + k] = __int_as_float(0x7fc00000);
         }
         return;
     }
-    if (D.pattern) {
+    if (SQUARE && D.pattern) {
         linearize_square(D, P, p, G, acc, RES ? res : nullptr);
         return;
     }
     const float i0[8] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
     // inverse-compositional form: geometric rows at the reference point
     // (identity pose) and the cached reference gradients times e^a
-    const bool ic = D.G0 != nullptr;
-    float4 g0[4];
+    const bool ic = IC && D.G0 != nullptr;
+    const float2* G0p = nullptr;
     if (ic) {
         const float4 q = D.pt[p];
         const float rho = D.dz[p].y;
@@ -266,11 +270,8 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
         G.a1[0] = 0.0f;
         G.a1[1] = fyl;
         G.a1[2] = -fyl * q.w;
-        const float4* gp = reinterpret_cast<const float4*>(D.G0 + ((size_t)P.level * D.Npad + p) * 8);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) g0[k] = gp[k];
+        G0p = D.G0 + ((size_t)P.level * D.Npad + p) * 8;
     }
-#define GLT_G0(k, c) (((k) & 1) ? ((c) ? g0[(k) >> 1].w : g0[(k) >> 1].z) : ((c) ? g0[(k) >> 1].y : g0[(k) >> 1].x))
     const float w00 = (1.0f - G.al) * (1.0f - G.be), w10 = G.al * (1.0f - G.be);
     const float w01 = (1.0f - G.al) * G.be, w11 = G.al * G.be;
     if (!MIXED) {
@@ -302,8 +303,9 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
             const float I = fmaf(w00, I00, fmaf(w10, I10, fmaf(w01, I01, w11 * I11)));
             float gx, gy;
             if (ic) {
-                gx = P.ea * GLT_G0(k, 0);
-                gy = P.ea * GLT_G0(k, 1);
+                const float2 g0 = G0p[k];
+                gx = P.ea * g0.x;
+                gy = P.ea * g0.y;
             } else {
                 // central differences at the four taps (the 1/2 is applied after interpolation)
                 gx = 0.5f * fmaf(w00, I10 - GLT_PX(r0, c0 - 1),
@@ -336,13 +338,13 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
             const float y01 = __low2float(*reinterpret_cast<const __half2*>(&p01.y));
             const float y11 = __low2float(*reinterpret_cast<const __half2*>(&p11.y));
             const float I = fmaf(w00, a00.x, fmaf(w10, a10.x, fmaf(w01, a01.x, w11 * a11.x)));
-            const float gx = ic ? P.ea * GLT_G0(k, 0) : fmaf(w00, a00.y, fmaf(w10, a10.y, fmaf(w01, a01.y, w11 * a11.y)));
-            const float gy = ic ? P.ea * GLT_G0(k, 1) : fmaf(w00, y00, fmaf(w10, y10, fmaf(w01, y01, w11 * y11)));
+            const float2 g0 = ic ? G0p[k] : make_float2(0.0f, 0.0f);
+            const float gx = ic ? P.ea * g0.x : fmaf(w00, a00.y, fmaf(w10, a10.y, fmaf(w01, a01.y, w11 * a11.y)));
+            const float gy = ic ? P.ea * g0.y : fmaf(w00, y00, fmaf(w10, y10, fmaf(w01, y01, w11 * y11)));
             accumulate_sample(G, I, gx, gy, i0[k], P.ea, P.b, D.huber_k, acc,
                               RES ? res + 8 * p + k : nullptr);
         }
     }
-#undef GLT_G0
 }
 
 // ---------------------------------------------------------------------------

@@ -101,6 +101,7 @@ struct glt_batch {
     glt::PyrJob* jobs_dev = nullptr;      // [L-1 rounds][S] caller order
     glt::PackJob* pack_dev = nullptr;     // [Lmax][S]
     int Lmax = 0;
+    int variant = 0;                      // kernel variant (track_variant of the streams)
     int cluster = 2, threads = 256;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -133,11 +134,17 @@ int pyr_tiles_y(int dH);
 cudaError_t launch_set_points(const glt_tracker* t, const float* uvd_dev, int n, cudaStream_t s);
 
 // track.cu
+// kernel variant of a configuration: 0 FP32 forward, 1 GLT_MIXED, 2 FP32 with
+// p x p patches, 3 FP32 inverse compositional
+inline int track_variant(const glt_config& c)
+{
+    return c.precision == GLT_MIXED ? 1 : c.pattern != 0 ? 2 : c.jacobian == GLT_IC ? 3 : 0;
+}
 cudaError_t launch_track(const StreamDesc* const* descs, const int* users, int S, int cluster,
-                         int threads, bool mixed, const double* init, glt_result* results,
+                         int threads, int variant, const double* init, glt_result* results,
                          cudaStream_t s);
 cudaError_t launch_linearize(const glt_tracker* t, const PassParams& P, bool want_res,
                              cudaStream_t s);
-bool track_shape_ok(int cluster, int threads, bool mixed);
+bool track_shape_ok(int cluster, int threads, int variant);
 
 }  // namespace glt

@@ -23,13 +23,18 @@ constexpr int kMaxCluster = 16;   // largest cluster a stream may use (config.cl
 // (batches of many small clusters); the wider shapes keep the registers the
 // compiler wants (a single stream's latency).
 
-template <int THREADS, bool MIXED>
+// VAR: 0 FP32 levels, forward Jacobian; 1 FP16-packed levels (GLT_MIXED);
+// 2 FP32 with the p x p patch path compiled in; 3 FP32 with the
+// inverse-compositional rows compiled in.  Variants 1-3 decide the Jacobian
+// form (and 2 the pattern) per stream, so one batch may mix them.
+template <int THREADS, int VAR>
 __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(const StreamDesc* const* __restrict__ descs,
                                                         const int* __restrict__ users,
                                                         const double* __restrict__ init,
                                                         glt_result* __restrict__ results)
 {
     constexpr int NW = THREADS / 32;
+    constexpr bool MIXED = VAR == 1, SQUARE = VAR == 2, IC = VAR != 0;
     __shared__ StreamDesc sD;
     __shared__ PassParams P;
     __shared__ Solver S;
@@ -60,7 +65,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
 #pragma unroll
         for (int i = 0; i < kAccPad; ++i) acc[i] = 0.0f;
         for (int p = rank * THREADS + tid; p < sD.N; p += C * THREADS)
-            linearize_point<MIXED, false>(sD, P, p, acc, nullptr);
+            linearize_point<MIXED, false, SQUARE, IC>(sD, P, p, acc, nullptr);
         block_reduce<THREADS, MIXED>(acc, red, part[par], part_c[par]);
         if (C > 1) cluster.sync();
         if (tid < kNumAcc) {
@@ -103,7 +108,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
 // One linearisation pass over all points of one tracker, many blocks, with a
 // single-pass finish: each block writes its 46 sums, the last block to arrive
 // (ticket counter) adds the block sums in block order in FP64.
-template <int THREADS, bool MIXED>
+template <int THREADS, int VAR>
 __global__ void __launch_bounds__(THREADS) linearize_kernel(const StreamDesc* __restrict__ desc,
                                                             PassParams P,
                                                             float* __restrict__ partials,
@@ -112,6 +117,7 @@ __global__ void __launch_bounds__(THREADS) linearize_kernel(const StreamDesc* __
                                                             float* __restrict__ res)
 {
     constexpr int NW = THREADS / 32;
+    constexpr bool MIXED = VAR == 1, SQUARE = VAR == 2, IC = VAR != 0;
     __shared__ float red[NW][kAccPad];
     __shared__ float part[kAccPad];
     __shared__ float part_c[kAccPad];
@@ -123,9 +129,9 @@ __global__ void __launch_bounds__(THREADS) linearize_kernel(const StreamDesc* __
     const int p = blockIdx.x * THREADS + threadIdx.x;
     if (p < D.N) {
         if (res)
-            linearize_point<MIXED, true>(D, P, p, acc, res);
+            linearize_point<MIXED, true, SQUARE, IC>(D, P, p, acc, res);
         else
-            linearize_point<MIXED, false>(D, P, p, acc, nullptr);
+            linearize_point<MIXED, false, SQUARE, IC>(D, P, p, acc, nullptr);
     }
     block_reduce<THREADS, MIXED>(acc, red, part, part_c);
     if (threadIdx.x < kNumAcc)
@@ -148,11 +154,11 @@ __global__ void __launch_bounds__(THREADS) linearize_kernel(const StreamDesc* __
 
 namespace {
 
-template <int THREADS, bool MIXED>
+template <int THREADS, int VAR>
 cudaError_t launch_track_t(const StreamDesc* const* descs, const int* users, int S, int cluster,
                            const double* init, glt_result* results, cudaStream_t s)
 {
-    auto kern = track_kernel<THREADS, MIXED>;
+    auto kern = track_kernel<THREADS, VAR>;
     if (cluster > 8) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
@@ -172,10 +178,10 @@ cudaError_t launch_track_t(const StreamDesc* const* descs, const int* users, int
     return cudaLaunchKernelEx(&cfg, kern, descs, users, init, results);
 }
 
-template <int THREADS, bool MIXED>
+template <int THREADS, int VAR>
 bool shape_ok_t(int cluster)
 {
-    auto kern = track_kernel<THREADS, MIXED>;
+    auto kern = track_kernel<THREADS, VAR>;
     if (cluster > 8 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
@@ -200,35 +206,53 @@ bool shape_ok_t(int cluster)
     return n > 0;
 }
 
+template <int VAR>
+bool shape_ok_v(int cluster, int threads)
+{
+    switch (threads) {
+    case 128: return shape_ok_t<128, VAR>(cluster);
+    case 256: return shape_ok_t<256, VAR>(cluster);
+    case 512: return shape_ok_t<512, VAR>(cluster);
+    default: return false;
+    }
+}
+
+template <int VAR>
+cudaError_t launch_track_v(const StreamDesc* const* descs, const int* users, int S, int cluster,
+                           int threads, const double* init, glt_result* results, cudaStream_t s)
+{
+    switch (threads) {
+    case 128: return launch_track_t<128, VAR>(descs, users, S, cluster, init, results, s);
+    case 256: return launch_track_t<256, VAR>(descs, users, S, cluster, init, results, s);
+    case 512: return launch_track_t<512, VAR>(descs, users, S, cluster, init, results, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
 
-bool track_shape_ok(int cluster, int threads, bool mixed)
+bool track_shape_ok(int cluster, int threads, int variant)
 {
     if (cluster < 1 || cluster > 16) return false;
-    switch (threads) {
-    case 128: return mixed ? shape_ok_t<128, true>(cluster) : shape_ok_t<128, false>(cluster);
-    case 256: return mixed ? shape_ok_t<256, true>(cluster) : shape_ok_t<256, false>(cluster);
-    case 512: return mixed ? shape_ok_t<512, true>(cluster) : shape_ok_t<512, false>(cluster);
+    switch (variant) {
+    case 0: return shape_ok_v<0>(cluster, threads);
+    case 1: return shape_ok_v<1>(cluster, threads);
+    case 2: return shape_ok_v<2>(cluster, threads);
+    case 3: return shape_ok_v<3>(cluster, threads);
     default: return false;
     }
 }
 
 cudaError_t launch_track(const StreamDesc* const* descs, const int* users, int S, int cluster,
-                         int threads, bool mixed, const double* init, glt_result* results,
+                         int threads, int variant, const double* init, glt_result* results,
                          cudaStream_t s)
 {
-    switch (threads) {
-    case 128:
-        return mixed ? launch_track_t<128, true>(descs, users, S, cluster, init, results, s)
-                     : launch_track_t<128, false>(descs, users, S, cluster, init, results, s);
-    case 256:
-        return mixed ? launch_track_t<256, true>(descs, users, S, cluster, init, results, s)
-                     : launch_track_t<256, false>(descs, users, S, cluster, init, results, s);
-    case 512:
-        return mixed ? launch_track_t<512, true>(descs, users, S, cluster, init, results, s)
-                     : launch_track_t<512, false>(descs, users, S, cluster, init, results, s);
-    default:
-        return cudaErrorInvalidValue;
+    switch (variant) {
+    case 0: return launch_track_v<0>(descs, users, S, cluster, threads, init, results, s);
+    case 1: return launch_track_v<1>(descs, users, S, cluster, threads, init, results, s);
+    case 2: return launch_track_v<2>(descs, users, S, cluster, threads, init, results, s);
+    case 3: return launch_track_v<3>(descs, users, S, cluster, threads, init, results, s);
+    default: return cudaErrorInvalidValue;
     }
 }
 
@@ -239,12 +263,19 @@ cudaError_t launch_linearize(const glt_tracker* t, const PassParams& P, bool wan
     const int blocks = (t->N + T - 1) / T;
     if (blocks <= 0 || blocks > t->lin_blocks) return cudaErrorInvalidValue;
     float* res = want_res ? t->lin_res : nullptr;
-    if (t->cfg.precision == GLT_MIXED)
-        linearize_kernel<T, true><<<blocks, T, 0, s>>>(t->desc_dev, P, t->lin_partials,
-                                                       t->lin_counter, t->lin_out, res);
+    const int v = track_variant(t->cfg);
+    if (v == 1)
+        linearize_kernel<T, 1><<<blocks, T, 0, s>>>(t->desc_dev, P, t->lin_partials,
+                                                    t->lin_counter, t->lin_out, res);
+    else if (v == 2)
+        linearize_kernel<T, 2><<<blocks, T, 0, s>>>(t->desc_dev, P, t->lin_partials,
+                                                    t->lin_counter, t->lin_out, res);
+    else if (v == 3)
+        linearize_kernel<T, 3><<<blocks, T, 0, s>>>(t->desc_dev, P, t->lin_partials,
+                                                    t->lin_counter, t->lin_out, res);
     else
-        linearize_kernel<T, false><<<blocks, T, 0, s>>>(t->desc_dev, P, t->lin_partials,
-                                                        t->lin_counter, t->lin_out, res);
+        linearize_kernel<T, 0><<<blocks, T, 0, s>>>(t->desc_dev, P, t->lin_partials,
+                                                    t->lin_counter, t->lin_out, res);
     return cudaGetLastError();
 }
 
