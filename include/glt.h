@@ -113,7 +113,7 @@ typedef struct glt_config {
     int pattern;                /* 0: the 8-pixel sparse pattern; odd p in 3..11: the
                                    paper's p x p patch (Sec. IV-A; 7 x 7 and 11 x 11 in
                                    Sec. V), samples row by row from (-(p-1)/2, -(p-1)/2);
-                                   p x p needs precision GLT_FP32 */
+                                   p x p needs precision GLT_FP32 and 256 (or 0) threads */
     int affine;                 /* 1: estimate (a, b); 0: keep the initial (a, b) (the
                                    paper estimates no brightness change) */
 } glt_config;

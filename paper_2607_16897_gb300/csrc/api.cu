@@ -112,6 +112,8 @@ static int check_config(const glt_config* c)
         return invalid("pattern must be 0 (8-pixel) or an odd patch size 3..11");
     if (c->pattern != 0 && c->precision != GLT_FP32)
         return invalid("p x p patches need precision GLT_FP32");
+    if (c->pattern != 0 && c->threads != 0 && c->threads != 256)
+        return invalid("p x p patches run with 256 threads per CTA");
     if (c->affine != 0 && c->affine != 1) return invalid("affine must be 0 or 1");
     return GLT_OK;
 }
@@ -123,8 +125,9 @@ static void resolve_shape(glt_tracker* t)
     int threads = t->cfg.threads ? t->cfg.threads : 256;
     int cluster = t->cfg.cluster;
     if (cluster == 0) {
-        cluster = (t->N + threads - 1) / threads;
-        cluster = std::min(16, std::max(1, cluster));
+        // about one point per thread, in units of the 8-pixel pattern's work
+        const long long work = (long long)t->N * std::max(1, t->K / 8);
+        cluster = (int)std::min<long long>(16, std::max<long long>(1, (work + threads - 1) / threads));
     }
     while (cluster > 1 && !track_shape_ok(cluster, threads, variant)) cluster = cluster > 8 ? 8 : cluster - 1;
     t->cluster = cluster;

@@ -176,27 +176,94 @@ __device__ __forceinline__ void accumulate_sample(const PointGeom& G, float I, f
     acc[kIdxN] += 1.0f;
 }
 
-// The p x p patch (the paper's Sec. IV-A patch): K = p*p samples read one by
-// one (four taps, plus the gradient taps in the forward form) through the
-// read-only cache; FP32 levels only.  Inlined so the accumulators stay in
-// registers.
-__device__ __forceinline__ void linearize_square(const StreamDesc& D, const PassParams& P, int p,
-                                              PointGeom& G, float* acc, float* res)
+// Geometric rows at the reference point (identity pose), for the
+// inverse-compositional form.
+__device__ __forceinline__ void ic_geometry(const StreamDesc& D, const PassParams& P, int p, PointGeom& G)
+{
+    const float4 q = D.pt[p];
+    const float rho = D.dz[p].y;
+    const float fxl = D.fx * P.scale * rho, fyl = D.fy * P.scale * rho;
+    G.a0[0] = fxl;
+    G.a0[1] = 0.0f;
+    G.a0[2] = -fxl * q.z;
+    G.a1[0] = 0.0f;
+    G.a1[1] = fyl;
+    G.a1[2] = -fyl * q.w;
+}
+
+// The p x p patch (the paper's Sec. IV-A patch) for p = 7 and 11: the point's
+// window of (p + 1) x (p + 1) bytes (inverse compositional) or (p + 3) x (p + 3)
+// (forward: the gradient taps) is loaded once with three aligned 8-byte loads
+// per row and funnel shifts, and all p*p samples are interpolated from
+// registers.  FP32 levels only.
+template <int PS, bool ICF>
+__device__ __forceinline__ void linearize_square_t(const StreamDesc& D, const PassParams& P, int p,
+                                                   PointGeom& G, float* acc, float* res)
+{
+    constexpr int h = (PS - 1) / 2, B = ICF ? 0 : 1, R = PS + 1 + 2 * B, NWD = (R + 3) / 4;
+    const LevelDev& lv = D.lv[P.level];
+    if (ICF) ic_geometry(D, P, p, G);
+    const int xs = G.xb - h - B, ys = G.yb - h - B;
+    const int a8 = xs & ~7, sh = xs - a8;
+    const int wb = sh >> 2, s8 = (sh & 3) * 8;
+    const uint8_t* base = lv.img + (size_t)ys * lv.pitch + a8;
+    uint32_t win[R][NWD];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint2* rp = reinterpret_cast<const uint2*>(base + (size_t)r * lv.pitch);
+        const uint2 u0 = __ldg(rp), u1 = __ldg(rp + 1), u2 = __ldg(rp + 2);
+        const uint32_t v[6] = {u0.x, u0.y, u1.x, u1.y, u2.x, u2.y};
+#pragma unroll
+        for (int i = 0; i < NWD; ++i) {
+            const uint32_t lo = wb ? v[i + 1] : v[i];
+            const uint32_t hi = wb ? v[i + 2] : v[i + 1];
+            win[r][i] = __funnelshift_r(lo, hi, s8);
+        }
+    }
+#define GLT_WX(r, c) ((float)((win[(r)][(c) >> 2] >> (8 * ((c) & 3))) & 0xffu))
+    const float w00 = (1.0f - G.al) * (1.0f - G.be), w10 = G.al * (1.0f - G.be);
+    const float w01 = (1.0f - G.al) * G.be, w11 = G.al * G.be;
+    const float* I0p = D.I0 + ((size_t)P.level * D.Npad + p) * (PS * PS);
+    const float2* G0p = ICF ? D.G0 + ((size_t)P.level * D.Npad + p) * (PS * PS) : nullptr;
+#pragma unroll
+    for (int j = 0; j < PS; ++j) {
+#pragma unroll
+        for (int i = 0; i < PS; ++i) {
+            const int r0 = j + B, c0 = i + B, k = j * PS + i;
+            const float I00 = GLT_WX(r0, c0), I10 = GLT_WX(r0, c0 + 1);
+            const float I01 = GLT_WX(r0 + 1, c0), I11 = GLT_WX(r0 + 1, c0 + 1);
+            const float I = fmaf(w00, I00, fmaf(w10, I10, fmaf(w01, I01, w11 * I11)));
+            float gx, gy;
+            if (ICF) {
+                const float2 g0 = G0p[k];
+                gx = P.ea * g0.x;
+                gy = P.ea * g0.y;
+            } else {
+                gx = 0.5f * fmaf(w00, I10 - GLT_WX(r0, c0 - 1),
+                            fmaf(w10, GLT_WX(r0, c0 + 2) - I00,
+                            fmaf(w01, I11 - GLT_WX(r0 + 1, c0 - 1),
+                                 w11 * (GLT_WX(r0 + 1, c0 + 2) - I01))));
+                gy = 0.5f * fmaf(w00, I01 - GLT_WX(r0 - 1, c0),
+                            fmaf(w10, I11 - GLT_WX(r0 - 1, c0 + 1),
+                            fmaf(w01, GLT_WX(r0 + 2, c0) - I00,
+                                 w11 * (GLT_WX(r0 + 2, c0 + 1) - I10))));
+            }
+            accumulate_sample(G, I, gx, gy, I0p[k], P.ea, P.b, D.huber_k, acc,
+                              res ? res + (size_t)(PS * PS) * p + k : nullptr);
+        }
+    }
+#undef GLT_WX
+}
+
+// Any other odd p (3..11): samples read one by one (four taps, plus the
+// gradient taps in the forward form) through the read-only cache.
+__device__ __forceinline__ void linearize_square_any(const StreamDesc& D, const PassParams& P, int p,
+                                                     PointGeom& G, float* acc, float* res)
 {
     const LevelDev& lv = D.lv[P.level];
     const int K = D.K, h = (D.pattern - 1) / 2, S = lv.pitch;
     const bool ic = D.G0 != nullptr;
-    if (ic) {
-        const float4 q = D.pt[p];
-        const float rho = D.dz[p].y;
-        const float fxl = D.fx * P.scale * rho, fyl = D.fy * P.scale * rho;
-        G.a0[0] = fxl;
-        G.a0[1] = 0.0f;
-        G.a0[2] = -fxl * q.z;
-        G.a1[0] = 0.0f;
-        G.a1[1] = fyl;
-        G.a1[2] = -fyl * q.w;
-    }
+    if (ic) ic_geometry(D, P, p, G);
     const float w00 = (1.0f - G.al) * (1.0f - G.be), w10 = G.al * (1.0f - G.be);
     const float w01 = (1.0f - G.al) * G.be, w11 = G.al * G.be;
     const float* I0p = D.I0 + ((size_t)P.level * D.Npad + p) * K;
@@ -222,6 +289,22 @@ __device__ __forceinline__ void linearize_square(const StreamDesc& D, const Pass
                              w11 * ((float)__ldg(t + 2 * S + 1) - I10))));
         }
         accumulate_sample(G, I, gx, gy, I0p[k], P.ea, P.b, D.huber_k, acc, res ? res + (size_t)K * p + k : nullptr);
+    }
+}
+
+// Inlined so the accumulators stay in registers.
+__device__ __forceinline__ void linearize_square(const StreamDesc& D, const PassParams& P, int p,
+                                                 PointGeom& G, float* acc, float* res)
+{
+    const bool ic = D.G0 != nullptr;
+    if (D.pattern == 7) {
+        if (ic) linearize_square_t<7, true>(D, P, p, G, acc, res);
+        else linearize_square_t<7, false>(D, P, p, G, acc, res);
+    } else if (D.pattern == 11) {
+        if (ic) linearize_square_t<11, true>(D, P, p, G, acc, res);
+        else linearize_square_t<11, false>(D, P, p, G, acc, res);
+    } else {
+        linearize_square_any(D, P, p, G, acc, res);
     }
 }
 
@@ -261,15 +344,7 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
     const bool ic = IC && D.G0 != nullptr;
     const float2* G0p = nullptr;
     if (ic) {
-        const float4 q = D.pt[p];
-        const float rho = D.dz[p].y;
-        const float fxl = D.fx * P.scale * rho, fyl = D.fy * P.scale * rho;
-        G.a0[0] = fxl;
-        G.a0[1] = 0.0f;
-        G.a0[2] = -fxl * q.z;
-        G.a1[0] = 0.0f;
-        G.a1[1] = fyl;
-        G.a1[2] = -fyl * q.w;
+        ic_geometry(D, P, p, G);
         G0p = D.G0 + ((size_t)P.level * D.Npad + p) * 8;
     }
     const float w00 = (1.0f - G.al) * (1.0f - G.be), w10 = G.al * (1.0f - G.be);

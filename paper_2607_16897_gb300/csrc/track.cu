@@ -217,6 +217,13 @@ bool shape_ok_v(int cluster, int threads)
     }
 }
 
+// the p x p variant is built for 256 threads only (its unrolled patches are long)
+template <>
+bool shape_ok_v<2>(int cluster, int threads)
+{
+    return threads == 256 && shape_ok_t<256, 2>(cluster);
+}
+
 template <int VAR>
 cudaError_t launch_track_v(const StreamDesc* const* descs, const int* users, int S, int cluster,
                            int threads, const double* init, glt_result* results, cudaStream_t s)
@@ -227,6 +234,14 @@ cudaError_t launch_track_v(const StreamDesc* const* descs, const int* users, int
     case 512: return launch_track_t<512, VAR>(descs, users, S, cluster, init, results, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+template <>
+cudaError_t launch_track_v<2>(const StreamDesc* const* descs, const int* users, int S, int cluster,
+                              int threads, const double* init, glt_result* results, cudaStream_t s)
+{
+    if (threads != 256) return cudaErrorInvalidValue;
+    return launch_track_t<256, 2>(descs, users, S, cluster, init, results, s);
 }
 
 }  // namespace
