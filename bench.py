@@ -135,9 +135,13 @@ class SequenceDriver:
     renderer's true pose and depth: that frame becomes the new reference."""
 
     def __init__(self, wl: Workload, interval=8, max_cost=None):
+        from paper_2607_16897_gb300.tween import TweenSwitch
         self.wl = wl
         self.interval = interval
         self.max_cost = wl.max_cost if max_cost is None else max_cost
+        p = wl.solver.get("pattern", 0)
+        self.switch = TweenSwitch(max_direct=interval, max_cost=self.max_cost,
+                                  samples_per_point=8 if p == 0 else p * p)
         self.rejected = 0
         self.r = 0
         self.since = 0
@@ -160,8 +164,8 @@ class SequenceDriver:
         self.ab = (float(res["a"]), float(res["b"]))
         self.Tw.pop(k - 3, None)
         self.since += 1
-        bad = (res["status"] != 0 or res["n_valid"] < 0.5 * 8 * self.wl.N
-               or not res["cost"] <= self.max_cost)
+        bad = not self.switch.direct_ok(res, self.wl.N)
+        self.switch.after_direct(res, self.wl.N)
         if bad:
             # the indirect pipeline re-localises this frame
             self.Tw[k] = self.wl.T_ref_world(k)
@@ -853,7 +857,10 @@ def run_batch(args):
                "median_trans_mm": float(1000 * np.median([e[1] for e in gt])),
                "p99_trans_mm": float(1000 * np.percentile([e[1] for e in gt], 99)),
                "status_nonzero": int(sum(1 for r in rec if r[4]["status"])),
-               "rejected_frames": int(sum(d.rejected for d in drvs))}
+               "rejected_frames": int(sum(d.rejected for d in drvs)),
+               "direct_acceptance": float(
+                   sum(d.switch.direct_accepted for d in drvs)
+                   / max(1, sum(d.switch.direct_accepted + d.switch.direct_rejected for d in drvs)))}
         return dict(dev_ms=dev_ms, dev_s=dev_s, t_wall=t_wall, clk=clk, rec=rec, n_ref=n_ref,
                     value=world * S * args.steps / dev_s, accuracy=acc,
                     iters_per_frame=float(np.mean([r[4]["iters_total"] for r in rec])),
