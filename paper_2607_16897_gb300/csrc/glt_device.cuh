@@ -817,36 +817,39 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
                 B = 2.0 * sh * sh / th2;
                 Cc = (th - sn) / (th2 * th);
             }
+            // ---- E = exp(delta_xi) as a 3x4 [R_e | t_e], one element (r, c) per lane
+            // 0-11, every lane running the same FP64 instructions on its own operands:
+            //   R_e(r, c) = d_rc + A W_rc + B (w_r w_c - d_rc th2)            (W = [w]x)
+            //   t_e(r)    = v_r + B (w x v)_r + C (w_r (w . v) - v_r th2)
+            // as  base + cA (a1 b1 - a2 b2) + cB (p q - d th2).
             const double v0 = dl[0], v1 = dl[1], v2 = dl[2];
-            const double c10 = fma(w1, v2, -w2 * v1), c11 = fma(w2, v0, -w0 * v2), c12 = fma(w0, v1, -w1 * v0);
-            const double c20 = fma(w1, c12, -w2 * c11), c21 = fma(w2, c10, -w0 * c12), c22 = fma(w0, c11, -w1 * c10);
-            const double te0 = fma(Cc, c20, fma(B, c10, v0));
-            const double te1 = fma(Cc, c21, fma(B, c11, v1));
-            const double te2 = fma(Cc, c22, fma(B, c12, v2));
-            // ---- Tc = T exp(delta_xi), one element (r, c) per lane:
-            // rotation  Rc_rc = R_rc + A (R_r x w)_c + B ((R_r . w) w_c - th2 R_rc)
-            // translation tc_r = R_r . t_e + t_r
+            const double wv = fma(w0, v0, fma(w1, v1, w2 * v2));
+            const int er = (lane >> 2) % 3, ec = lane & 3;
+            const double wr = er == 0 ? w0 : (er == 1 ? w1 : w2);
+            const double wr1 = er == 0 ? w1 : (er == 1 ? w2 : w0);   // w_{r+1}
+            const double wr2 = er == 0 ? w2 : (er == 1 ? w0 : w1);   // w_{r+2}
+            const double vr = er == 0 ? v0 : (er == 1 ? v1 : v2);
+            const double vr1 = er == 0 ? v1 : (er == 1 ? v2 : v0);
+            const double vr2 = er == 0 ? v2 : (er == 1 ? v0 : v1);
+            const double wc = ec == 0 ? w0 : (ec == 1 ? w1 : w2);
+            const bool rot = ec < 3;
+            const double drc = (rot && er == ec) ? 1.0 : 0.0;
+            // W_rc = +w_{r+2} if c = r+1, -w_{r+1} if c = r+2, 0 on the diagonal
+            const double Wrc = ec == (er + 1) % 3 ? -wr2 : (ec == (er + 2) % 3 ? wr1 : 0.0);
+            const double base = rot ? drc : vr;
+            const double a1 = rot ? Wrc : wr1, b1 = rot ? 1.0 : vr2;
+            const double a2 = rot ? 0.0 : wr2, b2 = rot ? 0.0 : vr1;
+            const double pq = rot ? wc : wv, dd = rot ? drc : vr;
+            const double ex = fma(a1, b1, -(a2 * b2));
+            const double ey = fma(wr, pq, -(dd * th2));
+            const double E = fma(rot ? B : Cc, ey, fma(rot ? A : B, ex, base));
+            // ---- Tc = T E: Tc(r, c) = sum_k T(r, k) E(k, c) (+ T(r, 3) for c = 3)
+            const double e0 = __shfl_sync(full, E, ec);
+            const double e1 = __shfl_sync(full, E, 4 + ec);
+            const double e2 = __shfl_sync(full, E, 8 + ec);
             if (lane < 12) {
-                const int r = lane >> 2, c = lane & 3;
-                const double* Tr = S.T + 4 * r;
-                const double R0 = Tr[0], R1 = Tr[1], R2 = Tr[2], t = Tr[3];
-                double out;
-                if (c == 3) {
-                    out = fma(R0, te0, fma(R1, te1, fma(R2, te2, t)));
-                } else {
-                    // (R_r x w)_c = R_{c+1} w_{c+2} - R_{c+2} w_{c+1} (indices mod 3)
-                    const double Ra = c == 0 ? R1 : (c == 1 ? R2 : R0);
-                    const double Rb = c == 0 ? R2 : (c == 1 ? R0 : R1);
-                    const double wa = c == 0 ? w1 : (c == 1 ? w2 : w0);
-                    const double wb = c == 0 ? w2 : (c == 1 ? w0 : w1);
-                    const double wc = c == 0 ? w0 : (c == 1 ? w1 : w2);
-                    const double Rc = c == 0 ? R0 : (c == 1 ? R1 : R2);
-                    const double q = fma(Ra, wb, -Rb * wa);
-                    const double pw = fma(R0, w0, fma(R1, w1, R2 * w2));
-                    const double t1 = fma(pw, wc, -th2 * Rc);
-                    out = fma(B, t1, fma(A, q, Rc));
-                }
-                S.Tc[lane] = out;
+                const double* Tr = S.T + 4 * er;
+                S.Tc[lane] = fma(Tr[0], e0, fma(Tr[1], e1, fma(Tr[2], e2, rot ? 0.0 : Tr[3])));
             }
             if (lane == 0) {
                 S.ac = S.a + dl[6];
