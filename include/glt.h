@@ -157,6 +157,8 @@ void glt_destroy(glt_tracker* trk);
  * [1 4 6 4 1]/16 in x and y with clamp-to-edge borders and even-sample
  * decimation, summed exactly in integers and rounded half up.  In GLT_MIXED
  * mode it also writes the FP16 (I, gx, gy) copy of every CUR level.
+ * A host frame is first copied into a device staging buffer of the tracker (so
+ * two host-frame builds on different streams must not overlap).
  * Asynchronous on `stream`.  Errors: INVALID_ARG (slot, pitch < width, NULL). */
 int glt_build_pyramid(glt_tracker* trk, int slot, const uint8_t* img, int pitch_bytes,
                       int is_device, void* stream);

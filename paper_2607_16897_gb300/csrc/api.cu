@@ -74,6 +74,7 @@ static void free_tracker(glt_tracker* t)
     cudaFree(t->lin_counter);
     cudaFree(t->lin_out);
     cudaFree(t->lin_res);
+    cudaFree(t->stage_dev);
     cudaFreeHost(t->h_init);
     cudaFreeHost(t->h_result);
     cudaFreeHost(t->h_lin);
@@ -245,6 +246,7 @@ int glt_create(const glt_config* cfg, glt_tracker** out)
     ALLOC(cudaMemset(t->lin_counter, 0, sizeof(unsigned)));
     ALLOC(dalloc(&t->lin_out, (size_t)kAccPad));
     ALLOC(dalloc(&t->lin_res, (size_t)maxp * t->K));
+    ALLOC(dalloc(&t->stage_dev, (size_t)t->W[0] * t->H[0]));
     ALLOC(cudaMallocHost(reinterpret_cast<void**>(&t->h_init), 14 * sizeof(double)));
     ALLOC(cudaMallocHost(reinterpret_cast<void**>(&t->h_result), sizeof(glt_result)));
     ALLOC(cudaMallocHost(reinterpret_cast<void**>(&t->h_lin), kAccPad * sizeof(double)));
@@ -333,6 +335,20 @@ int glt_build_pyramid(glt_tracker* t, int slot, const uint8_t* img, int pitch_by
     if (pitch_bytes < t->cfg.width) return invalid("pitch_bytes < width");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Pyramid& P = t->pyr[slot];
+    if (!is_device && t->L > 1) {
+        // host frame: one copy into the tracker's device staging buffer, then
+        // the device path (level 1 reads it and writes level 0)
+        const size_t W = (size_t)t->W[0], H = (size_t)t->H[0];
+        if ((size_t)pitch_bytes == W)
+            GLT_CHECK(cudaMemcpyAsync(t->stage_dev, img, W * H, cudaMemcpyHostToDevice, s), "frame upload");
+        else
+            GLT_CHECK(cudaMemcpy2DAsync(t->stage_dev, W, img, (size_t)pitch_bytes, W, H,
+                                        cudaMemcpyHostToDevice, s),
+                      "frame upload");
+        img = t->stage_dev;
+        pitch_bytes = (int)W;
+        is_device = 1;
+    }
     if (is_device && t->L > 1) {
         // level 1 straight from the caller's frame; its tiles write level 0
         for (int l = 1; l < t->L; ++l)
@@ -380,14 +396,14 @@ int glt_set_map_points(glt_tracker* t, const float* uvd, int n, int is_device, v
                   "map point upload");
         src = t->uvd_dev;
     }
+    const bool n_changed = t->N != n || !t->have_points;
     t->N = n;
     t->desc_host.N = n;
-    GLT_CHECK(cudaMemcpyAsync(t->desc_dev, &t->desc_host, sizeof(StreamDesc), cudaMemcpyHostToDevice, s),
-              "descriptor upload");
-    if (n > 0) GLT_CHECK(launch_set_points(t, src, n, s), "map point kernel");
+    // the kernel also stores n into the device descriptor (no host upload)
+    GLT_CHECK(launch_set_points(t, src, n, s), "map point kernel");
     t->have_points = true;
     t->version++;
-    resolve_shape(t);
+    if (n_changed) resolve_shape(t);
     return GLT_OK;
 }
 

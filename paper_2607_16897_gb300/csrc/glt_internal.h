@@ -82,6 +82,7 @@ struct glt_tracker {
     unsigned* lin_counter = nullptr;
     double* lin_out = nullptr;
     float* lin_res = nullptr;
+    uint8_t* stage_dev = nullptr;         // device copy of a host frame (glt_build_pyramid)
     int lin_blocks = 0;
     // pinned host staging
     double* h_init = nullptr;

@@ -15,14 +15,15 @@ struct RefLevels {
     const uint8_t* img[kMaxLevels];
 };
 
-__global__ void set_points_kernel(const StreamDesc* __restrict__ desc, RefLevels ref,
+__global__ void set_points_kernel(StreamDesc* __restrict__ desc, int n, RefLevels ref,
                                   const float* __restrict__ uvd, float cx, float cy,
                                   float4* __restrict__ pt, float2* __restrict__ dz,
                                   float* __restrict__ I0, float2* __restrict__ G0)
 {
     const StreamDesc& D = *desc;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= D.N) return;
+    if (p == 0) desc->N = n;      // the point count the kernels of later passes read
+    if (p >= n) return;
     const float u0 = uvd[3 * p], v0 = uvd[3 * p + 1], d = uvd[3 * p + 2];
     const bool finite = isfinite(u0) && isfinite(v0) && isfinite(d) && d > 0.0f &&
                         fabsf(u0) < 1e7f && fabsf(v0) < 1e7f;
@@ -75,11 +76,10 @@ __global__ void set_points_kernel(const StreamDesc* __restrict__ desc, RefLevels
 cudaError_t launch_set_points(const glt_tracker* t, const float* uvd_dev, int n, cudaStream_t s)
 {
     const int threads = 128;
-    const int blocks = (n + threads - 1) / threads;
-    if (blocks == 0) return cudaSuccess;
+    const int blocks = n > 0 ? (n + threads - 1) / threads : 1;
     RefLevels ref{};
     for (int l = 0; l < t->L; ++l) ref.img[l] = t->pyr[GLT_REF].base + t->pyr[GLT_REF].off[l];
-    set_points_kernel<<<blocks, threads, 0, s>>>(t->desc_dev, ref, uvd_dev, (float)t->cfg.cx,
+    set_points_kernel<<<blocks, threads, 0, s>>>(t->desc_dev, n, ref, uvd_dev, (float)t->cfg.cx,
                                                  (float)t->cfg.cy, t->pt, t->dz, t->I0, t->G0);
     return cudaGetLastError();
 }
