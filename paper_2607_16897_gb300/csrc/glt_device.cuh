@@ -89,12 +89,39 @@ struct PointGeom {
 // accurate at any image width:  with m = ((u0-cx)/fx, (v0-cy)/fy, 1) and
 // D = (R - I) m + t / d,  x_c = d (m + D)  and
 // u - u0 = fx (D_x - m_x D_z) / (1 + D_z)   (exactly Eq. 1's pi(R x_r + t)).
+// A point's data for one level: position, depth, reference patch (I0[0..7];
+// for a p x p patch only I0[0], the validity marker).  Loaded once per level
+// and kept across that level's passes when a thread owns a single point.
+struct PointCache {
+    float4 q;
+    float2 dz;
+    float4 ia, ib;
+    int p, level;
+};
+
+__device__ __forceinline__ void load_point(const StreamDesc& D, int level, int p, PointCache& c)
+{
+    c.q = D.pt[p];
+    c.dz = D.dz[p];
+    const float* I0b = D.I0 + ((size_t)level * D.Npad + p) * D.K;
+    if (D.pattern) {
+        c.ia = make_float4(I0b[0], 0.f, 0.f, 0.f);   // the p x p path reads its samples itself
+        c.ib = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        const float4* I0p = reinterpret_cast<const float4*>(I0b);   // K = 8: 32-byte rows
+        c.ia = I0p[0];
+        c.ib = I0p[1];
+    }
+    c.p = p;
+    c.level = level;
+}
+
 template <bool SQUARE = false>
 __device__ __forceinline__ bool project_point(const StreamDesc& D, const PassParams& P,
-                                              const LevelDev& lv, int p, PointGeom& G)
+                                              const LevelDev& lv, const PointCache& c, PointGeom& G)
 {
-    const float4 q = D.pt[p];
-    const float2 dz = D.dz[p];
+    const float4 q = c.q;
+    const float2 dz = c.dz;
     const float ub = q.z, vb = q.w, d = dz.x, rho = dz.y;
     const float Dx = fmaf(P.Rm[0], ub, fmaf(P.Rm[1], vb, fmaf(P.t[0], rho, P.Rm[2])));
     const float Dy = fmaf(P.Rm[3], ub, fmaf(P.Rm[4], vb, fmaf(P.t[1], rho, P.Rm[5])));
@@ -313,21 +340,14 @@ __device__ __forceinline__ void linearize_square(const StreamDesc& D, const Pass
 // SQUARE: the p x p path is compiled in; IC: the inverse-compositional rows
 // are compiled in (both decided per stream at run time when compiled in).
 template <bool MIXED, bool RES, bool SQUARE = false, bool IC = true>
-__device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassParams& P, int p,
-                                                float* acc, float* res)
+__device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassParams& P,
+                                                const PointCache& c, float* acc, float* res)
 {
     const LevelDev& lv = D.lv[P.level];
-    const float* I0b = D.I0 + ((size_t)P.level * D.Npad + p) * D.K;
-    float4 ia = make_float4(0.f, 0.f, 0.f, 0.f), ib = ia;
-    if (D.pattern) {
-        ia.x = I0b[0];              // the p x p path reads its samples itself
-    } else {
-        const float4* I0p = reinterpret_cast<const float4*>(I0b);   // K = 8: 32-byte rows
-        ia = I0p[0];
-        ib = I0p[1];
-    }
+    const int p = c.p;
+    const float4 ia = c.ia, ib = c.ib;
     PointGeom G;
-    bool ok = !isnan(ia.x) && project_point<SQUARE>(D, P, lv, p, G);
+    bool ok = !isnan(ia.x) && project_point<SQUARE>(D, P, lv, c, G);
     if (!ok) {
         if (RES) {
             for (int k = 0; k < D.K; ++k) res[(size_t)D.K * p + k] = __int_as_float(0x7fc00000);

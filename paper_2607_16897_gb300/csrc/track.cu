@@ -60,12 +60,20 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
     __syncthreads();
 
     int par = 0;
+    PointCache pc;
+    pc.p = -1;
+    pc.level = -1;
     while (!P.done) {
         float acc[kAccPad];
 #pragma unroll
         for (int i = 0; i < kAccPad; ++i) acc[i] = 0.0f;
-        for (int p = rank * THREADS + tid; p < sD.N; p += C * THREADS)
-            linearize_point<MIXED, false, SQUARE, IC>(sD, P, p, acc, nullptr);
+        for (int p = rank * THREADS + tid; p < sD.N; p += C * THREADS) {
+            // a thread that owns one point keeps its data for the whole level
+            // (the 128-thread shape, capped at 128 registers for batches of
+            // many streams, reloads it instead)
+            if (THREADS == 128 || pc.p != p || pc.level != P.level) load_point(sD, P.level, p, pc);
+            linearize_point<MIXED, false, SQUARE, IC>(sD, P, pc, acc, nullptr);
+        }
         block_reduce<THREADS, MIXED>(acc, red, part[par], part_c[par]);
         if (C > 1) cluster.sync();
         if (tid < kNumAcc) {
@@ -128,10 +136,12 @@ __global__ void __launch_bounds__(THREADS) linearize_kernel(const StreamDesc* __
     for (int i = 0; i < kAccPad; ++i) acc[i] = 0.0f;
     const int p = blockIdx.x * THREADS + threadIdx.x;
     if (p < D.N) {
+        PointCache pc;
+        load_point(D, P.level, p, pc);
         if (res)
-            linearize_point<MIXED, true, SQUARE, IC>(D, P, p, acc, res);
+            linearize_point<MIXED, true, SQUARE, IC>(D, P, pc, acc, res);
         else
-            linearize_point<MIXED, false, SQUARE, IC>(D, P, p, acc, nullptr);
+            linearize_point<MIXED, false, SQUARE, IC>(D, P, pc, acc, nullptr);
     }
     block_reduce<THREADS, MIXED>(acc, red, part, part_c);
     if (threadIdx.x < kNumAcc)
