@@ -755,6 +755,9 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
         const double a0 = fma(lambda, diag, diag);   // damped diagonal (lanes 0-7)
         double dg = a0;
         double dinv = 0.0;
+        // the forward substitution L y = -g rides along: y_i -= l_ij y_j with the
+        // l_ij the diagonal update already fetched (lanes 0-7 hold y_i)
+        double y = -S.g[row];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const double d = __shfl_sync(full, dg, j);
@@ -769,8 +772,12 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
                 const double ak = __shfl_sync(full, e, cj + (trail ? ek : j + 1));
                 const double ld = __shfl_sync(full, l, cj + (drow ? lane : j + 1));
                 const double ad = __shfl_sync(full, e, cj + (drow ? lane : j + 1));
+                const double yj = __shfl_sync(full, y, j);
                 if (trail) e = fma(-li, ak, e);
-                if (drow) dg = fma(-ld, ad, dg);
+                if (drow) {
+                    dg = fma(-ld, ad, dg);
+                    y = fma(-ld, yj, y);
+                }
                 if (lane < 28 && ek == j) e = l;
             }
         }
@@ -782,28 +789,15 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
             finish = true;
             next_level = true;
         } else {
-            // row `row` of L (entries left of the diagonal) and column `row`
-            // (entries below it) gathered into the row's lane
-            double Lrow[8], Lcol[8];
-#pragma unroll
-            for (int c = 0; c < 7; ++c) {
-                const int cc = c * 7 - (c * (c - 1)) / 2 - c - 1;
-                const double v = __shfl_sync(full, e, cc + (row > c ? row : c + 1));
-                Lrow[c] = row > c ? v : 0.0;
-            }
+            // column `row` of L (entries below the diagonal) gathered into the row's lane
+            double Lcol[8];
 #pragma unroll
             for (int i = 1; i < 8; ++i) {
                 const int cr = row * 7 - (row * (row - 1)) / 2 - row - 1;
                 const double v = __shfl_sync(full, e, row < i ? cr + i : 0);
                 Lcol[i] = row < i ? v : 0.0;
             }
-            // forward (L y = -g), diagonal, backward (L^T x = D^-1 y)
-            double y = -S.g[row];
-#pragma unroll
-            for (int j = 0; j < 7; ++j) {
-                const double yj = __shfl_sync(full, y, j);
-                if (row > j) y = fma(-Lrow[j], yj, y);
-            }
+            // diagonal, backward (L^T x = D^-1 y)
             double x = y * dinv;
 #pragma unroll
             for (int j = 7; j >= 1; --j) {
