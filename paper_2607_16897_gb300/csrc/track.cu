@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
     if (tid == 0) solver_init(sD, init + 14 * user, S, P);
     __syncthreads();
 
+    const int tail_warp = (int)(blockIdx.x % NW);
     int par = 0;
     PointCache pc;
     pc.p = -1;
@@ -104,7 +105,9 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
             tot[tid] = (double)hi + (double)lo;
         }
         __syncthreads();
-        if (tid < 32) solver_step_warp(sD, tot, S, P, tid, rank == 0);
+        // the FP64 tail runs on one warp; CTAs of different streams that share an
+        // SM use different warps so their tails spread over the SM's sub-partitions
+        if ((tid >> 5) == tail_warp) solver_step_warp(sD, tot, S, P, tid & 31, rank == 0);
         __syncthreads();
         par ^= 1;
     }
