@@ -343,6 +343,11 @@ int glt_nn_train_step(glt_nn* nn, const float* x_dev, const float* m_dev, const 
  * Errors: INVALID_ARG (size, max_batch < S), CUDA. */
 int glt_batch_set_proposal(glt_batch* batch, glt_nn* nn, const float* motion_dev);
 
+/* Name of a return code (GLT_OK, GLT_ERR_*) or, for a positive value, of the
+ * glt_result.status bits it holds ("ok", "too few points", "not positive
+ * definite", joined by "|"); never NULL, static storage. */
+const char* glt_status_string(int code);
+
 /* Thread-local message of the last error (never NULL). */
 const char* glt_last_error(void);
 

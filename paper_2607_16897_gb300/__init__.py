@@ -106,6 +106,7 @@ SIGNATURES = {
     "glt_nn_gradient": (_i, [_vp, _vp, _vp, _vp, _i, _P(ctypes.c_float), _P(ctypes.c_float), _vp]),
     "glt_nn_train_step": (_i, [_vp, _vp, _vp, _vp, _i, ctypes.c_float, _vp, _vp]),
     "glt_batch_set_proposal": (_i, [_vp, _vp, _vp]),
+    "glt_status_string": (ctypes.c_char_p, [_i]),
     "glt_last_error": (ctypes.c_char_p, []),
     "glt_version": (ctypes.c_char_p, []),
 }

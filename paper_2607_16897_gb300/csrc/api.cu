@@ -141,6 +141,22 @@ using namespace glt;
 
 extern "C" {
 
+const char* glt_status_string(int code)
+{
+    switch (code) {
+    case GLT_OK: return "ok";
+    case GLT_ERR_INVALID_ARG: return "invalid argument";
+    case GLT_ERR_CUDA: return "CUDA error";
+    case GLT_ERR_NO_REFERENCE: return "no reference";
+    case GLT_ERR_CAPACITY: return "capacity exceeded";
+    case GLT_ERR_UNSUPPORTED: return "unsupported";
+    case GLT_TRACK_TOO_FEW_POINTS: return "too few points";
+    case GLT_TRACK_NOT_PD: return "not positive definite";
+    case GLT_TRACK_TOO_FEW_POINTS | GLT_TRACK_NOT_PD: return "too few points|not positive definite";
+    default: return "unknown";
+    }
+}
+
 const char* glt_last_error(void) { return g_err.c_str(); }
 
 const char* glt_version(void) { return "glt 0.1 (sm_103a)"; }

@@ -72,3 +72,13 @@ def test_host_side_argument_checks(lib_path):
         assert glt.glt_last_error()
     assert glt.glt_build_pyramid(None, 0, None, 0, 0, None) == glt.GLT_ERR_INVALID_ARG
     assert glt.glt_batch_create(None, 0, ctypes.byref(ctypes.c_void_p())) == glt.GLT_ERR_INVALID_ARG
+
+
+def test_status_strings(lib_path):
+    import paper_2607_16897_gb300 as glt
+    assert glt.glt_status_string(0) == b"ok"
+    assert glt.glt_status_string(glt.GLT_ERR_INVALID_ARG) == b"invalid argument"
+    assert glt.glt_status_string(glt.GLT_ERR_CAPACITY) == b"capacity exceeded"
+    assert glt.glt_status_string(glt.GLT_TRACK_NOT_PD) == b"not positive definite"
+    assert glt.glt_status_string(3) == b"too few points|not positive definite"
+    assert glt.glt_status_string(-99) == b"unknown"
