@@ -37,6 +37,33 @@ TRACK_TRAFFIC = {"c2": 783616, "c3": 55166208}
 I34 = np.hstack([np.eye(3), np.zeros((3, 1))])
 
 
+# ---------------------------------------------------------------------------
+# replicas over ranks: independent streams per GPU, the slowest rank's time
+# ---------------------------------------------------------------------------
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Entry-wise maximum of `values` over the ranks of the process group (the
+    slowest rank bounds a step); the values themselves without a group."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def aggregate_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: every rank processed `units_per_rank` units in at
+    most `seconds` (weak scaling: the work per GPU is fixed)."""
+    return world * units_per_rank / seconds
+
+
+def stream_seed(kind, s, rank):
+    """Seed of stream s of workload `kind` on `rank` (replicas get disjoint
+    sequences)."""
+    base = {"c2": 1, "c2p": 1, "c2e": 1, "c4": 2000, "c3": 1000, "c4b": 2000, "c5": 5000}[kind]
+    return base + s + (100000 * rank if kind in ("c3", "c4b", "c5") else rank)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -475,11 +502,8 @@ def run_ours(args):
     trk_ms = [e1.elapsed_time(e2) for _, e1, e2 in ev]
     ref_ms = [a.elapsed_time(b) for a, b in ev_ref[:n_ref]]
     dev_s = sum(step_ms) / 1000.0
-    if dist:
-        t = torch.tensor([dev_s, t_wall], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s, t_wall = float(t[0]), float(t[1])
-    value = world * args.steps / dev_s
+    dev_s, t_wall = max_over_ranks([dev_s, t_wall], dist, f"cuda:{local}")
+    value = aggregate_rate(args.steps, world, dev_s)
     passes = [r[4]["passes"] for r in rec]
 
     # accuracy vs ground truth along the sequence
@@ -680,21 +704,21 @@ PAPER_SOLVER = dict(affine=False, lambda0=0.0, accept_step=1e30, eps_step=0.0,
 
 def single_workload(kind, rank=0):
     if kind == "c2p":
-        return Workload(seed=1 + rank, frames=300, N=2000, W=640, H=480, f=525.0, L=6,
+        return Workload(seed=stream_seed(kind, 0, rank), frames=300, N=2000, W=640, H=480, f=525.0, L=6,
                         exposure=False, solver=dict(PAPER_SOLVER, pattern=7), jacobian="ic",
                         max_cost=50.0,
                         label="C2 in the paper's configuration (TUM-like, 7x7 patches, IC, "
                               "6 levels, 10 GN iterations per level, no affine, no Huber)")
     if kind == "c2e":
-        return Workload(seed=1 + rank, frames=300, N=2000, W=752, H=480, f=458.0, L=6,
+        return Workload(seed=stream_seed(kind, 0, rank), frames=300, N=2000, W=752, H=480, f=458.0, L=6,
                         exposure=False, solver=dict(PAPER_SOLVER, pattern=11), jacobian="ic",
                         max_cost=50.0,
                         label="752x480 in the paper's configuration (EuRoC-like, 11x11 patches, "
                               "IC, 6 levels, 10 GN iterations per level, no affine, no Huber)")
     if kind == "c4":
-        return Workload(seed=2000 + rank, frames=300, N=8000, W=1280, H=720, f=1050.0, L=5,
+        return Workload(seed=stream_seed(kind, 0, rank), frames=300, N=8000, W=1280, H=720, f=1050.0, L=5,
                         speed=1.0, ang=60.0, label="C4 mixed precision, single stream")
-    return Workload(seed=1 + rank)
+    return Workload(seed=stream_seed("c2", 0, rank))
 
 
 def batch_workloads(kind, rank=0, nstreams=None, frames=24, pool=None):
@@ -712,18 +736,18 @@ def batch_workloads(kind, rank=0, nstreams=None, frames=24, pool=None):
     wls = []
     for s in range(nstreams):
         if kind == "c4b":
-            wls.append(Workload(seed=2000 + s + 100000 * rank, frames=frames, N=8000, W=1280, H=720,
+            wls.append(Workload(seed=stream_seed(kind, s, rank), frames=frames, N=8000, W=1280, H=720,
                                 f=1050.0, L=5, speed=1.0, ang=60.0, label="C4b stream",
                                 render=pool is None))
         elif kind == "c5":
-            seed = prop.TEST_SEED0 + s + 100000 * rank
+            seed = stream_seed(kind, s, rank)
             v, w = prop.stream_motion(seed)
             wls.append(Workload(seed=seed, frames=frames, N=2000, W=640, H=480, f=525.0, L=5,
                                 speed=v, ang=w, label="C5 stream", render=pool is None))
         else:
             W, H = sizes[int(rng.integers(4))]
             N = int(rng.integers(300, 4001))
-            wls.append(Workload(seed=1000 + s + 100000 * rank, frames=frames, N=N, W=W, H=H,
+            wls.append(Workload(seed=stream_seed(kind, s, rank), frames=frames, N=N, W=W, H=H,
                                 f=0.8 * W, L=4, label="C3 stream", render=pool is None))
     if pool is not None:
         jobs = [w.job + (k, 0, w.speed, w.ang) for w in wls for k in range(frames)]
@@ -916,10 +940,7 @@ def run_batch(args):
         t_wall = time.perf_counter() - t0
         clk = clocks.stop()
         dev_s = sum(dev_ms) / 1000.0
-        if dist:
-            t = torch.tensor([dev_s, t_wall], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dev_s, t_wall = float(t[0]), float(t[1])
+        dev_s, t_wall = max_over_ranks([dev_s, t_wall], dist, dev)
         gt = [pose_error(wls[r[0]], r[1], r[2], r[4]["T"]) for r in rec]
         acc = {"median_rot_deg": float(np.rad2deg(np.median([e[0] for e in gt]))),
                "median_trans_mm": float(1000 * np.median([e[1] for e in gt])),
@@ -930,7 +951,7 @@ def run_batch(args):
                    sum(d.switch.direct_accepted for d in drvs)
                    / max(1, sum(d.switch.direct_accepted + d.switch.direct_rejected for d in drvs)))}
         return dict(dev_ms=dev_ms, dev_s=dev_s, t_wall=t_wall, clk=clk, rec=rec, n_ref=n_ref,
-                    value=world * S * args.steps / dev_s, accuracy=acc,
+                    value=aggregate_rate(S * args.steps, world, dev_s), accuracy=acc,
                     iters_per_frame=float(np.mean([r[4]["iters_total"] for r in rec])),
                     passes_per_frame=float(np.mean([r[4]["passes"] for r in rec])))
 
