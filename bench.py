@@ -431,9 +431,14 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
     uvd_dev = {}
 
-    def refresh_dev(r):
+    def prepare_ref(r):
+        # the caller's map points of reference r, on the device (host work,
+        # kept outside the refresh events)
         if r not in uvd_dev:
             uvd_dev[r] = torch.from_numpy(wl.ref_points(r)).to(f"cuda:{local}")
+
+    def refresh_dev(r):
+        prepare_ref(r)
         trk.build_pyramid(glt.GLT_REF, frames_dev[r], stream=sh)
         trk.set_map_points(uvd_dev[r], stream=sh)
 
@@ -455,6 +460,7 @@ def run_ours(args):
             did = drv.refresh(k - 1)
             r_used = drv.r
             if did:
+                prepare_ref(drv.r)
                 with torch.cuda.stream(stream):
                     if timed:
                         ev_ref[n_ref][0].record(stream)
@@ -513,6 +519,19 @@ def run_ours(args):
                 "max_rot_deg": float(np.rad2deg(max(e[0] for e in gt))),
                 "max_trans_mm": float(1000 * max(e[1] for e in gt)),
                 "status_nonzero": int(sum(1 for r in rec if r[4]["status"]))}
+    launch = launch_overhead(stream, lambda: trk.track_frame_async(init_dev, out_dev, stream=sh))
+    launch["library_call"] = "glt_track_frame_async (one persistent track launch)"
+    # one frame's upload from pinned host memory, timed on its own
+    up = torch.empty_like(frames_dev[0])
+    u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        up.copy_(frames_pin[1], non_blocking=True)
+        u0.record(stream)
+        for _ in range(20):
+            up.copy_(frames_pin[1], non_blocking=True)
+        u1.record(stream)
+    stream.synchronize()
+    h2d_frame_ms = u0.elapsed_time(u1) / 20
     # e2e through the C ABI with host buffers (pinned), H2D + D2H inside
     e2e = None
     if not args.no_e2e:
@@ -554,9 +573,10 @@ def run_ours(args):
                 "breakdown_ms": {"pyramid": statistics.mean(pyr_ms),
                                  "track": statistics.mean(trk_ms),
                                  "reference_refresh": statistics.mean(ref_ms) if ref_ms else None,
+                                 "h2d_frame_upload": h2d_frame_ms,
                                  "wall_per_step": 1000.0 * t_wall / args.steps},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": args.steps * L + n_ref * L,
+                "gpu_launches": args.steps * L + n_ref * L, "launch_overhead": launch,
                 "parity_vs_oracle": parity, "accuracy_vs_truth": accuracy,
                 "linearization_error_vs_oracle": lin_err}
         print(json.dumps(line), flush=True)
@@ -640,6 +660,45 @@ def run_e2e(args, glt, trk, wl, frames_pin, stream):
             "note": "host-pinned frames and map points through the C ABI, reference refreshes "
                     "included; the next frame's upload and pyramid overlap the host's work on "
                     "the current result"}
+
+
+def launch_overhead(stream, enqueue, reps=1000):
+    """Launch cost, measured apart from the timed steps: the device time per
+    empty kernel inside a graph of 100 (events around 20 replays), the device
+    time per replay of a one-kernel graph issued back to back, and the host
+    time to enqueue one call of the library (`enqueue`, the median over
+    `reps` // 10 calls; the kernels it launches are not waited for)."""
+    import torch
+
+    def graph_of(n):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(n):
+                torch.cuda._sleep(0)
+        return g
+
+    def per_replay(g, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            g.replay()
+            e0.record(stream)
+            for _ in range(n):
+                g.replay()
+            e1.record(stream)
+        stream.synchronize()
+        return 1000.0 * e0.elapsed_time(e1) / n
+
+    g100, g1 = graph_of(100), graph_of(1)
+    out = {"empty_kernel_in_graph_us": per_replay(g100, 20) / 100,
+           "empty_graph_replay_us": per_replay(g1, reps)}
+    host = []
+    for _ in range(max(reps // 10, 5)):
+        t0 = time.perf_counter()
+        enqueue()
+        host.append(time.perf_counter() - t0)
+    stream.synchronize()
+    out["library_call_host_us"] = 1e6 * statistics.median(host)
+    return out
 
 
 def run_cpu_baseline(args, wl, rec):
@@ -958,6 +1017,8 @@ def run_batch(args):
     forms = ["plain", "proposal"] if use_prop else ["plain"]
     runs = {f: measure(f) for f in forms}
     head = runs[forms[-1]]
+    launch = launch_overhead(stream, lambda: batch.replay(stream=sh), reps=200)
+    launch["library_call"] = "glt_batch_replay (the whole step graph)"
     value, dev_s, dev_ms, rec = head["value"], head["dev_s"], head["dev_ms"], head["rec"]
     e2e = None
     if not args.no_e2e:
@@ -1020,7 +1081,7 @@ def run_batch(args):
                                             f"{peaks.get('sm_max_mhz', 2070.0):g} MHz ({src} clock)",
                              "samples_per_step": samples},
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": head["clk"],
-                "gpu_launches": args.steps * launches + head["n_ref"] * L,
+                "gpu_launches": args.steps * launches + head["n_ref"] * L, "launch_overhead": launch,
                 "parity_vs_oracle": parity, "accuracy_vs_truth": head["accuracy"],
                 "iters_per_frame": head["iters_per_frame"],
                 "passes_per_frame": head["passes_per_frame"]}

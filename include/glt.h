@@ -56,6 +56,7 @@ extern "C" {
 #define GLT_ERR_NO_REFERENCE (-3)
 #define GLT_ERR_CAPACITY (-4)
 #define GLT_ERR_UNSUPPORTED (-5)
+#define GLT_ERR_IO (-6)              /* a file could not be opened, read or written */
 
 /* glt_result.status bits (per-frame solver outcomes) */
 #define GLT_TRACK_TOO_FEW_POINTS 1 /* a level had fewer than min_valid samples */
@@ -175,6 +176,9 @@ int glt_set_map_points(glt_tracker* trk, const float* uvd, int n, int is_device,
  * current REF data and CUR pyramid, one persistent launch; writes the result
  * to the host struct `out` after synchronising `stream`.  The rotation of
  * T_init is first projected onto SO(3) (Gram-Schmidt on its rows).
+ * T_init = NULL (or ab_init = NULL) starts from the tracker's state instead:
+ * the constant-velocity prediction of glt_state_predict.  Every call then
+ * advances the tracker's state with the result (glt_state_update).
  * Errors: NO_REFERENCE without map points, INVALID_ARG for non-finite input. */
 int glt_track_frame(glt_tracker* trk, const double T_init[12], const double ab_init[2],
                     glt_result* out, void* stream);
@@ -195,6 +199,53 @@ int glt_track_frame_async(glt_tracker* trk, const double* init_dev, glt_result* 
 int glt_debug_linearize(glt_tracker* trk, int level, const double T[12], double a, double b,
                         double H[64], double g[8], double* E, int* n, float* res,
                         void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Tracking state of one stream (checkpoint / resume; the paper keeps none of
+ * its own: its tracker starts every frame from a constant-velocity motion
+ * model, Sec. IV-A).  Host memory, 216 bytes, no device work:
+ *   T_cr    the last tracked pose, row-major 3x4 [R|t], reference -> current
+ *           camera (x_c = R x_r + t), identity after glt_set_map_points;
+ *   a, b    the last affine pair (0, 0 after glt_set_map_points);
+ *   motion  M = T_k T_{k-1}^{-1}, the camera motion between the last two
+ *           tracked frames in the newer frame's camera coordinates (identity
+ *           at creation; a new reference keeps it);
+ *   reference  version of the map points T_cr is relative to (0 before the
+ *           first glt_set_map_points, +1 for every call);
+ *   frames  frames tracked against that reference.
+ * A new reference resets T_cr and (a, b), i.e. the library reads the new
+ * reference as the last tracked frame (what an indirect pipeline's keyframe
+ * refresh gives); a caller whose reference is another frame sets the pose
+ * with glt_set_state.  glt_track_frame reads and advances the state;
+ * glt_track_frame_async and the batch leave it alone (their callers can run
+ * glt_state_predict / glt_state_update on their own copies).
+ * ------------------------------------------------------------------------- */
+typedef struct glt_state {
+    double T_cr[12];
+    double a, b;
+    double motion[12];
+    unsigned reference;
+    int frames;
+} glt_state;
+
+/* Constant-velocity prediction from `state`: T_init = motion T_cr (FP64,
+ * rotation re-orthonormalised by Gram-Schmidt on its rows) and ab_init =
+ * (a, b).  Host only.  Errors: INVALID_ARG (NULL, non-finite state). */
+int glt_state_predict(const glt_state* state, double T_init[12], double ab_init[2]);
+
+/* Advances `state` by one tracked frame: motion = T T_cr^{-1}, T_cr = T,
+ * (a, b) from `result`, frames + 1.  Host only.  A result with a non-finite
+ * pose or affine pair leaves the state unchanged and returns INVALID_ARG. */
+int glt_state_update(glt_state* state, const glt_result* result);
+
+/* Copies the tracker's state to host memory `out`.  Host only, no sync. */
+int glt_get_state(const glt_tracker* trk, glt_state* out);
+
+/* Replaces the tracker's state (a checkpoint taken by glt_get_state, or the
+ * pose of the last frame relative to a new reference); `reference` is
+ * ignored and set to the tracker's current map-point version.  Host only.
+ * Errors: INVALID_ARG (NULL, non-finite values, frames < 0). */
+int glt_set_state(glt_tracker* trk, const glt_state* in);
 
 /* Copies level `level` of pyramid `slot` (unpadded, W_l * H_l bytes) to host
  * memory `out`.  Synchronous. */
@@ -330,6 +381,21 @@ int glt_nn_gradient(glt_nn* nn, const float* x_dev, const float* m_dev, const fl
  * be NULL).  Asynchronous. */
 int glt_nn_train_step(glt_nn* nn, const float* x_dev, const float* m_dev, const float* t_dev,
                       int B, float lr, float* loss_dev, void* stream);
+
+/* Writes a training checkpoint of `nn` to the file `path` (binary,
+ * little-endian): the 8 bytes "GLTNNCK1", int32 GLT_NN_PARAMS, int32 Adam step
+ * count, then GLT_NN_PARAMS FP32 values each of the master weights and of the
+ * Adam first and second moments.  Synchronous (waits for the device).
+ * Errors: INVALID_ARG (NULL), IO, CUDA. */
+int glt_nn_save(glt_nn* nn, const char* path);
+
+/* Reads `path` into `nn`: a checkpoint written by glt_nn_save (weights, Adam
+ * moments and step restored, so training resumes bit for bit), or a NumPy
+ * .npy file holding GLT_NN_PARAMS little-endian FP32 values in one dimension
+ * (weights only, as glt_nn_set_params: Adam state reset).  Refreshes the BF16
+ * copy.  Synchronous.  Errors: INVALID_ARG (NULL, unknown format, wrong
+ * size), IO (cannot open, short file), CUDA. */
+int glt_nn_load(glt_nn* nn, const char* path);
 
 /* Attaches `nn` (or detaches it, nn = NULL) as the proposal stage of the
  * batch: from then on glt_batch_track and glt_batch_capture first build each

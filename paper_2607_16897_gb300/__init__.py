@@ -24,6 +24,8 @@ GLT_ERR_INVALID_ARG = -1
 GLT_ERR_CUDA = -2
 GLT_ERR_NO_REFERENCE = -3
 GLT_ERR_CAPACITY = -4
+GLT_ERR_UNSUPPORTED = -5
+GLT_ERR_IO = -6
 GLT_TRACK_TOO_FEW_POINTS = 1
 GLT_TRACK_NOT_PD = 2
 GLT_REF, GLT_CUR = 0, 1
@@ -58,6 +60,12 @@ class glt_result(ctypes.Structure):
                 ("passes", ctypes.c_int), ("status", ctypes.c_int)]
 
 
+class glt_state(ctypes.Structure):
+    _fields_ = [("T_cr", ctypes.c_double * 12), ("a", ctypes.c_double), ("b", ctypes.c_double),
+                ("motion", ctypes.c_double * 12), ("reference", ctypes.c_uint),
+                ("frames", ctypes.c_int)]
+
+
 RESULT_BYTES = ctypes.sizeof(glt_result)
 RESULT_DTYPE = np.dtype({"names": ["T", "a", "b", "cost", "n_valid", "iters_total", "iters",
                                    "passes", "status"],
@@ -88,6 +96,10 @@ SIGNATURES = {
                                  _P(ctypes.c_float), _vp]),
     "glt_get_pyramid": (_i, [_vp, _i, _i, _P(ctypes.c_uint8), _vp]),
     "glt_get_trace": (_i, [_vp, _P(_d), _P(_i), _i, _P(_i), _vp]),
+    "glt_state_predict": (_i, [_P(glt_state), _P(_d), _P(_d)]),
+    "glt_state_update": (_i, [_P(glt_state), _P(glt_result)]),
+    "glt_get_state": (_i, [_vp, _P(glt_state)]),
+    "glt_set_state": (_i, [_vp, _P(glt_state)]),
     "glt_batch_create": (_i, [_P(_vp), _i, _P(_vp)]),
     "glt_batch_destroy": (None, [_vp]),
     "glt_batch_build_pyramid": (_i, [_vp, _vp, _vp]),
@@ -105,6 +117,8 @@ SIGNATURES = {
     "glt_nn_forward": (_i, [_vp, _vp, _vp, _vp, _i, _vp]),
     "glt_nn_gradient": (_i, [_vp, _vp, _vp, _vp, _i, _P(ctypes.c_float), _P(ctypes.c_float), _vp]),
     "glt_nn_train_step": (_i, [_vp, _vp, _vp, _vp, _i, ctypes.c_float, _vp, _vp]),
+    "glt_nn_save": (_i, [_vp, ctypes.c_char_p]),
+    "glt_nn_load": (_i, [_vp, ctypes.c_char_p]),
     "glt_batch_set_proposal": (_i, [_vp, _vp, _vp]),
     "glt_status_string": (ctypes.c_char_p, [_i]),
     "glt_last_error": (ctypes.c_char_p, []),
@@ -244,14 +258,31 @@ class Tracker:
                                            _stream_handle(stream)), "glt_set_map_points")
         self.N = n
 
-    def track_frame(self, T_init, ab_init=(0.0, 0.0), stream=None) -> dict:
-        T = np.ascontiguousarray(T_init, np.float64).reshape(12)
-        ab = np.ascontiguousarray(ab_init, np.float64).reshape(2)
+    def track_frame(self, T_init=None, ab_init=None, stream=None) -> dict:
+        """T_init None: start from the tracker's constant-velocity prediction
+        (and ab_init None from its last affine pair); ab_init None with a
+        given T_init: (0, 0)."""
+        Tp = abp = None
+        if T_init is not None:
+            T = np.ascontiguousarray(T_init, np.float64).reshape(12)
+            Tp = T.ctypes.data_as(_P(_d))
+            if ab_init is None:
+                ab_init = (0.0, 0.0)
+        if ab_init is not None:
+            ab = np.ascontiguousarray(ab_init, np.float64).reshape(2)
+            abp = ab.ctypes.data_as(_P(_d))
         r = glt_result()
-        _check(_lib.glt_track_frame(self.handle, T.ctypes.data_as(_P(_d)),
-                                    ab.ctypes.data_as(_P(_d)), ctypes.byref(r),
-                                    _stream_handle(stream)), "glt_track_frame")
+        _check(_lib.glt_track_frame(self.handle, Tp, abp, ctypes.byref(r), _stream_handle(stream)),
+               "glt_track_frame")
         return result_to_dict(r)
+
+    def get_state(self) -> glt_state:
+        st = glt_state()
+        _check(_lib.glt_get_state(self.handle, ctypes.byref(st)), "glt_get_state")
+        return st
+
+    def set_state(self, st: glt_state):
+        _check(_lib.glt_set_state(self.handle, ctypes.byref(st)), "glt_set_state")
 
     def track_frame_async(self, init_dev, out_dev, stream=None):
         _check(_lib.glt_track_frame_async(self.handle, _dptr(init_dev), _dptr(out_dev),
@@ -398,6 +429,14 @@ class NN:
                                     g.ctypes.data_as(_P(ctypes.c_float)), ctypes.byref(loss),
                                     _stream_handle(stream)), "glt_nn_gradient")
         return g, loss.value
+
+    def save(self, path):
+        """Training checkpoint: weights, Adam moments and step (glt_nn_save)."""
+        _check(_lib.glt_nn_save(self.handle, os.fsencode(path)), "glt_nn_save")
+
+    def load(self, path):
+        """A checkpoint of save(), or a .npy weight file (glt_nn_load)."""
+        _check(_lib.glt_nn_load(self.handle, os.fsencode(path)), "glt_nn_load")
 
     def train_step(self, x_dev, m_dev, t_dev, B, lr, loss_dev=None, stream=None):
         _check(_lib.glt_nn_train_step(self.handle, _dptr(x_dev), _dptr(m_dev), _dptr(t_dev), int(B),

@@ -36,6 +36,19 @@ static int invalid(const char* msg)
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+static void set_identity(double T[12])
+{
+    for (int i = 0; i < 12; ++i) T[i] = (i % 5 == 0) ? 1.0 : 0.0;   // entries 0, 5, 10
+}
+
+static void reset_state_pose(glt_state& st)
+{
+    set_identity(st.T_cr);
+    st.a = 0.0;
+    st.b = 0.0;
+    st.frames = 0;
+}
+
 static bool finite_all(const double* v, int n)
 {
     for (int i = 0; i < n; ++i)
@@ -150,6 +163,7 @@ const char* glt_status_string(int code)
     case GLT_ERR_NO_REFERENCE: return "no reference";
     case GLT_ERR_CAPACITY: return "capacity exceeded";
     case GLT_ERR_UNSUPPORTED: return "unsupported";
+    case GLT_ERR_IO: return "file error";
     case GLT_TRACK_TOO_FEW_POINTS: return "too few points";
     case GLT_TRACK_NOT_PD: return "not positive definite";
     case GLT_TRACK_TOO_FEW_POINTS | GLT_TRACK_NOT_PD: return "too few points|not positive definite";
@@ -202,6 +216,8 @@ int glt_create(const glt_config* cfg, glt_tracker** out)
     glt_tracker* t = new glt_tracker();
     t->cfg = *cfg;
     t->L = cfg->levels;
+    reset_state_pose(t->state);
+    set_identity(t->state.motion);
     cudaError_t e = cudaGetDevice(&t->device);
     if (e != cudaSuccess) {
         delete t;
@@ -419,6 +435,9 @@ int glt_set_map_points(glt_tracker* t, const float* uvd, int n, int is_device, v
     GLT_CHECK(launch_set_points(t, src, n, s), "map point kernel");
     t->have_points = true;
     t->version++;
+    // a new reference: the state's pose restarts at the reference (motion kept)
+    reset_state_pose(t->state);
+    t->state.reference = t->version;
     if (n_changed) resolve_shape(t);
     return GLT_OK;
 }
@@ -451,7 +470,14 @@ int glt_track_frame(glt_tracker* t, const double T_init[12], const double ab_ini
 {
     int rc = track_prereq(t);
     if (rc != GLT_OK) return rc;
-    if (!T_init || !ab_init || !out) return invalid("NULL argument");
+    if (!out) return invalid("NULL argument");
+    double Tp[12], abp[2];
+    if (!T_init || !ab_init) {
+        rc = glt_state_predict(&t->state, Tp, abp);
+        if (rc != GLT_OK) return rc;
+        if (!T_init) T_init = Tp;
+        if (!ab_init) ab_init = abp;
+    }
     if (!finite_all(T_init, 12) || !finite_all(ab_init, 2)) return invalid("non-finite initial state");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     std::memcpy(t->h_init, T_init, 12 * sizeof(double));
@@ -466,6 +492,99 @@ int glt_track_frame(glt_tracker* t, const double T_init[12], const double ab_ini
               "result download");
     GLT_CHECK(cudaStreamSynchronize(s), "track");
     *out = *t->h_result;
+    glt_state_update(&t->state, out);   // a non-finite result leaves the state as it was
+    return GLT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tracking state (host only)
+
+static void compose34(const double A[12], const double B[12], double C[12])
+{
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 4; ++c) {
+            double v = c == 3 ? A[4 * r + 3] : 0.0;
+            for (int k = 0; k < 3; ++k) v += A[4 * r + k] * B[4 * k + c];
+            C[4 * r + c] = v;
+        }
+    }
+}
+
+// rigid inverse [R^T | -R^T t]
+static void inverse34(const double T[12], double Ti[12])
+{
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) Ti[4 * r + c] = T[4 * c + r];
+        Ti[4 * r + 3] = -(T[r] * T[3] + T[4 + r] * T[7] + T[8 + r] * T[11]);
+    }
+}
+
+static bool orthonormalise_rows(double T[12])
+{
+    double* r0 = T;
+    double* r1 = T + 4;
+    double* r2 = T + 8;
+    const double n0 = std::sqrt(r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2]);
+    if (!(n0 > 0.0)) return false;
+    for (int i = 0; i < 3; ++i) r0[i] /= n0;
+    const double d = r1[0] * r0[0] + r1[1] * r0[1] + r1[2] * r0[2];
+    for (int i = 0; i < 3; ++i) r1[i] -= d * r0[i];
+    const double n1 = std::sqrt(r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2]);
+    if (!(n1 > 0.0)) return false;
+    for (int i = 0; i < 3; ++i) r1[i] /= n1;
+    r2[0] = r0[1] * r1[2] - r0[2] * r1[1];
+    r2[1] = r0[2] * r1[0] - r0[0] * r1[2];
+    r2[2] = r0[0] * r1[1] - r0[1] * r1[0];
+    return true;
+}
+
+static bool state_finite(const glt_state& st)
+{
+    return finite_all(st.T_cr, 12) && finite_all(st.motion, 12) && std::isfinite(st.a) &&
+           std::isfinite(st.b);
+}
+
+int glt_state_predict(const glt_state* st, double T_init[12], double ab_init[2])
+{
+    if (!st || !T_init || !ab_init) return invalid("NULL argument");
+    if (!state_finite(*st)) return invalid("non-finite state");
+    double T[12];
+    compose34(st->motion, st->T_cr, T);
+    if (!orthonormalise_rows(T)) return invalid("degenerate rotation in the state");
+    std::memcpy(T_init, T, sizeof(T));
+    ab_init[0] = st->a;
+    ab_init[1] = st->b;
+    return GLT_OK;
+}
+
+int glt_state_update(glt_state* st, const glt_result* r)
+{
+    if (!st || !r) return invalid("NULL argument");
+    if (!finite_all(r->T, 12) || !std::isfinite(r->a) || !std::isfinite(r->b))
+        return invalid("non-finite result");
+    double Ti[12];
+    inverse34(st->T_cr, Ti);
+    compose34(r->T, Ti, st->motion);
+    std::memcpy(st->T_cr, r->T, sizeof(st->T_cr));
+    st->a = r->a;
+    st->b = r->b;
+    st->frames += 1;
+    return GLT_OK;
+}
+
+int glt_get_state(const glt_tracker* t, glt_state* out)
+{
+    if (!t || !out) return invalid("NULL argument");
+    *out = t->state;
+    return GLT_OK;
+}
+
+int glt_set_state(glt_tracker* t, const glt_state* in)
+{
+    if (!t || !in) return invalid("NULL argument");
+    if (!state_finite(*in) || in->frames < 0) return invalid("non-finite state or frames < 0");
+    t->state = *in;
+    t->state.reference = t->version;
     return GLT_OK;
 }
 

@@ -89,6 +89,7 @@ struct glt_tracker {
     glt_result* h_result = nullptr;
     double* h_lin = nullptr;
     int cluster = 1, threads = 256;
+    glt_state state{};                    // host-side tracking state (glt_get_state)
 };
 
 struct glt_batch {

@@ -12,6 +12,8 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -749,6 +751,157 @@ int glt_nn_train_step(glt_nn* n, const float* x_dev, const float* m_dev, const f
     if (loss_dev) e = cudaMemcpyAsync(loss_dev, n->loss, sizeof(float), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? GLT_OK : cuda_fail(e, "glt_nn_train_step");
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpoints and weight files
+
+namespace {
+
+const char kCkptTag[8] = {'G', 'L', 'T', 'N', 'N', 'C', 'K', '1'};
+
+int io_fail(const char* what, const char* path)
+{
+    set_error(std::string(what) + ": " + (path ? path : "(null)"));
+    return GLT_ERR_IO;
+}
+
+// Little-endian int32 from 4 bytes, independent of the host's byte order.
+int32_t le32(const unsigned char* p)
+{
+    return (int32_t)((uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) |
+                     ((uint32_t)p[3] << 24));
+}
+
+void put_le32(unsigned char* p, int32_t v)
+{
+    const uint32_t u = (uint32_t)v;
+    for (int i = 0; i < 4; ++i) p[i] = (unsigned char)(u >> (8 * i));
+}
+
+bool read_floats(FILE* f, std::vector<float>& out, size_t n)
+{
+    std::vector<unsigned char> raw(n * 4);
+    if (std::fread(raw.data(), 1, raw.size(), f) != raw.size()) return false;
+    out.resize(n);
+    for (size_t i = 0; i < n; ++i) {
+        const uint32_t u = (uint32_t)le32(&raw[4 * i]);
+        std::memcpy(&out[i], &u, 4);
+    }
+    return true;
+}
+
+bool write_floats(FILE* f, const std::vector<float>& v)
+{
+    std::vector<unsigned char> raw(v.size() * 4);
+    for (size_t i = 0; i < v.size(); ++i) {
+        uint32_t u;
+        std::memcpy(&u, &v[i], 4);
+        put_le32(&raw[4 * i], (int32_t)u);
+    }
+    return std::fwrite(raw.data(), 1, raw.size(), f) == raw.size();
+}
+
+// The header of a NumPy .npy file (format versions 1-3): checks that it
+// describes GLT_NN_PARAMS little-endian float32 values in one C-order
+// dimension and leaves `f` at the data.
+int npy_header(FILE* f, const unsigned char* head8, const char* path)
+{
+    const int major = head8[6];
+    size_t hlen = 0;
+    if (major == 1) {
+        unsigned char b[2];
+        if (std::fread(b, 1, 2, f) != 2) return io_fail("short .npy header", path);
+        hlen = (size_t)b[0] | ((size_t)b[1] << 8);
+    } else if (major == 2 || major == 3) {
+        unsigned char b[4];
+        if (std::fread(b, 1, 4, f) != 4) return io_fail("short .npy header", path);
+        hlen = (size_t)(uint32_t)le32(b);
+    } else {
+        return invalid_arg_msg("unsupported .npy version");
+    }
+    if (hlen == 0 || hlen > 65536) return invalid_arg_msg("bad .npy header length");
+    std::string h(hlen, ' ');
+    if (std::fread(&h[0], 1, hlen, f) != hlen) return io_fail("short .npy header", path);
+    char shape[32];
+    std::snprintf(shape, sizeof(shape), "(%d,)", kParams);
+    if (h.find("'<f4'") == std::string::npos || h.find("'fortran_order': False") == std::string::npos ||
+        h.find(shape) == std::string::npos)
+        return invalid_arg_msg(".npy file is not GLT_NN_PARAMS little-endian float32 values");
+    return GLT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int glt_nn_save(glt_nn* n, const char* path)
+{
+    if (!n || !path) return invalid_arg_msg("NULL argument");
+    std::vector<float> w(kParams), m(kParams), v(kParams);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(w.data(), n->w, kParams * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(m.data(), n->m, kParams * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(v.data(), n->v, kParams * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "glt_nn_save");
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return io_fail("cannot open for writing", path);
+    unsigned char head[16];
+    std::memcpy(head, kCkptTag, 8);
+    put_le32(head + 8, kParams);
+    put_le32(head + 12, n->step);
+    bool ok = std::fwrite(head, 1, 16, f) == 16 && write_floats(f, w) && write_floats(f, m) &&
+              write_floats(f, v);
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? GLT_OK : io_fail("write failed", path);
+}
+
+int glt_nn_load(glt_nn* n, const char* path)
+{
+    if (!n || !path) return invalid_arg_msg("NULL argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return io_fail("cannot open", path);
+    unsigned char head[8];
+    std::vector<float> w, m, v;
+    int step = 0;
+    int rc = GLT_OK;
+    if (std::fread(head, 1, 8, f) != 8) {
+        rc = io_fail("short file", path);
+    } else if (std::memcmp(head, kCkptTag, 8) == 0) {
+        unsigned char b[8];
+        if (std::fread(b, 1, 8, f) != 8) {
+            rc = io_fail("short checkpoint header", path);
+        } else if (le32(b) != kParams || le32(b + 4) < 0) {
+            rc = invalid_arg_msg("checkpoint of another network size");
+        } else {
+            step = le32(b + 4);
+            if (!read_floats(f, w, kParams) || !read_floats(f, m, kParams) || !read_floats(f, v, kParams))
+                rc = io_fail("short checkpoint", path);
+        }
+    } else if (std::memcmp(head, "\x93NUMPY", 6) == 0) {
+        rc = npy_header(f, head, path);
+        if (rc == GLT_OK && !read_floats(f, w, kParams)) rc = io_fail("short .npy data", path);
+    } else {
+        rc = invalid_arg_msg("neither a network checkpoint nor a .npy file");
+    }
+    std::fclose(f);
+    if (rc != GLT_OK) return rc;
+    if (m.empty()) {
+        m.assign(kParams, 0.0f);
+        v.assign(kParams, 0.0f);
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(n->w, w.data(), kParams * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(n->m, m.data(), kParams * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(n->v, v.data(), kParams * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "glt_nn_load");
+    to_bf16<<<grid_for(kParams, 256), 256>>>(n->w, n->wbf, kParams);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "glt_nn_load");
+    n->step = step;
+    return GLT_OK;
 }
 
 }  // extern "C"

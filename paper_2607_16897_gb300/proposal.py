@@ -268,11 +268,20 @@ def init_params(seed=0) -> np.ndarray:
     return w
 
 
-def train(data, epochs=20, batch=256, lr=3e-4, val_frac=0.1, eval_every=50, seed=0, log=print):
+def train(data, epochs=20, batch=256, lr=3e-4, val_frac=0.1, eval_every=50, seed=0, log=print,
+          checkpoint=None):
     """Adam on the GPU with the library's training kernels; returns (params,
     summary).  The pairs of the last `val_frac` of the sequences are held out;
     the parameters with the lowest held-out loss (evaluated every
-    `eval_every` steps) are returned."""
+    `eval_every` steps) are returned.
+
+    `checkpoint` (a path): after every epoch the network's checkpoint
+    (weights, Adam moments and step, glt_nn_save) goes to that path, the best
+    weights to `<path>.best.npy` and the loop state (epoch, shuffling RNG,
+    history) to `<path>.json`; a call that finds them resumes after the last
+    finished epoch and ends with the same result as an uninterrupted run."""
+    import json
+
     import torch
     from . import NN
     x, m, t, seq = data["x"], data["m"], data["t"], data["seq"]
@@ -300,7 +309,16 @@ def train(data, epochs=20, batch=256, lr=3e-4, val_frac=0.1, eval_every=50, seed
 
     best, best_w, best_at = val_loss(), net.get_params(), 0
     hist = []
-    for ep in range(epochs):
+    start = 0
+    if checkpoint and os.path.exists(checkpoint + ".json"):
+        with open(checkpoint + ".json") as f:
+            saved = json.load(f)
+        net.load(checkpoint)
+        best_w = np.load(checkpoint + ".best.npy")
+        best, best_at, start = saved["best"], saved["best_at"], saved["epoch"] + 1
+        hist = [tuple(h) for h in saved["history"]]
+        rng.bit_generator.state = saved["rng"]
+    for ep in range(start, epochs):
         perm = torch.from_numpy(rng.permutation(ntr)).cuda()
         for s in range(steps):
             idx = perm[s * batch:(s + 1) * batch]
@@ -312,6 +330,12 @@ def train(data, epochs=20, batch=256, lr=3e-4, val_frac=0.1, eval_every=50, seed
                     best, best_w, best_at = vl, net.get_params(), ep * steps + s + 1
         tl = float(loss_dev.mean())
         hist.append((tl, vl))
+        if checkpoint:
+            net.save(checkpoint)
+            np.save(checkpoint + ".best.npy", best_w)
+            with open(checkpoint + ".json", "w") as f:
+                json.dump(dict(epoch=ep, best=best, best_at=best_at, history=hist,
+                               rng=rng.bit_generator.state), f)
         if log:
             log(f"epoch {ep}: train {tl:.4f} val {vl:.4f} best {best:.4f} at step {best_at} "
                 f"(zero proposal {base:.4f})")
@@ -424,6 +448,8 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=3e-4)
     ap.add_argument("--out", default=WEIGHTS_PATH)
     ap.add_argument("--log", default=None, help="JSON summary file")
+    ap.add_argument("--checkpoint", default=None,
+                    help="checkpoint path: written every epoch, resumed from if present")
     a = ap.parse_args(argv)
     pool = render_pool()
     t0 = time.time()
@@ -431,7 +457,7 @@ def main(argv=None):
     pool.close()
     pool.join()
     t1 = time.time()
-    w, info = train(data, epochs=a.epochs, lr=a.lr)
+    w, info = train(data, epochs=a.epochs, lr=a.lr, checkpoint=a.checkpoint)
     t2 = time.time()
     np.save(a.out, w)
     summary = dict(info, dropped=data["dropped"], generate_s=t1 - t0, train_s=t2 - t1,

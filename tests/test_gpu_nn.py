@@ -221,3 +221,90 @@ def test_proposal_stage_composes_network_output(glt, onn, orc, syn):
     for t in trks:
         t.close()
     net.close()
+
+
+def test_checkpoint_resumes_training_bit_for_bit(glt, onn, tmp_path):
+    """Weights, Adam moments and step count go through glt_nn_save /
+    glt_nn_load: training resumed from a checkpoint reproduces the
+    uninterrupted run exactly (the kernels are deterministic)."""
+    import torch
+    B, lr = 64, 1e-3
+    x, m, t = make_inputs(B, 31)
+    xd, md, td = dev(x), dev(m), dev(t)
+    a = glt.NN(B, make_params(onn, 12))
+    for _ in range(3):
+        a.train_step(xd, md, td, B, lr)
+    ck = str(tmp_path / "net.ckpt")
+    a.save(ck)
+    assert (tmp_path / "net.ckpt").stat().st_size == 16 + 3 * 4 * glt.GLT_NN_PARAMS
+    for _ in range(2):
+        a.train_step(xd, md, td, B, lr)
+    b = glt.NN(B)
+    b.load(ck)
+    for _ in range(2):
+        b.train_step(xd, md, td, B, lr)
+    assert np.array_equal(a.get_params(), b.get_params())
+    # a fresh Adam state (weights only) gives a different trajectory
+    c = glt.NN(B)
+    c.set_params(np.zeros(glt.GLT_NN_PARAMS, np.float32))
+    c.load(ck)
+    w3 = c.get_params()
+    c.set_params(w3)                 # resets the moments and the step count
+    for _ in range(2):
+        c.train_step(xd, md, td, B, lr)
+    assert not np.array_equal(a.get_params(), c.get_params())
+    for n in (a, b, c):
+        n.close()
+
+
+def test_load_npy_weights(glt, onn, tmp_path):
+    import torch
+    w = make_params(onn, 5)
+    p = tmp_path / "w.npy"
+    np.save(p, w)
+    B = 7
+    x, m, _ = make_inputs(B, 41)
+    a, b = glt.NN(B, w), glt.NN(B)
+    b.load(str(p))
+    assert np.array_equal(b.get_params(), w)
+    ya, yb = torch.zeros(B, 8, device="cuda"), torch.zeros(B, 8, device="cuda")
+    a.forward(dev(x), dev(m), ya, B)
+    b.forward(dev(x), dev(m), yb, B)
+    torch.cuda.synchronize()
+    assert torch.equal(ya, yb)
+    # the committed proposal weights load the same way
+    from paper_2607_16897_gb300 import proposal
+    b.load(proposal.WEIGHTS_PATH)
+    assert np.array_equal(b.get_params(), proposal.load_weights())
+    # errors: missing file, wrong size, wrong dtype, not a weight file
+    with pytest.raises(glt.GltError, match=r"\(-6\)"):
+        b.load(str(tmp_path / "missing.npy"))
+    np.save(tmp_path / "short.npy", w[:100])
+    np.save(tmp_path / "f64.npy", w.astype(np.float64))
+    (tmp_path / "junk.bin").write_bytes(b"0123456789abcdef")
+    for bad in ("short.npy", "f64.npy", "junk.bin"):
+        with pytest.raises(glt.GltError, match=r"\(-1\)"):
+            b.load(str(tmp_path / bad))
+    (tmp_path / "trunc.npy").write_bytes((tmp_path / "w.npy").read_bytes()[:4096])
+    with pytest.raises(glt.GltError, match=r"\(-6\)"):
+        b.load(str(tmp_path / "trunc.npy"))
+    assert np.array_equal(b.get_params(), proposal.load_weights())   # failed loads change nothing
+    a.close()
+    b.close()
+
+
+def test_training_loop_resumes_from_its_checkpoint(glt, onn, tmp_path):
+    """proposal.train with a checkpoint: stopped after one epoch and called
+    again, it ends where the uninterrupted two-epoch run ends."""
+    from paper_2607_16897_gb300 import proposal
+    S, per = 20, 40
+    x, m, t = make_inputs(S * per, 51)
+    data = dict(x=x, m=m, t=t * 0.1, seq=np.repeat(np.arange(S), per), S=S)
+    kw = dict(batch=64, lr=1e-3, eval_every=5, seed=3, log=None)
+    w_full, info_full = proposal.train(data, epochs=2, **kw)
+    ck = str(tmp_path / "train.ckpt")
+    proposal.train(data, epochs=1, checkpoint=ck, **kw)
+    w_res, info_res = proposal.train(data, epochs=2, checkpoint=ck, **kw)
+    assert np.array_equal(w_full, w_res)
+    assert info_full["best_step"] == info_res["best_step"]
+    assert [tuple(h) for h in info_full["history"]] == info_res["history"]
