@@ -33,7 +33,7 @@ FLOPS_PER_SAMPLE = 160      # algorithmic FP32 flops per residual sample per pas
 # (dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
 # launch as in the timed steps) on the workload named by the key; a value is
 # removed whenever the kernel changes after it was taken.
-TRACK_TRAFFIC = {"c2": 783616, "c3": 55166208}
+TRACK_TRAFFIC = {}
 I34 = np.hstack([np.eye(3), np.zeros((3, 1))])
 
 
@@ -417,6 +417,7 @@ def run_ours(args):
     if args.jacobian:
         wl.jacobian = args.jacobian
     precision = "mixed" if args.workload == "c4" else "fp32"
+    chained = True                     # pyramid + track as one chain of dependent launches
     Wd, Hd, L, N = wl.cam.W, wl.cam.H, wl.L, wl.N
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
@@ -475,10 +476,16 @@ def run_ours(args):
                 flush.zero_()                    # L2 flushed between steps
                 if timed:
                     ev[i][0].record(stream)
-                trk.build_pyramid(glt.GLT_CUR, frames_dev[k], stream=sh)
-                if timed:
-                    ev[i][1].record(stream)
-                trk.track_frame_async(init_dev, out_dev, stream=sh)
+                if chained:
+                    # pyramid kernels and the solve chained on the device
+                    trk.track_image_async(frames_dev[k], init_dev, out_dev, stream=sh)
+                    if timed:
+                        ev[i][1].record(stream)
+                else:
+                    trk.build_pyramid(glt.GLT_CUR, frames_dev[k], stream=sh)
+                    if timed:
+                        ev[i][1].record(stream)
+                    trk.track_frame_async(init_dev, out_dev, stream=sh)
                 if timed:
                     ev[i][2].record(stream)
                 out_pin.copy_(out_dev, non_blocking=True)
@@ -506,6 +513,8 @@ def run_ours(args):
     step_ms = [e0.elapsed_time(e2) for e0, _, e2 in ev]
     pyr_ms = [e0.elapsed_time(e1) for e0, e1, _ in ev]
     trk_ms = [e1.elapsed_time(e2) for _, e1, e2 in ev]
+    if chained:
+        trk_ms, pyr_ms = pyr_ms, None    # the chain overlaps pyramid and track: one interval
     ref_ms = [a.elapsed_time(b) for a, b in ev_ref[:n_ref]]
     dev_s = sum(step_ms) / 1000.0
     dev_s, t_wall = max_over_ranks([dev_s, t_wall], dist, f"cuda:{local}")
@@ -519,8 +528,13 @@ def run_ours(args):
                 "max_rot_deg": float(np.rad2deg(max(e[0] for e in gt))),
                 "max_trans_mm": float(1000 * max(e[1] for e in gt)),
                 "status_nonzero": int(sum(1 for r in rec if r[4]["status"]))}
-    launch = launch_overhead(stream, lambda: trk.track_frame_async(init_dev, out_dev, stream=sh))
-    launch["library_call"] = "glt_track_frame_async (one persistent track launch)"
+    if chained:
+        launch = launch_overhead(stream, lambda: trk.track_image_async(frames_dev[1], init_dev, out_dev,
+                                                                       stream=sh))
+        launch["library_call"] = f"glt_track_image_async ({L - 1} pyramid launches + the track launch)"
+    else:
+        launch = launch_overhead(stream, lambda: trk.track_frame_async(init_dev, out_dev, stream=sh))
+        launch["library_call"] = "glt_track_frame_async (one persistent track launch)"
     # one frame's upload from pinned host memory, timed on its own
     up = torch.empty_like(frames_dev[0])
     u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -535,7 +549,7 @@ def run_ours(args):
     # e2e through the C ABI with host buffers (pinned), H2D + D2H inside
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, glt, trk, wl, frames_pin, stream)
+        e2e = run_e2e(args, glt, trk, wl, frames_pin, stream, chained)
 
     # oracle on a bounded sample, same initial states and references
     cpu = None
@@ -570,13 +584,15 @@ def run_ours(args):
                            "parallelism": f"replicas x{world}",
                            "l2": "flushed between steps (256 MB write, outside the step events)",
                            "timing": "sum of per-step CUDA-event times (pyramid + track)"},
-                "breakdown_ms": {"pyramid": statistics.mean(pyr_ms),
+                "breakdown_ms": {"pyramid": statistics.mean(pyr_ms) if pyr_ms else
+                                 "chained with the track launch (inside 'track')",
                                  "track": statistics.mean(trk_ms),
                                  "reference_refresh": statistics.mean(ref_ms) if ref_ms else None,
                                  "h2d_frame_upload": h2d_frame_ms,
                                  "wall_per_step": 1000.0 * t_wall / args.steps},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": args.steps * L + n_ref * L, "launch_overhead": launch,
+                "gpu_launches": args.steps * (L + (1 if precision == "mixed" else 0)) + n_ref * L,
+                "launch_overhead": launch,
                 "parity_vs_oracle": parity, "accuracy_vs_truth": accuracy,
                 "linearization_error_vs_oracle": lin_err}
         print(json.dumps(line), flush=True)
@@ -585,7 +601,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, glt, trk, wl, frames_pin, stream):
+def run_e2e(args, glt, trk, wl, frames_pin, stream, chained=False):
     """Same frames through glt_build_pyramid / glt_set_map_points /
     glt_track_frame_async with HOST (pinned) buffers: every step copies its
     frame H2D and reads its result back.  The next frame's upload and pyramid
@@ -603,6 +619,16 @@ def run_e2e(args, glt, trk, wl, frames_pin, stream):
     out_dev = torch.zeros(glt.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     done = torch.cuda.Event()
     init_np = init_pin.numpy()
+    slot = torch.empty_like(frames_pin[0], device="cuda")
+
+    def load_cur(k):
+        # the frame's upload (its pyramid is chained with the track launch),
+        # or upload and pyramid through glt_build_pyramid
+        if chained:
+            with torch.cuda.stream(stream):
+                slot.copy_(frames_pin[k], non_blocking=True)
+        else:
+            trk.build_pyramid(glt.GLT_CUR, frames_pin[k].numpy(), stream=sh)
     # map points the caller holds in pinned memory, like the frames (prepared
     # before the timed loop: every reference the device-timed run used)
     for r in sorted(set(range(0, nF, 8)) | set(wl.refs)):
@@ -623,7 +649,7 @@ def run_e2e(args, glt, trk, wl, frames_pin, stream):
     drv = SequenceDriver(wl)
     k = 1
     refresh(drv, 0)
-    trk.build_pyramid(glt.GLT_CUR, frames_pin[k].numpy(), stream=sh)
+    load_cur(k)
     h2d += wl.frames[k].nbytes
     for i in range(steps):
         T_init = drv.init_for(k)
@@ -631,15 +657,18 @@ def run_e2e(args, glt, trk, wl, frames_pin, stream):
         init_np[12:] = drv.ab_init()
         with torch.cuda.stream(stream):
             init_dev.copy_(init_pin, non_blocking=True)
-            trk.track_frame_async(init_dev, out_dev, stream=sh)
+            if chained:
+                trk.track_image_async(slot, init_dev, out_dev, stream=sh)
+            else:
+                trk.track_frame_async(init_dev, out_dev, stream=sh)
             out_pin.copy_(out_dev, non_blocking=True)
             done.record(stream)
         h2d += 14 * 8
         d2h += glt.RESULT_BYTES
         kn = k + 1 if k + 1 < nF else 1
         if i + 1 < steps and kn != 1:
-            # the next frame's pyramid is queued behind this solve
-            trk.build_pyramid(glt.GLT_CUR, frames_pin[kn].numpy(), stream=sh)
+            # the next frame's upload (and pyramid) is queued behind this solve
+            load_cur(kn)
             h2d += wl.frames[kn].nbytes
         done.synchronize()
         res = glt.parse_results(out_pin.numpy())[0]
@@ -648,7 +677,7 @@ def run_e2e(args, glt, trk, wl, frames_pin, stream):
             drv = SequenceDriver(wl)
             refresh(drv, 0)
             if i + 1 < steps:
-                trk.build_pyramid(glt.GLT_CUR, frames_pin[kn].numpy(), stream=sh)
+                load_cur(kn)
                 h2d += wl.frames[kn].nbytes
         else:
             refresh(drv, k)
@@ -1055,7 +1084,8 @@ def run_batch(args):
                     "in the graph ahead of the track launch")
         else:
             desc = "sizes uniform over 320x240/640x480/752x480/1280x720, N uniform 300-4000, L=4"
-        launches = L + 1 + (1 if precision == "mixed" else 0) + (7 if use_prop else 0)
+        # L - 1 pyramid levels, the FP16 packing, the proposal stage, the track kernel
+        launches = L + (1 if precision == "mixed" else 0) + (1 if use_prop else 0)
         line = {"metric": "frames tracked/s", "value": value, "unit": "frames/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1000.0 * dev_s / args.steps, "higher_is_better": True,

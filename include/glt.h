@@ -189,6 +189,17 @@ int glt_track_frame(glt_tracker* trk, const double T_init[12], const double ab_i
 int glt_track_frame_async(glt_tracker* trk, const double* init_dev, glt_result* out_dev,
                           void* stream);
 
+/* glt_build_pyramid(GLT_CUR) from the DEVICE frame `frame_dev` (width x
+ * height, `pitch_bytes` per row) followed by glt_track_frame_async, issued as
+ * one chain: each pyramid kernel after the first, and the track kernel, is a
+ * programmatic dependent launch of the kernel before it, so it starts while
+ * that kernel runs (the track kernel loads its descriptor and initial state
+ * then) and waits on the device for the data it needs.  Same results as the
+ * two calls.  The frame must stay unchanged until the work completes.
+ * Asynchronous.  Errors: NO_REFERENCE, INVALID_ARG (NULL, pitch < width). */
+int glt_track_image_async(glt_tracker* trk, const uint8_t* frame_dev, int pitch_bytes,
+                          const double* init_dev, glt_result* out_dev, void* stream);
+
 /* One linearisation (Eqs. 3-5 at a given state) on `level` of the CUR pyramid:
  * the full symmetric H (64 doubles, row-major), g = J^T W r (8; the paper's
  * right-hand side b of Eq. 5 is -g), the Huber energy E and the number of
@@ -280,7 +291,9 @@ int glt_batch_track(glt_batch* batch, const double* init_dev, glt_result* out_de
                     void* stream);
 
 /* Captures glt_batch_build_pyramid + glt_batch_track with these arguments into
- * a CUDA graph owned by the batch (replacing any previous one). */
+ * a CUDA graph owned by the batch (replacing any previous one).  The kernels
+ * are chained as programmatic dependent launches, as in
+ * glt_track_image_async (the track kernel only without a proposal stage). */
 int glt_batch_capture(glt_batch* batch, const uint8_t* const* frames_dev, const double* init_dev,
                       glt_result* out_dev, void* stream);
 

@@ -92,6 +92,7 @@ SIGNATURES = {
     "glt_set_map_points": (_i, [_vp, _vp, _i, _i, _vp]),
     "glt_track_frame": (_i, [_vp, _P(_d), _P(_d), _P(glt_result), _vp]),
     "glt_track_frame_async": (_i, [_vp, _vp, _vp, _vp]),
+    "glt_track_image_async": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
     "glt_debug_linearize": (_i, [_vp, _i, _P(_d), _d, _d, _P(_d), _P(_d), _P(_d), _P(_i),
                                  _P(ctypes.c_float), _vp]),
     "glt_get_pyramid": (_i, [_vp, _i, _i, _P(ctypes.c_uint8), _vp]),
@@ -162,7 +163,8 @@ def _stream_handle(stream) -> int | None:
 
 
 def _dptr(t) -> int:
-    return int(t.data_ptr())
+    """Device address of a tensor (or an address given as an int)."""
+    return int(t) if isinstance(t, int) else int(t.data_ptr())
 
 
 def _is_cuda_tensor(x) -> bool:
@@ -287,6 +289,13 @@ class Tracker:
     def track_frame_async(self, init_dev, out_dev, stream=None):
         _check(_lib.glt_track_frame_async(self.handle, _dptr(init_dev), _dptr(out_dev),
                                           _stream_handle(stream)), "glt_track_frame_async")
+
+    def track_image_async(self, frame_dev, init_dev, out_dev, pitch=None, stream=None):
+        """Pyramid of the device frame + solve in one launch (glt_track_image_async)."""
+        pitch = self.W if pitch is None else int(pitch)
+        _check(_lib.glt_track_image_async(self.handle, _dptr(frame_dev), pitch, _dptr(init_dev),
+                                          _dptr(out_dev), _stream_handle(stream)),
+               "glt_track_image_async")
 
     def debug_linearize(self, level, T, a, b, want_res=True, stream=None) -> dict:
         T = np.ascontiguousarray(T, np.float64).reshape(12)

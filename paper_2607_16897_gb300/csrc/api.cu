@@ -381,15 +381,17 @@ int glt_build_pyramid(glt_tracker* t, int slot, const uint8_t* img, int pitch_by
         pitch_bytes = (int)W;
         is_device = 1;
     }
+    // every kernel after the first is a programmatic dependent of the one
+    // before it (it starts early and waits on the device for its source level)
     if (is_device && t->L > 1) {
         // level 1 straight from the caller's frame; its tiles write level 0
         for (int l = 1; l < t->L; ++l)
             GLT_CHECK(launch_pyr_down(t->jobs_dev + slot * GLT_MAX_LEVELS + (l - 1), 1,
                                       pyr_tiles_x(t->W[l]), pyr_tiles_y(t->H[l]), s, nullptr,
-                                      l == 1 ? img : nullptr, l == 1 ? pitch_bytes : 0),
+                                      l == 1 ? img : nullptr, l == 1 ? pitch_bytes : 0, l > 1),
                       "pyramid kernel");
         if (slot == GLT_CUR && t->packed)
-            GLT_CHECK(launch_pack(t->pack_dev, t->L, t->W[0] * t->H[0], s), "pack kernel");
+            GLT_CHECK(launch_pack(t->pack_dev, t->L, t->W[0] * t->H[0], s, true), "pack kernel");
         P.built = true;
         return GLT_OK;
     }
@@ -399,10 +401,11 @@ int glt_build_pyramid(glt_tracker* t, int slot, const uint8_t* img, int pitch_by
               "level-0 copy");
     for (int l = 1; l < t->L; ++l)
         GLT_CHECK(launch_pyr_down(t->jobs_dev + slot * GLT_MAX_LEVELS + (l - 1), 1,
-                                  pyr_tiles_x(t->W[l]), pyr_tiles_y(t->H[l]), s),
+                                  pyr_tiles_x(t->W[l]), pyr_tiles_y(t->H[l]), s, nullptr, nullptr, 0,
+                                  l > 1),
                   "pyramid kernel");
     if (slot == GLT_CUR && t->packed) {
-        GLT_CHECK(launch_pack(t->pack_dev, t->L, t->W[0] * t->H[0], s), "pack kernel");
+        GLT_CHECK(launch_pack(t->pack_dev, t->L, t->W[0] * t->H[0], s, t->L > 1), "pack kernel");
     }
     P.built = true;
     return GLT_OK;
@@ -461,6 +464,27 @@ int glt_track_frame_async(glt_tracker* t, const double* init_dev, glt_result* ou
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     GLT_CHECK(launch_track(t->desc_ptr_dev, t->user_dev, 1, t->cluster, t->threads,
                            track_variant(t->cfg), init_dev, out_dev, s),
+              "track kernel");
+    return GLT_OK;
+}
+
+int glt_track_image_async(glt_tracker* t, const uint8_t* frame_dev, int pitch, const double* init_dev,
+                          glt_result* out_dev, void* stream)
+{
+    if (!t) return invalid("tracker is NULL");
+    if (!frame_dev || !init_dev || !out_dev) return invalid("NULL argument");
+    if (pitch < t->W[0]) return invalid("pitch < width");
+    if (!t->have_points) {
+        set_error("glt_set_map_points must come first");
+        return GLT_ERR_NO_REFERENCE;
+    }
+    const int rc = glt_build_pyramid(t, GLT_CUR, frame_dev, pitch, 1, stream);
+    if (rc != GLT_OK) return rc;
+    // the track kernel is a programmatic dependent of the last pyramid kernel
+    // (with one FP32 level the pyramid is a plain copy, and it waits as usual)
+    const bool pdl = t->L > 1 || t->packed != nullptr;
+    GLT_CHECK(launch_track(t->desc_ptr_dev, t->user_dev, 1, t->cluster, t->threads, track_variant(t->cfg),
+                           init_dev, out_dev, reinterpret_cast<cudaStream_t>(stream), pdl),
               "track kernel");
     return GLT_OK;
 }
@@ -794,14 +818,21 @@ static int batch_pyramid(glt_batch* b, const uint8_t* const* frames_dev, cudaStr
     // only need the copy
     bool single_level = false;
     for (glt_tracker* t : b->trk) single_level |= t->L == 1;
-    if (single_level || b->Lmax == 1)
+    // every launch after the first is a programmatic dependent of the previous one
+    bool after_first = false;
+    if (single_level || b->Lmax == 1) {
         GLT_CHECK(launch_copy_frames(frames_dev, b->copy_dev, b->S, maxbytes, s), "batch copy kernel");
-    for (int l = 1; l < b->Lmax; ++l)
+        after_first = true;
+    }
+    for (int l = 1; l < b->Lmax; ++l) {
         GLT_CHECK(launch_pyr_down(b->jobs_dev + (size_t)(l - 1) * b->S, b->S, pyr_tiles_x(maxw[l]),
-                                  pyr_tiles_y(maxh[l]), s, (l == 1 && !single_level) ? frames_dev : nullptr),
+                                  pyr_tiles_y(maxh[l]), s, (l == 1 && !single_level) ? frames_dev : nullptr,
+                                  nullptr, 0, after_first),
                   "batch pyramid kernel");
+        after_first = true;
+    }
     if (b->precision == GLT_MIXED)
-        GLT_CHECK(launch_pack(b->pack_dev, b->Lmax * b->S, maxpix, s), "batch pack kernel");
+        GLT_CHECK(launch_pack(b->pack_dev, b->Lmax * b->S, maxpix, s, after_first), "batch pack kernel");
     for (glt_tracker* t : b->trk) t->pyr[GLT_CUR].built = true;
     return GLT_OK;
 }
@@ -862,9 +893,13 @@ int glt_batch_capture(glt_batch* b, const uint8_t* const* frames_dev, const doub
         e1 = launch_proposal(b, init_dev, s);
         init_dev = b->prop_init;
     }
+    // without the proposal stage the track kernel follows the last pyramid
+    // kernel as its programmatic dependent (its setup overlaps the pyramids);
+    // after the proposal stage it reads that stage's output from its first
+    // instruction, so it waits as usual
     if (e1 == cudaSuccess)
         e1 = launch_track(b->descs_dev, b->users_dev, b->S, b->cluster, b->threads,
-                          b->variant, init_dev, out_dev, s);
+                          b->variant, init_dev, out_dev, s, b->nn == nullptr);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
     if (r1 != GLT_OK) {

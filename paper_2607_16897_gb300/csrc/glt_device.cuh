@@ -30,6 +30,22 @@ constexpr int kAccPad = 48;      // padded for the 5-stage reduce-scatter
 __host__ __device__ constexpr int pat_dx(int k) { return k == 1 ? -2 : k == 2 ? 2 : k == 5 ? -1 : k == 6 ? 1 : k == 7 ? -1 : 0; }
 __host__ __device__ constexpr int pat_dy(int k) { return k == 3 ? -2 : k == 4 ? 2 : (k == 5 || k == 6) ? -1 : k == 7 ? 1 : 0; }
 
+// Programmatic dependent launch (sm_90 and later): a kernel launched with
+// cudaLaunchAttributeProgrammaticStreamSerialization may begin while the
+// previous kernel of its stream still runs.  griddep_wait() returns once that
+// kernel has completed and its writes are visible; griddep_launch_dependents()
+// lets the next such kernel begin.  Both are no-ops for an ordinary launch.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// The uint8 CUR levels may be written by a pyramid kernel that was still
+// running when the track kernel started (a programmatic dependent launch), so
+// the gathers read them with ld.global.ca (weak, L1-cached loads ordered by
+// the dependency wait), never through the read-only path, which assumes data
+// that is final for the whole lifetime of the kernel.
 struct LevelDev {
     const uint8_t* img;   // uint8 level, `pitch` bytes per row (pitch >= W + 8, multiple of 16)
     const uint2* packed;  // GLT_MIXED: FP16 (I, gx, gy, 0) per pixel, W pixels per row
@@ -238,7 +254,7 @@ __device__ __forceinline__ void linearize_square_t(const StreamDesc& D, const Pa
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const uint2* rp = reinterpret_cast<const uint2*>(base + (size_t)r * lv.pitch);
-        const uint2 u0 = __ldg(rp), u1 = __ldg(rp + 1), u2 = __ldg(rp + 2);
+        const uint2 u0 = __ldca(rp), u1 = __ldca(rp + 1), u2 = __ldca(rp + 2);
         const uint32_t v[6] = {u0.x, u0.y, u1.x, u1.y, u2.x, u2.y};
 #pragma unroll
         for (int i = 0; i < NWD; ++i) {
@@ -298,7 +314,7 @@ __device__ __forceinline__ void linearize_square_any(const StreamDesc& D, const 
     for (int k = 0; k < K; ++k) {
         const int dx = k % D.pattern - h, dy = k / D.pattern - h;
         const uint8_t* t = lv.img + (size_t)(G.yb + dy) * S + (G.xb + dx);
-        const float I00 = __ldg(t), I10 = __ldg(t + 1), I01 = __ldg(t + S), I11 = __ldg(t + S + 1);
+        const float I00 = __ldca(t), I10 = __ldca(t + 1), I01 = __ldca(t + S), I11 = __ldca(t + S + 1);
         const float I = fmaf(w00, I00, fmaf(w10, I10, fmaf(w01, I01, w11 * I11)));
         float gx, gy;
         if (ic) {
@@ -306,14 +322,14 @@ __device__ __forceinline__ void linearize_square_any(const StreamDesc& D, const 
             gx = P.ea * g0.x;
             gy = P.ea * g0.y;
         } else {
-            gx = 0.5f * fmaf(w00, I10 - (float)__ldg(t - 1),
-                        fmaf(w10, (float)__ldg(t + 2) - I00,
-                        fmaf(w01, I11 - (float)__ldg(t + S - 1),
-                             w11 * ((float)__ldg(t + S + 2) - I01))));
-            gy = 0.5f * fmaf(w00, I01 - (float)__ldg(t - S),
-                        fmaf(w10, I11 - (float)__ldg(t - S + 1),
-                        fmaf(w01, (float)__ldg(t + 2 * S) - I00,
-                             w11 * ((float)__ldg(t + 2 * S + 1) - I10))));
+            gx = 0.5f * fmaf(w00, I10 - (float)__ldca(t - 1),
+                        fmaf(w10, (float)__ldca(t + 2) - I00,
+                        fmaf(w01, I11 - (float)__ldca(t + S - 1),
+                             w11 * ((float)__ldca(t + S + 2) - I01))));
+            gy = 0.5f * fmaf(w00, I01 - (float)__ldca(t - S),
+                        fmaf(w10, I11 - (float)__ldca(t - S + 1),
+                        fmaf(w01, (float)__ldca(t + 2 * S) - I00,
+                             w11 * ((float)__ldca(t + 2 * S + 1) - I10))));
         }
         accumulate_sample(G, I, gx, gy, I0p[k], P.ea, P.b, D.huber_k, acc, res ? res + (size_t)K * p + k : nullptr);
     }
@@ -380,7 +396,7 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const uint2* rp = reinterpret_cast<const uint2*>(base + (size_t)r * lv.pitch);
-            const uint2 w0 = __ldg(rp), w1 = __ldg(rp + 1);
+            const uint2 w0 = __ldca(rp), w1 = __ldca(rp + 1);
             if (sh < 32) {
                 rw[r][0] = __funnelshift_r(w0.x, w0.y, sh);
                 rw[r][1] = __funnelshift_r(w0.y, w1.x, sh);
@@ -423,7 +439,7 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
             const int x0 = G.xb + pat_dx(k), y0 = G.yb + pat_dy(k);
             const uint2* t0 = pk + (size_t)y0 * lv.W + x0;
             const uint2* t1 = t0 + lv.W;
-            const uint2 p00 = __ldg(t0), p10 = __ldg(t0 + 1), p01 = __ldg(t1), p11 = __ldg(t1 + 1);
+            const uint2 p00 = __ldca(t0), p10 = __ldca(t0 + 1), p01 = __ldca(t1), p11 = __ldca(t1 + 1);
             const float2 a00 = __half22float2(*reinterpret_cast<const __half2*>(&p00.x));
             const float2 a10 = __half22float2(*reinterpret_cast<const __half2*>(&p10.x));
             const float2 a01 = __half22float2(*reinterpret_cast<const __half2*>(&p01.x));

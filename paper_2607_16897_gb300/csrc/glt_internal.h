@@ -123,12 +123,15 @@ cudaError_t launch_proposal(glt_batch* b, const double* init_dev, cudaStream_t s
 int cuda_fail(cudaError_t e, const char* what);
 
 // pyramid.cu
+// pyramid-family launches; pdl as for launch_track (the kernels wait for
+// their predecessor before reading what it writes)
 cudaError_t launch_pyr_down(const PyrJob* jobs_dev, int njobs, int tiles_x, int tiles_y,
                             cudaStream_t s, const uint8_t* const* frames = nullptr,
-                            const uint8_t* src = nullptr, int sp = 0);
+                            const uint8_t* src = nullptr, int sp = 0, bool pdl = false);
 cudaError_t launch_copy_frames(const uint8_t* const* frames, const CopyJob* jobs, int njobs,
-                               int max_bytes, cudaStream_t s);
-cudaError_t launch_pack(const PackJob* jobs, int njobs, int max_pixels, cudaStream_t s);
+                               int max_bytes, cudaStream_t s, bool pdl = false);
+cudaError_t launch_pack(const PackJob* jobs, int njobs, int max_pixels, cudaStream_t s,
+                        bool pdl = false);
 int pyr_tiles_x(int dW);
 int pyr_tiles_y(int dH);
 
@@ -142,9 +145,14 @@ inline int track_variant(const glt_config& c)
 {
     return c.precision == GLT_MIXED ? 1 : c.pattern != 0 ? 2 : c.jacobian == GLT_IC ? 3 : 0;
 }
+// pdl: launch as a programmatic dependent of the previous kernel in the
+// stream (cudaLaunchAttributeProgrammaticStreamSerialization): the kernel may
+// start while that kernel runs and waits for its results on the device
+// (griddepcontrol.wait) before it reads them.  Only for launches whose
+// predecessor is one of the library's pyramid kernels.
 cudaError_t launch_track(const StreamDesc* const* descs, const int* users, int S, int cluster,
                          int threads, int variant, const double* init, glt_result* results,
-                         cudaStream_t s);
+                         cudaStream_t s, bool pdl = false);
 cudaError_t launch_linearize(const glt_tracker* t, const PassParams& P, bool want_res,
                              cudaStream_t s);
 bool track_shape_ok(int cluster, int threads, int variant);

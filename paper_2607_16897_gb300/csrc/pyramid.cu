@@ -149,7 +149,11 @@ __global__ void __launch_bounds__(PYR_THREADS) pyr_down_kernel(const PyrJob* __r
 {
     __shared__ __align__(16) uint8_t in[IH][IW];
     __shared__ __align__(16) uint16_t vs[TH][IW];
+    // the next level's kernel (or the track kernel) may start its setup now;
+    // this level's source is read only once the previous kernel is done
+    griddep_launch_dependents();
     PyrJob J = jobs[blockIdx.z];
+    griddep_wait();
     const int ox0 = blockIdx.x * TW, oy0 = blockIdx.y * TH;
     if (ox0 >= J.dW || oy0 >= J.dH) return;
     if (frames || src) {
@@ -159,22 +163,44 @@ __global__ void __launch_bounds__(PYR_THREADS) pyr_down_kernel(const PyrJob* __r
         J.sp = frames ? J.sW : sp;
         pyr_tile<false>(J, ox0, oy0, in, vs, level0, p0);
     } else {
-        pyr_tile<false>(J, ox0, oy0, in, vs);
+        // a level written by the previous kernel: L2 loads, not the read-only path
+        pyr_tile<true>(J, ox0, oy0, in, vs);
     }
 }
 
+namespace {
+// ordinary or programmatic-dependent launch of a pyramid-family kernel
+template <typename... KArgs, typename... Args>
+cudaError_t launch_ex(void (*kern)(KArgs...), dim3 grid, int threads, cudaStream_t s, bool pdl,
+                      Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+}  // namespace
+
 cudaError_t launch_pyr_down(const PyrJob* jobs_dev, int njobs, int tiles_x, int tiles_y,
-                            cudaStream_t s, const uint8_t* const* frames, const uint8_t* src, int sp)
+                            cudaStream_t s, const uint8_t* const* frames, const uint8_t* src, int sp,
+                            bool pdl)
 {
     dim3 grid((unsigned)tiles_x, (unsigned)tiles_y, (unsigned)njobs);
-    pyr_down_kernel<<<grid, PYR_THREADS, 0, s>>>(jobs_dev, frames, src, sp);
-    return cudaGetLastError();
+    return launch_ex(pyr_down_kernel, grid, PYR_THREADS, s, pdl, jobs_dev, frames, src, sp);
 }
 
 // Batched level-0 copy: frame s (contiguous, pitch W) -> pitched level 0.
 __global__ void copy_frames_kernel(const uint8_t* const* __restrict__ frames,
                                    const CopyJob* __restrict__ jobs)
 {
+    griddep_launch_dependents();
+    griddep_wait();
     const CopyJob J = jobs[blockIdx.y];
     const uint8_t* src = frames[blockIdx.y];
     const int n = J.W * J.H;
@@ -195,20 +221,21 @@ __global__ void copy_frames_kernel(const uint8_t* const* __restrict__ frames,
 }
 
 cudaError_t launch_copy_frames(const uint8_t* const* frames, const CopyJob* jobs, int njobs,
-                               int max_bytes, cudaStream_t s)
+                               int max_bytes, cudaStream_t s, bool pdl)
 {
     const int threads = 256;
     int bx = (max_bytes / 4 + threads - 1) / threads;
     if (bx > 256) bx = 256;
     if (bx < 1) bx = 1;
-    copy_frames_kernel<<<dim3((unsigned)bx, (unsigned)njobs), threads, 0, s>>>(frames, jobs);
-    return cudaGetLastError();
+    return launch_ex(copy_frames_kernel, dim3((unsigned)bx, (unsigned)njobs), threads, s, pdl, frames, jobs);
 }
 
 // Mixed precision storage: FP16 (I, gx, gy, 0) per pixel, central differences
 // halved (exact in FP16: multiples of 1/2 with |g| <= 127.5), 0 on the border.
 __global__ void pack_kernel(const PackJob* __restrict__ jobs)
 {
+    griddep_launch_dependents();
+    griddep_wait();
     const PackJob J = jobs[blockIdx.y];
     const int n = J.W * J.H;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -227,14 +254,13 @@ __global__ void pack_kernel(const PackJob* __restrict__ jobs)
     }
 }
 
-cudaError_t launch_pack(const PackJob* jobs, int njobs, int max_pixels, cudaStream_t s)
+cudaError_t launch_pack(const PackJob* jobs, int njobs, int max_pixels, cudaStream_t s, bool pdl)
 {
     const int threads = 256;
     int bx = (max_pixels + threads - 1) / threads;
     if (bx > 512) bx = 512;
     if (bx < 1) bx = 1;
-    pack_kernel<<<dim3((unsigned)bx, (unsigned)njobs), threads, 0, s>>>(jobs);
-    return cudaGetLastError();
+    return launch_ex(pack_kernel, dim3((unsigned)bx, (unsigned)njobs), threads, s, pdl, jobs);
 }
 
 }  // namespace glt

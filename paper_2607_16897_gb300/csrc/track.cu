@@ -58,6 +58,12 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
     __syncthreads();
     if (tid == 0) solver_init(sD, init + 14 * user, S, P);
     __syncthreads();
+    // Everything above reads data that was final before the previous kernel
+    // of the stream started; the CUR levels it may still be writing are read
+    // only after this wait (a no-op unless launched as a programmatic
+    // dependent, which is how glt_track_image_async and the batch graph chain
+    // the track launch behind the pyramid kernels).
+    griddep_wait();
 
     const int tail_warp = (int)(blockIdx.x % NW);
     int par = 0;
@@ -169,7 +175,7 @@ namespace {
 
 template <int THREADS, int VAR>
 cudaError_t launch_track_t(const StreamDesc* const* descs, const int* users, int S, int cluster,
-                           const double* init, glt_result* results, cudaStream_t s)
+                           const double* init, glt_result* results, cudaStream_t s, bool pdl)
 {
     auto kern = track_kernel<THREADS, VAR>;
     if (cluster > 8) {
@@ -181,13 +187,15 @@ cudaError_t launch_track_t(const StreamDesc* const* descs, const int* users, int
     cfg.blockDim = dim3(THREADS, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)cluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, kern, descs, users, init, results);
 }
 
@@ -239,22 +247,24 @@ bool shape_ok_v<2>(int cluster, int threads)
 
 template <int VAR>
 cudaError_t launch_track_v(const StreamDesc* const* descs, const int* users, int S, int cluster,
-                           int threads, const double* init, glt_result* results, cudaStream_t s)
+                           int threads, const double* init, glt_result* results, cudaStream_t s,
+                           bool pdl)
 {
     switch (threads) {
-    case 128: return launch_track_t<128, VAR>(descs, users, S, cluster, init, results, s);
-    case 256: return launch_track_t<256, VAR>(descs, users, S, cluster, init, results, s);
-    case 512: return launch_track_t<512, VAR>(descs, users, S, cluster, init, results, s);
+    case 128: return launch_track_t<128, VAR>(descs, users, S, cluster, init, results, s, pdl);
+    case 256: return launch_track_t<256, VAR>(descs, users, S, cluster, init, results, s, pdl);
+    case 512: return launch_track_t<512, VAR>(descs, users, S, cluster, init, results, s, pdl);
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <>
 cudaError_t launch_track_v<2>(const StreamDesc* const* descs, const int* users, int S, int cluster,
-                              int threads, const double* init, glt_result* results, cudaStream_t s)
+                              int threads, const double* init, glt_result* results, cudaStream_t s,
+                              bool pdl)
 {
     if (threads != 256) return cudaErrorInvalidValue;
-    return launch_track_t<256, 2>(descs, users, S, cluster, init, results, s);
+    return launch_track_t<256, 2>(descs, users, S, cluster, init, results, s, pdl);
 }
 
 }  // namespace
@@ -273,13 +283,13 @@ bool track_shape_ok(int cluster, int threads, int variant)
 
 cudaError_t launch_track(const StreamDesc* const* descs, const int* users, int S, int cluster,
                          int threads, int variant, const double* init, glt_result* results,
-                         cudaStream_t s)
+                         cudaStream_t s, bool pdl)
 {
     switch (variant) {
-    case 0: return launch_track_v<0>(descs, users, S, cluster, threads, init, results, s);
-    case 1: return launch_track_v<1>(descs, users, S, cluster, threads, init, results, s);
-    case 2: return launch_track_v<2>(descs, users, S, cluster, threads, init, results, s);
-    case 3: return launch_track_v<3>(descs, users, S, cluster, threads, init, results, s);
+    case 0: return launch_track_v<0>(descs, users, S, cluster, threads, init, results, s, pdl);
+    case 1: return launch_track_v<1>(descs, users, S, cluster, threads, init, results, s, pdl);
+    case 2: return launch_track_v<2>(descs, users, S, cluster, threads, init, results, s, pdl);
+    case 3: return launch_track_v<3>(descs, users, S, cluster, threads, init, results, s, pdl);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -119,3 +119,17 @@ def test_autotune_picks_a_valid_shape(glt, orc, syn):
     batch.close()
     for s in streams:
         s["trk"].close()
+
+
+def test_chained_graph_builds_the_pyramids(glt, orc, syn):
+    """The batch graph chains its kernels as programmatic dependent launches:
+    every stream's CUR pyramid is byte for byte the oracle's afterwards."""
+    streams = make_streams(syn, orc, glt, "fp32")
+    run_batch(glt, streams, shape=(8, 128), graph=True)
+    for i, (s, (W, H, f, N, L)) in enumerate(zip(streams, SPECS)):
+        cur = s["cur"].cpu().numpy()
+        for l, lv in enumerate(orc.pyramid(cur, L)):
+            np.testing.assert_array_equal(s["trk"].get_pyramid(glt.GLT_CUR, l), lv,
+                                          err_msg=f"stream {i} level {l}")
+    for s in streams:
+        s["trk"].close()
