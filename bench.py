@@ -33,7 +33,7 @@ FLOPS_PER_SAMPLE = 160      # algorithmic FP32 flops per residual sample per pas
 # (dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
 # launch as in the timed steps) on the workload named by the key; a value is
 # removed whenever the kernel changes after it was taken.
-TRACK_TRAFFIC = {}
+TRACK_TRAFFIC = {"c2": 780672}
 I34 = np.hstack([np.eye(3), np.zeros((3, 1))])
 
 
@@ -87,6 +87,8 @@ def parse():
                     help="batched forms: fixed tile shape 'cluster,threads' instead of the "
                          "autotuner's pick (profiling runs, where the tuner's timings are distorted)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-launch-overhead", action="store_true",
+                    help="skip the launch-overhead measurement (e.g. for a profiler's launch list)")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -417,7 +419,6 @@ def run_ours(args):
     if args.jacobian:
         wl.jacobian = args.jacobian
     precision = "mixed" if args.workload == "c4" else "fp32"
-    chained = True                     # pyramid + track as one chain of dependent launches
     Wd, Hd, L, N = wl.cam.W, wl.cam.H, wl.L, wl.N
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
@@ -444,8 +445,8 @@ def run_ours(args):
         trk.set_map_points(uvd_dev[r], stream=sh)
 
     nF = len(wl.frames)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
     ev_ref = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
 
@@ -476,18 +477,10 @@ def run_ours(args):
                 flush.zero_()                    # L2 flushed between steps
                 if timed:
                     ev[i][0].record(stream)
-                if chained:
-                    # pyramid kernels and the solve chained on the device
-                    trk.track_image_async(frames_dev[k], init_dev, out_dev, stream=sh)
-                    if timed:
-                        ev[i][1].record(stream)
-                else:
-                    trk.build_pyramid(glt.GLT_CUR, frames_dev[k], stream=sh)
-                    if timed:
-                        ev[i][1].record(stream)
-                    trk.track_frame_async(init_dev, out_dev, stream=sh)
+                # the pyramid kernels and the solve, chained on the device
+                trk.track_image_async(frames_dev[k], init_dev, out_dev, stream=sh)
                 if timed:
-                    ev[i][2].record(stream)
+                    ev[i][1].record(stream)
                 out_pin.copy_(out_dev, non_blocking=True)
             stream.synchronize()
             res = glt.parse_results(out_pin.numpy())[0]
@@ -510,11 +503,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
-    step_ms = [e0.elapsed_time(e2) for e0, _, e2 in ev]
-    pyr_ms = [e0.elapsed_time(e1) for e0, e1, _ in ev]
-    trk_ms = [e1.elapsed_time(e2) for _, e1, e2 in ev]
-    if chained:
-        trk_ms, pyr_ms = pyr_ms, None    # the chain overlaps pyramid and track: one interval
+    # the chain overlaps the pyramid kernels with the track kernel's setup:
+    # one interval per step
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    trk_ms = step_ms
     ref_ms = [a.elapsed_time(b) for a, b in ev_ref[:n_ref]]
     dev_s = sum(step_ms) / 1000.0
     dev_s, t_wall = max_over_ranks([dev_s, t_wall], dist, f"cuda:{local}")
@@ -528,13 +520,11 @@ def run_ours(args):
                 "max_rot_deg": float(np.rad2deg(max(e[0] for e in gt))),
                 "max_trans_mm": float(1000 * max(e[1] for e in gt)),
                 "status_nonzero": int(sum(1 for r in rec if r[4]["status"]))}
-    if chained:
+    launch = None
+    if not args.no_launch_overhead:
         launch = launch_overhead(stream, lambda: trk.track_image_async(frames_dev[1], init_dev, out_dev,
                                                                        stream=sh))
         launch["library_call"] = f"glt_track_image_async ({L - 1} pyramid launches + the track launch)"
-    else:
-        launch = launch_overhead(stream, lambda: trk.track_frame_async(init_dev, out_dev, stream=sh))
-        launch["library_call"] = "glt_track_frame_async (one persistent track launch)"
     # one frame's upload from pinned host memory, timed on its own
     up = torch.empty_like(frames_dev[0])
     u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -549,7 +539,7 @@ def run_ours(args):
     # e2e through the C ABI with host buffers (pinned), H2D + D2H inside
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, glt, trk, wl, frames_pin, stream, chained)
+        e2e = run_e2e(args, glt, trk, wl, frames_pin, stream)
 
     # oracle on a bounded sample, same initial states and references
     cpu = None
@@ -584,8 +574,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{world}",
                            "l2": "flushed between steps (256 MB write, outside the step events)",
                            "timing": "sum of per-step CUDA-event times (pyramid + track)"},
-                "breakdown_ms": {"pyramid": statistics.mean(pyr_ms) if pyr_ms else
-                                 "chained with the track launch (inside 'track')",
+                "breakdown_ms": {"pyramid": "chained with the track launch (inside 'track')",
                                  "track": statistics.mean(trk_ms),
                                  "reference_refresh": statistics.mean(ref_ms) if ref_ms else None,
                                  "h2d_frame_upload": h2d_frame_ms,
@@ -601,38 +590,23 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, glt, trk, wl, frames_pin, stream, chained=False):
-    """Same frames through glt_build_pyramid / glt_set_map_points /
-    glt_track_frame_async with HOST (pinned) buffers: every step copies its
-    frame H2D and reads its result back.  The next frame's upload and pyramid
-    are queued behind the current solve, so they run while the host waits for
-    and digests the current result."""
+def run_e2e(args, glt, trk, wl, frames_pin, stream):
+    """Same frames through the C ABI with HOST (pinned) buffers: every step is
+    one glt_track_image call (frame upload, chained pyramid + solve, result
+    read back, state update) from the sequence driver's initial state;
+    reference refreshes go through glt_build_pyramid / glt_set_map_points
+    with host buffers."""
     import torch
     sh = stream.cuda_stream
     nF = len(wl.frames)
     h2d = d2h = 0
     refs_pin = {}
     steps = args.steps
-    init_pin = torch.zeros(14, dtype=torch.float64).pin_memory()
-    init_dev = torch.zeros(14, dtype=torch.float64, device="cuda")
-    out_pin = torch.zeros(glt.RESULT_BYTES, dtype=torch.uint8).pin_memory()
-    out_dev = torch.zeros(glt.RESULT_BYTES, dtype=torch.uint8, device="cuda")
-    done = torch.cuda.Event()
-    init_np = init_pin.numpy()
-    slot = torch.empty_like(frames_pin[0], device="cuda")
-
-    def load_cur(k):
-        # the frame's upload (its pyramid is chained with the track launch),
-        # or upload and pyramid through glt_build_pyramid
-        if chained:
-            with torch.cuda.stream(stream):
-                slot.copy_(frames_pin[k], non_blocking=True)
-        else:
-            trk.build_pyramid(glt.GLT_CUR, frames_pin[k].numpy(), stream=sh)
     # map points the caller holds in pinned memory, like the frames (prepared
     # before the timed loop: every reference the device-timed run used)
     for r in sorted(set(range(0, nF, 8)) | set(wl.refs)):
         refs_pin[r] = torch.from_numpy(wl.ref_points(r)).pin_memory()
+    frames_np = [f.numpy() for f in frames_pin]
 
     def refresh(drv, k):
         nonlocal h2d
@@ -640,7 +614,7 @@ def run_e2e(args, glt, trk, wl, frames_pin, stream, chained=False):
             r = drv.r
             if r not in refs_pin:
                 refs_pin[r] = torch.from_numpy(wl.ref_points(r)).pin_memory()
-            trk.build_pyramid(glt.GLT_REF, frames_pin[r].numpy(), stream=sh)
+            trk.build_pyramid(glt.GLT_REF, frames_np[r], stream=sh)
             trk.set_map_points(refs_pin[r].numpy(), stream=sh)
             h2d += wl.frames[r].nbytes + refs_pin[r].numel() * 4
 
@@ -649,36 +623,15 @@ def run_e2e(args, glt, trk, wl, frames_pin, stream, chained=False):
     drv = SequenceDriver(wl)
     k = 1
     refresh(drv, 0)
-    load_cur(k)
-    h2d += wl.frames[k].nbytes
     for i in range(steps):
-        T_init = drv.init_for(k)
-        init_np[:12] = T_init.ravel()
-        init_np[12:] = drv.ab_init()
-        with torch.cuda.stream(stream):
-            init_dev.copy_(init_pin, non_blocking=True)
-            if chained:
-                trk.track_image_async(slot, init_dev, out_dev, stream=sh)
-            else:
-                trk.track_frame_async(init_dev, out_dev, stream=sh)
-            out_pin.copy_(out_dev, non_blocking=True)
-            done.record(stream)
-        h2d += 14 * 8
+        res = trk.track_image(frames_np[k], drv.init_for(k), drv.ab_init(), stream=sh)
+        h2d += wl.frames[k].nbytes + 14 * 8
         d2h += glt.RESULT_BYTES
-        kn = k + 1 if k + 1 < nF else 1
-        if i + 1 < steps and kn != 1:
-            # the next frame's upload (and pyramid) is queued behind this solve
-            load_cur(kn)
-            h2d += wl.frames[kn].nbytes
-        done.synchronize()
-        res = glt.parse_results(out_pin.numpy())[0]
         drv.record(k, res)
+        kn = k + 1 if k + 1 < nF else 1
         if kn == 1:
             drv = SequenceDriver(wl)
             refresh(drv, 0)
-            if i + 1 < steps:
-                load_cur(kn)
-                h2d += wl.frames[kn].nbytes
         else:
             refresh(drv, k)
         k = kn
@@ -686,9 +639,9 @@ def run_e2e(args, glt, trk, wl, frames_pin, stream, chained=False):
     t = time.perf_counter() - t0
     return {"value": steps / t, "unit": "frames/s", "h2d_bytes_per_step": h2d / steps,
             "d2h_bytes_per_step": d2h / steps,
-            "note": "host-pinned frames and map points through the C ABI, reference refreshes "
-                    "included; the next frame's upload and pyramid overlap the host's work on "
-                    "the current result"}
+            "note": "one glt_track_image call per frame from pinned host memory (upload, chained "
+                    "pyramid + solve, result read back), reference refreshes through the C ABI "
+                    "with host buffers, host-side sequence driver included"}
 
 
 def launch_overhead(stream, enqueue, reps=1000):
@@ -1046,8 +999,10 @@ def run_batch(args):
     forms = ["plain", "proposal"] if use_prop else ["plain"]
     runs = {f: measure(f) for f in forms}
     head = runs[forms[-1]]
-    launch = launch_overhead(stream, lambda: batch.replay(stream=sh), reps=200)
-    launch["library_call"] = "glt_batch_replay (the whole step graph)"
+    launch = None
+    if not args.no_launch_overhead:
+        launch = launch_overhead(stream, lambda: batch.replay(stream=sh), reps=200)
+        launch["library_call"] = "glt_batch_replay (the whole step graph)"
     value, dev_s, dev_ms, rec = head["value"], head["dev_s"], head["dev_ms"], head["rec"]
     e2e = None
     if not args.no_e2e:

@@ -200,6 +200,19 @@ int glt_track_frame_async(glt_tracker* trk, const double* init_dev, glt_result* 
 int glt_track_image_async(glt_tracker* trk, const uint8_t* frame_dev, int pitch_bytes,
                           const double* init_dev, glt_result* out_dev, void* stream);
 
+/* glt_build_pyramid(GLT_CUR) + glt_track_frame in one call, the form a
+ * per-frame caller uses: the frame `img` (host memory, uploaded first through
+ * the tracker's staging buffer, or device memory per `is_device`; `pitch_bytes`
+ * per row) is chained with the solve as in glt_track_image_async, the result
+ * is written to the host struct `out` after synchronising `stream`, and the
+ * tracker's state advances.  T_init / ab_init NULL: start from the state's
+ * constant-velocity prediction (glt_state_predict).
+ * Errors: NO_REFERENCE, INVALID_ARG (NULL img / out, pitch < width,
+ * non-finite initial state). */
+int glt_track_image(glt_tracker* trk, const uint8_t* img, int pitch_bytes, int is_device,
+                    const double T_init[12], const double ab_init[2], glt_result* out,
+                    void* stream);
+
 /* One linearisation (Eqs. 3-5 at a given state) on `level` of the CUR pyramid:
  * the full symmetric H (64 doubles, row-major), g = J^T W r (8; the paper's
  * right-hand side b of Eq. 5 is -g), the Huber energy E and the number of

@@ -93,6 +93,7 @@ SIGNATURES = {
     "glt_track_frame": (_i, [_vp, _P(_d), _P(_d), _P(glt_result), _vp]),
     "glt_track_frame_async": (_i, [_vp, _vp, _vp, _vp]),
     "glt_track_image_async": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
+    "glt_track_image": (_i, [_vp, _vp, _i, _i, _P(_d), _P(_d), _P(glt_result), _vp]),
     "glt_debug_linearize": (_i, [_vp, _i, _P(_d), _d, _d, _P(_d), _P(_d), _P(_d), _P(_i),
                                  _P(ctypes.c_float), _vp]),
     "glt_get_pyramid": (_i, [_vp, _i, _i, _P(ctypes.c_uint8), _vp]),
@@ -236,7 +237,14 @@ class Tracker:
         except Exception:
             pass
 
+    def _check_frame(self, img):
+        # the library reads height rows of width bytes: refuse smaller arrays
+        if len(img.shape) != 2 or img.shape[0] < self.H or img.shape[1] < self.W:
+            raise ValueError(f"frame of shape {tuple(img.shape)}; the tracker needs "
+                             f"{self.H} x {self.W} uint8")
+
     def build_pyramid(self, slot, img, stream=None):
+        self._check_frame(img)
         if _is_cuda_tensor(img):
             assert img.dtype.itemsize == 1 and img.is_contiguous()
             pitch = img.shape[-1]
@@ -290,8 +298,37 @@ class Tracker:
         _check(_lib.glt_track_frame_async(self.handle, _dptr(init_dev), _dptr(out_dev),
                                           _stream_handle(stream)), "glt_track_frame_async")
 
+    def track_image(self, img, T_init=None, ab_init=None, stream=None) -> dict:
+        """One frame end to end (glt_track_image): `img` is a host numpy array
+        (uploaded by the library; pinned memory uploads fastest) or a CUDA
+        tensor.  T_init None: the state's constant-velocity prediction."""
+        Tp = abp = None
+        if T_init is not None:
+            T = np.ascontiguousarray(T_init, np.float64).reshape(12)
+            Tp = T.ctypes.data_as(_P(_d))
+            if ab_init is None:
+                ab_init = (0.0, 0.0)
+        if ab_init is not None:
+            ab = np.ascontiguousarray(ab_init, np.float64).reshape(2)
+            abp = ab.ctypes.data_as(_P(_d))
+        r = glt_result()
+        self._check_frame(img)
+        if _is_cuda_tensor(img):
+            assert img.dtype.itemsize == 1 and img.stride(1) == 1
+            ptr, pitch, dev = img.data_ptr(), int(img.stride(0)), 1
+        else:
+            a = np.asarray(img)
+            if a.dtype != np.uint8 or a.ndim != 2 or a.strides[1] != 1:
+                a = np.ascontiguousarray(a, np.uint8)
+            ptr, pitch, dev = a.ctypes.data, int(a.strides[0]), 0   # rows may be pitched
+        _check(_lib.glt_track_image(self.handle, ctypes.c_void_p(ptr), pitch, dev, Tp, abp,
+                                    ctypes.byref(r), _stream_handle(stream)), "glt_track_image")
+        return result_to_dict(r)
+
     def track_image_async(self, frame_dev, init_dev, out_dev, pitch=None, stream=None):
-        """Pyramid of the device frame + solve in one launch (glt_track_image_async)."""
+        """Pyramid of the device frame chained with the solve (glt_track_image_async)."""
+        if not isinstance(frame_dev, int):
+            self._check_frame(frame_dev)
         pitch = self.W if pitch is None else int(pitch)
         _check(_lib.glt_track_image_async(self.handle, _dptr(frame_dev), pitch, _dptr(init_dev),
                                           _dptr(out_dev), _stream_handle(stream)),

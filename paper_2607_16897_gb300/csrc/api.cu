@@ -489,6 +489,50 @@ int glt_track_image_async(glt_tracker* t, const uint8_t* frame_dev, int pitch, c
     return GLT_OK;
 }
 
+int glt_track_image(glt_tracker* t, const uint8_t* img, int pitch, int is_device, const double T_init[12],
+                    const double ab_init[2], glt_result* out, void* stream)
+{
+    if (!t) return invalid("tracker is NULL");
+    if (!img || !out) return invalid("NULL argument");
+    if (pitch < t->W[0]) return invalid("pitch < width");
+    if (!t->have_points) {
+        set_error("glt_set_map_points must come first");
+        return GLT_ERR_NO_REFERENCE;
+    }
+    double Tp[12], abp[2];
+    if (!T_init || !ab_init) {
+        const int rc = glt_state_predict(&t->state, Tp, abp);
+        if (rc != GLT_OK) return rc;
+        if (!T_init) T_init = Tp;
+        if (!ab_init) ab_init = abp;
+    }
+    if (!finite_all(T_init, 12) || !finite_all(ab_init, 2)) return invalid("non-finite initial state");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::memcpy(t->h_init, T_init, 12 * sizeof(double));
+    t->h_init[12] = ab_init[0];
+    t->h_init[13] = ab_init[1];
+    GLT_CHECK(cudaMemcpyAsync(t->init_dev, t->h_init, 14 * sizeof(double), cudaMemcpyHostToDevice, s),
+              "init upload");
+    if (!is_device) {
+        const size_t W = (size_t)t->W[0], H = (size_t)t->H[0];
+        if ((size_t)pitch == W)
+            GLT_CHECK(cudaMemcpyAsync(t->stage_dev, img, W * H, cudaMemcpyHostToDevice, s), "frame upload");
+        else
+            GLT_CHECK(cudaMemcpy2DAsync(t->stage_dev, W, img, (size_t)pitch, W, H, cudaMemcpyHostToDevice, s),
+                      "frame upload");
+        img = t->stage_dev;
+        pitch = (int)W;
+    }
+    int rc = glt_track_image_async(t, img, pitch, t->init_dev, t->result_dev, stream);
+    if (rc != GLT_OK) return rc;
+    GLT_CHECK(cudaMemcpyAsync(t->h_result, t->result_dev, sizeof(glt_result), cudaMemcpyDeviceToHost, s),
+              "result download");
+    GLT_CHECK(cudaStreamSynchronize(s), "track");
+    *out = *t->h_result;
+    glt_state_update(&t->state, out);   // a non-finite result leaves the state as it was
+    return GLT_OK;
+}
+
 int glt_track_frame(glt_tracker* t, const double T_init[12], const double ab_init[2], glt_result* out,
                     void* stream)
 {

@@ -5,6 +5,8 @@ the FP64 oracle's byte for byte, and the result must equal the unchained path
 (glt_build_pyramid + glt_track_frame_async) bit for bit, for every image size
 class (odd sizes, widths that allow 16-, 4- and 1-byte loads, one level), every
 cluster shape and the Jacobian / pattern / precision variants."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -129,4 +131,37 @@ def test_arguments(glt, orc, syn):
     trk.set_map_points(p.uvd)
     with pytest.raises(glt.GltError, match=r"\(-1\)"):
         trk.track_image_async(cur, init, out, pitch=p.cam.W - 1)
+    trk.close()
+
+
+def test_one_call_per_frame(glt, orc, syn):
+    """glt_track_image (host or device frame, explicit or state-driven start)
+    returns what the asynchronous chain returns, and advances the state."""
+    import torch
+    p = syn.pair_c1(4, sigma=2.0)
+    trk, o = both_sides(glt, orc, p.cam.W, p.cam.H, p.cam.K, p.ref, p.cur, p.uvd, levels=3)
+    init = torch.tensor(np.concatenate([I34.ravel(), [0.0, 0.0]]), dtype=torch.float64).cuda()
+    out = torch.zeros(glt.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    trk.track_image_async(torch.from_numpy(p.cur).cuda(), init, out)
+    want = glt.parse_results(out)[0]
+    host = trk.track_image(p.cur, I34, (0.0, 0.0))
+    dev = trk.track_image(torch.from_numpy(p.cur).cuda(), I34, (0.0, 0.0))
+    for g in (host, dev):
+        assert np.array_equal(g["T"], want["T"]) and g["passes"] == want["passes"]
+    st = trk.get_state()
+    assert st.frames == 2 and np.array_equal(np.array(st.T_cr[:]).reshape(3, 4), dev["T"])
+    # pitched host frame, state-driven start (the motion is identity after two equal frames)
+    padded = np.zeros((p.cam.H, p.cam.W + 24), np.uint8)
+    padded[:, :p.cam.W] = p.cur
+    g = trk.track_image(padded[:, :p.cam.W])
+    r = o.track_frame(want["T"])
+    ang, dt = pose_diff(g["T"], r["T"])
+    assert ang <= ROT_TOL and dt <= TRANS_TOL
+    assert trk.get_state().frames == 3
+    with pytest.raises(ValueError):
+        trk.track_image(p.cur[:, :10])              # narrower than the tracker
+    r = glt.glt_result()
+    rc = glt.glt_track_image(trk.handle, p.cur.ctypes.data, p.cam.W - 1, 0, None, None,
+                             ctypes.byref(r), None)
+    assert rc == glt.GLT_ERR_INVALID_ARG             # pitch below the width
     trk.close()
