@@ -386,8 +386,8 @@ int glt_build_pyramid(glt_tracker* t, int slot, const uint8_t* img, int pitch_by
     if (is_device && t->L > 1) {
         // level 1 straight from the caller's frame; its tiles write level 0
         for (int l = 1; l < t->L; ++l)
-            GLT_CHECK(launch_pyr_down(t->jobs_dev + slot * GLT_MAX_LEVELS + (l - 1), 1,
-                                      pyr_tiles_x(t->W[l]), pyr_tiles_y(t->H[l]), s, nullptr,
+            GLT_CHECK(launch_pyr_down(t->jobs_dev + slot * GLT_MAX_LEVELS + (l - 1), nullptr,
+                                      pyr_tiles_x(t->W[l]) * pyr_tiles_y(t->H[l]), s, nullptr,
                                       l == 1 ? img : nullptr, l == 1 ? pitch_bytes : 0, l > 1),
                       "pyramid kernel");
         if (slot == GLT_CUR && t->packed)
@@ -400,8 +400,8 @@ int glt_build_pyramid(glt_tracker* t, int slot, const uint8_t* img, int pitch_by
                                 is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
               "level-0 copy");
     for (int l = 1; l < t->L; ++l)
-        GLT_CHECK(launch_pyr_down(t->jobs_dev + slot * GLT_MAX_LEVELS + (l - 1), 1,
-                                  pyr_tiles_x(t->W[l]), pyr_tiles_y(t->H[l]), s, nullptr, nullptr, 0,
+        GLT_CHECK(launch_pyr_down(t->jobs_dev + slot * GLT_MAX_LEVELS + (l - 1), nullptr,
+                                  pyr_tiles_x(t->W[l]) * pyr_tiles_y(t->H[l]), s, nullptr, nullptr, 0,
                                   l > 1),
                   "pyramid kernel");
     if (slot == GLT_CUR && t->packed) {
@@ -741,6 +741,7 @@ static void free_batch(glt_batch* b)
     cudaFree(b->users_dev);
     cudaFree(b->copy_dev);
     cudaFree(b->jobs_dev);
+    cudaFree(b->tile_map_dev);
     cudaFree(b->pack_dev);
     cudaFree(b->prop_jobs);
     cudaFree(b->prop_init);
@@ -824,6 +825,22 @@ int glt_batch_create(glt_tracker* const* trackers, int S, glt_batch** out)
             }
         }
     }
+    // per round, every output tile of every stream as (stream << 16) | tile:
+    // one CTA per entry in the batched pyramid kernel
+    const int rounds = std::max(1, b->Lmax - 1);
+    std::vector<unsigned> tmap;
+    for (int r = 0; r < rounds; ++r) {
+        b->tile_map_off[r] = tmap.size();
+        for (int i = 0; i < S; ++i) {
+            const PyrJob& J = jobs[(size_t)r * S + i];
+            const int n = pyr_tiles_x(J.dW) * pyr_tiles_y(J.dH);
+            for (int k = 0; k < n; ++k) tmap.push_back(((unsigned)i << 16) | (unsigned)k);
+        }
+        b->tile_total[r] = (int)(tmap.size() - b->tile_map_off[r]);
+    }
+    if (tmap.empty()) tmap.push_back(0u);
+    BALLOC(dalloc(&b->tile_map_dev, tmap.size()));
+    BALLOC(cudaMemcpy(b->tile_map_dev, tmap.data(), tmap.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
     BALLOC(dalloc(&b->copy_dev, (size_t)S));
     BALLOC(dalloc(&b->jobs_dev, jobs.size()));
     BALLOC(dalloc(&b->pack_dev, packs.size()));
@@ -849,14 +866,10 @@ void glt_batch_destroy(glt_batch* b) { free_batch(b); }
 
 static int batch_pyramid(glt_batch* b, const uint8_t* const* frames_dev, cudaStream_t s)
 {
-    int maxbytes = 0, maxw[GLT_MAX_LEVELS] = {}, maxh[GLT_MAX_LEVELS] = {}, maxpix = 0;
+    int maxbytes = 0, maxpix = 0;
     for (glt_tracker* t : b->trk) {
         maxbytes = std::max(maxbytes, t->W[0] * t->H[0]);
         maxpix = std::max(maxpix, t->W[0] * t->H[0]);
-        for (int l = 0; l < t->L; ++l) {
-            maxw[l] = std::max(maxw[l], t->W[l]);
-            maxh[l] = std::max(maxh[l], t->H[l]);
-        }
     }
     // level 1 reads the frames and writes level 0; streams with one level
     // only need the copy
@@ -869,8 +882,9 @@ static int batch_pyramid(glt_batch* b, const uint8_t* const* frames_dev, cudaStr
         after_first = true;
     }
     for (int l = 1; l < b->Lmax; ++l) {
-        GLT_CHECK(launch_pyr_down(b->jobs_dev + (size_t)(l - 1) * b->S, b->S, pyr_tiles_x(maxw[l]),
-                                  pyr_tiles_y(maxh[l]), s, (l == 1 && !single_level) ? frames_dev : nullptr,
+        GLT_CHECK(launch_pyr_down(b->jobs_dev + (size_t)(l - 1) * b->S,
+                                  b->tile_map_dev + b->tile_map_off[l - 1], b->tile_total[l - 1],
+                                  s, (l == 1 && !single_level) ? frames_dev : nullptr,
                                   nullptr, 0, after_first),
                   "batch pyramid kernel");
         after_first = true;

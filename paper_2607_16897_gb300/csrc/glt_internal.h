@@ -101,6 +101,9 @@ struct glt_batch {
     int* users_dev = nullptr;              // launch order -> caller index
     glt::CopyJob* copy_dev = nullptr;     // caller order
     glt::PyrJob* jobs_dev = nullptr;      // [L-1 rounds][S] caller order
+    unsigned* tile_map_dev = nullptr;     // per round: (stream << 16) | tile, for every tile
+    size_t tile_map_off[GLT_MAX_LEVELS] = {};  // offset of round l-1 in tile_map_dev
+    int tile_total[GLT_MAX_LEVELS] = {};  // tiles of round l-1 over all streams
     glt::PackJob* pack_dev = nullptr;     // [Lmax][S]
     int Lmax = 0;
     int variant = 0;                      // kernel variant (track_variant of the streams)
@@ -125,15 +128,17 @@ int cuda_fail(cudaError_t e, const char* what);
 // pyramid.cu
 // pyramid-family launches; pdl as for launch_track (the kernels wait for
 // their predecessor before reading what it writes)
-cudaError_t launch_pyr_down(const PyrJob* jobs_dev, int njobs, int tiles_x, int tiles_y,
+// launch_pyr_down: one level, `total` output tiles over all jobs;
+// tile_map_dev[f] = (job << 16) | tile within the job, or NULL for one job
+cudaError_t launch_pyr_down(const PyrJob* jobs_dev, const unsigned* tile_map_dev, int total,
                             cudaStream_t s, const uint8_t* const* frames = nullptr,
                             const uint8_t* src = nullptr, int sp = 0, bool pdl = false);
 cudaError_t launch_copy_frames(const uint8_t* const* frames, const CopyJob* jobs, int njobs,
                                int max_bytes, cudaStream_t s, bool pdl = false);
 cudaError_t launch_pack(const PackJob* jobs, int njobs, int max_pixels, cudaStream_t s,
                         bool pdl = false);
-int pyr_tiles_x(int dW);
-int pyr_tiles_y(int dH);
+__host__ __device__ int pyr_tiles_x(int dW);
+__host__ __device__ int pyr_tiles_y(int dH);
 
 // points.cu
 cudaError_t launch_set_points(const glt_tracker* t, const float* uvd_dev, int n, cudaStream_t s);
