@@ -591,12 +591,16 @@ def run_ours(args):
 
 
 def run_e2e(args, glt, trk, wl, frames_pin, stream):
-    """Same frames through the C ABI with HOST (pinned) buffers: every step is
-    one glt_track_image call (frame upload, chained pyramid + solve, result
-    read back, state update) from the sequence driver's initial state;
-    reference refreshes go through glt_build_pyramid / glt_set_map_points
-    with host buffers."""
+    """Same frames through the C ABI with HOST (pinned) buffers, the way a
+    per-frame caller uses the library: every frame is one glt_track_image call
+    started from the tracker's own constant-velocity state (frame upload,
+    chained pyramid + solve, result read back, state update); the host keeps
+    the tween-frame schedule (acceptance test, reference every 8 frames) and
+    hands a new reference in through glt_build_pyramid / glt_set_map_points
+    with host buffers and glt_set_state (the reference's pose from the
+    indirect pipeline, as SequenceDriver does)."""
     import torch
+    from paper_2607_16897_gb300.tween import TweenSwitch
     sh = stream.cuda_stream
     nF = len(wl.frames)
     h2d = d2h = 0
@@ -607,41 +611,62 @@ def run_e2e(args, glt, trk, wl, frames_pin, stream):
     for r in sorted(set(range(0, nF, 8)) | set(wl.refs)):
         refs_pin[r] = torch.from_numpy(wl.ref_points(r)).pin_memory()
     frames_np = [f.numpy() for f in frames_pin]
+    p = wl.solver.get("pattern", 0)
+    interval = 8
 
-    def refresh(drv, k):
+    def new_reference(k, motion):
+        """Frame k becomes the reference; the state restarts there with the
+        given camera motion (identity at a sequence start)."""
         nonlocal h2d
-        if drv.refresh(k):
-            r = drv.r
-            if r not in refs_pin:
-                refs_pin[r] = torch.from_numpy(wl.ref_points(r)).pin_memory()
-            trk.build_pyramid(glt.GLT_REF, frames_np[r], stream=sh)
-            trk.set_map_points(refs_pin[r].numpy(), stream=sh)
-            h2d += wl.frames[r].nbytes + refs_pin[r].numel() * 4
+        if k not in refs_pin:
+            refs_pin[k] = torch.from_numpy(wl.ref_points(k)).pin_memory()
+        trk.build_pyramid(glt.GLT_REF, frames_np[k], stream=sh)
+        trk.set_map_points(refs_pin[k].numpy(), stream=sh)
+        h2d += wl.frames[k].nbytes + refs_pin[k].numel() * 4
+        st = trk.get_state()
+        for i in range(12):
+            st.motion[i] = motion[i // 4, i % 4]
+        trk.set_state(st)
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    drv = SequenceDriver(wl)
-    k = 1
-    refresh(drv, 0)
+    k, r, since = 1, 0, 0
+    switch = TweenSwitch(max_direct=interval, max_cost=wl.max_cost,
+                         samples_per_point=8 if p == 0 else p * p)
+    new_reference(0, I34)
+    prev = None                      # (frame, pose relative to its reference, reference)
     for i in range(steps):
-        res = trk.track_image(frames_np[k], drv.init_for(k), drv.ab_init(), stream=sh)
+        res = trk.track_image(frames_np[k], stream=sh)
         h2d += wl.frames[k].nbytes + 14 * 8
         d2h += glt.RESULT_BYTES
-        drv.record(k, res)
+        ok = switch.direct_ok(res, wl.N)
+        switch.after_direct(res, wl.N)
+        since += 1
         kn = k + 1 if k + 1 < nF else 1
-        if kn == 1:
-            drv = SequenceDriver(wl)
-            refresh(drv, 0)
+        if kn == 1:                  # the sequence starts over
+            new_reference(0, I34)
+            r, since, prev = 0, 0, None
+        elif not ok or since >= interval:
+            # frame k becomes the reference at its true pose; the motion is
+            # that pose against the previous frame's estimate (or truth)
+            Tw_k = wl.T_ref_world(k)
+            if prev is None or prev[0] == prev[2]:
+                Tw_prev = wl.T_ref_world(k - 1)
+            else:
+                Tw_prev = orthonormalised(pose_mul(prev[1], wl.T_ref_world(prev[2])))
+            new_reference(k, pose_mul(Tw_k, pose_inv(Tw_prev)))
+            r, since, prev = k, 0, (k, None, k)
         else:
-            refresh(drv, k)
+            prev = (k, res["T"], r)
         k = kn
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
     return {"value": steps / t, "unit": "frames/s", "h2d_bytes_per_step": h2d / steps,
             "d2h_bytes_per_step": d2h / steps,
-            "note": "one glt_track_image call per frame from pinned host memory (upload, chained "
-                    "pyramid + solve, result read back), reference refreshes through the C ABI "
-                    "with host buffers, host-side sequence driver included"}
+            "note": "one glt_track_image call per frame from pinned host memory, started from the "
+                    "tracker's constant-velocity state (upload, chained pyramid + solve, result read "
+                    "back), reference refreshes through the C ABI with host buffers, tween-frame "
+                    "schedule on the host"}
 
 
 def launch_overhead(stream, enqueue, reps=1000):
