@@ -57,6 +57,13 @@ def aggregate_rate(units_per_rank, world, seconds):
     return world * units_per_rank / seconds
 
 
+def step_percentiles(ms):
+    """Median, 90th percentile and spread of the per-step device times (ms)."""
+    a = np.asarray(ms, dtype=np.float64)
+    return {"p50": float(np.percentile(a, 50)), "p90": float(np.percentile(a, 90)),
+            "min": float(a.min()), "max": float(a.max())}
+
+
 def stream_seed(kind, s, rank):
     """Seed of stream s of workload `kind` on `rank` (replicas get disjoint
     sequences)."""
@@ -574,6 +581,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{world}",
                            "l2": "flushed between steps (256 MB write, outside the step events)",
                            "timing": "sum of per-step CUDA-event times (pyramid + track)"},
+                "step_ms_percentiles": step_percentiles(step_ms),
                 "breakdown_ms": {"pyramid": "chained with the track launch (inside 'track')",
                                  "track": statistics.mean(trk_ms),
                                  "reference_refresh": statistics.mean(ref_ms) if ref_ms else None,
@@ -1082,6 +1090,7 @@ def run_batch(args):
                                                "ms": shape[2]},
                            "l2": "flushed between steps (256 MB write, outside the step events)",
                            "timing": "sum of per-step CUDA-event times around the graph replay"},
+                "step_ms_percentiles": step_percentiles(dev_ms),
                 "breakdown_ms": {"replay": statistics.mean(dev_ms),
                                  "wall_per_step": 1000.0 * head["t_wall"] / args.steps},
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

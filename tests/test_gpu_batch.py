@@ -133,3 +133,36 @@ def test_chained_graph_builds_the_pyramids(glt, orc, syn):
                                           err_msg=f"stream {i} level {l}")
     for s in streams:
         s["trk"].close()
+
+
+def test_chained_graph_with_single_level_and_mixed_streams(glt, orc, syn):
+    """Graph chains with their other first kernels: a one-level stream (the
+    level-0 copy kernel heads the chain, the pyramid kernels read level 0),
+    and FP16-packed levels (the packing kernel joins the chain).  Each stream
+    matches its unchained launch and the oracle's pyramid."""
+    import torch
+    for precision, specs in (("fp32", [(320, 240, 256.0, 300, 1), (640, 480, 525.0, 800, 4),
+                                       (752, 480, 601.6, 500, 3)]),
+                             ("mixed", [(640, 480, 525.0, 800, 4), (320, 240, 256.0, 300, 3)])):
+        streams = []
+        for i, (W, H, f, N, L) in enumerate(specs):
+            cam = syn.camera_for(W, H, f)
+            seq = syn.sequence(700 + i, 6, cam, syn.ROOM_LARGE, 0.5, 30.0)
+            ref, uvd = syn.reference_points(seq, 0, N, 0.5, 8.0)
+            cur, _ = seq.frame(2)
+            trk = glt.Tracker(W, H, cam.K, levels=L, max_points=N, precision=precision)
+            trk.build_pyramid(glt.GLT_REF, ref)
+            trk.set_map_points(uvd)
+            streams.append(dict(trk=trk, cur=torch.from_numpy(cur).cuda(), L=L,
+                                T_init=syn.relative(seq.T_wc[0], seq.T_wc[1])))
+        graph = run_batch(glt, streams, shape=(2, 256), graph=True)
+        for i, s in enumerate(streams):
+            cur = s["cur"].cpu().numpy()
+            for l, lv in enumerate(orc.pyramid(cur, s["L"])):
+                np.testing.assert_array_equal(s["trk"].get_pyramid(glt.GLT_CUR, l), lv,
+                                              err_msg=f"{precision} stream {i} level {l}")
+        direct = run_batch(glt, streams, shape=(2, 256))
+        for d, g in zip(direct, graph):
+            assert np.array_equal(d["T"], g["T"]) and d["passes"] == g["passes"], precision
+        for s in streams:
+            s["trk"].close()
