@@ -234,6 +234,132 @@ class SequenceDriver:
         return True
 
 
+def poses_mul(A, B):
+    """Batched pose_mul over the leading axis: (S, 3, 4) x (S, 3, 4)."""
+    out = np.matmul(A[:, :, :3], B)
+    out[:, :, 3] += A[:, :, 3]
+    return out
+
+
+def poses_inv(A):
+    """Batched pose_inv: [R^T | -R^T t] for (S, 3, 4)."""
+    Rt = np.transpose(A[:, :, :3], (0, 2, 1))
+    return np.concatenate([Rt, -np.matmul(Rt, A[:, :, 3:])], axis=2)
+
+
+def poses_orthonormalised(T):
+    """Batched orthonormalised: Gram-Schmidt on the rotation rows."""
+    out = np.array(T, np.float64, copy=True)
+    r0, r1 = T[:, 0, :3], T[:, 1, :3]
+    q0 = r0 / np.sqrt(np.sum(r0 * r0, axis=1, keepdims=True))
+    q1 = r1 - np.sum(r1 * q0, axis=1, keepdims=True) * q0
+    q1 = q1 / np.sqrt(np.sum(q1 * q1, axis=1, keepdims=True))
+    out[:, 0, :3], out[:, 1, :3], out[:, 2, :3] = q0, q1, np.cross(q0, q1)
+    return out
+
+
+def se3_logs(T):
+    """Batched SE(3) log (v, w) of (S, 3, 4) poses; the same closed form and
+    small-angle series as the proposal module's se3_log."""
+    R, t = T[:, :, :3], T[:, :, 3]
+    s = 0.5 * np.stack([R[:, 2, 1] - R[:, 1, 2], R[:, 0, 2] - R[:, 2, 0], R[:, 1, 0] - R[:, 0, 1]], 1)
+    c = 0.5 * (np.trace(R, axis1=1, axis2=2) - 1.0)
+    sn = np.linalg.norm(s, axis=1)
+    th = np.arctan2(sn, c)
+    w = np.where((sn < 1e-12)[:, None], s, s * (th / np.where(sn < 1e-12, 1.0, sn))[:, None])
+    Z = np.zeros_like(th)
+    W = np.stack([np.stack([Z, -w[:, 2], w[:, 1]], 1), np.stack([w[:, 2], Z, -w[:, 0]], 1),
+                  np.stack([-w[:, 1], w[:, 0], Z], 1)], 1)
+    th2 = th * th
+    small = th < 1e-3
+    ths = np.where(small, 1.0, th)
+    A = np.sin(ths) / ths
+    B = (1.0 - np.cos(ths)) / (ths * ths)
+    k = np.where(small, 1.0 / 12.0 + th2 / 720.0 + th2 * th2 / 30240.0,
+                 (1.0 - A / (2.0 * B)) / (ths * ths))
+    Vinv = np.eye(3)[None] - 0.5 * W + k[:, None, None] * np.matmul(W, W)
+    return np.concatenate([np.matmul(Vinv, t[:, :, None])[:, :, 0], w], 1)
+
+
+class BatchDriver:
+    """SequenceDriver for S streams at once (numpy over the stream axis): the
+    same constant-velocity start, affine carry-over, acceptance test and
+    reference schedule, for the batched end-to-end loop, where one Python
+    driver per stream would cost more host time than the GPU step."""
+
+    def __init__(self, wls, interval=8, min_valid_frac=0.5):
+        self.wls = wls
+        self.S = len(wls)
+        self.interval = interval
+        self.min_valid = np.array([min_valid_frac * (8 if w.solver.get("pattern", 0) == 0
+                                                     else w.solver["pattern"] ** 2) * w.N
+                                   for w in wls])
+        self.max_cost = np.array([w.max_cost for w in wls], np.float64)
+        self.reset()
+
+    def truth(self, idx, k):
+        return np.stack([self.wls[s].T_ref_world(k) for s in idx]) if len(idx) else np.zeros((0, 3, 4))
+
+    def reset(self):
+        S = self.S
+        self.r = np.zeros(S, np.int64)
+        self.since = np.zeros(S, np.int64)
+        self.need = np.ones(S, bool)
+        self.Tk1 = self.truth(range(S), 0)       # world -> camera of the last frame
+        self.Tk2 = np.zeros((S, 3, 4))           # and of the one before (if has2)
+        self.has2 = np.zeros(S, bool)
+        self.Tref = self.Tk1.copy()              # world -> camera of each reference
+        self.ab = np.zeros((S, 2))
+        self.rejected = np.zeros(S, np.int64)
+        self.accepted = np.zeros(S, np.int64)
+
+    def refresh(self, k):
+        """Streams that need a new reference take frame k (its true pose, as
+        the indirect pipeline would provide); returns their indices."""
+        idx = np.nonzero(self.need)[0]
+        if len(idx):
+            T = self.truth(idx, k)
+            self.r[idx] = k
+            self.Tk1[idx] = T
+            self.Tref[idx] = T
+            self.ab[idx] = 0.0
+            self.since[idx] = 0
+            self.need[idx] = False
+        return idx
+
+    def motion(self):
+        """A = T_{k-1} T_{k-2}^-1 per stream (identity before two frames)."""
+        A = np.broadcast_to(I34, (self.S, 3, 4)).copy()
+        if self.has2.any():
+            h = self.has2
+            A[h] = poses_mul(self.Tk1[h], poses_inv(self.Tk2[h]))
+        return A
+
+    def init_for(self):
+        return poses_mul(poses_mul(self.motion(), self.Tk1), poses_inv(self.Tref))
+
+    def motion_features(self):
+        """The proposal network's motion input per stream (zeros before two frames)."""
+        out = np.zeros((self.S, 6), np.float32)
+        if self.has2.any():
+            from paper_2607_16897_gb300.proposal import MOTION_SCALE
+            out[self.has2] = (se3_logs(self.motion()[self.has2]) / MOTION_SCALE).astype(np.float32)
+        return out
+
+    def record(self, k, T, a, b, status, n_valid, cost):
+        Tw = poses_orthonormalised(poses_mul(T, self.Tref))
+        self.ab = np.stack([a, b], 1).astype(np.float64)
+        self.since += 1
+        ok = (status == 0) & (n_valid >= self.min_valid) & np.isfinite(cost) & (cost <= self.max_cost)
+        bad = np.nonzero(~ok)[0]
+        if len(bad):
+            Tw[bad] = self.truth(bad, k)
+        self.rejected += ~ok
+        self.accepted += ok
+        self.Tk2, self.Tk1, self.has2 = self.Tk1, Tw, np.ones(self.S, bool)
+        self.need |= (self.since >= self.interval) | ~ok
+
+
 def pose_error(wl, k, r, T):
     import synth
     Tt = synth.relative(wl.seq.T_wc[r], wl.seq.T_wc[k])
@@ -870,8 +996,18 @@ def run_batch(args):
                         jacobian=w.jacobian, **w.solver) for w in wls]
     batch = glt.Batch(trks)
     frames_dev = [torch.from_numpy(np.stack(w.frames)).to(dev) for w in wls]
-    frames_pin = [torch.from_numpy(np.stack(w.frames)).pin_memory() for w in wls]
-    slots = [torch.empty((w.cam.H, w.cam.W), dtype=torch.uint8, device=dev) for w in wls]
+    # host frames in pinned memory, laid out per step (every stream's frame k
+    # contiguous), so that a step's upload is one copy; per-stream views serve
+    # the reference refreshes
+    frame_off = np.concatenate([[0], np.cumsum([w.cam.W * w.cam.H for w in wls])]).astype(np.int64)
+    step_np = np.empty((F, int(frame_off[-1])), np.uint8)
+    for s_, w in enumerate(wls):
+        for k_ in range(F):
+            step_np[k_, frame_off[s_]:frame_off[s_ + 1]] = w.frames[k_].ravel()
+    step_pin = torch.from_numpy(step_np).pin_memory()
+    del step_np
+    frames_pin = [[step_pin[k_, frame_off[s_]:frame_off[s_ + 1]].view(w.cam.H, w.cam.W) for k_ in range(F)]
+                  for s_, w in enumerate(wls)]
     ptr_dev = torch.zeros(S, dtype=torch.int64, device=dev)
     ptr_pin = torch.zeros(S, dtype=torch.int64).pin_memory()
     init_dev = torch.zeros((S, 14), dtype=torch.float64, device=dev)
@@ -911,27 +1047,26 @@ def run_batch(args):
 
     drvs = [SequenceDriver(w) for w in wls]
 
-    def restart(host=False):
+    def restart():
         for d in drvs:
             d.__init__(d.wl)
         for s in range(S):
             drvs[s].refresh(0)
-            refresh(s, 0, host=host)
+            refresh(s, 0)
 
     init_np, motion_np, ptr_np = init_pin.numpy(), motion_pin.numpy(), ptr_pin.numpy()
-    slot_ptrs = [t.data_ptr() for t in slots]
     frame_ptrs = [[f[k].data_ptr() for k in range(F)] for f in frames_dev]
 
-    def prepare(k, use_slots):
+    def prepare(k):
         for s in range(S):
             d = drvs[s]
             init_np[s, :12] = d.init_for(k).ravel()
             init_np[s, 12:] = d.ab_init()
             if use_prop:
                 motion_np[s] = prop.motion_feature(d.Tw.get(k - 1), d.Tw.get(k - 2))
-            ptr_np[s] = slot_ptrs[s] if use_slots else frame_ptrs[s][k]
+            ptr_np[s] = frame_ptrs[s][k]
 
-    def finish(k, record, refresh_host=False):
+    def finish(k, record):
         res = glt.parse_results(out_pin.numpy())
         n_ref = 0
         for s in range(S):
@@ -940,30 +1075,25 @@ def run_batch(args):
                                motion_pin[s].numpy().copy()))
             drvs[s].record(k, res[s])
             if k + 1 < F and drvs[s].refresh(k):
-                refresh(s, k, host=refresh_host)
+                refresh(s, k)
                 n_ref += 1
         return res, n_ref
 
-    def run_steps(nsteps, timed, record, e2e=False):
-        restart(host=e2e)
+    def run_steps(nsteps, timed, record):
+        """Device-resident steps: frames already in HBM, L2 flushed before each
+        replay (outside its events), one SequenceDriver per stream."""
+        restart()
         stream.synchronize()
         k = 0
         dev_ms, n_ref_total = [], 0
-        h2d = d2h = 0
         for i in range(nsteps):
             k += 1
             if k >= F:
                 k = 1
-                restart(host=e2e)
-            prepare(k, e2e)
+                restart()
+            prepare(k)
             with torch.cuda.stream(stream):
-                if e2e:
-                    for s in range(S):
-                        slots[s].copy_(frames_pin[s][k], non_blocking=True)
-                        h2d += slots[s].numel()
-                    h2d += init_pin.numel() * 8 + (motion_pin.numel() * 4 if use_prop else 0)
-                else:
-                    flush.zero_()
+                flush.zero_()
                 ptr_dev.copy_(ptr_pin, non_blocking=True)
                 init_dev.copy_(init_pin, non_blocking=True)
                 motion_dev.copy_(motion_pin, non_blocking=True)
@@ -973,18 +1103,63 @@ def run_batch(args):
                 batch.replay(stream=sh)
                 e1.record(stream)
                 out_pin.copy_(out_dev, non_blocking=True)
-                d2h += out_pin.numel()
             stream.synchronize()
             if timed:
                 dev_ms.append(e0.elapsed_time(e1))
-            _, nr = finish(k, record, refresh_host=e2e)
+            _, nr = finish(k, record)
             n_ref_total += nr
-        return dev_ms, n_ref_total, h2d, d2h
+        return dev_ms, n_ref_total
+
+    def run_e2e_steps(nsteps):
+        """The end-to-end loop: host frames and states in, results out, every
+        step; the drivers of all streams advance together (BatchDriver, the
+        same schedule as SequenceDriver)."""
+        bd = BatchDriver(wls)
+        step_dev = torch.empty(int(frame_off[-1]), dtype=torch.uint8, device=dev)
+        ptr_np[:] = step_dev.data_ptr() + frame_off[:-1]
+        h2d = d2h = 0
+
+        def refresh_streams(idx, k):
+            nonlocal h2d
+            for s_ in idx:
+                refresh(int(s_), k, host=True)
+                h2d += wls[s_].cam.W * wls[s_].cam.H + uvd_pin[(int(s_), k)].numel() * 4
+
+        with torch.cuda.stream(stream):
+            ptr_dev.copy_(ptr_pin, non_blocking=True)
+        refresh_streams(bd.refresh(0), 0)
+        k = 1
+        res = np.frombuffer(out_pin.numpy(), dtype=glt.RESULT_DTYPE)
+        for _ in range(nsteps):
+            init_np[:, :12] = bd.init_for().reshape(S, 12)
+            init_np[:, 12:] = bd.ab
+            if use_prop:
+                motion_np[:] = bd.motion_features()
+            with torch.cuda.stream(stream):
+                step_dev.copy_(step_pin[k], non_blocking=True)
+                init_dev.copy_(init_pin, non_blocking=True)
+                if use_prop:
+                    motion_dev.copy_(motion_pin, non_blocking=True)
+                batch.replay(stream=sh)
+                out_pin.copy_(out_dev, non_blocking=True)
+            h2d += step_pin[k].numel() + init_pin.numel() * 8 + (motion_pin.numel() * 4 if use_prop else 0)
+            d2h += out_pin.numel()
+            stream.synchronize()
+            bd.record(k, res["T"].reshape(S, 3, 4), res["a"], res["b"], res["status"], res["n_valid"],
+                      res["cost"])
+            if k + 1 < F:
+                refresh_streams(bd.refresh(k), k)
+                k += 1
+            else:
+                bd.reset()
+                refresh_streams(bd.refresh(0), 0)
+                k = 1
+        return h2d, d2h
 
     # every stream starts on its frame 0 as reference; autotune the tile shape
     # on frame 1 (plain form)
     restart()
-    prepare(1, False)
+    prepare(1)
     with torch.cuda.stream(stream):
         ptr_dev.copy_(ptr_pin, non_blocking=True)
         init_dev.copy_(init_pin, non_blocking=True)
@@ -1009,7 +1184,7 @@ def run_batch(args):
         torch.cuda.synchronize()
         rec = []
         t0 = time.perf_counter()
-        dev_ms, n_ref, _, _ = run_steps(args.steps, True, rec)
+        dev_ms, n_ref = run_steps(args.steps, True, rec)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t0
         clk = clocks.stop()
@@ -1042,14 +1217,15 @@ def run_batch(args):
         pin_refs()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        _, _, h2d, d2h = run_steps(args.steps, False, None, e2e=True)
+        h2d, d2h = run_e2e_steps(args.steps)
         torch.cuda.synchronize()
         te = time.perf_counter() - t1
         e2e = {"value": S * args.steps / te, "unit": "frames/s",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-               "note": "every step copies all streams' frames from pinned host memory, replays the "
-                       "graph, reads all results back; reference refreshes through the C ABI with "
-                       "host buffers"}
+               "note": "every step copies all streams' frames from pinned host memory (one copy), "
+                       "replays the graph, reads all results back and runs the sequence drivers of "
+                       "all streams at once (BatchDriver); reference refreshes through the C ABI "
+                       "with host buffers"}
     cpu = parity = None
     if rank == 0 and not args.no_cpu:
         pw = None
