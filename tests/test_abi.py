@@ -71,6 +71,10 @@ def test_host_side_argument_checks(lib_path):
         assert rc == glt.GLT_ERR_INVALID_ARG, kw
         assert glt.glt_last_error()
     assert glt.glt_build_pyramid(None, 0, None, 0, 0, None) == glt.GLT_ERR_INVALID_ARG
+    r = glt.glt_result()
+    assert glt.glt_track_image(None, None, 0, 0, None, None, ctypes.byref(r), None) == glt.GLT_ERR_INVALID_ARG
+    assert glt.glt_track_image_async(None, None, 0, None, None, None) == glt.GLT_ERR_INVALID_ARG
+    assert glt.glt_track_frame(None, None, None, ctypes.byref(r), None) == glt.GLT_ERR_INVALID_ARG
     assert glt.glt_batch_create(None, 0, ctypes.byref(ctypes.c_void_p())) == glt.GLT_ERR_INVALID_ARG
 
 
