@@ -189,7 +189,8 @@ int glt_track_frame(glt_tracker* trk, const double T_init[12], const double ab_i
 int glt_track_frame_async(glt_tracker* trk, const double* init_dev, glt_result* out_dev,
                           void* stream);
 
-/* glt_build_pyramid(GLT_CUR) from the DEVICE frame `frame_dev` (width x
+/* Sec. IV-C "Image pyramids" + "Track" for one frame:
+ * glt_build_pyramid(GLT_CUR) from the DEVICE frame `frame_dev` (width x
  * height, `pitch_bytes` per row) followed by glt_track_frame_async, issued as
  * one chain: each pyramid kernel after the first, and the track kernel, is a
  * programmatic dependent launch of the kernel before it, so it starts while
@@ -200,7 +201,8 @@ int glt_track_frame_async(glt_tracker* trk, const double* init_dev, glt_result* 
 int glt_track_image_async(glt_tracker* trk, const uint8_t* frame_dev, int pitch_bytes,
                           const double* init_dev, glt_result* out_dev, void* stream);
 
-/* glt_build_pyramid(GLT_CUR) + glt_track_frame in one call, the form a
+/* Sec. IV-C "Image pyramids" + "Track" for one frame, from the host:
+ * glt_build_pyramid(GLT_CUR) + glt_track_frame in one call, the form a
  * per-frame caller uses: the frame `img` (host memory, uploaded first through
  * the tracker's staging buffer, or device memory per `is_device`; `pitch_bytes`
  * per row) is chained with the solve as in glt_track_image_async, the result
