@@ -34,6 +34,9 @@ FLOPS_PER_SAMPLE = 160      # algorithmic FP32 flops per residual sample per pas
 # launch as in the timed steps) on the workload named by the key; a value is
 # removed whenever the kernel changes after it was taken.
 TRACK_TRAFFIC = {"c2": 780672, "c3": 55125248}
+# the trained proposal network's parameters (data file; read here as plain
+# numbers so that the oracle legs need nothing but oracle/ and synth/)
+WEIGHTS_PATH = os.path.join(ROOT, "paper_2607_16897_gb300", "proposal_weights.npy")
 I34 = np.hstack([np.eye(3), np.zeros((3, 1))])
 
 
@@ -93,6 +96,9 @@ def parse():
     ap.add_argument("--shape", default=None,
                     help="batched forms: fixed tile shape 'cluster,threads' instead of the "
                          "autotuner's pick (profiling runs, where the tuner's timings are distorted)")
+    ap.add_argument("--precision", default=None, choices=["fp32", "mixed"],
+                    help="storage precision of the levels: c4 / c4b default to mixed (FP16 "
+                         "levels and gradients, Kahan sums), every other workload to fp32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-launch-overhead", action="store_true",
                     help="skip the launch-overhead measurement (e.g. for a profiler's launch list)")
@@ -422,6 +428,13 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def proposal_weights():
+    w = np.load(WEIGHTS_PATH).astype(np.float32)
+    if w.size != 189064:
+        raise ValueError(f"{WEIGHTS_PATH}: {w.size} values, expected 189064")
+    return w
+
+
 def fp32_peak_tflops(sm_mhz):
     # 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -459,16 +472,16 @@ def oracle_track_sequence(wl, frames, inits=None, proposal=None, motions=None):
         t0 = time.perf_counter()
         trk.build_pyramid(1, wl.frames[k])
         if proposal is not None:
+            # the oracle network in front of the oracle tracker: its inputs and
+            # the composition of its output are the oracle's own arithmetic
             from oracle import nn as onn
-            from paper_2607_16897_gb300.proposal import OUT_SCALE
-            from paper_2607_16897_gb300.proposal import motion_feature
-            mk = motions[k] if motions is not None else motion_feature(drv.Tw.get(k - 1),
-                                                                      drv.Tw.get(k - 2))
+            if motions is not None:
+                mk = np.asarray(motions[k], np.float64)
+            else:
+                mk = onn.motion_feature(drv.Tw.get(k - 1), drv.Tw.get(k - 2))
             x = (oracle.pyramid(wl.frames[k], wl.L)[-1].astype(np.float64) - ref_coarse) / 64.0
-            y, _ = onn.forward(proposal, x[None, None], np.asarray(mk, np.float64)[None])
-            d = y[0] * OUT_SCALE
-            T_init = oracle.se3_mul(T_init, oracle.se3_exp(d[:6]))
-            ab = (ab[0] + d[6], ab[1] + d[7])
+            y, _ = onn.forward(proposal, x[None, None], mk[None])
+            T_init, ab = onn.apply_output(T_init, ab, y[0])
         res = trk.track_frame(T_init, ab)
         t_track += time.perf_counter() - t0
         out[k] = res
@@ -486,8 +499,8 @@ def run_reference(args):
     W, K = args.warmup, args.steps
     if args.workload in ("c3", "c4b", "c5"):
         import concurrent.futures
-        from paper_2607_16897_gb300 import proposal as prop
-        pool = prop.render_pool()
+        from synth import jobs as rj
+        pool = rj.render_pool()
         wls = batch_workloads(args.workload, rank, pool=pool)
         pool.close()
         pool.join()
@@ -497,7 +510,7 @@ def run_reference(args):
         pw = None
         if args.workload == "c5":
             from oracle import nn as onn
-            pw = onn.unflatten(onn.to_bf16(prop.load_weights()))
+            pw = onn.unflatten(onn.to_bf16(proposal_weights()))
         F = len(wls[0].frames)
         n = min(F - 1, W + K)
         workers = os.cpu_count() or 1
@@ -551,7 +564,7 @@ def run_ours(args):
     wl = single_workload(args.workload, rank)   # replicas: one independent stream per GPU
     if args.jacobian:
         wl.jacobian = args.jacobian
-    precision = "mixed" if args.workload == "c4" else "fp32"
+    precision = args.precision or ("mixed" if args.workload == "c4" else "fp32")
     Wd, Hd, L, N = wl.cam.W, wl.cam.H, wl.L, wl.N
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
@@ -917,7 +930,7 @@ def single_workload(kind, rank=0):
                               "IC, 6 levels, 10 GN iterations per level, no affine, no Huber)")
     if kind == "c4":
         return Workload(seed=stream_seed(kind, 0, rank), frames=300, N=8000, W=1280, H=720, f=1050.0, L=5,
-                        speed=1.0, ang=60.0, label="C4 mixed precision, single stream")
+                        speed=1.0, ang=60.0, label="C4 single stream")
     return Workload(seed=stream_seed("c2", 0, rank))
 
 
@@ -929,7 +942,7 @@ def batch_workloads(kind, rank=0, nstreams=None, frames=24, pool=None):
     held-out seeds 5000..5255 with the proposal's training motion range (mean
     speed 0.5-2 m/s, 30-90 deg/s per stream).  With a process pool the
     frames and the references at multiples of 8 are rendered in parallel."""
-    from paper_2607_16897_gb300 import proposal as prop
+    from synth import jobs as rj
     rng = np.random.default_rng(1000 + rank)
     sizes = [(320, 240), (640, 480), (752, 480), (1280, 720)]
     nstreams = nstreams or (256 if kind == "c5" else 64)
@@ -941,7 +954,7 @@ def batch_workloads(kind, rank=0, nstreams=None, frames=24, pool=None):
                                 render=pool is None))
         elif kind == "c5":
             seed = stream_seed(kind, s, rank)
-            v, w = prop.stream_motion(seed)
+            v, w = rj.stream_motion(seed)
             wls.append(Workload(seed=seed, frames=frames, N=2000, W=640, H=480, f=525.0, L=5,
                                 speed=v, ang=w, label="C5 stream", render=pool is None))
         else:
@@ -951,11 +964,11 @@ def batch_workloads(kind, rank=0, nstreams=None, frames=24, pool=None):
                                 f=0.8 * W, L=4, label="C3 stream", render=pool is None))
     if pool is not None:
         jobs = [w.job + (k, 0, w.speed, w.ang) for w in wls for k in range(frames)]
-        imgs = pool.map(prop._render_job, jobs, chunksize=8)
+        imgs = pool.map(rj._render_job, jobs, chunksize=8)
         for i, w in enumerate(wls):
             w.frames = [imgs[i * frames + k][0] for k in range(frames)]
         refs = [(i, r) for i in range(len(wls)) for r in range(0, frames - 1, 8)]
-        pts = pool.map(prop._render_job, [wls[i].job + (r, wls[i].N, wls[i].speed, wls[i].ang)
+        pts = pool.map(rj._render_job, [wls[i].job + (r, wls[i].N, wls[i].speed, wls[i].ang)
                                           for i, r in refs], chunksize=4)
         for (i, r), (_, uvd) in zip(refs, pts):
             wls[i].refs[r] = uvd
@@ -973,7 +986,8 @@ def run_batch(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    pool = prop.render_pool()          # spawned before the first CUDA call
+    from synth import jobs as rj
+    pool = rj.render_pool()            # spawned before the first CUDA call
     wls = batch_workloads(args.workload, rank, pool=pool)
     pool.close()
     pool.join()
@@ -986,7 +1000,7 @@ def run_batch(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    precision = "mixed" if args.workload == "c4b" else "fp32"
+    precision = args.precision or ("mixed" if args.workload == "c4b" else "fp32")
     use_prop = args.workload == "c5"
     S = len(wls)
     F = len(wls[0].frames)
@@ -1231,7 +1245,7 @@ def run_batch(args):
         pw = None
         if use_prop:
             from oracle import nn as onn
-            pw = onn.unflatten(onn.to_bf16(prop.load_weights()))
+            pw = onn.unflatten(onn.to_bf16(proposal_weights()))
         cpu, parity = batch_cpu_baseline(wls, rec, proposal=pw)
     # roofline of the persistent tracker (the graph's dominant kernel)
     samples = sum(r[4]["passes"] * 8 * wls[r[0]].N for r in rec) / args.steps

@@ -61,6 +61,8 @@ extern "C" {
 /* glt_result.status bits (per-frame solver outcomes) */
 #define GLT_TRACK_TOO_FEW_POINTS 1 /* a level had fewer than min_valid samples */
 #define GLT_TRACK_NOT_PD 2         /* the damped normal matrix was not positive definite */
+#define GLT_TRACK_DIVERGED 4       /* a non-finite start, pass sum (FP32 overflow) or
+                                      candidate state; the state before it is returned */
 
 /* pyramid slots */
 #define GLT_REF 0
@@ -273,6 +275,14 @@ int glt_get_state(const glt_tracker* trk, glt_state* out);
  * Errors: INVALID_ARG (NULL, non-finite values, frames < 0). */
 int glt_set_state(glt_tracker* trk, const glt_state* in);
 
+/* Test access to the solver's FP64 reciprocal (the pivot reciprocals of the
+ * L D L^T factorisation inside the track kernel): r_dev[i] = 1 / d_dev[i] for
+ * n DEVICE doubles, computed as the kernel computes it (one Newton-Raphson
+ * step on an FP32 seed for 2^-100 <= |d| < 2^100, relative error below 1e-13;
+ * an IEEE division elsewhere).  Not part of the method; no paper counterpart.
+ * Asynchronous.  Errors: INVALID_ARG (n < 0, NULL with n > 0), CUDA. */
+int glt_debug_rcp(const double* d_dev, double* r_dev, int n, void* stream);
+
 /* Copies level `level` of pyramid `slot` (unpadded, W_l * H_l bytes) to host
  * memory `out`.  Synchronous. */
 int glt_get_pyramid(glt_tracker* trk, int slot, int level, uint8_t* out, void* stream);
@@ -324,28 +334,30 @@ int glt_batch_autotune(glt_batch* batch, const double* init_dev, glt_result* out
 /* Sets the (cluster, threads) shape used by glt_batch_track / capture. */
 int glt_batch_set_shape(glt_batch* batch, int cluster, int threads);
 
-/* Allocation-free linearisation.  The paper has no counterpart: this entry
- * point exists for callers that must not allocate device memory where they
- * call it -- code recorded into a CUDA graph by stream capture, real-time
- * loops with a memory budget fixed at start-up, plugins whose host framework
- * owns all device memory -- and who therefore cannot use glt_create.
- * It runs one linearisation of Eqs. 3-5 (same arithmetic as
- * glt_debug_linearize) on caller-owned DEVICE buffers: the REF and CUR images
- * of pyramid level `level` (uint8, (width >> level) x (height >> level), row
+/* Allocation-free linearisation.  The paper has no counterpart.  It serves
+ * callers that may not allocate device memory at the point where they need a
+ * linearisation and therefore cannot use glt_create: real-time loops whose
+ * memory budget is fixed at start-up, and plugins whose host framework owns
+ * every device allocation.  It computes what glt_debug_linearize computes
+ * (same arithmetic) on caller-owned DEVICE buffers: the REF and CUR images of
+ * pyramid level `level` (uint8, (width >> level) x (height >> level), row
  * pitches in bytes >= the level width), n map points uvd_dev[n][3] =
  * (u0, v0, depth) at level-0 pixels, level-0 intrinsics, the state (T
  * host-side 3x4, a, b), Huber k and zmin; the reference patch is sampled on
  * the fly.  It writes out_dev[46] (device doubles): the 36 upper-triangle
  * entries of H row by row, g (8), the Huber energy E and the valid-sample
- * count n.  Asynchronous on `stream`; allocates nothing.
- * Scratch: a file-scope device array holding up to 512 block partial sums
- * (n <= 65536 points; larger n returns GLT_ERR_CAPACITY), which every GPU
- * that loads the library keeps until the process exits.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  Every call shares the array
- * and clears its ticket counter first, so calls that overlap on the GPU (on
- * different streams, or concurrently from several host threads) race and
- * must be serialised by the caller. */
+ * count n.  Asynchronous on `stream`; calls no cudaMalloc or cudaFree.
+ * Scratch: a file-scope device array of 512 block partial sums plus a ticket
+ * (n <= 65536 points; larger n returns GLT_ERR_CAPACITY before any GPU work),
+ * which every GPU that loads the library keeps until the process exits.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) and keeps it for the device; make that first call
+ * before any stream capture.  The kept address does not survive
+ * cudaDeviceReset (or any other reset of the device's primary context):
+ * after one, this entry point must not be called again in the process.
+ * Every call shares the array and clears its ticket counter first, so calls
+ * that overlap on the GPU (on different streams, or concurrently from several
+ * host threads) race and must be serialised by the caller. */
 int glt_linearize_noalloc(const uint8_t* ref_dev, int ref_pitch, const uint8_t* cur_dev,
                           int cur_pitch, int width, int height, int level, double fx, double fy,
                           double cx, double cy, const float* uvd_dev, int n, const double T[12],
@@ -439,7 +451,7 @@ int glt_batch_set_proposal(glt_batch* batch, glt_nn* nn, const float* motion_dev
 
 /* Name of a return code (GLT_OK, GLT_ERR_*) or, for a positive value, of the
  * glt_result.status bits it holds ("ok", "too few points", "not positive
- * definite", joined by "|"); never NULL, static storage. */
+ * definite", "diverged", joined by "|"); never NULL, static storage. */
 const char* glt_status_string(int code);
 
 /* Thread-local message of the last error (never NULL). */

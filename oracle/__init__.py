@@ -37,6 +37,7 @@ _lib = None
 
 TOO_FEW_POINTS = 1
 NOT_PD = 2
+DIVERGED = 4
 
 PATTERN = np.array([[0, 0], [-2, 0], [2, 0], [0, -2], [0, 2], [-1, -1], [1, -1], [-1, 1]])
 

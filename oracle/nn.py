@@ -18,9 +18,18 @@ Flat parameter layout (an interface both implementations follow): conv1.w
 [64,32,3,3], conv3.b [64], fc1.w [128,1286], fc1.b [128], fc2.w [8,128],
 fc2.b [8], each row-major, concatenated in that order (189064 values).
 
+Inputs and outputs of the proposal (the network's interface to the tracker):
+the motion input is log(M) / MOTION_SCALE with M = T_{k-1} T_{k-2}^-1 the last
+inter-frame camera motion (world -> camera poses), and the output y is the
+increment delta = OUT_SCALE * y, applied to the constant-velocity start as
+T' = T_init exp(delta[0:6]), a' = a + delta[6], b' = b + delta[7].  The SE(3)
+arithmetic is the FP64 oracle's (``oracle.se3_log / se3_exp / se3_mul``).
+
 Parity status: pinned by central finite differences of the loss in FP64 (all
 parameters and inputs), by a library 2-D correlation (scipy) for the
-convolution, and by numpy matmul for the fully connected layers.
+convolution, and by numpy matmul for the fully connected layers; the motion
+feature and the composition of the output by scipy's matrix logarithm and
+exponential.
 """
 from __future__ import annotations
 
@@ -32,6 +41,38 @@ SHAPES = [("conv1.w", (16, 1, 3, 3)), ("conv1.b", (16,)),
           ("fc1.w", (128, 1286)), ("fc1.b", (128,)),
           ("fc2.w", (8, 128)), ("fc2.b", (8,))]
 N_PARAMS = int(sum(np.prod(s) for _, s in SHAPES))
+MOTION_SCALE = 0.02                          # motion input = log(M) / MOTION_SCALE
+OUT_SCALE = np.array([0.01] * 7 + [1.0])     # increment = OUT_SCALE * y
+
+
+def _inverse34(T):
+    T = np.asarray(T, np.float64).reshape(3, 4)
+    R = T[:, :3].T
+    return np.hstack([R, (-R @ T[:, 3])[:, None]])
+
+
+def motion_input(M):
+    """Network motion input from the last inter-frame motion M (3x4)."""
+    import oracle
+    return oracle.se3_log(M) / MOTION_SCALE
+
+
+def motion_feature(Tw_prev, Tw_prevprev):
+    """Motion input from the two previous world -> camera poses (zeros when
+    either is missing): log(T_{k-1} T_{k-2}^-1) / MOTION_SCALE."""
+    import oracle
+    if Tw_prev is None or Tw_prevprev is None:
+        return np.zeros(6)
+    return motion_input(oracle.se3_mul(Tw_prev, _inverse34(Tw_prevprev)))
+
+
+def apply_output(T_init, ab_init, y):
+    """Start state proposed by output y: (T_init exp(delta[0:6]),
+    (a + delta[6], b + delta[7])) with delta = OUT_SCALE * y."""
+    import oracle
+    d = np.asarray(y, np.float64).reshape(8) * OUT_SCALE
+    T = oracle.se3_mul(T_init, oracle.se3_exp(d[:6]))
+    return T, (float(ab_init[0]) + d[6], float(ab_init[1]) + d[7])
 
 
 def unflatten(flat):

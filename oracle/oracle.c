@@ -476,6 +476,14 @@ static int cholesky_solve8(const double A[64], const double g[8], double delta[8
     return 1;
 }
 
+static int sums_are_finite(const double Hm[64], const double g[8], double E)
+{
+    int ok = isfinite(E);
+    for (int i = 0; i < 64; ++i) ok = ok && isfinite(Hm[i]);
+    for (int i = 0; i < 8; ++i) ok = ok && isfinite(g[i]);
+    return ok;
+}
+
 static void trace_pass(orc_result* out, double* tc, int* ti, double* ts, int max_trace,
                        double cost, int level, int accepted, int candidate, double step)
 {
@@ -537,6 +545,22 @@ void orc_track2(const double* cur, int W0, int H0, orc_cam K0, const double* x_r
     }
     memset(out, 0, sizeof(*out));
     out->cost = NAN;
+    /* Reading (failure detection): a start that is not finite (or whose
+     * rotation Gram-Schmidt cannot orthonormalise) is not solved;
+     * a pass whose sums are not finite is unusable (like one with too few
+     * samples) and a candidate state that is not finite ends the level; each
+     * sets the DIVERGED bit. */
+    {
+        int finite_start = isfinite(a) && isfinite(b);
+        for (int i = 0; i < 12; ++i) finite_start = finite_start && isfinite(T[i]);
+        if (!finite_start) {
+            out->status |= ORC_DIVERGED;
+            memcpy(out->T, T, sizeof(T));
+            out->a = a;
+            out->b = b;
+            return;
+        }
+    }
     double Hm[64], g[8], E;
     int n;
     int pdx[121], pdy[121];
@@ -549,11 +573,12 @@ void orc_track2(const double* cur, int W0, int H0, orc_cam K0, const double* x_r
         const double* Jl = (cfg->ic && Jic) ? Jic + (size_t)l * N * K * 6 : NULL;
         orc_linearize2(img, Ws[l], Hs[l], K0, l, x_r, I0l, vl, Jl, N, cfg->pattern, T, a, b,
                        cfg->huber_k, cfg->zmin, Hm, g, &E, &n, NULL, NULL, NULL, NULL);
-        int enough = n >= cfg->min_valid && n > 0;
+        int sums_finite = sums_are_finite(Hm, g, E);
+        int enough = n >= cfg->min_valid && n > 0 && sums_finite;
         trace_pass(out, trace_cost, trace_info, trace_step, max_trace, enough ? E / n : INFINITY,
                    l, 0, 0, 0.0);
         if (!enough) {
-            out->status |= ORC_TOO_FEW_POINTS;
+            out->status |= sums_finite ? ORC_TOO_FEW_POINTS : ORC_DIVERGED;
             continue;
         }
         double cost = E / n;
@@ -582,6 +607,12 @@ void orc_track2(const double* cur, int W0, int H0, orc_cam K0, const double* x_r
             orc_se3_exp(delta, dT);
             orc_se3_mul(T, dT, Tn);
             double an = a + delta[6], bn = b + delta[7];
+            int cand_finite = isfinite(an) && isfinite(bn);
+            for (int d = 0; d < 12; ++d) cand_finite = cand_finite && isfinite(Tn[d]);
+            if (!cand_finite) {
+                out->status |= ORC_DIVERGED;
+                break;
+            }
             double Hn[64], gn[8], En;
             int nn;
             orc_linearize2(img, Ws[l], Hs[l], K0, l, x_r, I0l, vl, Jl, N, cfg->pattern, Tn, an,
@@ -589,7 +620,9 @@ void orc_track2(const double* cur, int W0, int H0, orc_cam K0, const double* x_r
             ++it;
             double m = 0;
             for (int d = 0; d < 6; ++d) m = fmax(m, fabs(delta[d]));
-            double cn = (nn >= cfg->min_valid && nn > 0) ? En / nn : INFINITY;
+            int nfin = sums_are_finite(Hn, gn, En);
+            if (!nfin) out->status |= ORC_DIVERGED;
+            double cn = (nn >= cfg->min_valid && nn > 0 && nfin) ? En / nn : INFINITY;
             int accepted = cn < cost || (cn < INFINITY && m < cfg->accept_step);
             trace_pass(out, trace_cost, trace_info, trace_step, max_trace, cn, l, accepted, 1, m);
             int flat = !accepted && cn - cost <= cfg->eps_cost * cost;

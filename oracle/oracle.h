@@ -56,10 +56,10 @@ typedef struct {
     int iters_total;
     int iters[8];
     int passes;
-    int status; /* bit 0 too few points, bit 1 not positive definite */
+    int status; /* bit 0 too few points, bit 1 not positive definite, bit 2 diverged */
 } orc_result;
 
-enum { ORC_TOO_FEW_POINTS = 1, ORC_NOT_PD = 2 };
+enum { ORC_TOO_FEW_POINTS = 1, ORC_NOT_PD = 2, ORC_DIVERGED = 4 };
 
 /* the 8-pixel sparse pattern, offsets in level pixels */
 extern const int orc_pattern_dx[8];

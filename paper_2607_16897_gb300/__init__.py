@@ -6,8 +6,11 @@ streams (``torch.cuda.current_stream().cuda_stream``).  The functions
 ``glt_*`` are the C entry points of ``include/glt.h`` under the same names;
 ``Tracker`` and ``Batch`` wrap them for numpy / torch callers.
 
-Importing this package needs the built library (``build.build()``); there is
-no fallback of any kind.
+The library is loaded on first use (a ``glt_*`` attribute, a wrapper object,
+or ``load()``); if ``libglt.so`` has not been built that first use raises
+ImportError.  There is no fallback of any kind.  The pure host modules of the
+package (``tween``, ``proposal``'s feature and training helpers) import
+without the library.
 """
 from __future__ import annotations
 
@@ -28,6 +31,7 @@ GLT_ERR_UNSUPPORTED = -5
 GLT_ERR_IO = -6
 GLT_TRACK_TOO_FEW_POINTS = 1
 GLT_TRACK_NOT_PD = 2
+GLT_TRACK_DIVERGED = 4
 GLT_REF, GLT_CUR = 0, 1
 GLT_FP32, GLT_MIXED = 0, 1
 GLT_FORWARD, GLT_IC = 0, 1
@@ -96,6 +100,7 @@ SIGNATURES = {
     "glt_track_image": (_i, [_vp, _vp, _i, _i, _P(_d), _P(_d), _P(glt_result), _vp]),
     "glt_debug_linearize": (_i, [_vp, _i, _P(_d), _d, _d, _P(_d), _P(_d), _P(_d), _P(_i),
                                  _P(ctypes.c_float), _vp]),
+    "glt_debug_rcp": (_i, [_vp, _vp, _i, _vp]),
     "glt_get_pyramid": (_i, [_vp, _i, _i, _P(ctypes.c_uint8), _vp]),
     "glt_get_trace": (_i, [_vp, _P(_d), _P(_i), _i, _P(_i), _vp]),
     "glt_state_predict": (_i, [_P(glt_state), _P(_d), _P(_d)]),
@@ -128,7 +133,7 @@ SIGNATURES = {
 }
 
 
-def _load():
+def _open():
     if not os.path.exists(LIB_PATH):
         raise ImportError(
             f"{LIB_PATH} is not built; run paper_2607_16897_gb300.build.build() "
@@ -141,8 +146,33 @@ def _load():
     return lib
 
 
-_lib = _load()
-globals().update({name: getattr(_lib, name) for name in SIGNATURES})
+_handle = None
+
+
+def load():
+    """The loaded library (opened on the first call; ImportError if it is not
+    built)."""
+    global _handle
+    if _handle is None:
+        _handle = _open()
+    return _handle
+
+
+class _Lazy:
+    """Forwards attribute access to the library, opening it on first use."""
+
+    def __getattr__(self, name):
+        return getattr(load(), name)
+
+
+_lib = _Lazy()
+
+
+def __getattr__(name):
+    # module attributes glt_* are the C entry points (PEP 562)
+    if name in SIGNATURES:
+        return getattr(load(), name)
+    raise AttributeError(f"module {__name__!r} has no attribute {name!r}")
 
 
 class GltError(RuntimeError):

@@ -164,11 +164,15 @@ const char* glt_status_string(int code)
     case GLT_ERR_CAPACITY: return "capacity exceeded";
     case GLT_ERR_UNSUPPORTED: return "unsupported";
     case GLT_ERR_IO: return "file error";
-    case GLT_TRACK_TOO_FEW_POINTS: return "too few points";
-    case GLT_TRACK_NOT_PD: return "not positive definite";
-    case GLT_TRACK_TOO_FEW_POINTS | GLT_TRACK_NOT_PD: return "too few points|not positive definite";
-    default: return "unknown";
+    default: break;
     }
+    // status bits: every combination of the three per-frame outcomes
+    static const char* const kBits[8] = {
+        "ok", "too few points", "not positive definite", "too few points|not positive definite",
+        "diverged", "too few points|diverged", "not positive definite|diverged",
+        "too few points|not positive definite|diverged"};
+    if (code > 0 && code < 8) return kBits[code];
+    return "unknown";
 }
 
 const char* glt_last_error(void) { return g_err.c_str(); }

@@ -544,8 +544,11 @@ __device__ __forceinline__ void block_reduce(float (&acc)[kAccPad], float (*red)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double rcp_d(double d)
 {
-    // FP32 seed built from the bit pattern (no F2F conversions on the FP64
-    // pipe), then one Newton step in FP64: relative error < 1e-13.  Only for
+    // Reciprocal by one Newton-Raphson iteration for f(r) = 1/r - d,
+    // r' = r + r (1 - d r), from an FP32 seed: the seed is rcp.approx.ftz.f32
+    // of d rounded to FP32 through its bit pattern (no F2F conversions on the
+    // FP64 pipe), relative error e0 <= 2^-22, and the iteration squares it
+    // (e1 = e0^2 plus FP64 rounding): relative error < 1e-13.  Only for
     // 2^-100 <= |d| < 2^100 (exponent tested as an integer), where the
     // exponent fits FP32; zero, infinities, NaN and the rest divide.
     const int hi = __double2hiint(d);
@@ -570,6 +573,9 @@ __device__ __forceinline__ long long abs_bits(double x)
 {
     return __double_as_longlong(x) & 0x7fffffffffffffffll;
 }
+
+// Bits of +infinity: x is finite iff abs_bits(x) < kInfBits.
+constexpr long long kInfBits = 0x7ff0000000000000ll;
 
 // Pass parameters for state (T, a, b) on `level` (single thread).
 __device__ __host__ inline void make_pass_params(const double* T, double a, double b, int level,
@@ -651,6 +657,9 @@ __device__ inline void solver_init(const StreamDesc& D, const double* init, Solv
     S.a = init[12];
     S.b = init[13];
     S.status = 0;
+    bool finite_start = true;
+    for (int i = 0; i < 12; ++i) finite_start &= abs_bits(S.T[i]) < kInfBits;
+    finite_start &= abs_bits(S.a) < kInfBits && abs_bits(S.b) < kInfBits;
     S.passes = 0;
     S.it = 0;
     S.n = 0;
@@ -663,6 +672,12 @@ __device__ inline void solver_init(const StreamDesc& D, const double* init, Solv
     for (int l = 0; l < kMaxLevels; ++l) S.iters[l] = 0;
     int l = D.L - 1;
     while (l >= 0 && D.max_iters[l] <= 0) --l;
+    if (!finite_start) {
+        // a start that is not finite (or whose rotation is degenerate) is
+        // not solved: the result is the start, flagged
+        S.status |= GLT_TRACK_DIVERGED;
+        l = -1;
+    }
     S.level = l;
     S.phase = PH_START;
     if (l < 0) {
@@ -684,17 +699,22 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
     const double E = tot[kIdxE];
     const double nd = tot[kIdxN];           // exact integer count
     const int n = (int)nd;
-    const bool enough = n >= D.min_valid && n > 0;
+    // sums that are not finite (an FP32 overflow) make the pass unusable
+    bool sums_finite = abs_bits(E) < kInfBits;
+#pragma unroll
+    for (int i = 0; i < kIdxE; ++i) sums_finite &= abs_bits(tot[i]) < kInfBits;
+    const bool enough = n >= D.min_valid && n > 0 && sums_finite;
+    int status = S.status;
+    if (!sums_finite) status |= GLT_TRACK_DIVERGED;
     const int level = S.level;
     const int phase = S.phase;
     int it = S.it;
     double lambda = S.lambda;
-    int status = S.status;
     const long long step_bits = S.maxstep_bits;
     bool load_normal = false, accept = false, finish = false, candidate = false;
     if (phase == PH_START) {
         if (!enough) {
-            status |= GLT_TRACK_TOO_FEW_POINTS;
+            if (sums_finite) status |= GLT_TRACK_TOO_FEW_POINTS;
         } else {
             load_normal = true;
             lambda = D.lambda0;
@@ -877,18 +897,29 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
             const double e0 = __shfl_sync(full, E, ec);
             const double e1 = __shfl_sync(full, E, 4 + ec);
             const double e2 = __shfl_sync(full, E, 8 + ec);
-            if (lane < 12) {
-                const double* Tr = S.T + 4 * er;
-                S.Tc[lane] = fma(Tr[0], e0, fma(Tr[1], e1, fma(Tr[2], e2, rot ? 0.0 : Tr[3])));
+            const double tc = lane < 12 ? fma(S.T[4 * er], e0, fma(S.T[4 * er + 1], e1,
+                                                  fma(S.T[4 * er + 2], e2, rot ? 0.0 : S.T[4 * er + 3])))
+                                        : 0.0;
+            const double ac = S.a + dl[6], bc = S.b + dl[7];
+            const bool cand_finite = __all_sync(full, abs_bits(tc) < kInfBits) &&
+                                     abs_bits(ac) < kInfBits && abs_bits(bc) < kInfBits;
+            if (!cand_finite) {
+                // the solve produced a state that is not finite: keep the
+                // accepted one and end the level
+                if (lane == 0) S.status |= GLT_TRACK_DIVERGED;
+                finish = true;
+                next_level = true;
+            } else {
+                if (lane < 12) S.Tc[lane] = tc;
+                if (lane == 0) {
+                    S.ac = ac;
+                    S.bc = bc;
+                    S.maxstep_bits = mbits;
+                    S.phase = PH_CAND;
+                }
+                __syncwarp();
+                make_pass_params_warp(S.Tc, ac, bc, level, P, lane);
             }
-            if (lane == 0) {
-                S.ac = S.a + dl[6];
-                S.bc = S.b + dl[7];
-                S.maxstep_bits = mbits;
-                S.phase = PH_CAND;
-            }
-            __syncwarp();
-            make_pass_params_warp(S.Tc, S.a + dl[6], S.b + dl[7], level, P, lane);
         }
     }
     if (finish && lane == 0) {

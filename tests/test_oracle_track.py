@@ -126,6 +126,26 @@ def test_too_few_points(orc, syn):
     assert res["iters_total"] == 0 and res["passes"] == 3
 
 
+def test_non_finite_start_and_sums_diverge(orc, syn):
+    """Failure detection: a start that is not finite is returned unsolved; a
+    gain e^a beyond the FP64 range makes every level start's sums NaN, so no
+    level runs; both set DIVERGED and nothing else."""
+    p = syn.pair_c1(0, sigma=2.0)
+    tr = tracker_for(orc, p)
+    T0 = I34.copy()
+    T0[1, 3] = np.nan
+    res = tr.track_frame(T0)
+    assert res["status"] == orc.DIVERGED and res["passes"] == 0
+    res = tr.track_frame(np.zeros((3, 4)))          # rotation with no direction
+    assert res["status"] == orc.DIVERGED and res["passes"] == 0
+    res = tr.track_frame(I34, (1000.0, 0.0))
+    assert res["status"] == orc.DIVERGED and res["passes"] == 3
+    np.testing.assert_array_equal(res["T"], I34)
+    assert res["a"] == 1000.0 and res["iters_total"] == 0
+    # an ordinary start after them is untouched by the rule
+    assert tr.track_frame(I34)["status"] == 0
+
+
 def test_singular_hessian_is_not_pd(orc, syn):
     p = syn.pair_c1(0, sigma=2.0)
     p.cur = np.full_like(p.cur, 100)   # no texture: the pose block of H is zero
