@@ -2,11 +2,10 @@
 // buffers that allocates nothing.
 //
 // Who needs it: callers that are not allowed to allocate device memory at
-// the point where they want a linearisation -- code recorded into a CUDA
-// graph by stream capture (where cudaMalloc is not permitted), real-time
-// loops that fix their memory budget at start-up, and plugins whose host
-// framework owns every device allocation.  glt_create allocates, so such a
-// caller cannot build a tracker there; this entry point needs none.
+// the point where they want a linearisation -- real-time loops that fix their
+// memory budget at start-up, and plugins whose host framework owns every
+// device allocation.  glt_create allocates, so such a caller cannot build a
+// tracker there; this entry point needs none.
 //
 // The only memory it uses besides the caller's inputs and outputs is a
 // file-scope scratch array (block partial sums and the last-block ticket),
@@ -161,7 +160,8 @@ __global__ void __launch_bounds__(kNaThreads)
     }
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device and kept
+// (an address that a reset of the device's primary context would invalidate).
 constexpr int kNaMaxDevices = 64;
 std::mutex g_na_mutex;
 float* g_na_ptr[kNaMaxDevices] = {};
