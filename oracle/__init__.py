@@ -68,7 +68,7 @@ class _Config(ctypes.Structure):
                 ("eps_cost", ctypes.c_double),
                 ("accept_step", ctypes.c_double), ("min_valid", ctypes.c_int),
                 ("zmin", ctypes.c_double), ("ic", ctypes.c_int), ("pattern", ctypes.c_int),
-                ("affine", ctypes.c_int)]
+                ("affine", ctypes.c_int), ("hcache", ctypes.c_int)]
 
 
 class _Result(ctypes.Structure):
@@ -101,6 +101,8 @@ def _load():
             lib.orc_linearize2.argtypes = [dp, i, i, _Cam, i, dp, dp, u8p, dp, i, i, dp, d, d, d,
                                            d, dp, dp, dp, ip, dp, dp, dp, u8p]
             lib.orc_ref_patch2.argtypes = [dp, i, i, i, fp, i, i, dp, u8p]
+            lib.orc_ic_hessian.argtypes = [dp, u8p, i, i, dp]
+            lib.orc_ic_hessian.restype = None
             lib.orc_pattern.argtypes = [i, ip, ip]
             lib.orc_pattern.restype = i
             lib.orc_ref_patch2.restype = None
@@ -239,6 +241,17 @@ def ic_jacobian(ref_l, K0, level, x_r, uvd, valid_l, pattern: int = 0):
     return out.reshape(N, K, 6)
 
 
+def ic_hessian(Jic_l, valid_l) -> np.ndarray:
+    """Per-reference Hessian [6, 6] of one level from its IC cache [N, K, 6]."""
+    J = _f64(Jic_l)
+    N, K = J.shape[0], J.shape[1]
+    valid_l = np.ascontiguousarray(valid_l, np.uint8)
+    H6 = np.zeros(36)
+    _load().orc_ic_hessian(_p(J, ctypes.c_double), _p(valid_l, ctypes.c_uint8), N, K,
+                           _p(H6, ctypes.c_double))
+    return H6.reshape(6, 6)
+
+
 def linearize(img_l, K0, level, x_r, I0_l, valid_l, T, a, b, huber_k=9.0, zmin=1e-3,
               per_sample=True, Jic=None, pattern=0):
     img = _f64(img_l)
@@ -280,7 +293,8 @@ def linearize(img_l, K0, level, x_r, I0_l, valid_l, T, a, b, huber_k=9.0, zmin=1
 # --------------------------------------------------------------------------
 DEFAULT_CONFIG = dict(levels=4, max_iters=[10] * 8, huber_k=9.0, lambda0=1e-4, lambda_up=4.0,
                       lambda_down=0.5, eps_step=1e-6, eps_step_coarse=3e-4, eps_cost=0.0, accept_step=1e-3,
-                      min_valid=16, zmin=1e-3, jacobian="forward", pattern=0, affine=True)
+                      min_valid=16, zmin=1e-3, jacobian="forward", pattern=0, affine=True,
+                      hessian="pass")
 
 
 def make_config(**kw) -> dict:
@@ -309,6 +323,7 @@ def _cconfig(c: dict) -> _Config:
     cc.ic = {"forward": 0, "ic": 1}[c["jacobian"]]
     cc.pattern = int(c["pattern"])
     cc.affine = 1 if c["affine"] else 0
+    cc.hcache = {"pass": 0, "cached": 1}[c["hessian"]]
     return cc
 
 
@@ -386,11 +401,25 @@ class OracleTracker:
             self.Jic = np.stack([ic_jacobian(self.pyr[self.REF][l], self.K, l, self.x_r, uvd,
                                              self.valid[l], pat) for l in range(self.L)])
 
+    def cached_hessian(self, level):
+        """The per-reference Hessian [6, 6] of a level (jacobian "ic")."""
+        return ic_hessian(self.Jic[level], self.valid[level])
+
     def debug_linearize(self, level, T, a, b, per_sample=True):
-        return linearize(self.pyr[self.CUR][level], self.K, level, self.x_r, self.I0[level],
-                         self.valid[level], T, a, b, self.cfg["huber_k"], self.cfg["zmin"],
-                         per_sample, Jic=None if self.Jic is None else self.Jic[level],
-                         pattern=self.cfg["pattern"])
+        """The normal equations a pass of the solve uses: with hessian
+        "cached", H is e^{2a} times the per-reference Hessian (pose block; the
+        affine rows, unused, are zero) and g keeps its pose part."""
+        out = linearize(self.pyr[self.CUR][level], self.K, level, self.x_r, self.I0[level],
+                        self.valid[level], T, a, b, self.cfg["huber_k"], self.cfg["zmin"],
+                        per_sample, Jic=None if self.Jic is None else self.Jic[level],
+                        pattern=self.cfg["pattern"])
+        if self.cfg["hessian"] == "cached":
+            Hm = np.zeros((8, 8))
+            Hm[:6, :6] = np.exp(2.0 * a) * self.cached_hessian(level)
+            out["H"] = Hm
+            out["g"] = out["g"].copy()
+            out["g"][6:] = 0.0
+        return out
 
     def track_frame(self, T_init, ab_init=(0.0, 0.0)) -> dict:
         return track(self.pyr[self.CUR], self.K, self.x_r, self.I0, self.valid, self.cfg,

@@ -333,6 +333,19 @@ void orc_ic_jacobian(const double* ref, int W, int H, orc_cam K0, int level, con
     }
 }
 
+void orc_ic_hessian(const double* Jic, const uint8_t* valid_ref, int N, int K, double H6[36])
+{
+    memset(H6, 0, 36 * sizeof(double));
+    for (int i = 0; i < N; ++i) {
+        if (!valid_ref[i]) continue;
+        for (int k = 0; k < K; ++k) {
+            const double* J = Jic + ((size_t)K * i + k) * 6;
+            for (int p = 0; p < 6; ++p)
+                for (int q = 0; q < 6; ++q) H6[6 * p + q] += J[p] * J[q];
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------
  * Linearisation (Sec. IV-A Eqs. 1-5; forward form of Sec. IV-B: J uses the
  * current image's gradient at the warped location; with Jic, the
@@ -476,6 +489,20 @@ static int cholesky_solve8(const double A[64], const double g[8], double delta[8
     return 1;
 }
 
+/* Sec. IV-B / IV-C: the pose block of the pass's normal matrix replaced by
+ * the per-reference Hessian H6 of the level, scaled by e^{2a} because the
+ * rows the pass uses are e^a J_ic; the affine rows and columns are cleared
+ * (the affine pair is held fixed in this form, so the solve never uses them). */
+static void use_cached_hessian(double Hm[64], double g[8], const double H6[36], double a)
+{
+    double s = exp(2.0 * a);
+    memset(Hm, 0, 64 * sizeof(double));
+    for (int p = 0; p < 6; ++p)
+        for (int q = 0; q < 6; ++q) Hm[8 * p + q] = s * H6[6 * p + q];
+    g[6] = 0.0;
+    g[7] = 0.0;
+}
+
 static int sums_are_finite(const double Hm[64], const double g[8], double E)
 {
     int ok = isfinite(E);
@@ -565,14 +592,18 @@ void orc_track2(const double* cur, int W0, int H0, orc_cam K0, const double* x_r
     int n;
     int pdx[121], pdy[121];
     const int K = orc_pattern(cfg->pattern, pdx, pdy);
+    const int hcache = cfg->hcache && cfg->ic && Jic && !cfg->affine;
     for (int l = L - 1; l >= 0; --l) {
         if (cfg->max_iters[l] <= 0) continue;
         const double* img = cur + off[l];
         const double* I0l = I0 + (size_t)l * N * K;
         const uint8_t* vl = valid + (size_t)l * N;
         const double* Jl = (cfg->ic && Jic) ? Jic + (size_t)l * N * K * 6 : NULL;
+        double H6[36];
+        if (hcache) orc_ic_hessian(Jl, vl, N, K, H6);
         orc_linearize2(img, Ws[l], Hs[l], K0, l, x_r, I0l, vl, Jl, N, cfg->pattern, T, a, b,
                        cfg->huber_k, cfg->zmin, Hm, g, &E, &n, NULL, NULL, NULL, NULL);
+        if (hcache) use_cached_hessian(Hm, g, H6, a);
         int sums_finite = sums_are_finite(Hm, g, E);
         int enough = n >= cfg->min_valid && n > 0 && sums_finite;
         trace_pass(out, trace_cost, trace_info, trace_step, max_trace, enough ? E / n : INFINITY,
@@ -617,6 +648,7 @@ void orc_track2(const double* cur, int W0, int H0, orc_cam K0, const double* x_r
             int nn;
             orc_linearize2(img, Ws[l], Hs[l], K0, l, x_r, I0l, vl, Jl, N, cfg->pattern, Tn, an,
                            bn, cfg->huber_k, cfg->zmin, Hn, gn, &En, &nn, NULL, NULL, NULL, NULL);
+            if (hcache) use_cached_hessian(Hn, gn, H6, an);
             ++it;
             double m = 0;
             for (int d = 0; d < 6; ++d) m = fmax(m, fabs(delta[d]));

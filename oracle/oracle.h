@@ -47,6 +47,9 @@ typedef struct {
     int ic; /* 0: forward Jacobian (current image), 1: inverse-compositional (reference side) */
     int pattern; /* 0: the 8-pixel sparse pattern; odd p (3..11): the paper's p x p patch */
     int affine;  /* 1: estimate (a, b); 0: keep them at their initial values (the paper's form) */
+    int hcache;  /* 1 (with ic, affine 0): the pose block of the normal matrix is the
+                    per-reference Hessian of orc_ic_hessian times e^{2a}, not the per-pass
+                    sum (Sec. IV-B: H precomputed once per reference update) */
 } orc_config;
 
 typedef struct {
@@ -111,6 +114,13 @@ void orc_linearize(const double* img, int W, int H, orc_cam K0, int level, const
 void orc_ic_jacobian(const double* ref, int W, int H, orc_cam K0, int level, const double* x_r,
                      const float* uvd, const uint8_t* valid_ref, int N, int pattern, double* Jic);
 
+/* Per-reference Hessian of one level (Sec. IV-B: with the IC rows fixed, H =
+ * J^T J is constant while the reference is; Sec. IV-C "Precompute IC": the
+ * per-point contributions H_i reduced over the points into one per-level H):
+ * H6[36] (row-major 6x6) = sum over the points with valid_ref[i] of
+ * sum_k J_ic(i,k)^T J_ic(i,k), from the [N][K][6] cache of orc_ic_jacobian. */
+void orc_ic_hessian(const double* Jic, const uint8_t* valid_ref, int N, int K, double H6[36]);
+
 /* As orc_linearize for any pattern (I0[N*K], per-sample outputs with K
  * samples per point); with Jic non-NULL the pose columns of each Jacobian row
  * are e^a J_ic (the template approximation of the current-side Jacobian: the
@@ -134,7 +144,10 @@ void orc_track(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
                double* trace_cost, int* trace_info, double* trace_step, int max_trace);
 /* As orc_track with cfg->pattern (I0 [L][N][K]) and cfg->affine; with cfg->ic
  * set, Jic is the [L][N*K*6] inverse-compositional cache of orc_ic_jacobian,
- * used by every linearisation of the solve. */
+ * used by every linearisation of the solve; with cfg->hcache also set (and
+ * cfg->affine 0) every pass solves with the per-reference Hessian of
+ * orc_ic_hessian scaled by e^{2a} (the rows are e^a J_ic) instead of the pass's
+ * own sum, while g, the energy and the sample count stay per pass. */
 void orc_track2(const double* cur, int W0, int H0, orc_cam K0, const double* x_r,
                 const double* I0, const uint8_t* valid, const double* Jic, int N,
                 const orc_config* cfg, const double T_init[12], double a0, double b0,
