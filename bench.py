@@ -93,6 +93,9 @@ def parse():
     ap.add_argument("--jacobian", default=None, choices=["forward", "ic"],
                     help="Jacobian form: forward (current image, default) or ic "
                          "(inverse compositional, reference-side rows cached per reference)")
+    ap.add_argument("--hessian", default=None, choices=["pass", "cached"],
+                    help="paper-configuration workloads (c2p / c2e): the normal matrix summed in "
+                         "every pass, or cached per reference and level as in the paper (default)")
     ap.add_argument("--shape", default=None,
                     help="batched forms: fixed tile shape 'cluster,threads' instead of the "
                          "autotuner's pick (profiling runs, where the tuner's timings are distorted)")
@@ -505,8 +508,7 @@ def run_reference(args):
         pool.close()
         pool.join()
         for w in wls:
-            if args.jacobian:
-                w.jacobian = args.jacobian
+            apply_overrides(w, args)
         pw = None
         if args.workload == "c5":
             from oracle import nn as onn
@@ -525,8 +527,7 @@ def run_reference(args):
         jac = wls[0].jacobian
     else:
         wl = single_workload(args.workload, rank)
-        if args.jacobian:
-            wl.jacobian = args.jacobian
+        apply_overrides(wl, args)
         n = min(len(wl.frames) - 1, W + K)
         t, _, _ = oracle_track_sequence(wl, n)
         frames = n
@@ -562,8 +563,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     wl = single_workload(args.workload, rank)   # replicas: one independent stream per GPU
-    if args.jacobian:
-        wl.jacobian = args.jacobian
+    apply_overrides(wl, args)
     precision = args.precision or ("mixed" if args.workload == "c4" else "fp32")
     Wd, Hd, L, N = wl.cam.W, wl.cam.H, wl.L, wl.N
     stream = torch.cuda.Stream()
@@ -715,7 +715,8 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f16 storage / f32 math" if precision == "mixed" else "f32",
                 "data": "synthetic",
-                "config": {"workload": wl.name, "jacobian": wl.jacobian, "global_batch": world,
+                "config": {"workload": wl.name, "jacobian": wl.jacobian,
+                           "hessian": wl.solver.get("hessian", "pass"), "global_batch": world,
                            "streams_per_gpu": 1,
                            "parallelism": f"replicas x{world}",
                            "l2": "flushed between steps (256 MB write, outside the step events)",
@@ -909,10 +910,22 @@ def linearization_error(glt, wl, rec_entry, precision):
     return out
 
 
-# the paper's configuration: p x p patches, IC Jacobians, plain Gauss-Newton
-# with 10 iterations on each of 6 levels, no affine brightness, no Huber weights
+# the paper's configuration: p x p patches, IC Jacobians with the Hessian
+# cached per reference and level, plain Gauss-Newton with 10 iterations on each
+# of 6 levels, no affine brightness, no Huber weights
 PAPER_SOLVER = dict(affine=False, lambda0=0.0, accept_step=1e30, eps_step=0.0,
-                    eps_step_coarse=0.0, huber_k=1e30)
+                    eps_step_coarse=0.0, huber_k=1e30, hessian="cached")
+
+
+def apply_overrides(wl, args):
+    """--jacobian / --hessian on a workload (the cached Hessian exists only
+    with the inverse-compositional rows)."""
+    if args.jacobian:
+        wl.jacobian = args.jacobian
+    if getattr(args, "hessian", None) and "hessian" in wl.solver:
+        wl.solver["hessian"] = args.hessian
+    if wl.jacobian != "ic" and wl.solver.get("hessian") == "cached":
+        wl.solver["hessian"] = "pass"
 
 
 def single_workload(kind, rank=0):
@@ -920,14 +933,16 @@ def single_workload(kind, rank=0):
         return Workload(seed=stream_seed(kind, 0, rank), frames=300, N=2000, W=640, H=480, f=525.0, L=6,
                         exposure=False, solver=dict(PAPER_SOLVER, pattern=7), jacobian="ic",
                         max_cost=50.0,
-                        label="C2 in the paper's configuration (TUM-like, 7x7 patches, IC, "
-                              "6 levels, 10 GN iterations per level, no affine, no Huber)")
+                        label="C2 in the paper's configuration (TUM-like, 7x7 patches, IC rows "
+                              "and the Hessian cached per reference, 6 levels, 10 GN iterations "
+                              "per level, no affine, no Huber)")
     if kind == "c2e":
         return Workload(seed=stream_seed(kind, 0, rank), frames=300, N=2000, W=752, H=480, f=458.0, L=6,
                         exposure=False, solver=dict(PAPER_SOLVER, pattern=11), jacobian="ic",
                         max_cost=50.0,
                         label="752x480 in the paper's configuration (EuRoC-like, 11x11 patches, "
-                              "IC, 6 levels, 10 GN iterations per level, no affine, no Huber)")
+                              "IC rows and the Hessian cached per reference, 6 levels, 10 GN "
+                              "iterations per level, no affine, no Huber)")
     if kind == "c4":
         return Workload(seed=stream_seed(kind, 0, rank), frames=300, N=8000, W=1280, H=720, f=1050.0, L=5,
                         speed=1.0, ang=60.0, label="C4 single stream")
@@ -992,8 +1007,7 @@ def run_batch(args):
     pool.close()
     pool.join()
     for w in wls:
-        if args.jacobian:
-            w.jacobian = args.jacobian
+        apply_overrides(w, args)
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
     dist = None

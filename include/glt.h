@@ -76,6 +76,12 @@ extern "C" {
 #define GLT_FORWARD 0 /* current image's gradient at the warped location, every pass */
 #define GLT_IC 1      /* inverse compositional: reference-side rows cached per reference */
 
+/* Normal matrix of the solve (Sec. IV-B / IV-C) */
+#define GLT_HESSIAN_PASS 0   /* J^T W J summed again in every pass */
+#define GLT_HESSIAN_CACHED 1 /* the paper's cache: H = J^T J of the reference-side rows over
+                                the reference's usable points, once per reference and
+                                level; each pass reduces only g, E and n */
+
 typedef struct glt_tracker glt_tracker;
 typedef struct glt_batch glt_batch;
 typedef struct glt_nn glt_nn;
@@ -119,6 +125,21 @@ typedef struct glt_config {
                                    p x p needs precision GLT_FP32 and 256 (or 0) threads */
     int affine;                 /* 1: estimate (a, b); 0: keep the initial (a, b) (the
                                    paper estimates no brightness change) */
+    int hessian;                /* GLT_HESSIAN_PASS or GLT_HESSIAN_CACHED.  CACHED (Sec.
+                                   IV-B: with the rows on the reference side H = J^T J is
+                                   constant while the reference is, so it is precomputed
+                                   once per reference update; Sec. IV-C "Precompute IC":
+                                   per-point H_i reduced into one H per level):
+                                   glt_set_map_points also reduces H over the points usable
+                                   on each level of the reference and inverts it in FP64;
+                                   every pass then reduces only g = J^T W r, E and n (over
+                                   the points usable at the pass state) and steps by
+                                   delta = -(e^{2a} H)^-1 g (the rows are e^a times the
+                                   reference rows).  Points out of view stay in H, as in
+                                   the paper.  Needs jacobian GLT_IC, affine 0, lambda0 0
+                                   (plain Gauss-Newton), precision GLT_FP32 and 256 (or 0)
+                                   threads; an H that is not positive definite ends the
+                                   level with GLT_TRACK_NOT_PD */
 } glt_config;
 
 typedef struct glt_result {
@@ -137,11 +158,13 @@ typedef struct glt_result {
  * lambda0 1e-4 (x4 up, x0.5 down), eps_step 1e-6 (finest level),
  * eps_step_coarse 3e-4 (coarser levels), eps_cost 0 (off),
  * accept_step 1e-3, min_valid 16, zmin 1e-3, FP32, automatic cluster/threads,
- * max_points 4096, GLT_FORWARD, the 8-pixel pattern, affine estimated.
+ * max_points 4096, GLT_FORWARD, the 8-pixel pattern, affine estimated,
+ * GLT_HESSIAN_PASS.
  * The paper's configuration is levels 6, pattern 7 (or 11), affine 0,
- * jacobian GLT_IC, huber_k very large (no robust weights), lambda0 0,
- * accept_step very large and eps_step = eps_step_coarse = 0 (plain
- * Gauss-Newton with a fixed number of iterations per level). */
+ * jacobian GLT_IC, hessian GLT_HESSIAN_CACHED, huber_k very large (no robust
+ * weights), lambda0 0, accept_step very large and eps_step =
+ * eps_step_coarse = 0 (plain Gauss-Newton with a fixed number of iterations
+ * per level). */
 void glt_default_config(glt_config* cfg, int width, int height, double fx, double fy,
                         double cx, double cy);
 
@@ -222,7 +245,10 @@ int glt_track_image(glt_tracker* trk, const uint8_t* img, int pitch_bytes, int i
  * right-hand side b of Eq. 5 is -g), the Huber energy E and the number of
  * valid samples n, all written to host memory; if `res` is not NULL it gets
  * the N*K FP32 residuals, K samples of the pattern per point (8, or p*p),
- * NaN for samples of unused points.  Synchronous.
+ * NaN for samples of unused points.  With GLT_HESSIAN_CACHED these are the
+ * normal equations the solve uses: H is e^{2a} times the level's cached
+ * reference Hessian in its pose block (the affine rows and columns zero) and
+ * g keeps its pose part (g[6] = g[7] = 0).  Synchronous.
  * Uses a multi-block kernel with a single-pass last-block finish. */
 int glt_debug_linearize(glt_tracker* trk, int level, const double T[12], double a, double b,
                         double H[64], double g[8], double* E, int* n, float* res,
@@ -299,8 +325,9 @@ int glt_get_trace(glt_tracker* trk, double* cost, int* info, int max, int* count
  * ------------------------------------------------------------------------- */
 
 /* Builds a batch over `trackers[0..S-1]` (all created on the current device,
- * all with the same precision).  The batch references, but does not own, the
- * trackers; they must outlive it.  Errors: INVALID_ARG. */
+ * all with the same precision, and all or none with GLT_HESSIAN_CACHED).  The
+ * batch references, but does not own, the trackers; they must outlive it.
+ * Errors: INVALID_ARG. */
 int glt_batch_create(glt_tracker* const* trackers, int S, glt_batch** out);
 void glt_batch_destroy(glt_batch* batch);
 

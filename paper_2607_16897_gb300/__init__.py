@@ -35,6 +35,7 @@ GLT_TRACK_DIVERGED = 4
 GLT_REF, GLT_CUR = 0, 1
 GLT_FP32, GLT_MIXED = 0, 1
 GLT_FORWARD, GLT_IC = 0, 1
+GLT_HESSIAN_PASS, GLT_HESSIAN_CACHED = 0, 1
 MAX_LEVELS = 8
 GLT_NN_PARAMS = 189064
 GLT_NN_INPUT = 1200
@@ -54,7 +55,7 @@ class glt_config(ctypes.Structure):
                 ("min_valid", ctypes.c_int),
                 ("zmin", ctypes.c_double), ("precision", ctypes.c_int), ("cluster", ctypes.c_int),
                 ("threads", ctypes.c_int), ("jacobian", ctypes.c_int), ("pattern", ctypes.c_int),
-                ("affine", ctypes.c_int)]
+                ("affine", ctypes.c_int), ("hessian", ctypes.c_int)]
 
 
 class glt_result(ctypes.Structure):
@@ -216,6 +217,8 @@ def default_config(width, height, K, **kw) -> glt_config:
             c.precision = {"fp32": GLT_FP32, "mixed": GLT_MIXED}[v]
         elif k == "jacobian" and isinstance(v, str):
             c.jacobian = {"forward": GLT_FORWARD, "ic": GLT_IC}[v]
+        elif k == "hessian" and isinstance(v, str):
+            c.hessian = {"pass": GLT_HESSIAN_PASS, "cached": GLT_HESSIAN_CACHED}[v]
         else:
             if not hasattr(c, k):
                 raise KeyError(k)

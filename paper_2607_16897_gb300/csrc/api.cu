@@ -72,6 +72,7 @@ static void free_tracker(glt_tracker* t)
     cudaFree(t->dz);
     cudaFree(t->I0);
     cudaFree(t->G0);
+    cudaFree(t->Hc);
     cudaFree(t->desc_dev);
     cudaFree(t->desc_ptr_dev);
     cudaFree(t->user_dev);
@@ -129,6 +130,13 @@ static int check_config(const glt_config* c)
     if (c->pattern != 0 && c->threads != 0 && c->threads != 256)
         return invalid("p x p patches run with 256 threads per CTA");
     if (c->affine != 0 && c->affine != 1) return invalid("affine must be 0 or 1");
+    if (c->hessian != GLT_HESSIAN_PASS && c->hessian != GLT_HESSIAN_CACHED)
+        return invalid("hessian must be GLT_HESSIAN_PASS or GLT_HESSIAN_CACHED");
+    if (c->hessian == GLT_HESSIAN_CACHED &&
+        (c->jacobian != GLT_IC || c->affine != 0 || c->lambda0 != 0.0 || c->precision != GLT_FP32 ||
+         (c->threads != 0 && c->threads != 256)))
+        return invalid("GLT_HESSIAN_CACHED needs jacobian GLT_IC, affine 0, lambda0 0, "
+                       "precision GLT_FP32 and 256 (or 0) threads");
     return GLT_OK;
 }
 
@@ -262,6 +270,7 @@ int glt_create(const glt_config* cfg, glt_tracker** out)
     t->K = cfg->pattern == 0 ? 8 : cfg->pattern * cfg->pattern;
     ALLOC(dalloc(&t->I0, (size_t)t->L * t->Npad * t->K));
     if (cfg->jacobian == GLT_IC) ALLOC(dalloc(&t->G0, (size_t)t->L * t->Npad * t->K));
+    if (cfg->hessian == GLT_HESSIAN_CACHED) ALLOC(dalloc(&t->Hc, (size_t)t->L * 72));
     ALLOC(dalloc(&t->desc_dev, 1));
     ALLOC(dalloc(&t->desc_ptr_dev, 1));
     ALLOC(dalloc(&t->user_dev, 1));
@@ -308,6 +317,7 @@ int glt_create(const glt_config* cfg, glt_tracker** out)
     D.dz = t->dz;
     D.I0 = t->I0;
     D.G0 = t->G0;
+    D.Hc = t->Hc;
     D.pattern = cfg->pattern;
     D.K = t->K;
     D.affine = cfg->affine;
@@ -440,6 +450,7 @@ int glt_set_map_points(glt_tracker* t, const float* uvd, int n, int is_device, v
     t->desc_host.N = n;
     // the kernel also stores n into the device descriptor (no host upload)
     GLT_CHECK(launch_set_points(t, src, n, s), "map point kernel");
+    if (t->Hc) GLT_CHECK(launch_ic_hessian(t, s), "reference Hessian kernel");
     t->have_points = true;
     t->version++;
     // a new reference: the state's pose restarts at the reference (motion kept)
@@ -684,6 +695,21 @@ int glt_debug_linearize(glt_tracker* t, int level, const double T[12], double a,
     if (res)
         GLT_CHECK(cudaMemcpyAsync(res, t->lin_res, (size_t)t->N * t->K * sizeof(float), cudaMemcpyDeviceToHost, s),
                   "residual download");
+    if (t->Hc) {
+        // the cached-Hessian form: H of the level from the reference, the pass's g0 (no e^a)
+        double Hl[36];
+        GLT_CHECK(cudaMemcpyAsync(Hl, t->Hc + 72 * level, sizeof(Hl), cudaMemcpyDeviceToHost, s),
+                  "reference Hessian download");
+        GLT_CHECK(cudaStreamSynchronize(s), "linearize");
+        const double ea = std::exp(a);
+        std::memset(H, 0, 64 * sizeof(double));
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) H[8 * i + j] = ea * ea * Hl[6 * i + j];
+        for (int i = 0; i < 8; ++i) g[i] = i < 6 ? ea * t->h_lin[i] : 0.0;
+        *E = t->h_lin[kHcE];
+        *n = (int)t->h_lin[kHcN];
+        return GLT_OK;
+    }
     GLT_CHECK(cudaStreamSynchronize(s), "linearize");
     int idx = 0;
     for (int i = 0; i < 8; ++i)
@@ -762,6 +788,8 @@ int glt_batch_create(glt_tracker* const* trackers, int S, glt_batch** out)
         if (!trackers[i]) return invalid("NULL tracker in batch");
         if (trackers[i]->cfg.precision != prec) return invalid("all trackers of a batch need the same precision");
         if (trackers[i]->device != trackers[0]->device) return invalid("all trackers must be on one device");
+        if ((trackers[i]->Hc != nullptr) != (trackers[0]->Hc != nullptr))
+            return invalid("all or none of the trackers of a batch need GLT_HESSIAN_CACHED");
     }
     glt_batch* b = new glt_batch();
     b->S = S;
@@ -858,7 +886,7 @@ int glt_batch_create(glt_tracker* const* trackers, int S, glt_batch** out)
     b->variant = 0;
     for (int i = 0; i < S; ++i) {
         const int v = track_variant(trackers[i]->cfg);
-        if (v == 1 || v == 2) b->variant = v;
+        if (v == 1 || v == 2 || v == 4) b->variant = v;
         else if (v == 3 && b->variant == 0) b->variant = 3;
     }
     if (!track_shape_ok(b->cluster, b->threads, b->variant)) b->cluster = 1;

@@ -25,6 +25,10 @@ constexpr int kIdxE = 44;        // Huber energy
 constexpr int kIdxN = 45;        // valid sample count
 constexpr int kNumAcc = 46;
 constexpr int kAccPad = 48;      // padded for the 5-stage reduce-scatter
+// cached-Hessian form: g0 = sum w r J_ic (6), Huber energy, sample count
+constexpr int kHcAcc = 8;
+constexpr int kHcE = 6;
+constexpr int kHcN = 7;
 
 // 8-pixel sparse pattern (offsets du_k of Eq. 2), level pixels.
 __host__ __device__ constexpr int pat_dx(int k) { return k == 1 ? -2 : k == 2 ? 2 : k == 5 ? -1 : k == 6 ? 1 : k == 7 ? -1 : 0; }
@@ -64,6 +68,8 @@ struct StreamDesc {
     const float2* G0;      // GLT_IC: reference gradient (gx, gy) [L][Npad][K], else null
     int pattern, K;        // 0 and 8: the 8-pixel pattern; p and p*p: the p x p patch
     int affine;            // 0: (a, b) held at their initial values
+    const double* Hc;      // GLT_HESSIAN_CACHED: per level H (36) then H^-1 (36), row-major
+                           // 6x6 pose blocks of the reference rows; H^-1[0] NaN if H is not PD
     int max_iters[kMaxLevels];
     int min_valid;
     int max_trace;
@@ -219,6 +225,41 @@ __device__ __forceinline__ void accumulate_sample(const PointGeom& G, float I, f
     acc[kIdxN] += 1.0f;
 }
 
+// Cached-Hessian form (Sec. IV-B: with the rows on the reference side H is
+// fixed per reference and level; Sec. IV-C "Track": each point contributes
+// only its right-hand side b_i = -sum_k J_ik^T r_ik).  A sample adds its
+// Huber-weighted residual times the cached reference gradient to the point's
+// (sx, sy); the point then folds them into g0 = sum w r J_ic:
+// J_k = [Jt_k, x_r x Jt_k] with Jt_k = gx_k a0 + gy_k a1, so
+// sum_k w_k r_k J_k = [v, x_r x v] with v = sx a0 + sy a1.
+__device__ __forceinline__ void hc_sample(float I, float i0, float2 g0, float ea, float b, float k,
+                                          float& sx, float& sy, float* acc, float* res_out)
+{
+    const float r = fmaf(-ea, i0, I) - b;
+    const float ar = fabsf(r);
+    const float w = ar <= k ? 1.0f : k / ar;
+    const float rho = ar <= k ? 0.5f * r * r : k * (ar - 0.5f * k);
+    if (res_out) *res_out = r;
+    const float wr = w * r;
+    sx = fmaf(wr, g0.x, sx);
+    sy = fmaf(wr, g0.y, sy);
+    acc[kHcE] += rho;
+    acc[kHcN] += 1.0f;
+}
+
+__device__ __forceinline__ void hc_fold(const PointGeom& G, float sx, float sy, float* acc)
+{
+    const float v0 = fmaf(sx, G.a0[0], sy * G.a1[0]);
+    const float v1 = fmaf(sx, G.a0[1], sy * G.a1[1]);
+    const float v2 = fmaf(sx, G.a0[2], sy * G.a1[2]);
+    acc[0] += v0;
+    acc[1] += v1;
+    acc[2] += v2;
+    acc[3] += fmaf(G.xr[1], v2, -G.xr[2] * v1);
+    acc[4] += fmaf(G.xr[2], v0, -G.xr[0] * v2);
+    acc[5] += fmaf(G.xr[0], v1, -G.xr[1] * v0);
+}
+
 // Geometric rows at the reference point (identity pose), for the
 // inverse-compositional form.
 __device__ __forceinline__ void ic_geometry(const StreamDesc& D, const PassParams& P, int p, PointGeom& G)
@@ -239,10 +280,12 @@ __device__ __forceinline__ void ic_geometry(const StreamDesc& D, const PassParam
 // (forward: the gradient taps) is loaded once with three aligned 8-byte loads
 // per row and funnel shifts, and all p*p samples are interpolated from
 // registers.  FP32 levels only.
-template <int PS, bool ICF>
+template <int PS, bool ICF, bool HC = false>
 __device__ __forceinline__ void linearize_square_t(const StreamDesc& D, const PassParams& P, int p,
                                                    PointGeom& G, float* acc, float* res)
 {
+    static_assert(!HC || ICF, "the cached Hessian needs the inverse-compositional rows");
+    float sx = 0.0f, sy = 0.0f;
     constexpr int h = (PS - 1) / 2, B = ICF ? 0 : 1, R = PS + 1 + 2 * B, NWD = (R + 3) / 4;
     const LevelDev& lv = D.lv[P.level];
     if (ICF) ic_geometry(D, P, p, G);
@@ -276,6 +319,11 @@ __device__ __forceinline__ void linearize_square_t(const StreamDesc& D, const Pa
             const float I00 = GLT_WX(r0, c0), I10 = GLT_WX(r0, c0 + 1);
             const float I01 = GLT_WX(r0 + 1, c0), I11 = GLT_WX(r0 + 1, c0 + 1);
             const float I = fmaf(w00, I00, fmaf(w10, I10, fmaf(w01, I01, w11 * I11)));
+            if (HC) {
+                hc_sample(I, I0p[k], G0p[k], P.ea, P.b, D.huber_k, sx, sy, acc,
+                          res ? res + (size_t)(PS * PS) * p + k : nullptr);
+                continue;
+            }
             float gx, gy;
             if (ICF) {
                 const float2 g0 = G0p[k];
@@ -296,13 +344,16 @@ __device__ __forceinline__ void linearize_square_t(const StreamDesc& D, const Pa
         }
     }
 #undef GLT_WX
+    if (HC) hc_fold(G, sx, sy, acc);
 }
 
 // Any other odd p (3..11): samples read one by one (four taps, plus the
 // gradient taps in the forward form) through the read-only cache.
+template <bool HC = false>
 __device__ __forceinline__ void linearize_square_any(const StreamDesc& D, const PassParams& P, int p,
                                                      PointGeom& G, float* acc, float* res)
 {
+    float sx = 0.0f, sy = 0.0f;
     const LevelDev& lv = D.lv[P.level];
     const int K = D.K, h = (D.pattern - 1) / 2, S = lv.pitch;
     const bool ic = D.G0 != nullptr;
@@ -316,6 +367,11 @@ __device__ __forceinline__ void linearize_square_any(const StreamDesc& D, const 
         const uint8_t* t = lv.img + (size_t)(G.yb + dy) * S + (G.xb + dx);
         const float I00 = __ldca(t), I10 = __ldca(t + 1), I01 = __ldca(t + S), I11 = __ldca(t + S + 1);
         const float I = fmaf(w00, I00, fmaf(w10, I10, fmaf(w01, I01, w11 * I11)));
+        if (HC) {
+            hc_sample(I, I0p[k], G0p[k], P.ea, P.b, D.huber_k, sx, sy, acc,
+                      res ? res + (size_t)K * p + k : nullptr);
+            continue;
+        }
         float gx, gy;
         if (ic) {
             const float2 g0 = G0p[k];
@@ -333,12 +389,20 @@ __device__ __forceinline__ void linearize_square_any(const StreamDesc& D, const 
         }
         accumulate_sample(G, I, gx, gy, I0p[k], P.ea, P.b, D.huber_k, acc, res ? res + (size_t)K * p + k : nullptr);
     }
+    if (HC) hc_fold(G, sx, sy, acc);
 }
 
 // Inlined so the accumulators stay in registers.
+template <bool HC = false>
 __device__ __forceinline__ void linearize_square(const StreamDesc& D, const PassParams& P, int p,
                                                  PointGeom& G, float* acc, float* res)
 {
+    if (HC) {
+        if (D.pattern == 7) linearize_square_t<7, true, true>(D, P, p, G, acc, res);
+        else if (D.pattern == 11) linearize_square_t<11, true, true>(D, P, p, G, acc, res);
+        else linearize_square_any<true>(D, P, p, G, acc, res);
+        return;
+    }
     const bool ic = D.G0 != nullptr;
     if (D.pattern == 7) {
         if (ic) linearize_square_t<7, true>(D, P, p, G, acc, res);
@@ -355,10 +419,13 @@ __device__ __forceinline__ void linearize_square(const StreamDesc& D, const Pass
 // residuals (NaN for an unusable point) to res[Kp..Kp+K-1].
 // SQUARE: the p x p path is compiled in; IC: the inverse-compositional rows
 // are compiled in (both decided per stream at run time when compiled in).
-template <bool MIXED, bool RES, bool SQUARE = false, bool IC = true>
+// HC: the cached-Hessian accumulation (acc holds kHcAcc values; FP32 levels
+// and inverse-compositional rows only).
+template <bool MIXED, bool RES, bool SQUARE = false, bool IC = true, bool HC = false>
 __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassParams& P,
                                                 const PointCache& c, float* acc, float* res)
 {
+    static_assert(!HC || (IC && !MIXED), "the cached Hessian needs FP32 levels and IC rows");
     const LevelDev& lv = D.lv[P.level];
     const int p = c.p;
     const float4 ia = c.ia, ib = c.ib;
@@ -371,7 +438,7 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
         return;
     }
     if (SQUARE && D.pattern) {
-        linearize_square(D, P, p, G, acc, RES ? res : nullptr);
+        linearize_square<HC>(D, P, p, G, acc, RES ? res : nullptr);
         return;
     }
     const float i0[8] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
@@ -388,6 +455,7 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
     if (!MIXED) {
         // 8x8 byte window, rows yb-3..yb+4, columns xb-3..xb+4: two aligned
         // 8-byte loads per row, then a funnel shift to the window start.
+        float hsx = 0.0f, hsy = 0.0f;   // cached-Hessian form: the point's (sx, sy)
         const int xs = G.xb - 3;
         const int a8 = xs & ~7;
         const int sh = (xs - a8) * 8;
@@ -412,6 +480,11 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
             const float I00 = GLT_PX(r0, c0), I10 = GLT_PX(r0, c0 + 1);
             const float I01 = GLT_PX(r0 + 1, c0), I11 = GLT_PX(r0 + 1, c0 + 1);
             const float I = fmaf(w00, I00, fmaf(w10, I10, fmaf(w01, I01, w11 * I11)));
+            if (HC) {
+                hc_sample(I, i0[k], G0p[k], P.ea, P.b, D.huber_k, hsx, hsy, acc,
+                          RES ? res + 8 * p + k : nullptr);
+                continue;
+            }
             float gx, gy;
             if (ic) {
                 const float2 g0 = G0p[k];
@@ -432,6 +505,7 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
                               RES ? res + 8 * p + k : nullptr);
         }
 #undef GLT_PX
+        if (HC) hc_fold(G, hsx, hsy, acc);
     } else {
         const uint2* pk = lv.packed;
 #pragma unroll
@@ -488,6 +562,50 @@ __device__ __forceinline__ void warp_reduce_scatter48(float (&v)[kAccPad], int l
 #undef GLT_RS_STAGE
 #pragma unroll
     for (int i = 0; i < 3; ++i) v[i] += __shfl_xor_sync(full, v[i], 1);
+}
+
+// Butterfly reduce-scatter of the 8 cached-Hessian accumulators (7 shuffles),
+// then two pair stages: afterwards lanes with (lane & 3) == 0 hold the warp
+// sum of value ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1).
+__device__ __forceinline__ int rs8_index(int lane)
+{
+    return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+}
+
+__device__ __forceinline__ void warp_reduce_scatter8(float (&v)[kHcAcc], int lane)
+{
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int half = 4, off = 16; half >= 1; half >>= 1, off >>= 1) {
+        const bool hi = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = hi ? v[i] : v[i + half];
+            const float keep = hi ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(full, send, off);
+        }
+    }
+    v[0] += __shfl_xor_sync(full, v[0], 2);
+    v[0] += __shfl_xor_sync(full, v[0], 1);
+}
+
+// Block reduction of the 8 cached-Hessian accumulators into out[0..8).
+// Ends with __syncthreads().
+template <int THREADS>
+__device__ __forceinline__ void block_reduce8(float (&acc)[kHcAcc], float (*red)[kAccPad], float* out)
+{
+    constexpr int NW = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    warp_reduce_scatter8(acc, lane);
+    if ((lane & 3) == 0) red[warp][rs8_index(lane)] = acc[0];
+    __syncthreads();
+    if (threadIdx.x < kHcAcc) {
+        float s = 0.0f;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
 }
 
 // Block reduction of the per-thread accumulators into out[0..kNumAcc).
@@ -627,6 +745,7 @@ enum { PH_START = 0, PH_CAND = 1 };
 
 struct Solver {
     double T[12], a, b;       // accepted state
+    double ema;               // cached-Hessian form: e^-a (a is held fixed there)
     double Tc[12], ac, bc;    // candidate under evaluation
     double H[64], g[8];       // normal equations at the accepted state
     double E, nd, lambda, res_E;   // energy / samples (as double) at the accepted state
@@ -670,6 +789,7 @@ __device__ inline void solver_init(const StreamDesc& D, const double* init, Solv
     S.res_E = __longlong_as_double(0x7ff8000000000000ll);
     S.done = 0;
     for (int l = 0; l < kMaxLevels; ++l) S.iters[l] = 0;
+    S.ema = (D.Hc && finite_start) ? exp(-S.a) : 1.0;
     int l = D.L - 1;
     while (l >= 0 && D.max_iters[l] <= 0) --l;
     if (!finite_start) {
@@ -691,18 +811,22 @@ __device__ inline void solver_init(const StreamDesc& D, const double* init, Solv
 // One LM decision after a pass whose cluster-wide sums are `tot`; executed
 // by all 32 lanes of one warp with uniform control flow.  FP64 instructions
 // are kept to the minimum the method needs (each costs ~64 issue cycles).
+// HC: the cached-Hessian form (tot holds g0 = sum w r J_ic, E and n; the
+// step is -e^-a H^-1 g0 with the level's per-reference H^-1, since the rows
+// are e^a J_ic and the normal matrix e^2a H).
+template <bool HC = false>
 __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, Solver& S,
                                         PassParams& P, int lane, bool write_trace)
 {
     const unsigned full = 0xffffffffu;
     const int row = lane & 7;
-    const double E = tot[kIdxE];
-    const double nd = tot[kIdxN];           // exact integer count
+    const double E = tot[HC ? kHcE : kIdxE];
+    const double nd = tot[HC ? kHcN : kIdxN];   // exact integer count
     const int n = (int)nd;
     // sums that are not finite (an FP32 overflow) make the pass unusable
     bool sums_finite = abs_bits(E) < kInfBits;
 #pragma unroll
-    for (int i = 0; i < kIdxE; ++i) sums_finite &= abs_bits(tot[i]) < kInfBits;
+    for (int i = 0; i < (HC ? kHcE : kIdxE); ++i) sums_finite &= abs_bits(tot[i]) < kInfBits;
     const bool enough = n >= D.min_valid && n > 0 && sums_finite;
     int status = S.status;
     if (!sums_finite) status |= GLT_TRACK_DIVERGED;
@@ -746,7 +870,16 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
     __syncwarp();
     // commit the pass outcome to the shared state
     if (accept && lane < 12) S.T[lane] = S.Tc[lane];
-    if (load_normal && lane < 8) {
+    if (HC) {
+        if (load_normal) {
+            // g0 of the accepted state, and the level's H^-1 (read again at every
+            // acceptance: two loads per lane)
+            if (lane < 6) S.g[lane] = tot[lane];
+            const double* Hi = D.Hc + 72 * level + 36;
+            S.H[lane] = Hi[lane];
+            if (lane < 4) S.H[32 + lane] = Hi[32 + lane];
+        }
+    } else if (load_normal && lane < 8) {
         // with (a, b) held fixed their rows and columns become the identity and
         // their right-hand side zero, so the solve gives da = db = 0
         const bool fixed_ab = !D.affine;
@@ -776,7 +909,28 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
     __syncwarp();
 
     bool next_level = (phase == PH_START && !enough) || finish;
-    if (candidate) {
+    bool solved = false;
+    double dl[8];
+    if (candidate && HC) {
+        // ---- delta = -e^-a H^-1 g0, one row per lane (lanes 0-5); the affine
+        // pair is held fixed in this form
+        if (!(abs_bits(S.H[0]) < kInfBits)) {
+            if (lane == 0) S.status |= GLT_TRACK_NOT_PD;
+            finish = true;
+            next_level = true;
+        } else {
+            const int r6 = lane < 6 ? lane : 0;
+            double x = 0.0;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) x = fma(S.H[6 * r6 + j], S.g[j], x);
+            x *= -S.ema;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) dl[c] = __shfl_sync(full, x, c);
+            dl[6] = 0.0;
+            dl[7] = 0.0;
+            solved = true;
+        }
+    } else if (candidate) {
         // ---- (H + lambda diag H) delta = -g by L D L^T, right-looking, one
         // matrix entry per lane: lanes 0-27 hold the strictly lower entries
         // (i, k), i > k, column by column; lanes 0-7 also hold the diagonal
@@ -840,9 +994,13 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
                 const double xj = __shfl_sync(full, x, j);
                 if (row < j) x = fma(-Lcol[j], xj, x);
             }
-            double dl[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) dl[c] = __shfl_sync(full, x, c);
+            solved = true;
+        }
+    }
+    if (solved) {
+        {
             long long mbits = 0;
 #pragma unroll
             for (int c = 0; c < 6; ++c) mbits = max(mbits, abs_bits(dl[c]));

@@ -59,6 +59,7 @@ struct glt_tracker {
     float2* dz = nullptr;
     float* I0 = nullptr;
     float2* G0 = nullptr;                 // GLT_IC reference gradients [L][Npad][K]
+    double* Hc = nullptr;                 // GLT_HESSIAN_CACHED: per level H, H^-1 [L][72]
     int K = 8;                            // samples per point of the pattern
     int Npad = 0;
     int N = 0;
@@ -142,13 +143,16 @@ __host__ __device__ int pyr_tiles_y(int dH);
 
 // points.cu
 cudaError_t launch_set_points(const glt_tracker* t, const float* uvd_dev, int n, cudaStream_t s);
+// per-reference Hessian of every level and its inverse (GLT_HESSIAN_CACHED)
+cudaError_t launch_ic_hessian(const glt_tracker* t, cudaStream_t s);
 
 // track.cu
 // kernel variant of a configuration: 0 FP32 forward, 1 GLT_MIXED, 2 FP32 with
-// p x p patches, 3 FP32 inverse compositional
+// p x p patches, 3 FP32 inverse compositional, 4 the cached Hessian (FP32, IC)
 inline int track_variant(const glt_config& c)
 {
-    return c.precision == GLT_MIXED ? 1 : c.pattern != 0 ? 2 : c.jacobian == GLT_IC ? 3 : 0;
+    return c.hessian == GLT_HESSIAN_CACHED ? 4
+         : c.precision == GLT_MIXED ? 1 : c.pattern != 0 ? 2 : c.jacobian == GLT_IC ? 3 : 0;
 }
 // pdl: launch as a programmatic dependent of the previous kernel in the
 // stream (cudaLaunchAttributeProgrammaticStreamSerialization): the kernel may

@@ -73,6 +73,119 @@ __global__ void set_points_kernel(StreamDesc* __restrict__ desc, int n, RefLevel
     }
 }
 
+// Sec. IV-B: with the inverse-compositional rows J_ik evaluated on the
+// reference, H = sum_i sum_k J_ik^T J_ik is fixed while the reference is;
+// Sec. IV-C "Precompute IC": each point's H_i is reduced into one H per level.
+// One block per level: every thread sums the 21 upper-triangle products of
+// its points' rows in FP32 per point (J_k = [Jt_k, x_r x Jt_k], Jt_k =
+// gx_k a0 + gy_k a1 with the cached reference gradient and the projection
+// rows at x_r, e^a = 1) and in FP64 across its points; the block adds the
+// thread sums in a fixed tree order; thread 0 factorises H = L D L^T in FP64
+// (pivots d > 0 and d > 1e-13 H_jj, else H^-1[0] = NaN: not positive
+// definite) and writes H and H^-1 to Hc[72 l ..].
+constexpr int kHessThreads = 256;
+
+__global__ void __launch_bounds__(kHessThreads) ic_hessian_kernel(const StreamDesc* __restrict__ desc,
+                                                                  double* __restrict__ Hc)
+{
+    __shared__ double red[kHessThreads][21];
+    const StreamDesc& D = *desc;
+    const int l = blockIdx.x;
+    const int tid = threadIdx.x;
+    const float s = ldexpf(1.0f, -l);
+    double acc[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) acc[i] = 0.0;
+    for (int p = tid; p < D.N; p += kHessThreads) {
+        const size_t base = ((size_t)l * D.Npad + p) * D.K;
+        if (isnan(D.I0[base])) continue;          // not usable on this level of the reference
+        const float4 q = D.pt[p];
+        const float2 dz = D.dz[p];
+        const float fxl = D.fx * s * dz.y, fyl = D.fy * s * dz.y;
+        const float a0[3] = {fxl, 0.0f, -fxl * q.z};
+        const float a1[3] = {0.0f, fyl, -fyl * q.w};
+        const float xr[3] = {dz.x * q.z, dz.x * q.w, dz.x};
+        float h[21];
+#pragma unroll
+        for (int i = 0; i < 21; ++i) h[i] = 0.0f;
+        for (int k = 0; k < D.K; ++k) {
+            const float2 g0 = D.G0[base + k];
+            float J[6];
+            J[0] = fmaf(g0.x, a0[0], g0.y * a1[0]);
+            J[1] = fmaf(g0.x, a0[1], g0.y * a1[1]);
+            J[2] = fmaf(g0.x, a0[2], g0.y * a1[2]);
+            J[3] = fmaf(xr[1], J[2], -xr[2] * J[1]);
+            J[4] = fmaf(xr[2], J[0], -xr[0] * J[2]);
+            J[5] = fmaf(xr[0], J[1], -xr[1] * J[0]);
+            int idx = 0;
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+#pragma unroll
+                for (int j = i; j < 6; ++j) {
+                    h[idx] = fmaf(J[i], J[j], h[idx]);
+                    ++idx;
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < 21; ++i) acc[i] += (double)h[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 21; ++i) red[tid][i] = acc[i];
+    __syncthreads();
+    for (int half = kHessThreads / 2; half > 0; half >>= 1) {
+        if (tid < half)
+            for (int i = 0; i < 21; ++i) red[tid][i] += red[tid + half][i];
+        __syncthreads();
+    }
+    if (tid != 0) return;
+    double H[36], L[36] = {}, d[6], Hi[36];
+    int idx = 0;
+    for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j) {
+            H[6 * i + j] = H[6 * j + i] = red[0][idx];
+            ++idx;
+        }
+    bool pd = true;
+    for (int j = 0; j < 6 && pd; ++j) {
+        double dj = H[6 * j + j];
+        for (int k = 0; k < j; ++k) dj -= L[6 * j + k] * L[6 * j + k] * d[k];
+        pd = dj > 0.0 && dj > 1e-13 * H[6 * j + j];
+        d[j] = dj;
+        L[6 * j + j] = 1.0;
+        for (int i = j + 1; i < 6 && pd; ++i) {
+            double v = H[6 * i + j];
+            for (int k = 0; k < j; ++k) v -= L[6 * i + k] * L[6 * j + k] * d[k];
+            L[6 * i + j] = v / dj;
+        }
+    }
+    for (int c = 0; c < 6 && pd; ++c) {
+        // column c of H^-1: L y = e_c, z = D^-1 y, L^T x = z
+        double y[6], x[6];
+        for (int i = 0; i < 6; ++i) {
+            double v = i == c ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) v -= L[6 * i + k] * y[k];
+            y[i] = v;
+        }
+        for (int i = 5; i >= 0; --i) {
+            double v = y[i] / d[i];
+            for (int k = i + 1; k < 6; ++k) v -= L[6 * k + i] * x[k];
+            x[i] = v;
+        }
+        for (int i = 0; i < 6; ++i) Hi[6 * i + c] = x[i];
+    }
+    double* out = Hc + 72 * l;
+    for (int i = 0; i < 36; ++i) {
+        out[i] = H[i];
+        out[36 + i] = pd ? Hi[i] : __longlong_as_double(0x7ff8000000000000ll);
+    }
+}
+
+cudaError_t launch_ic_hessian(const glt_tracker* t, cudaStream_t s)
+{
+    ic_hessian_kernel<<<t->L, kHessThreads, 0, s>>>(t->desc_dev, t->Hc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_set_points(const glt_tracker* t, const float* uvd_dev, int n, cudaStream_t s)
 {
     const int threads = 128;

@@ -25,8 +25,11 @@ constexpr int kMaxCluster = 16;   // largest cluster a stream may use (config.cl
 
 // VAR: 0 FP32 levels, forward Jacobian; 1 FP16-packed levels (GLT_MIXED);
 // 2 FP32 with the p x p patch path compiled in; 3 FP32 with the
-// inverse-compositional rows compiled in.  Variants 1-3 decide the Jacobian
-// form (and 2 the pattern) per stream, so one batch may mix them.
+// inverse-compositional rows compiled in; 4 the cached-Hessian form (FP32,
+// inverse-compositional rows, any pattern: per pass only g, E and n are
+// reduced and the step uses the per-reference H^-1).  Variants 1-3 decide the
+// Jacobian form (and 2 the pattern) per stream, so one batch may mix them;
+// variant 4 runs only streams of that form.
 template <int THREADS, int VAR>
 __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(const StreamDesc* const* __restrict__ descs,
                                                         const int* __restrict__ users,
@@ -34,7 +37,9 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
                                                         glt_result* __restrict__ results)
 {
     constexpr int NW = THREADS / 32;
-    constexpr bool MIXED = VAR == 1, SQUARE = VAR == 2, IC = VAR != 0;
+    constexpr bool MIXED = VAR == 1, SQUARE = VAR == 2 || VAR == 4, IC = VAR != 0, HC = VAR == 4;
+    constexpr int NACC = HC ? kHcAcc : kAccPad;    // accumulators per thread
+    constexpr int NSUM = HC ? kHcAcc : kNumAcc;    // sums exchanged per pass
     __shared__ StreamDesc sD;
     __shared__ PassParams P;
     __shared__ Solver S;
@@ -71,19 +76,22 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
     pc.p = -1;
     pc.level = -1;
     while (!P.done) {
-        float acc[kAccPad];
+        float acc[NACC];
 #pragma unroll
-        for (int i = 0; i < kAccPad; ++i) acc[i] = 0.0f;
+        for (int i = 0; i < NACC; ++i) acc[i] = 0.0f;
         for (int p = rank * THREADS + tid; p < sD.N; p += C * THREADS) {
             // a thread that owns one point keeps its data for the whole level
             // (the 128-thread shape, capped at 128 registers for batches of
             // many streams, reloads it instead)
             if (THREADS == 128 || pc.p != p || pc.level != P.level) load_point(sD, P.level, p, pc);
-            linearize_point<MIXED, false, SQUARE, IC>(sD, P, pc, acc, nullptr);
+            linearize_point<MIXED, false, SQUARE, IC, HC>(sD, P, pc, acc, nullptr);
         }
-        block_reduce<THREADS, MIXED>(acc, red, part[par], part_c[par]);
+        if constexpr (HC)
+            block_reduce8<THREADS>(acc, red, part[par]);
+        else
+            block_reduce<THREADS, MIXED>(acc, red, part[par], part_c[par]);
         if (C > 1) cluster.sync();
-        if (tid < kNumAcc) {
+        if (tid < NSUM) {
             // finish over the CTAs of the cluster: a compensated FP32 sum
             // (TwoSum, error-free per step) converted to FP64 once; the FP64
             // pipe of this GPU is too slow to carry a chain of C adds
@@ -113,7 +121,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
         __syncthreads();
         // the FP64 tail runs on one warp; CTAs of different streams that share an
         // SM use different warps so their tails spread over the SM's sub-partitions
-        if ((tid >> 5) == tail_warp) solver_step_warp(sD, tot, S, P, tid & 31, rank == 0);
+        if ((tid >> 5) == tail_warp) solver_step_warp<HC>(sD, tot, S, P, tid & 31, rank == 0);
         __syncthreads();
         par ^= 1;
     }
@@ -134,26 +142,31 @@ __global__ void __launch_bounds__(THREADS) linearize_kernel(const StreamDesc* __
                                                             float* __restrict__ res)
 {
     constexpr int NW = THREADS / 32;
-    constexpr bool MIXED = VAR == 1, SQUARE = VAR == 2, IC = VAR != 0;
+    constexpr bool MIXED = VAR == 1, SQUARE = VAR == 2 || VAR == 4, IC = VAR != 0, HC = VAR == 4;
+    constexpr int NACC = HC ? kHcAcc : kAccPad;
+    constexpr int NSUM = HC ? kHcAcc : kNumAcc;
     __shared__ float red[NW][kAccPad];
     __shared__ float part[kAccPad];
     __shared__ float part_c[kAccPad];
     __shared__ int is_last;
     const StreamDesc& D = *desc;
-    float acc[kAccPad];
+    float acc[NACC];
 #pragma unroll
-    for (int i = 0; i < kAccPad; ++i) acc[i] = 0.0f;
+    for (int i = 0; i < NACC; ++i) acc[i] = 0.0f;
     const int p = blockIdx.x * THREADS + threadIdx.x;
     if (p < D.N) {
         PointCache pc;
         load_point(D, P.level, p, pc);
         if (res)
-            linearize_point<MIXED, true, SQUARE, IC>(D, P, pc, acc, res);
+            linearize_point<MIXED, true, SQUARE, IC, HC>(D, P, pc, acc, res);
         else
-            linearize_point<MIXED, false, SQUARE, IC>(D, P, pc, acc, nullptr);
+            linearize_point<MIXED, false, SQUARE, IC, HC>(D, P, pc, acc, nullptr);
     }
-    block_reduce<THREADS, MIXED>(acc, red, part, part_c);
-    if (threadIdx.x < kNumAcc)
+    if constexpr (HC)
+        block_reduce8<THREADS>(acc, red, part);
+    else
+        block_reduce<THREADS, MIXED>(acc, red, part, part_c);
+    if (threadIdx.x < NSUM)
         partials[(size_t)blockIdx.x * kAccPad + threadIdx.x] = part[threadIdx.x] + (MIXED ? part_c[threadIdx.x] : 0.0f);
     __threadfence();
     __syncthreads();
@@ -161,7 +174,7 @@ __global__ void __launch_bounds__(THREADS) linearize_kernel(const StreamDesc* __
     __syncthreads();
     if (is_last) {
         __threadfence();
-        if (threadIdx.x < kNumAcc) {
+        if (threadIdx.x < NSUM) {
             double s = 0.0;
             for (unsigned b = 0; b < gridDim.x; ++b)
                 s += (double)__ldcg(partials + (size_t)b * kAccPad + threadIdx.x);
@@ -267,6 +280,23 @@ cudaError_t launch_track_v<2>(const StreamDesc* const* descs, const int* users, 
     return launch_track_t<256, 2>(descs, users, S, cluster, init, results, s, pdl);
 }
 
+// the cached-Hessian variant is built for 256 threads only (it carries the
+// unrolled p x p patches too)
+template <>
+bool shape_ok_v<4>(int cluster, int threads)
+{
+    return threads == 256 && shape_ok_t<256, 4>(cluster);
+}
+
+template <>
+cudaError_t launch_track_v<4>(const StreamDesc* const* descs, const int* users, int S, int cluster,
+                              int threads, const double* init, glt_result* results, cudaStream_t s,
+                              bool pdl)
+{
+    if (threads != 256) return cudaErrorInvalidValue;
+    return launch_track_t<256, 4>(descs, users, S, cluster, init, results, s, pdl);
+}
+
 }  // namespace
 
 bool track_shape_ok(int cluster, int threads, int variant)
@@ -277,6 +307,7 @@ bool track_shape_ok(int cluster, int threads, int variant)
     case 1: return shape_ok_v<1>(cluster, threads);
     case 2: return shape_ok_v<2>(cluster, threads);
     case 3: return shape_ok_v<3>(cluster, threads);
+    case 4: return shape_ok_v<4>(cluster, threads);
     default: return false;
     }
 }
@@ -290,6 +321,7 @@ cudaError_t launch_track(const StreamDesc* const* descs, const int* users, int S
     case 1: return launch_track_v<1>(descs, users, S, cluster, threads, init, results, s, pdl);
     case 2: return launch_track_v<2>(descs, users, S, cluster, threads, init, results, s, pdl);
     case 3: return launch_track_v<3>(descs, users, S, cluster, threads, init, results, s, pdl);
+    case 4: return launch_track_v<4>(descs, users, S, cluster, threads, init, results, s, pdl);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -310,6 +342,9 @@ cudaError_t launch_linearize(const glt_tracker* t, const PassParams& P, bool wan
                                                     t->lin_counter, t->lin_out, res);
     else if (v == 3)
         linearize_kernel<T, 3><<<blocks, T, 0, s>>>(t->desc_dev, P, t->lin_partials,
+                                                    t->lin_counter, t->lin_out, res);
+    else if (v == 4)
+        linearize_kernel<T, 4><<<blocks, T, 0, s>>>(t->desc_dev, P, t->lin_partials,
                                                     t->lin_counter, t->lin_out, res);
     else
         linearize_kernel<T, 0><<<blocks, T, 0, s>>>(t->desc_dev, P, t->lin_partials,

@@ -43,15 +43,16 @@ def test_library_exports_every_declared_symbol(lib_path):
 def test_binding_covers_header_and_layouts(lib_path):
     import paper_2607_16897_gb300 as glt
     assert set(glt.SIGNATURES) == set(declared_functions())
-    assert ctypes.sizeof(glt.glt_config) == 192
+    assert ctypes.sizeof(glt.glt_config) == 200
     # the C struct has the binding's layout: glt_default_config writes exactly
     # sizeof(glt_config) bytes and its last field lands where the binding has it
     buf = (ctypes.c_uint8 * 256)(*([0xA5] * 256))
     glt.glt_default_config(ctypes.cast(buf, ctypes.POINTER(glt.glt_config)), 640, 480, 525.0,
                            525.0, 320.0, 240.0)
-    assert bytes(buf[192:]) == bytes([0xA5] * 64)
-    cfg = glt.glt_config.from_buffer_copy(bytes(buf[:192]))
+    assert bytes(buf[200:]) == bytes([0xA5] * 56)
+    cfg = glt.glt_config.from_buffer_copy(bytes(buf[:200]))
     assert cfg.affine == 1 and cfg.pattern == 0 and cfg.jacobian == 0 and cfg.width == 640
+    assert cfg.hessian == glt.GLT_HESSIAN_PASS
     assert ctypes.sizeof(glt.glt_result) == 168
     assert glt.RESULT_DTYPE.itemsize == glt.RESULT_BYTES
     c = glt.default_config(640, 480, (525, 525, 320, 240))
