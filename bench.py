@@ -106,6 +106,9 @@ def parse():
     ap.add_argument("--no-launch-overhead", action="store_true",
                     help="skip the launch-overhead measurement (e.g. for a profiler's launch list)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default workload only: skip the batched forms (C3, C5 plain and "
+                         "learned) that the line otherwise carries under 'batched'")
     return ap.parse_args()
 
 
@@ -558,10 +561,7 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    dist = process_group(world)
     wl = single_workload(args.workload, rank)   # replicas: one independent stream per GPU
     apply_overrides(wl, args)
     precision = args.precision or ("mixed" if args.workload == "c4" else "fp32")
@@ -732,10 +732,8 @@ def run_ours(args):
                 "launch_overhead": launch,
                 "parity_vs_oracle": parity, "accuracy_vs_truth": accuracy,
                 "linearization_error_vs_oracle": lin_err}
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+        return line
+    return None
 
 
 def run_e2e(args, glt, trk, wl, frames_pin, stream):
@@ -1010,10 +1008,7 @@ def run_batch(args):
         apply_overrides(w, args)
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    dist = process_group(world)
     precision = args.precision or ("mixed" if args.workload == "c4b" else "fp32")
     use_prop = args.workload == "c5"
     S = len(wls)
@@ -1329,10 +1324,8 @@ def run_batch(args):
                     "within_1e-5": int(sum(1 for a in agree if a[0] <= 1e-5 and a[1] <= 1e-5)),
                     "median_rot_rad": float(np.median([a[0] for a in agree])) if agree else None,
                     "median_trans_m": float(np.median([a[1] for a in agree])) if agree else None}}
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+        return line
+    return None
 
 
 def batch_cpu_baseline(wls, rec, frames_per_stream=8, proposal=None):
@@ -1387,14 +1380,62 @@ def batch_cpu_baseline(wls, rec, frames_per_stream=8, proposal=None):
     return cpu, parity
 
 
+_GROUP = {}
+
+
+def process_group(world):
+    """The replicas' process group (NCCL, one rank per GPU), created once per
+    run and shared by every workload the run measures; None for one GPU."""
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not _GROUP:
+        dist.init_process_group("nccl")
+        _GROUP["dist"] = dist
+    return dist
+
+
+# the batched forms measured with the default (single-stream) workload
+BATCHED_FORMS = ("c3", "c5")
+
+
+def nested_batched(args):
+    """The batched workloads' records (C3: 64 mixed streams; C5: 256 streams,
+    plain and with the learned proposal), measured in the same run with the
+    same step counts, keyed by workload."""
+    out = {}
+    for kind in BATCHED_FORMS:
+        sub = argparse.Namespace(**vars(args))
+        sub.workload = kind
+        sub.precision = None
+        rec = run_batch(sub)
+        if rec is not None:
+            for k in ("metric", "n_gpus", "steps", "warmup", "higher_is_better", "scaling",
+                      "vs_baseline", "data"):
+                rec.pop(k, None)
+            out[kind] = rec
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload in ("c3", "c4b", "c5"):
-        run_batch(args)
+        return
+    if args.workload in ("c3", "c4b", "c5"):
+        line = run_batch(args)
     else:
-        run_ours(args)
+        line = run_ours(args)
+        if args.workload == "c2" and not args.no_batched:
+            batched = nested_batched(args)
+            if line is not None:
+                line["batched"] = batched
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    dist = _GROUP.get("dist")
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":
