@@ -459,6 +459,11 @@ void orc_linearize2(const double* img, int W, int H, orc_cam K0, int level, cons
  * ones).  A level stops after max_iters candidates, once a step is
  * below eps_step (eps_step_coarse on the levels above the finest), or when a
  * rejected candidate raised the cost by no more than eps_cost * cost.
+ * Reading (coarse levels): a step below eps_step_coarse is below accept_step
+ * too, so it would be taken whatever its cost and would end the level; on a
+ * level above the finest it is therefore taken without a pass of its own, and
+ * the next level's start pass is the first evaluation of the new state (the
+ * finest level keeps the pass: its cost and sample count are reported).
  * ------------------------------------------------------------------------ */
 static int cholesky_solve8(const double A[64], const double g[8], double delta[8])
 {
@@ -644,14 +649,22 @@ void orc_track2(const double* cur, int W0, int H0, orc_cam K0, const double* x_r
                 out->status |= ORC_DIVERGED;
                 break;
             }
+            double m = 0;
+            for (int d = 0; d < 6; ++d) m = fmax(m, fabs(delta[d]));
+            if (l > 0 && m < cfg->eps_step_coarse && m < cfg->accept_step) {
+                /* the level's last step, taken without a pass of its own */
+                memcpy(T, Tn, sizeof(T));
+                a = an;
+                b = bn;
+                ++it;
+                break;
+            }
             double Hn[64], gn[8], En;
             int nn;
             orc_linearize2(img, Ws[l], Hs[l], K0, l, x_r, I0l, vl, Jl, N, cfg->pattern, Tn, an,
                            bn, cfg->huber_k, cfg->zmin, Hn, gn, &En, &nn, NULL, NULL, NULL, NULL);
             if (hcache) use_cached_hessian(Hn, gn, H6, an);
             ++it;
-            double m = 0;
-            for (int d = 0; d < 6; ++d) m = fmax(m, fabs(delta[d]));
             int nfin = sums_are_finite(Hn, gn, En);
             if (!nfin) out->status |= ORC_DIVERGED;
             double cn = (nn >= cfg->min_valid && nn > 0 && nfin) ? En / nn : INFINITY;

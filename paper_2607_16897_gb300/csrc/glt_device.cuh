@@ -1061,10 +1061,25 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
             const double ac = S.a + dl[6], bc = S.b + dl[7];
             const bool cand_finite = __all_sync(full, abs_bits(tc) < kInfBits) &&
                                      abs_bits(ac) < kInfBits && abs_bits(bc) < kInfBits;
+            // a step below eps_step_coarse on a level above the finest would be
+            // taken whatever its cost and would end the level, so it is taken
+            // here without a pass of its own; the next level's start pass is
+            // the first evaluation of the new state
+            const bool take_now = level > 0 && mbits < abs_bits(D.eps_step_coarse) &&
+                                  mbits < abs_bits(D.accept_step);
             if (!cand_finite) {
                 // the solve produced a state that is not finite: keep the
                 // accepted one and end the level
                 if (lane == 0) S.status |= GLT_TRACK_DIVERGED;
+                finish = true;
+                next_level = true;
+            } else if (take_now) {
+                if (lane < 12) S.T[lane] = tc;
+                if (lane == 0) {
+                    S.a = ac;
+                    S.b = bc;
+                }
+                ++it;
                 finish = true;
                 next_level = true;
             } else {

@@ -103,7 +103,12 @@ def test_initial_state_far_is_worse_than_converged(orc, syn):
     start = tr.debug_linearize(0, I34, 0.0, 0.0, per_sample=False)
     assert res["cost"] < 0.2 * start["E"] / start["n"]
     assert sum(res["iters"]) == res["iters_total"]
-    assert res["passes"] == res["iters_total"] + 3
+    # one start pass per level and one pass per candidate, except the last
+    # step of a coarse level that ends on its step threshold (taken unevaluated)
+    evaluated = [sum(1 for e in res["trace"] if e["candidate"] and e["level"] == l) for l in range(3)]
+    unevaluated = [res["iters"][l] - evaluated[l] for l in range(3)]
+    assert unevaluated[0] == 0 and all(u in (0, 1) for u in unevaluated)
+    assert res["passes"] == len(res["trace"]) == res["iters_total"] + 3 - sum(unevaluated)
 
 
 def test_zero_iterations_leave_state(orc, syn):
@@ -226,10 +231,12 @@ def test_initial_rotation_is_reorthonormalised(orc, syn):
 @pytest.mark.parametrize("seed", [3, 8])
 def test_coarse_level_stop_rule_keeps_the_fixed_point(orc, syn, seed):
     """Levels above the finest stop once a candidate step is below
-    eps_step_coarse (trace: every earlier candidate of such a level is at or
-    above it), and the final state equals the one of a schedule that runs
-    every level to eps_step: the coarse levels only have to bring the state
-    into the finest level's basin, where Gauss-Newton has one fixed point."""
+    eps_step_coarse; that step is taken without a pass of its own (it would be
+    accepted whatever its cost), so every evaluated candidate of such a level
+    is at or above the threshold and the level counts one step more than it
+    evaluated.  The final state equals the one of a schedule that runs every
+    level to eps_step: the coarse levels only have to bring the state into the
+    finest level's basin, where Gauss-Newton has one fixed point."""
     p = syn.pair_c1(seed, sigma=2.0)
     tracker = tracker_for(orc, p)
     res = tracker.track_frame(I34)
@@ -238,8 +245,12 @@ def test_coarse_level_stop_rule_keeps_the_fixed_point(orc, syn, seed):
     tr = res["trace"]
     for lvl in (2, 1):
         steps = [e["step"] for e in tr if e["candidate"] and e["level"] == lvl]
-        assert steps and all(s >= eps_c for s in steps[:-1])
-        assert steps[-1] < eps_c or len(steps) == tracker.cfg["max_iters"][lvl]
+        assert all(s >= eps_c for s in steps)
+        assert res["iters"][lvl] == len(steps) + 1 or len(steps) == tracker.cfg["max_iters"][lvl]
+    # the levels' start passes follow one another with no coarse pass between
+    # the unevaluated step and the next level's start
+    starts = [k for k, e in enumerate(tr) if not e["candidate"]]
+    assert [tr[k]["level"] for k in starts] == [2, 1, 0]
     fine = orc.OracleTracker(p.cam.W, p.cam.H, p.cam.K, levels=3, eps_step_coarse=1e-6)
     fine.build_pyramid(0, p.ref)
     fine.set_map_points(p.uvd)
