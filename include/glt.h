@@ -110,7 +110,8 @@ typedef struct glt_config {
     double zmin;                /* minimum current-camera depth of a usable point (m) */
     int precision;              /* GLT_FP32 or GLT_MIXED */
     int cluster;                /* CTAs cooperating on one stream (1..16, 0 = auto) */
-    int threads;                /* threads per CTA (128, 256 or 512; 0 = auto) */
+    int threads;                /* threads per CTA (128, 256 or 512; 0 = auto; p x p
+                                   patches 256, the cached Hessian 512) */
     int jacobian;               /* GLT_FORWARD or GLT_IC.  GLT_IC (Sec. IV-B, IV-C
                                    "Precompute IC"): glt_set_map_points also caches
                                    the reference gradient at every pattern sample of
@@ -137,9 +138,10 @@ typedef struct glt_config {
                                    delta = -(e^{2a} H)^-1 g (the rows are e^a times the
                                    reference rows).  Points out of view stay in H, as in
                                    the paper.  Needs jacobian GLT_IC, affine 0, lambda0 0
-                                   (plain Gauss-Newton), precision GLT_FP32 and 256 (or 0)
-                                   threads; an H that is not positive definite ends the
-                                   level with GLT_TRACK_NOT_PD */
+                                   (plain Gauss-Newton), precision GLT_FP32 and 512 (or 0)
+                                   threads (7 x 7 and 11 x 11 patches are split over four
+                                   threads each); an H that is not positive definite ends
+                                   the level with GLT_TRACK_NOT_PD */
 } glt_config;
 
 typedef struct glt_result {

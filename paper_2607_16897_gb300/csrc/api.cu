@@ -127,16 +127,16 @@ static int check_config(const glt_config* c)
         return invalid("pattern must be 0 (8-pixel) or an odd patch size 3..11");
     if (c->pattern != 0 && c->precision != GLT_FP32)
         return invalid("p x p patches need precision GLT_FP32");
-    if (c->pattern != 0 && c->threads != 0 && c->threads != 256)
-        return invalid("p x p patches run with 256 threads per CTA");
     if (c->affine != 0 && c->affine != 1) return invalid("affine must be 0 or 1");
     if (c->hessian != GLT_HESSIAN_PASS && c->hessian != GLT_HESSIAN_CACHED)
         return invalid("hessian must be GLT_HESSIAN_PASS or GLT_HESSIAN_CACHED");
     if (c->hessian == GLT_HESSIAN_CACHED &&
         (c->jacobian != GLT_IC || c->affine != 0 || c->lambda0 != 0.0 || c->precision != GLT_FP32 ||
-         (c->threads != 0 && c->threads != 256)))
+         (c->threads != 0 && c->threads != 512)))
         return invalid("GLT_HESSIAN_CACHED needs jacobian GLT_IC, affine 0, lambda0 0, "
-                       "precision GLT_FP32 and 256 (or 0) threads");
+                       "precision GLT_FP32 and 512 (or 0) threads");
+    if (c->hessian != GLT_HESSIAN_CACHED && c->pattern != 0 && c->threads != 0 && c->threads != 256)
+        return invalid("p x p patches run with 256 threads per CTA");
     return GLT_OK;
 }
 
@@ -144,11 +144,13 @@ static int check_config(const glt_config* c)
 static void resolve_shape(glt_tracker* t)
 {
     const int variant = track_variant(t->cfg);
-    int threads = t->cfg.threads ? t->cfg.threads : 256;
+    int threads = t->cfg.threads ? t->cfg.threads : (variant == 4 ? 512 : 256);
     int cluster = t->cfg.cluster;
     if (cluster == 0) {
         // about one point per thread, in units of the 8-pixel pattern's work
-        const long long work = (long long)t->N * std::max(1, t->K / 8);
+        // (the cached-Hessian form: one task per thread)
+        const long long work = variant == 4 ? (long long)t->N * hc_groups(t->cfg.pattern)
+                                            : (long long)t->N * std::max(1, t->K / 8);
         cluster = (int)std::min<long long>(16, std::max<long long>(1, (work + threads - 1) / threads));
     }
     while (cluster > 1 && !track_shape_ok(cluster, threads, variant)) cluster = cluster > 8 ? 8 : cluster - 1;
@@ -889,6 +891,7 @@ int glt_batch_create(glt_tracker* const* trackers, int S, glt_batch** out)
         if (v == 1 || v == 2 || v == 4) b->variant = v;
         else if (v == 3 && b->variant == 0) b->variant = 3;
     }
+    if (b->variant == 4) b->threads = 512;   // the cached-Hessian kernel's only width
     if (!track_shape_ok(b->cluster, b->threads, b->variant)) b->cluster = 1;
     *out = b;
     return GLT_OK;
@@ -1030,7 +1033,7 @@ int glt_batch_autotune(glt_batch* b, const double* init_dev, glt_result* out_dev
     if (!init_dev || !out_dev || reps < 1) return invalid("bad argument");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int shapes[][2] = {{1, 128}, {1, 256}, {2, 128}, {2, 256}, {4, 128}, {4, 256},
-                             {8, 128}, {8, 256}, {1, 512}, {2, 512}};
+                             {8, 128}, {8, 256}, {1, 512}, {2, 512}, {4, 512}, {8, 512}};
     cudaEvent_t e0, e1;
     GLT_CHECK(cudaEventCreate(&e0), "event");
     GLT_CHECK(cudaEventCreate(&e1), "event");

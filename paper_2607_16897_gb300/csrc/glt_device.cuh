@@ -415,6 +415,69 @@ __device__ __forceinline__ void linearize_square(const StreamDesc& D, const Pass
     }
 }
 
+// The cached-Hessian form splits a p x p patch (p = 7 or 11) into
+// kHcGroups groups of consecutive rows, one thread per group: each of the
+// point's threads projects the point (the same FP32 arithmetic, so the same
+// validity decision), samples its rows from its own (rows + 1) x (p + 1)
+// byte window and folds its rows' sums into g0; the fold is linear, so the
+// threads of a point exchange nothing.
+constexpr int kHcGroups = 4;
+
+template <int PS>
+__device__ __forceinline__ void linearize_rows_hc(const StreamDesc& D, const PassParams& P, int p,
+                                                  int group, PointGeom& G, float* acc)
+{
+    constexpr int h = (PS - 1) / 2, RG = (PS + kHcGroups - 1) / kHcGroups, R = RG + 1;
+    constexpr int NWD = (PS + 1 + 3) / 4;
+    const LevelDev& lv = D.lv[P.level];
+    ic_geometry(D, P, p, G);
+    const int j0 = group * RG;
+    const int xs = G.xb - h, ys = G.yb - h + j0;
+    const int a8 = xs & ~7, sh = xs - a8;
+    const int wb = sh >> 2, s8 = (sh & 3) * 8;
+    const uint8_t* base = lv.img + (size_t)ys * lv.pitch + a8;
+    uint32_t win[R][NWD];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        // rows of the patch (and the lower bilinear tap of its last row) only
+        if (j0 + r <= PS) {
+            const uint2* rp = reinterpret_cast<const uint2*>(base + (size_t)r * lv.pitch);
+            const uint2 u0 = __ldca(rp), u1 = __ldca(rp + 1), u2 = __ldca(rp + 2);
+            const uint32_t v[6] = {u0.x, u0.y, u1.x, u1.y, u2.x, u2.y};
+#pragma unroll
+            for (int i = 0; i < NWD; ++i) {
+                const uint32_t lo = wb ? v[i + 1] : v[i];
+                const uint32_t hi = wb ? v[i + 2] : v[i + 1];
+                win[r][i] = __funnelshift_r(lo, hi, s8);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NWD; ++i) win[r][i] = 0u;
+        }
+    }
+#define GLT_WR(r, c) ((float)((win[(r)][(c) >> 2] >> (8 * ((c) & 3))) & 0xffu))
+    const float w00 = (1.0f - G.al) * (1.0f - G.be), w10 = G.al * (1.0f - G.be);
+    const float w01 = (1.0f - G.al) * G.be, w11 = G.al * G.be;
+    const float* I0p = D.I0 + ((size_t)P.level * D.Npad + p) * (PS * PS);
+    const float2* G0p = D.G0 + ((size_t)P.level * D.Npad + p) * (PS * PS);
+    float sx = 0.0f, sy = 0.0f;
+#pragma unroll
+    for (int j = 0; j < RG; ++j) {
+        if (j0 + j < PS) {
+#pragma unroll
+            for (int i = 0; i < PS; ++i) {
+                const int k = (j0 + j) * PS + i;
+                const float I00 = GLT_WR(j, i), I10 = GLT_WR(j, i + 1);
+                const float I01 = GLT_WR(j + 1, i), I11 = GLT_WR(j + 1, i + 1);
+                const float I = fmaf(w00, I00, fmaf(w10, I10, fmaf(w01, I01, w11 * I11)));
+                hc_sample(I, I0p[k], G0p[k], P.ea, P.b, D.huber_k, sx, sy, acc, nullptr);
+            }
+        }
+    }
+#undef GLT_WR
+    hc_fold(G, sx, sy, acc);
+}
+
 // Linearises map point p at the pass state into acc.  RES: also write the K
 // residuals (NaN for an unusable point) to res[Kp..Kp+K-1].
 // SQUARE: the p x p path is compiled in; IC: the inverse-compositional rows
@@ -530,6 +593,31 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
                               RES ? res + 8 * p + k : nullptr);
         }
     }
+}
+
+// One task of a cached-Hessian pass: row group `group` of point c.p for the
+// 7 x 7 and 11 x 11 patches (groups = kHcGroups), the whole point otherwise
+// (groups = 1).
+__device__ __forceinline__ void linearize_task_hc(const StreamDesc& D, const PassParams& P,
+                                                  const PointCache& c, int group, int groups,
+                                                  float* acc)
+{
+    if (groups == 1) {
+        linearize_point<false, false, true, true, true>(D, P, c, acc, nullptr);
+        return;
+    }
+    const LevelDev& lv = D.lv[P.level];
+    PointGeom G;
+    if (isnan(c.ia.x) || !project_point<true>(D, P, lv, c, G)) return;
+    if (D.pattern == 7)
+        linearize_rows_hc<7>(D, P, c.p, group, G, acc);
+    else
+        linearize_rows_hc<11>(D, P, c.p, group, G, acc);
+}
+
+__host__ __device__ inline int hc_groups(int pattern)
+{
+    return (pattern == 7 || pattern == 11) ? kHcGroups : 1;
 }
 
 // ---------------------------------------------------------------------------

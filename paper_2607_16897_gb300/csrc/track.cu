@@ -79,12 +79,23 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
         float acc[NACC];
 #pragma unroll
         for (int i = 0; i < NACC; ++i) acc[i] = 0.0f;
-        for (int p = rank * THREADS + tid; p < sD.N; p += C * THREADS) {
-            // a thread that owns one point keeps its data for the whole level
-            // (the 128-thread shape, capped at 128 registers for batches of
-            // many streams, reloads it instead)
-            if (THREADS == 128 || pc.p != p || pc.level != P.level) load_point(sD, P.level, p, pc);
-            linearize_point<MIXED, false, SQUARE, IC, HC>(sD, P, pc, acc, nullptr);
+        if constexpr (HC) {
+            // tasks: row groups of the p x p patches (kHcGroups per point) or whole points
+            const int groups = hc_groups(sD.pattern);
+            const int tasks = sD.N * groups;
+            for (int t = rank * THREADS + tid; t < tasks; t += C * THREADS) {
+                const int p = groups == 1 ? t : t / kHcGroups;
+                if (pc.p != p || pc.level != P.level) load_point(sD, P.level, p, pc);
+                linearize_task_hc(sD, P, pc, t - p * groups, groups, acc);
+            }
+        } else {
+            for (int p = rank * THREADS + tid; p < sD.N; p += C * THREADS) {
+                // a thread that owns one point keeps its data for the whole level
+                // (the 128-thread shape, capped at 128 registers for batches of
+                // many streams, reloads it instead)
+                if (THREADS == 128 || pc.p != p || pc.level != P.level) load_point(sD, P.level, p, pc);
+                linearize_point<MIXED, false, SQUARE, IC, HC>(sD, P, pc, acc, nullptr);
+            }
         }
         if constexpr (HC)
             block_reduce8<THREADS>(acc, red, part[par]);
@@ -280,12 +291,12 @@ cudaError_t launch_track_v<2>(const StreamDesc* const* descs, const int* users, 
     return launch_track_t<256, 2>(descs, users, S, cluster, init, results, s, pdl);
 }
 
-// the cached-Hessian variant is built for 256 threads only (it carries the
-// unrolled p x p patches too)
+// the cached-Hessian variant is built for 512 threads only (a p x p point is
+// split over kHcGroups threads, so it wants many threads per stream)
 template <>
 bool shape_ok_v<4>(int cluster, int threads)
 {
-    return threads == 256 && shape_ok_t<256, 4>(cluster);
+    return threads == 512 && shape_ok_t<512, 4>(cluster);
 }
 
 template <>
@@ -293,8 +304,8 @@ cudaError_t launch_track_v<4>(const StreamDesc* const* descs, const int* users, 
                               int threads, const double* init, glt_result* results, cudaStream_t s,
                               bool pdl)
 {
-    if (threads != 256) return cudaErrorInvalidValue;
-    return launch_track_t<256, 4>(descs, users, S, cluster, init, results, s, pdl);
+    if (threads != 512) return cudaErrorInvalidValue;
+    return launch_track_t<512, 4>(descs, users, S, cluster, init, results, s, pdl);
 }
 
 }  // namespace

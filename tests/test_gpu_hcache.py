@@ -134,6 +134,6 @@ def test_cached_hessian_arguments_are_checked(glt):
     ok = dict(CACHED, max_points=10)
     glt.Tracker(320, 240, K, **ok).close()
     for bad in (dict(jacobian="forward"), dict(affine=True), dict(lambda0=1e-4),
-                dict(precision="mixed"), dict(threads=128), dict(hessian=2)):
+                dict(precision="mixed"), dict(threads=256), dict(hessian=2)):
         with pytest.raises(glt.GltError):
             glt.Tracker(320, 240, K, **dict(ok, **bad))
