@@ -209,12 +209,15 @@ class SequenceDriver:
         self.ab = (0.0, 0.0)
         self.need_refresh = True
 
-    def init_for(self, k):
-        wl = self.wl
-        Tprev = self.Tw[k - 1]
+    def motion(self, k):
+        """The last inter-frame motion before frame k, T_{k-1} T_{k-2}^-1
+        (identity before two tracked frames)."""
         Tpp = self.Tw.get(k - 2)
-        A = pose_mul(Tprev, pose_inv(Tpp)) if Tpp is not None else I34
-        return pose_mul(pose_mul(A, Tprev), pose_inv(wl.T_ref_world(self.r)))
+        return pose_mul(self.Tw[k - 1], pose_inv(Tpp)) if Tpp is not None else I34
+
+    def init_for(self, k):
+        return pose_mul(pose_mul(self.motion(k), self.Tw[k - 1]),
+                        pose_inv(self.wl.T_ref_world(self.r)))
 
     def ab_init(self):
         return self.ab
@@ -268,29 +271,6 @@ def poses_orthonormalised(T):
     q1 = q1 / np.sqrt(np.sum(q1 * q1, axis=1, keepdims=True))
     out[:, 0, :3], out[:, 1, :3], out[:, 2, :3] = q0, q1, np.cross(q0, q1)
     return out
-
-
-def se3_logs(T):
-    """Batched SE(3) log (v, w) of (S, 3, 4) poses; the same closed form and
-    small-angle series as the proposal module's se3_log."""
-    R, t = T[:, :, :3], T[:, :, 3]
-    s = 0.5 * np.stack([R[:, 2, 1] - R[:, 1, 2], R[:, 0, 2] - R[:, 2, 0], R[:, 1, 0] - R[:, 0, 1]], 1)
-    c = 0.5 * (np.trace(R, axis1=1, axis2=2) - 1.0)
-    sn = np.linalg.norm(s, axis=1)
-    th = np.arctan2(sn, c)
-    w = np.where((sn < 1e-12)[:, None], s, s * (th / np.where(sn < 1e-12, 1.0, sn))[:, None])
-    Z = np.zeros_like(th)
-    W = np.stack([np.stack([Z, -w[:, 2], w[:, 1]], 1), np.stack([w[:, 2], Z, -w[:, 0]], 1),
-                  np.stack([-w[:, 1], w[:, 0], Z], 1)], 1)
-    th2 = th * th
-    small = th < 1e-3
-    ths = np.where(small, 1.0, th)
-    A = np.sin(ths) / ths
-    B = (1.0 - np.cos(ths)) / (ths * ths)
-    k = np.where(small, 1.0 / 12.0 + th2 / 720.0 + th2 * th2 / 30240.0,
-                 (1.0 - A / (2.0 * B)) / (ths * ths))
-    Vinv = np.eye(3)[None] - 0.5 * W + k[:, None, None] * np.matmul(W, W)
-    return np.concatenate([np.matmul(Vinv, t[:, :, None])[:, :, 0], w], 1)
 
 
 class BatchDriver:
@@ -349,14 +329,6 @@ class BatchDriver:
 
     def init_for(self):
         return poses_mul(poses_mul(self.motion(), self.Tk1), poses_inv(self.Tref))
-
-    def motion_features(self):
-        """The proposal network's motion input per stream (zeros before two frames)."""
-        out = np.zeros((self.S, 6), np.float32)
-        if self.has2.any():
-            from paper_2607_16897_gb300.proposal import MOTION_SCALE
-            out[self.has2] = (se3_logs(self.motion()[self.has2]) / MOTION_SCALE).astype(np.float32)
-        return out
 
     def record(self, k, T, a, b, status, n_valid, cost):
         Tw = poses_orthonormalised(poses_mul(T, self.Tref))
@@ -454,7 +426,8 @@ def oracle_track_sequence(wl, frames, inits=None, proposal=None, motions=None):
     pyramid+track, results, inits used).  inits: optional {k: (r, T_init, ab)}
     to replay exactly the GPU's initial states and references.  proposal:
     optional oracle network parameters (BF16-rounded, FP64) applied to each
-    initial state, with motions[k] the network's motion input."""
+    initial state, with motions[k] the inter-frame motion (3x4) behind the
+    network's motion input."""
     import oracle
     K = wl.cam.K
     trk = oracle.OracleTracker(wl.cam.W, wl.cam.H, K, levels=wl.L, jacobian=wl.jacobian, **wl.solver)
@@ -482,7 +455,8 @@ def oracle_track_sequence(wl, frames, inits=None, proposal=None, motions=None):
             # the composition of its output are the oracle's own arithmetic
             from oracle import nn as onn
             if motions is not None:
-                mk = np.asarray(motions[k], np.float64)
+                # the inter-frame motion the GPU run handed to its proposal stage
+                mk = onn.motion_input(np.asarray(motions[k], np.float64).reshape(3, 4))
             else:
                 mk = onn.motion_feature(drv.Tw.get(k - 1), drv.Tw.get(k - 2))
             x = (oracle.pyramid(wl.frames[k], wl.L)[-1].astype(np.float64) - ref_coarse) / 64.0
@@ -1035,8 +1009,9 @@ def run_batch(args):
     ptr_pin = torch.zeros(S, dtype=torch.int64).pin_memory()
     init_dev = torch.zeros((S, 14), dtype=torch.float64, device=dev)
     init_pin = torch.zeros((S, 14), dtype=torch.float64).pin_memory()
-    motion_dev = torch.zeros((S, 6), dtype=torch.float32, device=dev)
-    motion_pin = torch.zeros((S, 6), dtype=torch.float32).pin_memory()
+    # each stream's last inter-frame motion (3x4): the proposal stage's input
+    motion_dev = torch.zeros((S, 12), dtype=torch.float64, device=dev)
+    motion_pin = torch.zeros((S, 12), dtype=torch.float64).pin_memory()
     out_dev = torch.zeros(S * glt.RESULT_BYTES, dtype=torch.uint8, device=dev)
     out_pin = torch.zeros(S * glt.RESULT_BYTES, dtype=torch.uint8).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -1086,7 +1061,7 @@ def run_batch(args):
             init_np[s, :12] = d.init_for(k).ravel()
             init_np[s, 12:] = d.ab_init()
             if use_prop:
-                motion_np[s] = prop.motion_feature(d.Tw.get(k - 1), d.Tw.get(k - 2))
+                motion_np[s] = d.motion(k).ravel()
             ptr_np[s] = frame_ptrs[s][k]
 
     def finish(k, record):
@@ -1157,7 +1132,7 @@ def run_batch(args):
             init_np[:, :12] = bd.init_for().reshape(S, 12)
             init_np[:, 12:] = bd.ab
             if use_prop:
-                motion_np[:] = bd.motion_features()
+                motion_np[:] = bd.motion().reshape(S, 12)
             with torch.cuda.stream(stream):
                 step_dev.copy_(step_pin[k], non_blocking=True)
                 init_dev.copy_(init_pin, non_blocking=True)
@@ -1165,7 +1140,7 @@ def run_batch(args):
                     motion_dev.copy_(motion_pin, non_blocking=True)
                 batch.replay(stream=sh)
                 out_pin.copy_(out_dev, non_blocking=True)
-            h2d += step_pin[k].numel() + init_pin.numel() * 8 + (motion_pin.numel() * 4 if use_prop else 0)
+            h2d += step_pin[k].numel() + init_pin.numel() * 8 + (motion_pin.numel() * 8 if use_prop else 0)
             d2h += out_pin.numel()
             stream.synchronize()
             bd.record(k, res["T"].reshape(S, 3, 4), res["a"], res["b"], res["status"], res["n_valid"],

@@ -398,8 +398,9 @@ int glt_linearize_noalloc(const uint8_t* ref_dev, int ref_pitch, const uint8_t* 
  * frame with a constant-velocity guess only.  This optional stage maps the
  * coarsest-level residual image of a stream (current minus reference at the
  * identity warp, 40 x 30, divided by 64) and the stream's previous inter-frame
- * motion (a 6-vector: log of that motion divided by 0.02) to an increment of
- * the initial state, which then starts the same LM solve.
+ * motion (a 6-vector: log of that motion divided by 0.02, computed by the
+ * proposal stage from the motion itself) to an increment of the initial
+ * state, which then starts the same LM solve.
  * Network: 3 x (conv 3x3, stride 2, zero padding 1, ReLU) with 16, 32, 64
  * channels -> flatten (1280) ++ motion (6) -> fc 128 + ReLU -> fc 8.
  * The 8 outputs y give delta = (0.01 y[0..6], y[7]) and the proposal
@@ -468,15 +469,17 @@ int glt_nn_load(glt_nn* nn, const char* path);
 
 /* Attaches `nn` (or detaches it, nn = NULL) as the proposal stage of the
  * batch: from then on glt_batch_track and glt_batch_capture first build each
- * stream's residual image from its REF and CUR coarsest levels, run the
- * network on all S streams with the motions motion_dev[S][6] (a DEVICE array
- * read at run time) and start every stream's LM from the proposed state
- * instead of init_dev.  Every tracker of the batch needs a 40 x 30 coarsest
+ * stream's residual image from its REF and CUR coarsest levels, compute each
+ * stream's motion input log(M) / 0.02 in FP64 from motion_dev[S][12] (a DEVICE
+ * array of doubles read at run time: the last inter-frame motion M of every
+ * stream, row-major 3x4, as glt_state.motion holds it; the identity for a
+ * stream without two tracked frames), run the network on all S streams and
+ * start every stream's LM from the proposed state instead of init_dev.  Every tracker of the batch needs a 40 x 30 coarsest
  * level (640 x 480 with 5 levels, 320 x 240 with 4).  The batch references
  * the network, which must outlive it and must not be trained while the batch
  * uses it.  Invalidates a captured graph.  The autotuner ignores the stage.
  * Errors: INVALID_ARG (size, max_batch < S), CUDA. */
-int glt_batch_set_proposal(glt_batch* batch, glt_nn* nn, const float* motion_dev);
+int glt_batch_set_proposal(glt_batch* batch, glt_nn* nn, const double* motion_dev);
 
 /* Name of a return code (GLT_OK, GLT_ERR_*) or, for a positive value, of the
  * glt_result.status bits it holds ("ok", "too few points", "not positive

@@ -454,8 +454,9 @@ class Batch:
         return c.value, t.value, ms.value
 
     def set_proposal(self, nn, motion_dev):
-        """Attach a proposal network (``NN``) with per-stream motions
-        motion_dev [S, 6] (float32, device); ``nn=None`` detaches it."""
+        """Attach a proposal network (``NN``) with each stream's last
+        inter-frame motion motion_dev [S, 12] (row-major 3x4, float64, device,
+        read at every track); ``nn=None`` detaches it."""
         self._nn = nn
         self._motion = motion_dev
         _check(_lib.glt_batch_set_proposal(self.handle, nn.handle if nn is not None else None,

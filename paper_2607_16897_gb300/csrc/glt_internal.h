@@ -113,7 +113,7 @@ struct glt_batch {
     cudaGraphExec_t exec = nullptr;
     // learned initial-pose proposal (optional)
     glt_nn* nn = nullptr;
-    const float* motion_dev = nullptr;
+    const double* motion_dev = nullptr;   // [S][12] each stream's last inter-frame motion
     glt::PropJob* prop_jobs = nullptr;
     double* prop_init = nullptr;
 };

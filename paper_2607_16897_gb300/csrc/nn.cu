@@ -472,8 +472,64 @@ __device__ __forceinline__ void conv_block(const float* __restrict__ in, const _
     }
 }
 
+// Network motion input from the stream's last inter-frame motion M = [R | t]
+// (FP64, row-major 3x4): log(M) / 0.02 as (upsilon, omega).  The rotation
+// angle is atan2 of the skew part's half norm and (trace - 1) / 2; omega =
+// th / (2 sin th) vee(R - R^T) (its series below th = 1e-4; near pi the axis
+// comes from the symmetric part instead); upsilon = V^-1 t with
+// V^-1 = I - W/2 + k W^2, k = (1 - A / (2 B)) / th^2, A = sin th / th,
+// B = (1 - cos th) / th^2 (the series of k below th = 0.1).
+constexpr double kMotionScale = 0.02;
+
+__device__ void motion_feature(const double* __restrict__ M, float* __restrict__ f6)
+{
+    const double R[9] = {M[0], M[1], M[2], M[4], M[5], M[6], M[8], M[9], M[10]};
+    const double t[3] = {M[3], M[7], M[11]};
+    const double vee[3] = {R[7] - R[5], R[2] - R[6], R[3] - R[1]};
+    const double sn = 0.5 * sqrt(vee[0] * vee[0] + vee[1] * vee[1] + vee[2] * vee[2]);
+    const double cs = 0.5 * (R[0] + R[4] + R[8] - 1.0);
+    const double th = atan2(sn, cs);
+    const double pi = 3.14159265358979323846;
+    double w[3];
+    if (th < 1e-4) {
+        const double k = 0.5 * (1.0 + th * th / 6.0);
+        for (int i = 0; i < 3; ++i) w[i] = k * vee[i];
+    } else if (th < pi - 1e-4) {
+        const double k = th / (2.0 * sin(th));
+        for (int i = 0; i < 3; ++i) w[i] = k * vee[i];
+    } else {
+        int m = 0;
+        for (int i = 1; i < 3; ++i)
+            if (R[4 * i] > R[4 * m]) m = i;
+        const double d = sqrt(0.5 * (R[4 * m] + 1.0));
+        double a[3];
+        for (int i = 0; i < 3; ++i) a[i] = i == m ? d : 0.5 * (R[3 * i + m] + R[3 * m + i]) / (2.0 * d);
+        const double na = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+        const double sg = (a[0] * vee[0] + a[1] * vee[1] + a[2] * vee[2]) < 0.0 ? -1.0 : 1.0;
+        for (int i = 0; i < 3; ++i) w[i] = sg * th * a[i] / na;
+    }
+    const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double k;
+    if (th < 0.1) {
+        const double t4 = th2 * th2;
+        k = 1.0 / 12.0 + th2 / 720.0 + t4 / 30240.0 + t4 * th2 / 1209600.0;
+    } else {
+        const double sh = sin(0.5 * th);
+        const double A = sin(th) / th, B = 2.0 * sh * sh / th2;
+        k = (1.0 - A / (2.0 * B)) / th2;
+    }
+    // W = [w]x;  V^-1 t = t - (w x t) / 2 + k w x (w x t)
+    const double wt[3] = {w[1] * t[2] - w[2] * t[1], w[2] * t[0] - w[0] * t[2], w[0] * t[1] - w[1] * t[0]};
+    const double wwt[3] = {w[1] * wt[2] - w[2] * wt[1], w[2] * wt[0] - w[0] * wt[2],
+                           w[0] * wt[1] - w[1] * wt[0]};
+    for (int i = 0; i < 3; ++i) {
+        f6[i] = (float)((t[i] - 0.5 * wt[i] + k * wwt[i]) / kMotionScale);
+        f6[3 + i] = (float)(w[i] / kMotionScale);
+    }
+}
+
 __global__ void __launch_bounds__(kPropThreads)
-proposal_kernel(const PropJob* __restrict__ jobs, const float* __restrict__ motion,
+proposal_kernel(const PropJob* __restrict__ jobs, const double* __restrict__ motion,
                 const double* __restrict__ init, const __nv_bfloat16* __restrict__ w,
                 double* __restrict__ out)
 {
@@ -517,10 +573,11 @@ proposal_kernel(const PropJob* __restrict__ jobs, const float* __restrict__ moti
         xp[(r + 1) * 42 + (c + 1)] =
             ((float)J.cur[r * J.pitch + c] - (float)J.ref[r * J.pitch + c]) * (1.0f / 64.0f);
     }
-    if (tid < kMotion) f[kFlat + tid] = motion[s * kMotion + tid];
     __syncthreads();
     conv_block<1, 30, 40, 16, 4, true>(xp, w, kC1.w, kC1.b, a1);
     __syncthreads();
+    // the motion input, on a thread that conv2's 160 tiles leave idle
+    if (tid == kPropThreads - 1) motion_feature(motion + 12 * s, f + kFlat);
     conv_gemm<16, 15, 20, 32, 4, true>(a1, w2t, w, kC2.b, a2);
     __syncthreads();
     conv_gemm<32, 8, 10, 64, 2, false>(a2, w3t, w, kC3.b, f);
@@ -619,7 +676,7 @@ cudaError_t launch_proposal(glt_batch* b, const double* init_dev, cudaStream_t s
 
 extern "C" {
 
-int glt_batch_set_proposal(glt_batch* b, glt_nn* n, const float* motion_dev)
+int glt_batch_set_proposal(glt_batch* b, glt_nn* n, const double* motion_dev)
 {
     if (!b) return invalid_arg_msg("batch is NULL");
     if (b->exec) {

@@ -8,8 +8,10 @@ part; the proposal is this library's addition.  What it computes:
 
 * input 1: the coarsest-level (40 x 30) residual image at the identity warp,
   (I_cur - I_ref) / 64, formed on the device by the proposal stage;
-* input 2: the previous inter-frame motion, ``motion_feature``: the SE(3) log
-  of the last tracked camera motion (x_{k-1} = M x_{k-2}) divided by 0.02;
+* input 2: the previous inter-frame motion: the SE(3) log of the last tracked
+  camera motion (x_{k-1} = M x_{k-2}) divided by 0.02, computed on the device
+  by the proposal stage from M itself (``motion_feature`` computes the same
+  value on the host for the training set);
 * output: y (8 values), increment delta = (0.01 y[0:7], y[7]) applied as
   T' = T_init exp(delta[0:6]), a' = a + delta[6], b' = b + delta[7].
 
@@ -334,7 +336,7 @@ def evaluate(weights, seeds, frames=16, W=640, H=480, f=525.0, N=2000, L=5, inte
            for k, kw in forms.items()}
     batches = {k: Batch(trk[k]) for k in forms}
     net = NN(S, weights)
-    motion = torch.zeros((S, 6), dtype=torch.float32, device="cuda")
+    motion = torch.zeros((S, 12), dtype=torch.float64, device="cuda")   # M per stream
     batches["proposal"].set_proposal(net, motion)
     batches["init"].set_proposal(net, motion)
     cur = [torch.empty((H, W), dtype=torch.uint8, device="cuda") for _ in seeds]
@@ -363,7 +365,7 @@ def evaluate(weights, seeds, frames=16, W=640, H=480, f=525.0, N=2000, L=5, inte
             M = pose_mul(Tp, pose_inv(Tpp)) if Tpp is not None else np.hstack([np.eye(3), np.zeros((3, 1))])
             starts.append(np.concatenate([pose_mul(pose_mul(M, Tp), pose_inv(Tw[i][ref_k[i]])).ravel(),
                                           list(ab[i])]))
-            mot.append(motion_feature(Tp, Tpp))
+            mot.append(M.ravel())
             cur[i].copy_(torch.from_numpy(rendered[i][0]))
         init.copy_(torch.from_numpy(np.stack(starts)))
         motion.copy_(torch.from_numpy(np.stack(mot)))

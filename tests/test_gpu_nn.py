@@ -162,7 +162,10 @@ def test_proposal_stage_composes_network_output(glt, onn, orc, syn):
     """With every level's iteration budget at zero the batched tracker returns
     its initial state, so the output is the proposal itself:
     T_init exp(0.01 y[0:6]), a + 0.01 y[6], b + y[7] with y the network on the
-    coarsest-level residual image (cur - ref) / 64 and the stream's motion."""
+    coarsest-level residual image (cur - ref) / 64 and the motion input
+    log(M) / 0.02 the stage computes from each stream's inter-frame motion M
+    (the oracle's SE(3) log on the other side; one M near a half turn takes
+    the log's other branch, one is the identity)."""
     import torch
     specs = [(640, 480, 525.0, 5), (320, 240, 256.0, 4), (640, 480, 600.0, 5)]
     w = make_params(onn, 11)
@@ -184,10 +187,12 @@ def test_proposal_stage_composes_network_output(glt, onn, orc, syn):
         T = syn.relative(seq.T_wc[0], seq.T_wc[3])
         inits.append(np.concatenate([T.ravel(), rng.normal(0, 0.05, 1), rng.normal(0, 3, 1)]))
     S = len(specs)
-    motion = rng.normal(size=(S, 6)).astype(np.float32)
+    twists = [rng.normal(0, 0.02, 6), np.array([0.01, -0.02, 0.03, 0.0, 0.0, 3.1415]), np.zeros(6)]
+    Ms = [orc.se3_exp(t) for t in twists]
     batch = glt.Batch(trks)
-    md = dev(motion)
+    md = torch.tensor(np.stack([M.ravel() for M in Ms]), dtype=torch.float64).cuda()
     batch.set_proposal(net, md)
+    motion = np.stack([onn.motion_input(M) for M in Ms])
     ptrs = torch.tensor([c.data_ptr() for c in curs], dtype=torch.int64).cuda()
     init = torch.tensor(np.stack(inits), dtype=torch.float64).cuda()
     out = torch.zeros(S * glt.RESULT_BYTES, dtype=torch.uint8, device="cuda")
@@ -308,3 +313,70 @@ def test_training_loop_resumes_from_its_checkpoint(glt, onn, tmp_path):
     assert np.array_equal(w_full, w_res)
     assert info_full["best_step"] == info_res["best_step"]
     assert [tuple(h) for h in info_full["history"]] == info_res["history"]
+
+
+def test_proposal_form_at_full_size_matches_oracle(glt, onn, orc, syn):
+    """Two streams of the learned-proposal workload (640x480, 2000 points,
+    5 levels, fast motion), 6 frames each: the batch with the trained network
+    in front of the LM against the FP64 oracle network and the oracle tracker,
+    from the same constant-velocity starts and inter-frame motions."""
+    import torch
+    from paper_2607_16897_gb300.proposal import load_weights
+    from synth.jobs import stream_motion
+    from helpers import I34, pose_diff
+    w = load_weights()
+    pw = onn.unflatten(onn.to_bf16(w))
+    net = glt.NN(2, w)
+    S, N, L = 2, 2000, 5
+    cam = syn.camera_for(640, 480, 525.0)
+    seqs, trks, orcs, refs = [], [], [], []
+    for s in range(S):
+        v, a = stream_motion(5000 + s)
+        seq = syn.sequence(5000 + s, 24, cam, syn.ROOM_LARGE, v, a)
+        ref, uvd = syn.reference_points(seq, 0, N, 0.5, 8.0)
+        t = glt.Tracker(640, 480, cam.K, levels=L, max_points=N)
+        t.build_pyramid(glt.GLT_REF, ref)
+        t.set_map_points(uvd)
+        o = orc.OracleTracker(640, 480, cam.K, levels=L)
+        o.build_pyramid(0, ref)
+        o.set_map_points(uvd)
+        seqs.append(seq)
+        trks.append(t)
+        orcs.append(o)
+        refs.append(orc.pyramid(ref, L)[-1].astype(np.float64))
+    batch = glt.Batch(trks)
+    motion = torch.zeros((S, 12), dtype=torch.float64, device="cuda")
+    batch.set_proposal(net, motion)
+    init = torch.zeros((S, 14), dtype=torch.float64, device="cuda")
+    out = torch.zeros(S * glt.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    T_prev = [I34] * S
+    T_pp = [None] * S
+    ab = [(0.0, 0.0)] * S
+    for k in range(1, 7):
+        curs = [torch.from_numpy(seq.frame(k)[0]).cuda() for seq in seqs]
+        ptrs = torch.tensor([c.data_ptr() for c in curs], dtype=torch.int64, device="cuda")
+        Ms = [syn.pose_mul(T_prev[s], syn.pose_inv(T_pp[s])) if T_pp[s] is not None else I34
+              for s in range(S)]
+        T0 = [syn.pose_mul(Ms[s], T_prev[s]) for s in range(S)]
+        init.copy_(torch.tensor(np.stack([np.concatenate([T0[s].ravel(), ab[s]]) for s in range(S)])))
+        motion.copy_(torch.tensor(np.stack([M.ravel() for M in Ms])))
+        batch.build_pyramid(ptrs)
+        batch.track(init, out)
+        torch.cuda.synchronize()
+        res = glt.parse_results(out)
+        for s in range(S):
+            cur = curs[s].cpu().numpy()
+            x = (orc.pyramid(cur, L)[-1].astype(np.float64) - refs[s]) / 64.0
+            y, _ = onn.forward(pw, x[None, None], onn.motion_input(Ms[s])[None])
+            Tp, abp = onn.apply_output(T0[s], ab[s], y[0])
+            orcs[s].build_pyramid(1, cur)
+            r = orcs[s].track_frame(Tp, abp)
+            ang, dt = pose_diff(res[s]["T"], r["T"])
+            assert ang <= 1e-5 and dt <= 1e-5, (s, k, ang, dt)
+            assert abs(res[s]["a"] - r["a"]) <= 1e-5 and abs(res[s]["b"] - r["b"]) <= 1e-3
+            assert res[s]["status"] == r["status"] == 0
+            T_pp[s], T_prev[s], ab[s] = T_prev[s], res[s]["T"], (res[s]["a"], res[s]["b"])
+    batch.close()
+    for t in trks:
+        t.close()
+    net.close()
