@@ -1169,6 +1169,7 @@ def run_batch(args):
         shape = (c, t, None)
     else:
         shape = batch.autotune(init_dev, out_dev, reps=3, stream=sh)
+    classes = batch.classes()
 
     def measure(form):
         """Captures the step graph of `form` ("plain" / "proposal") and times it."""
@@ -1261,7 +1262,9 @@ def run_batch(args):
                            "global_batch": world * S, "streams_per_gpu": S,
                            "parallelism": f"replicas x{world}",
                            "autotuned_shape": {"cluster": shape[0], "threads": shape[1],
-                                               "ms": shape[2]},
+                                               "ms": shape[2],
+                                               "heavy_streams": classes["heavy"],
+                                               "light_shape": list(classes["light_shape"])},
                            "l2": "flushed between steps (256 MB write, outside the step events)",
                            "timing": "sum of per-step CUDA-event times around the graph replay"},
                 "step_ms_percentiles": step_percentiles(dev_ms),

@@ -354,14 +354,40 @@ int glt_batch_capture(glt_batch* batch, const uint8_t* const* frames_dev, const 
 /* Replays the captured graph on `stream`.  Errors: INVALID_ARG if none. */
 int glt_batch_replay(glt_batch* batch, void* stream);
 
-/* Autotuner: times the batched track over the candidate (cluster, threads)
- * shapes on the current inputs (replaying `reps` times each), keeps the
- * fastest, and reports it.  Synchronous; invalidates a captured graph. */
+/* Autotuner: times the batched track on the current inputs (`reps` timed
+ * launches each) over the candidate launch configurations and keeps the
+ * fastest: one (cluster, threads) shape for every stream, or two launch
+ * classes (see glt_batch_set_classes) with the first quarter or half of the
+ * launch order as the heavy class on a wide shape and the rest on a narrow
+ * one.  Results are cached for the process, keyed by the batch's signature
+ * (kernel variant and, in launch order, every stream's width, height, point
+ * capacity and levels): a batch with a known signature takes the cached
+ * configuration without timing.  Reports the heavy class's shape (the only
+ * one for a single class) and the measured ms per track.  Synchronous;
+ * invalidates a captured graph.  The proposal stage is not timed. */
 int glt_batch_autotune(glt_batch* batch, const double* init_dev, glt_result* out_dev, int reps,
                        int* best_cluster, int* best_threads, float* best_ms, void* stream);
 
-/* Sets the (cluster, threads) shape used by glt_batch_track / capture. */
+/* Sets one (cluster, threads) shape for every stream of the batch.
+ * Invalidates a captured graph. */
 int glt_batch_set_shape(glt_batch* batch, int cluster, int threads);
+
+/* Launch classes: the streams in the batch's launch order (heaviest first,
+ * by point capacity times samples per point, then frame width) split into a
+ * heavy class, the first
+ * `heavy` streams, tracked with (heavy_cluster, heavy_threads), and a light
+ * class, the rest, with (light_cluster, light_threads).  The two classes run
+ * as concurrent launches: glt_batch_track forks the light class onto an
+ * internal stream and joins it back into the caller's stream; a captured
+ * graph holds them as parallel nodes.  heavy = S (or 0) is one launch with
+ * the heavy (light) shape.  Invalidates a captured graph.
+ * Errors: INVALID_ARG (heavy outside [0, S], a shape that cannot launch). */
+int glt_batch_set_classes(glt_batch* batch, int heavy, int heavy_cluster, int heavy_threads,
+                          int light_cluster, int light_threads);
+
+/* The batch's current launch classes (any pointer may be NULL). */
+int glt_batch_get_classes(const glt_batch* batch, int* heavy, int* heavy_cluster,
+                          int* heavy_threads, int* light_cluster, int* light_threads);
 
 /* Allocation-free linearisation.  The paper has no counterpart.  It serves
  * callers that may not allocate device memory at the point where they need a

@@ -116,6 +116,8 @@ SIGNATURES = {
     "glt_batch_replay": (_i, [_vp, _vp]),
     "glt_batch_autotune": (_i, [_vp, _vp, _vp, _i, _P(_i), _P(_i), _P(ctypes.c_float), _vp]),
     "glt_batch_set_shape": (_i, [_vp, _i, _i]),
+    "glt_batch_set_classes": (_i, [_vp, _i, _i, _i, _i, _i]),
+    "glt_batch_get_classes": (_i, [_vp, _P(_i), _P(_i), _P(_i), _P(_i), _P(_i)]),
     "glt_linearize_noalloc": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _d, _d, _d, _d, _vp, _i, _P(_d),
                                    _d, _d, _d, _d, _vp, _vp]),
     "glt_nn_create": (_i, [_i, _P(_vp)]),
@@ -445,6 +447,20 @@ class Batch:
     def set_shape(self, cluster, threads):
         _check(_lib.glt_batch_set_shape(self.handle, int(cluster), int(threads)),
                "glt_batch_set_shape")
+
+    def set_classes(self, heavy, heavy_shape, light_shape):
+        """Two launch classes: the first `heavy` streams of the launch order
+        with heavy_shape = (cluster, threads), the rest with light_shape."""
+        _check(_lib.glt_batch_set_classes(self.handle, int(heavy), int(heavy_shape[0]),
+                                          int(heavy_shape[1]), int(light_shape[0]),
+                                          int(light_shape[1])), "glt_batch_set_classes")
+
+    def classes(self) -> dict:
+        v = [ctypes.c_int() for _ in range(5)]
+        _check(_lib.glt_batch_get_classes(self.handle, *[ctypes.byref(x) for x in v]),
+               "glt_batch_get_classes")
+        return {"heavy": v[0].value, "heavy_shape": (v[1].value, v[2].value),
+                "light_shape": (v[3].value, v[4].value)}
 
     def autotune(self, init_dev, out_dev, reps=3, stream=None):
         c, t, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()

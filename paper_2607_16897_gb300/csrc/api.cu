@@ -5,6 +5,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -35,6 +37,14 @@ static int invalid(const char* msg)
     } while (0)
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Autotuner results of this process, keyed by the batch signature.
+struct TuneResult {
+    int heavy, cluster, threads, cluster_light, threads_light;
+    float ms;
+};
+static std::mutex g_tune_mutex;
+static std::map<std::string, TuneResult> g_tune_cache;
 
 static void set_identity(double T[12])
 {
@@ -769,6 +779,9 @@ static void free_batch(glt_batch* b)
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->aux) cudaStreamDestroy(b->aux);
     cudaFree(b->descs_dev);
     cudaFree(b->users_dev);
     cudaFree(b->copy_dev);
@@ -799,11 +812,13 @@ int glt_batch_create(glt_tracker* const* trackers, int S, glt_batch** out)
     b->trk.assign(trackers, trackers + S);
     b->order.resize(S);
     for (int i = 0; i < S; ++i) b->order[i] = i;
-    // longest streams first (points x level-0 pixels as the work estimate)
+    // heaviest streams first: a pass costs about its residual samples (point
+    // capacity x samples per point); the frame size breaks ties
     std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
-        const double wx = (double)trackers[x]->cfg.max_points * trackers[x]->cfg.width;
-        const double wy = (double)trackers[y]->cfg.max_points * trackers[y]->cfg.width;
-        return wx > wy;
+        const double wx = (double)trackers[x]->cfg.max_points * trackers[x]->K;
+        const double wy = (double)trackers[y]->cfg.max_points * trackers[y]->K;
+        if (wx != wy) return wx > wy;
+        return trackers[x]->cfg.width > trackers[y]->cfg.width;
     });
     for (int i = 0; i < S; ++i) b->Lmax = std::max(b->Lmax, trackers[i]->L);
 #define BALLOC(call)                                  \
@@ -893,8 +908,55 @@ int glt_batch_create(glt_tracker* const* trackers, int S, glt_batch** out)
     }
     if (b->variant == 4) b->threads = 512;   // the cached-Hessian kernel's only width
     if (!track_shape_ok(b->cluster, b->threads, b->variant)) b->cluster = 1;
+    b->heavy = S;
+    b->cluster_light = b->cluster;
+    b->threads_light = b->threads;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return cuda_fail(e, "batch stream / events");
+    }
     *out = b;
     return GLT_OK;
+}
+
+// The track launch(es) of a batch: one launch when every stream is in class
+// 0, else class 0 on `s` and class 1 on the auxiliary stream, forked from and
+// joined back into `s` (under stream capture: two parallel graph nodes).
+// pdl applies to the single-launch form only.
+static cudaError_t launch_batch_track(glt_batch* b, const double* init, glt_result* out,
+                                      cudaStream_t s, bool pdl)
+{
+    if (b->heavy >= b->S || b->heavy <= 0) {
+        const int cl = b->heavy <= 0 ? b->cluster_light : b->cluster;
+        const int th = b->heavy <= 0 ? b->threads_light : b->threads;
+        return launch_track(b->descs_dev, b->users_dev, b->S, cl, th, b->variant, init, out, s, pdl);
+    }
+    cudaError_t e = cudaEventRecord(b->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_fork, 0);
+    if (e == cudaSuccess)
+        e = launch_track(b->descs_dev, b->users_dev, b->heavy, b->cluster, b->threads, b->variant,
+                         init, out, s, false);
+    if (e == cudaSuccess)
+        e = launch_track(b->descs_dev + b->heavy, b->users_dev + b->heavy, b->S - b->heavy,
+                         b->cluster_light, b->threads_light, b->variant, init, out, b->aux, false);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join, 0);
+    return e;
+}
+
+static void drop_graph(glt_batch* b)
+{
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
 }
 
 void glt_batch_destroy(glt_batch* b) { free_batch(b); }
@@ -957,9 +1019,7 @@ int glt_batch_track(glt_batch* b, const double* init_dev, glt_result* out_dev, v
         GLT_CHECK(launch_proposal(b, init_dev, s), "proposal kernels");
         init_dev = b->prop_init;
     }
-    GLT_CHECK(launch_track(b->descs_dev, b->users_dev, b->S, b->cluster, b->threads,
-                           b->variant, init_dev, out_dev, s),
-              "batch track kernel");
+    GLT_CHECK(launch_batch_track(b, init_dev, out_dev, s, false), "batch track kernel");
     return GLT_OK;
 }
 
@@ -990,9 +1050,7 @@ int glt_batch_capture(glt_batch* b, const uint8_t* const* frames_dev, const doub
     // kernel as its programmatic dependent (its setup overlaps the pyramids);
     // after the proposal stage it reads that stage's output from its first
     // instruction, so it waits as usual
-    if (e1 == cudaSuccess)
-        e1 = launch_track(b->descs_dev, b->users_dev, b->S, b->cluster, b->threads,
-                          b->variant, init_dev, out_dev, s, b->nn == nullptr);
+    if (e1 == cudaSuccess) e1 = launch_batch_track(b, init_dev, out_dev, s, b->nn == nullptr);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
     if (r1 != GLT_OK) {
@@ -1020,8 +1078,39 @@ int glt_batch_set_shape(glt_batch* b, int cluster, int threads)
 {
     if (!b) return invalid("batch is NULL");
     if (!track_shape_ok(cluster, threads, b->variant)) return invalid("shape cannot launch");
-    b->cluster = cluster;
-    b->threads = threads;
+    b->cluster = b->cluster_light = cluster;
+    b->threads = b->threads_light = threads;
+    b->heavy = b->S;
+    drop_graph(b);
+    return GLT_OK;
+}
+
+int glt_batch_set_classes(glt_batch* b, int heavy, int heavy_cluster, int heavy_threads,
+                          int light_cluster, int light_threads)
+{
+    if (!b) return invalid("batch is NULL");
+    if (heavy < 0 || heavy > b->S) return invalid("heavy must be in [0, S]");
+    if ((heavy > 0 && !track_shape_ok(heavy_cluster, heavy_threads, b->variant)) ||
+        (heavy < b->S && !track_shape_ok(light_cluster, light_threads, b->variant)))
+        return invalid("shape cannot launch");
+    b->heavy = heavy;
+    b->cluster = heavy > 0 ? heavy_cluster : light_cluster;
+    b->threads = heavy > 0 ? heavy_threads : light_threads;
+    b->cluster_light = heavy < b->S ? light_cluster : b->cluster;
+    b->threads_light = heavy < b->S ? light_threads : b->threads;
+    drop_graph(b);
+    return GLT_OK;
+}
+
+int glt_batch_get_classes(const glt_batch* b, int* heavy, int* heavy_cluster, int* heavy_threads,
+                          int* light_cluster, int* light_threads)
+{
+    if (!b) return invalid("batch is NULL");
+    if (heavy) *heavy = b->heavy;
+    if (heavy_cluster) *heavy_cluster = b->cluster;
+    if (heavy_threads) *heavy_threads = b->threads;
+    if (light_cluster) *light_cluster = b->cluster_light;
+    if (light_threads) *light_threads = b->threads_light;
     return GLT_OK;
 }
 
@@ -1032,55 +1121,90 @@ int glt_batch_autotune(glt_batch* b, const double* init_dev, glt_result* out_dev
     if (rc != GLT_OK) return rc;
     if (!init_dev || !out_dev || reps < 1) return invalid("bad argument");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int shapes[][2] = {{1, 128}, {1, 256}, {2, 128}, {2, 256}, {4, 128}, {4, 256},
-                             {8, 128}, {8, 256}, {1, 512}, {2, 512}, {4, 512}, {8, 512}};
-    cudaEvent_t e0, e1;
-    GLT_CHECK(cudaEventCreate(&e0), "event");
-    GLT_CHECK(cudaEventCreate(&e1), "event");
-    float best = 1e30f;
-    int bc = b->cluster, bt = b->threads;
-    const int variant = b->variant;
-    for (auto& sh : shapes) {
-        if (!track_shape_ok(sh[0], sh[1], variant)) continue;
-        cudaError_t e = launch_track(b->descs_dev, b->users_dev, b->S, sh[0], sh[1], variant, init_dev, out_dev, s);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < reps; ++r)
-            launch_track(b->descs_dev, b->users_dev, b->S, sh[0], sh[1], variant, init_dev, out_dev, s);
-        cudaEventRecord(e1, s);
-        cudaError_t es = cudaEventSynchronize(e1);
-        if (es != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return cuda_fail(es, "autotune");
-        }
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= reps;
-        if (ms < best) {
-            best = ms;
-            bc = sh[0];
-            bt = sh[1];
+    // the batch's signature: kernel variant and, in launch order, every
+    // stream's frame size, point capacity and level count
+    std::string key = std::to_string(b->variant);
+    for (int i = 0; i < b->S; ++i) {
+        const glt_tracker* t = b->trk[b->order[i]];
+        key += "|" + std::to_string(t->W[0]) + "x" + std::to_string(t->H[0]) + "x" +
+               std::to_string(t->cfg.max_points) + "x" + std::to_string(t->L);
+    }
+    TuneResult best{};
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            best = it->second;
+            cached = true;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    b->cluster = bc;
-    b->threads = bt;
-    if (b->exec) {
-        cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
+    if (!cached) {
+        // candidates: one shape for every stream, then a heavy class (the
+        // first quarter or half of the launch order) with a wide shape and
+        // the light rest with a narrow one, run concurrently
+        const int uniform[][2] = {{1, 128}, {1, 256}, {2, 128}, {2, 256}, {4, 128}, {4, 256},
+                                  {8, 128}, {8, 256}, {1, 512}, {2, 512}, {4, 512}, {8, 512}};
+        const int wide[][2] = {{8, 128}, {16, 128}, {8, 256}, {4, 512}, {8, 512}};
+        const int narrow[][2] = {{1, 128}, {2, 128}, {4, 128}, {8, 128}, {2, 256}, {2, 512}};
+        std::vector<TuneResult> cands;
+        for (auto& u : uniform)
+            if (track_shape_ok(u[0], u[1], b->variant)) cands.push_back({b->S, u[0], u[1], u[0], u[1], 0.f});
+        if (b->S >= 4) {
+            for (int part = 4; part >= 2; part /= 2) {
+                const int heavy = std::max(1, b->S / part);
+                for (auto& w : wide) {
+                    if (!track_shape_ok(w[0], w[1], b->variant)) continue;
+                    for (auto& n : narrow)
+                        if (track_shape_ok(n[0], n[1], b->variant))
+                            cands.push_back({heavy, w[0], w[1], n[0], n[1], 0.f});
+                }
+            }
+        }
+        cudaEvent_t e0, e1;
+        GLT_CHECK(cudaEventCreate(&e0), "event");
+        GLT_CHECK(cudaEventCreate(&e1), "event");
+        best.ms = 1e30f;
+        for (TuneResult& c : cands) {
+            b->heavy = c.heavy;
+            b->cluster = c.cluster;
+            b->threads = c.threads;
+            b->cluster_light = c.cluster_light;
+            b->threads_light = c.threads_light;
+            cudaError_t e = launch_batch_track(b, init_dev, out_dev, s, false);   // warm-up
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps; ++r) launch_batch_track(b, init_dev, out_dev, s, false);
+            cudaEventRecord(e1, s);
+            cudaError_t es = cudaEventSynchronize(e1);
+            if (es != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_fail(es, "autotune");
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            c.ms = ms / reps;
+            if (c.ms < best.ms) best = c;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (best.ms >= 1e30f) return invalid("no shape could launch");
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = best;
     }
-    if (b->graph) {
-        cudaGraphDestroy(b->graph);
-        b->graph = nullptr;
-    }
-    if (best_cluster) *best_cluster = bc;
-    if (best_threads) *best_threads = bt;
-    if (best_ms) *best_ms = best;
+    b->heavy = best.heavy;
+    b->cluster = best.cluster;
+    b->threads = best.threads;
+    b->cluster_light = best.cluster_light;
+    b->threads_light = best.threads_light;
+    drop_graph(b);
+    if (best_cluster) *best_cluster = best.cluster;
+    if (best_threads) *best_threads = best.threads;
+    if (best_ms) *best_ms = best.ms;
     return GLT_OK;
 }
 

@@ -108,7 +108,15 @@ struct glt_batch {
     glt::PackJob* pack_dev = nullptr;     // [Lmax][S]
     int Lmax = 0;
     int variant = 0;                      // kernel variant (track_variant of the streams)
-    int cluster = 2, threads = 256;
+    // launch classes over the launch order: class 0 = the first `heavy`
+    // streams (all of them when heavy = S), class 1 = the rest, each with its
+    // own (cluster, threads); the two run as concurrent launches (graph
+    // branches), class 1 on the batch's auxiliary stream
+    int heavy = 0;
+    int cluster = 2, threads = 256;       // class 0
+    int cluster_light = 2, threads_light = 256;   // class 1
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     // learned initial-pose proposal (optional)

@@ -2,6 +2,8 @@
 tracked in one persistent launch (and one CUDA-graph replay) must each agree
 with the FP64 oracle run on the same stream alone (pose within 1e-5 rad /
 1e-5 m)."""
+import time
+
 import numpy as np
 import pytest
 
@@ -46,12 +48,14 @@ def make_streams(syn, orc, glt, precision):
     return streams
 
 
-def run_batch(glt, streams, shape=None, graph=False):
+def run_batch(glt, streams, shape=None, graph=False, classes=None):
     import torch
     S = len(streams)
     batch = glt.Batch([s["trk"] for s in streams])
     if shape:
         batch.set_shape(*shape)
+    if classes:
+        batch.set_classes(*classes)
     ptrs = torch.tensor([s["cur"].data_ptr() for s in streams], dtype=torch.int64).cuda()
     init = torch.tensor(np.stack([np.concatenate([s["T_init"].ravel(), [0.0, 0.0]])
                                   for s in streams]), dtype=torch.float64).cuda()
@@ -112,11 +116,52 @@ def test_autotune_picks_a_valid_shape(glt, orc, syn):
                                   for s in streams]), dtype=torch.float64).cuda()
     out = torch.zeros(len(streams) * glt.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     batch.build_pyramid(ptrs)
+    t0 = time.perf_counter()
     c, t, ms = batch.autotune(init, out, reps=2)
-    assert c in (1, 2, 4, 8) and t in (128, 256, 512) and ms > 0
+    first = time.perf_counter() - t0
+    assert c in (1, 2, 4, 8, 16) and t in (128, 256, 512) and ms > 0
+    cls = batch.classes()
+    assert 1 <= cls["heavy"] <= len(streams) and cls["heavy_shape"] == (c, t)
+    # the tuned configuration tracks every stream to the oracle's pose
+    batch.build_pyramid(ptrs)
+    batch.track(init, out)
+    torch.cuda.synchronize()
+    for s, g in zip(streams, glt.parse_results(out)):
+        o = s["orc"].track_frame(s["T_init"])
+        ang, dt = pose_diff(g["T"], o["T"])
+        assert ang <= ROT_TOL and dt <= TRANS_TOL, (cls, ang, dt)
+    # a second batch with the same signature takes the cached result untimed
+    other = glt.Batch([s["trk"] for s in streams])
+    t0 = time.perf_counter()
+    assert other.autotune(init, out, reps=2) == (c, t, ms)
+    assert time.perf_counter() - t0 < 0.25 * first
+    assert other.classes() == cls
+    other.close()
     with pytest.raises(glt.GltError):
         batch.set_shape(3, 100)
+    with pytest.raises(glt.GltError):
+        batch.set_classes(len(streams) + 1, (2, 128), (1, 128))
     batch.close()
+    for s in streams:
+        s["trk"].close()
+
+
+def test_two_launch_classes_match_oracle_and_graph(glt, orc, syn):
+    """A heavy class (the first streams of the launch order) on a wide shape
+    and the light rest on a narrow one, as two concurrent launches: direct
+    launches and graph replay agree bit for bit, and every stream matches the
+    oracle."""
+    streams = make_streams(syn, orc, glt, "fp32")
+    for classes in [(2, (8, 128), (1, 128)), (3, (16, 128), (2, 256)), (1, (4, 256), (1, 512))]:
+        direct = run_batch(glt, streams, classes=classes)
+        graph = run_batch(glt, streams, classes=classes, graph=True)
+        for d, g in zip(direct, graph):
+            assert np.array_equal(d["T"], g["T"]) and d["passes"] == g["passes"], classes
+        for i, (s, g) in enumerate(zip(streams, direct)):
+            o = s["orc"].track_frame(s["T_init"])
+            ang, dt = pose_diff(g["T"], o["T"])
+            assert ang <= ROT_TOL and dt <= TRANS_TOL, (classes, i, ang, dt)
+            assert g["status"] == o["status"], (classes, i)
     for s in streams:
         s["trk"].close()
 
