@@ -106,6 +106,9 @@ def parse():
     ap.add_argument("--no-launch-overhead", action="store_true",
                     help="skip the launch-overhead measurement (e.g. for a profiler's launch list)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--table3", action="store_true",
+                    help="print the direct-tracking acceptance over a sweep of motion speeds and "
+                         "exposure jumps (the Table III analogue) instead of a benchmark line")
     ap.add_argument("--no-batched", action="store_true",
                     help="default workload only: skip the batched forms (C3, C5 plain and "
                          "learned) that the line otherwise carries under 'batched'")
@@ -1358,6 +1361,74 @@ def batch_cpu_baseline(wls, rec, frames_per_stream=8, proposal=None):
     return cpu, parity
 
 
+# the sweep behind the Table III analogue: mean camera speeds (m/s, deg/s)
+# and exposure jumps (gray levels added to, then taken off, the offset b every
+# third frame)
+TABLE3_MOTION = [(0.5, 30.0), (1.0, 45.0), (2.0, 90.0), (3.0, 135.0), (4.0, 180.0)]
+TABLE3_JUMPS = [0.0, 40.0]
+
+
+def table3(args):
+    """Direct-tracking acceptance on sequences of rising difficulty, the
+    quantity of the paper's Table III (Sec. IV-D): per setting, 16 streams of
+    640x480 (f 525, 2000 points, 4 levels, 24 frames) tracked by the batched
+    GPU tracker with the tween-frame switch of the sequence driver (a frame is
+    accepted if its status is clean, at least half of its samples are valid
+    and its mean Huber energy is at most 2.5; a rejected frame and every 8th
+    frame go to the indirect pipeline, which here is the renderer's truth)."""
+    import torch
+    import paper_2607_16897_gb300 as glt
+    S, F = 16, 24
+    out = torch.zeros(S * glt.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    rows = []
+    for speed, ang in TABLE3_MOTION:
+        for jump in TABLE3_JUMPS:
+            wls = [Workload(seed=7000 + s, frames=F, N=2000, W=640, H=480, f=525.0, L=4,
+                            speed=speed, ang=ang, render=False, label="Table III sweep stream")
+                   for s in range(S)]
+            for w in wls:
+                if jump:
+                    w.seq.b = w.seq.b + jump * ((np.arange(F) // 3) % 2)
+                w.frames = [w.seq.frame(k)[0] for k in range(F)]
+            trks = [glt.Tracker(640, 480, w.cam.K, levels=4, max_points=2000) for w in wls]
+            batch = glt.Batch(trks)
+            frames = [torch.from_numpy(np.stack(w.frames)).cuda() for w in wls]
+            bd = BatchDriver(wls)
+            errs = []
+            for k in range(1, F):
+                for s in bd.refresh(k - 1):
+                    trks[s].build_pyramid(glt.GLT_REF, frames[s][bd.r[s]])
+                    trks[s].set_map_points(wls[s].ref_points(int(bd.r[s])))
+                init = np.concatenate([bd.init_for().reshape(S, 12), bd.ab], 1)
+                ptrs = torch.tensor([frames[s][k].data_ptr() for s in range(S)], dtype=torch.int64,
+                                    device="cuda")
+                batch.build_pyramid(ptrs)
+                batch.track(torch.from_numpy(init).cuda(), out)
+                res = glt.parse_results(out)
+                before = bd.accepted.copy()
+                ref_used = bd.r.copy()
+                bd.record(k, np.stack([r["T"] for r in res]), np.array([r["a"] for r in res]),
+                          np.array([r["b"] for r in res]), np.array([r["status"] for r in res]),
+                          np.array([r["n_valid"] for r in res]), np.array([r["cost"] for r in res]))
+                for s in np.nonzero(bd.accepted > before)[0]:
+                    errs.append(pose_error(wls[s], k, int(ref_used[s]), res[s]["T"]))
+            step = [np.linalg.norm(w.seq.T_wc[k + 1][:, 3] - w.seq.T_wc[k][:, 3]) for w in wls
+                    for k in range(F - 1)]
+            acc, rej = int(bd.accepted.sum()), int(bd.rejected.sum())
+            rows.append({"speed_mps": speed, "ang_dps": ang, "exposure_jump": jump,
+                         "mean_step_cm": 100.0 * float(np.mean(step)),
+                         "frames": acc + rej, "accepted": acc, "rejected": rej,
+                         "acceptance": acc / max(1, acc + rej),
+                         "accepted_median_trans_mm": 1000.0 * float(np.median([e[1] for e in errs]))
+                         if errs else None})
+            batch.close()
+            for t in trks:
+                t.close()
+    print(json.dumps({"metric": "direct-tracking acceptance (Table III analogue)", "unit": "fraction",
+                      "data": "synthetic", "streams_per_setting": S, "frames_per_stream": F,
+                      "rows": rows}), flush=True)
+
+
 _GROUP = {}
 
 
@@ -1397,6 +1468,9 @@ def nested_batched(args):
 
 def main():
     args = parse()
+    if args.table3:
+        table3(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
