@@ -29,6 +29,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLOPS_PER_SAMPLE = 160      # algorithmic FP32 flops per residual sample per pass
+# the cached-Hessian form: bilinear sample (7), residual and Huber weight (6), the
+# two gradient-weighted sums (4), energy and count (2), the per-point fold amortised (1)
+FLOPS_PER_SAMPLE_CACHED = 20
+
+
+def samples_per_point(wl):
+    p = wl.solver.get("pattern", 0)
+    return 8 if p == 0 else p * p
+
+
+def flops_per_sample(wl):
+    return FLOPS_PER_SAMPLE_CACHED if wl.solver.get("hessian") == "cached" else FLOPS_PER_SAMPLE
 # DRAM bytes (read + write) per track_kernel launch, measured with ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
 # launch as in the timed steps) on the workload named by the key; a value is
@@ -674,17 +686,28 @@ def run_ours(args):
 
     # roofline of the dominant kernel (the persistent tracker)
     mean_trk = statistics.mean(trk_ms) / 1000.0
-    samples_per_launch = statistics.mean(p * 8 * N for p in passes)
-    achieved = FLOPS_PER_SAMPLE * samples_per_launch / mean_trk / 1e12
+    samples_per_launch = statistics.mean(p * samples_per_point(wl) * N for p in passes)
+    achieved = flops_per_sample(wl) * samples_per_launch / mean_trk / 1e12
     peaks, src = measured_peaks()
     peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    # the chain's own yardstick: the fixed part of a pass (reduction, cluster
+    # barrier, distributed-shared-memory finish, FP64 tail) with no points
+    cl, th = trk.shape()
+    floor_us = glt.pass_floor(cl, th, cached=wl.solver.get("hessian") == "cached", stream=sh)
+    floor_ms = statistics.mean(passes) * floor_us / 1000.0
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": TRACK_TRAFFIC.get(args.workload),
             "kernel": "track_kernel",
             "peak_source": f"FP32 FMA peak from unit counts (152 SMs x 128 lanes x 2) at "
                            f"{peaks.get('sm_max_mhz', 2070.0):g} MHz ({src} clock)",
             "launch_ms": statistics.mean(trk_ms), "passes_per_launch": statistics.mean(passes),
-            "samples_per_launch": samples_per_launch}
+            "samples_per_launch": samples_per_launch, "flops_per_sample": flops_per_sample(wl),
+            "latency_floor": {"us_per_pass": floor_us, "shape": [cl, th],
+                              "floor_ms_per_launch": floor_ms,
+                              "frac": floor_ms / statistics.mean(trk_ms),
+                              "what": "passes x (block reduction + cluster barrier + "
+                                      "distributed-shared-memory finish + FP64 tail) with no "
+                                      "points (glt_debug_pass_floor), over the measured launch"}}
     if rank == 0:
         line = {"metric": "frames tracked/s", "value": value, "unit": "frames/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -1236,8 +1259,9 @@ def run_batch(args):
             pw = onn.unflatten(onn.to_bf16(proposal_weights()))
         cpu, parity = batch_cpu_baseline(wls, rec, proposal=pw)
     # roofline of the persistent tracker (the graph's dominant kernel)
-    samples = sum(r[4]["passes"] * 8 * wls[r[0]].N for r in rec) / args.steps
-    achieved = FLOPS_PER_SAMPLE * samples / (dev_s / args.steps) / 1e12
+    samples = sum(r[4]["passes"] * samples_per_point(wls[r[0]]) * wls[r[0]].N for r in rec) / args.steps
+    achieved = sum(r[4]["passes"] * samples_per_point(wls[r[0]]) * wls[r[0]].N * flops_per_sample(wls[r[0]])
+                   for r in rec) / args.steps / (dev_s / args.steps) / 1e12
     peaks, src = measured_peaks()
     peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
     if rank == 0:

@@ -311,6 +311,25 @@ int glt_set_state(glt_tracker* trk, const glt_state* in);
  * Asynchronous.  Errors: INVALID_ARG (n < 0, NULL with n > 0), CUDA. */
 int glt_debug_rcp(const double* d_dev, double* r_dev, int n, void* stream);
 
+/* Latency floor of one tracker pass: times (CUDA events, after one warm-up
+ * launch) a launch of one stream's cluster (`cluster` CTAs of `threads`
+ * threads) that runs `passes` passes of the track kernel's fixed part --
+ * the block reduction, the cluster barrier, the distributed-shared-memory
+ * finish and the FP64 tail (the LM decision, the solve -- the L D L^T
+ * factorisation, or with `cached` the product with a cached H^-1 -- and
+ * the SE(3) exponential and composition) on a fixed normal system -- with no
+ * map point, and writes the microseconds per pass to *us_per_pass.  What a
+ * real pass costs beyond it is the linearisation of its points.  Not part of
+ * the method; no paper counterpart.  Synchronous; allocates 8 bytes.
+ * Errors: INVALID_ARG (passes outside [1, 100000], a shape that cannot
+ * launch: cached needs 512 threads), CUDA. */
+int glt_debug_pass_floor(int cluster, int threads, int cached, int passes, float* us_per_pass,
+                         void* stream);
+
+/* The (cluster, threads) shape the tracker's solve launches with (chosen at
+ * glt_create and again when the point count changes, or set in the config). */
+int glt_get_shape(const glt_tracker* trk, int* cluster, int* threads);
+
 /* Copies level `level` of pyramid `slot` (unpadded, W_l * H_l bytes) to host
  * memory `out`.  Synchronous. */
 int glt_get_pyramid(glt_tracker* trk, int slot, int level, uint8_t* out, void* stream);

@@ -102,6 +102,8 @@ SIGNATURES = {
     "glt_debug_linearize": (_i, [_vp, _i, _P(_d), _d, _d, _P(_d), _P(_d), _P(_d), _P(_i),
                                  _P(ctypes.c_float), _vp]),
     "glt_debug_rcp": (_i, [_vp, _vp, _i, _vp]),
+    "glt_debug_pass_floor": (_i, [_i, _i, _i, _i, _P(ctypes.c_float), _vp]),
+    "glt_get_shape": (_i, [_vp, _P(_i), _P(_i)]),
     "glt_get_pyramid": (_i, [_vp, _i, _i, _P(ctypes.c_uint8), _vp]),
     "glt_get_trace": (_i, [_vp, _P(_d), _P(_i), _i, _P(_i), _vp]),
     "glt_state_predict": (_i, [_P(glt_state), _P(_d), _P(_d)]),
@@ -388,6 +390,12 @@ class Tracker:
             out["res"] = res[:self.N * K].reshape(self.N, K)
         return out
 
+    def shape(self):
+        """(cluster, threads) of the tracker's solve launch."""
+        c, t = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.glt_get_shape(self.handle, ctypes.byref(c), ctypes.byref(t)), "glt_get_shape")
+        return c.value, t.value
+
     def get_pyramid(self, slot, level, stream=None) -> np.ndarray:
         w, h = self.W >> level, self.H >> level
         out = np.zeros((h, w), np.uint8)
@@ -538,6 +546,15 @@ class NN:
         _check(_lib.glt_nn_train_step(self.handle, _dptr(x_dev), _dptr(m_dev), _dptr(t_dev), int(B),
                                       float(lr), _dptr(loss_dev) if loss_dev is not None else None,
                                       _stream_handle(stream)), "glt_nn_train_step")
+
+
+def pass_floor(cluster, threads, cached=False, passes=400, stream=None) -> float:
+    """Microseconds per pass of the track kernel's fixed part (no points) for
+    one stream's (cluster, threads) shape (glt_debug_pass_floor)."""
+    us = ctypes.c_float()
+    _check(_lib.glt_debug_pass_floor(int(cluster), int(threads), int(bool(cached)), int(passes),
+                                     ctypes.byref(us), _stream_handle(stream)), "glt_debug_pass_floor")
+    return us.value
 
 
 def version() -> str:

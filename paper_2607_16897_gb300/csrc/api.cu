@@ -736,6 +736,14 @@ int glt_debug_linearize(glt_tracker* t, int level, const double T[12], double a,
     return GLT_OK;
 }
 
+int glt_get_shape(const glt_tracker* t, int* cluster, int* threads)
+{
+    if (!t || !cluster || !threads) return invalid("NULL argument");
+    *cluster = t->cluster;
+    *threads = t->threads;
+    return GLT_OK;
+}
+
 int glt_get_pyramid(glt_tracker* t, int slot, int level, uint8_t* out, void* stream)
 {
     if (!t || !out) return invalid("NULL argument");

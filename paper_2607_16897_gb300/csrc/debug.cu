@@ -25,3 +25,32 @@ extern "C" int glt_debug_rcp(const double* d_dev, double* r_dev, int n, void* st
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GLT_OK : cuda_fail(e, "glt_debug_rcp kernel");
 }
+
+extern "C" int glt_debug_pass_floor(int cluster, int threads, int cached, int passes,
+                                    float* us_per_pass, void* stream)
+{
+    if (!us_per_pass || passes < 1 || passes > 100000 || cluster < 1 || cluster > 16)
+        return invalid_arg_msg("glt_debug_pass_floor: bad argument");
+    if (!track_shape_ok(cluster, threads, cached ? 4 : 0))
+        return invalid_arg_msg("glt_debug_pass_floor: shape cannot launch");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    long long* cyc = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&cyc), sizeof(long long));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    // one launch to warm up, then the timed one
+    if (e == cudaSuccess) e = launch_pass_floor(cluster, threads, cached != 0, passes, cyc, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = launch_pass_floor(cluster, threads, cached != 0, passes, cyc, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(cyc);
+    if (e != cudaSuccess) return cuda_fail(e, "glt_debug_pass_floor");
+    *us_per_pass = 1000.0f * ms / (float)passes;
+    return GLT_OK;
+}

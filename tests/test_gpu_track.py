@@ -142,3 +142,26 @@ def test_track_async_device_io(glt, orc, syn):
     g = glt.parse_results(out)[0]
     check_same(g, o.track_frame(I34), "async")
     trk.close()
+
+
+def test_pass_floor_is_below_a_real_pass(glt, orc, syn):
+    """The latency floor of a pass (no points) is positive and below the mean
+    pass time of a real solve on the same shape; the cached-Hessian tail
+    (a matrix-vector product) is cheaper than the factorisation."""
+    import torch
+    p = syn.pair_c1(1, sigma=2.0)
+    trk, _ = both_sides(glt, orc, p.cam.W, p.cam.H, p.cam.K, p.ref, p.cur, p.uvd, levels=3,
+                        cluster=4, threads=256)
+    trk.track_frame(I34)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    g = trk.track_frame(I34)
+    e1.record()
+    torch.cuda.synchronize()
+    per_pass = 1000.0 * e0.elapsed_time(e1) / g["passes"]
+    floor = glt.pass_floor(4, 256)
+    assert 0.5 < floor < per_pass, (floor, per_pass)
+    assert glt.pass_floor(4, 512, cached=True) < glt.pass_floor(4, 512)
+    with pytest.raises(glt.GltError):
+        glt.pass_floor(4, 256, cached=True)       # the cached-Hessian kernel runs 512 threads
+    trk.close()
