@@ -100,7 +100,8 @@ typedef struct glt_config {
     double lambda_down;         /* damping factor after an accepted candidate */
     double eps_step;            /* stop the finest level once max |delta_xi| < eps_step */
     double eps_step_coarse;     /* ... and every coarser level once max |delta_xi| <
-                                   eps_step_coarse */
+                                   eps_step_coarse; such a final step (if also below
+                                   accept_step) is taken without a pass of its own */
     double eps_cost;            /* ... or once a rejected candidate raised the cost by
                                    no more than eps_cost * cost */
     double accept_step;         /* candidates with max |delta_xi| < accept_step are taken
@@ -147,8 +148,11 @@ typedef struct glt_config {
 typedef struct glt_result {
     double T[12];               /* final pose, row-major 3x4 */
     double a, b;                /* final affine brightness, cur ~ e^a ref + b */
-    double cost;                /* mean Huber energy sum(rho)/n at the final state on the
-                                   last level that ran (NaN if none ran) */
+    double cost;                /* mean Huber energy sum(rho)/n of the last evaluated state
+                                   on the last level that ran (NaN if none ran); a level's
+                                   final step below its stop threshold is taken without a
+                                   pass of its own, so T may differ from that state by a
+                                   step below eps_step */
     int n_valid;                /* valid residual samples behind `cost` */
     int iters_total;            /* candidate evaluations over all levels */
     int iters[GLT_MAX_LEVELS];  /* candidate evaluations per level */

@@ -459,11 +459,13 @@ void orc_linearize2(const double* img, int W, int H, orc_cam K0, int level, cons
  * ones).  A level stops after max_iters candidates, once a step is
  * below eps_step (eps_step_coarse on the levels above the finest), or when a
  * rejected candidate raised the cost by no more than eps_cost * cost.
- * Reading (coarse levels): a step below eps_step_coarse is below accept_step
- * too, so it would be taken whatever its cost and would end the level; on a
- * level above the finest it is therefore taken without a pass of its own, and
- * the next level's start pass is the first evaluation of the new state (the
- * finest level keeps the pass: its cost and sample count are reported).
+ * Reading (a level's final step): a step below the level's stop threshold
+ * (eps_step_coarse above the finest level, eps_step on it) that is also below
+ * accept_step would be taken whatever its cost and would end the level; it is
+ * therefore taken without a pass of its own.  Above the finest level the next
+ * level's start pass is the first evaluation of the new state; on the finest
+ * level the reported cost and sample count are those of the last evaluated
+ * state, which the returned pose differs from by that final step.
  * ------------------------------------------------------------------------ */
 static int cholesky_solve8(const double A[64], const double g[8], double delta[8])
 {
@@ -651,7 +653,7 @@ void orc_track2(const double* cur, int W0, int H0, orc_cam K0, const double* x_r
             }
             double m = 0;
             for (int d = 0; d < 6; ++d) m = fmax(m, fabs(delta[d]));
-            if (l > 0 && m < cfg->eps_step_coarse && m < cfg->accept_step) {
+            if (m < (l > 0 ? cfg->eps_step_coarse : cfg->eps_step) && m < cfg->accept_step) {
                 /* the level's last step, taken without a pass of its own */
                 memcpy(T, Tn, sizeof(T));
                 a = an;

@@ -1149,11 +1149,13 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
             const double ac = S.a + dl[6], bc = S.b + dl[7];
             const bool cand_finite = __all_sync(full, abs_bits(tc) < kInfBits) &&
                                      abs_bits(ac) < kInfBits && abs_bits(bc) < kInfBits;
-            // a step below eps_step_coarse on a level above the finest would be
-            // taken whatever its cost and would end the level, so it is taken
-            // here without a pass of its own; the next level's start pass is
-            // the first evaluation of the new state
-            const bool take_now = level > 0 && mbits < abs_bits(D.eps_step_coarse) &&
+            // a step below the level's stop threshold (and below accept_step)
+            // would be taken whatever its cost and would end the level, so it
+            // is taken here without a pass of its own: the next level's start
+            // pass is the first evaluation of the new state; on the finest
+            // level the result keeps the cost and count of the last evaluated
+            // state
+            const bool take_now = mbits < abs_bits(level > 0 ? D.eps_step_coarse : D.eps_step) &&
                                   mbits < abs_bits(D.accept_step);
             if (!cand_finite) {
                 // the solve produced a state that is not finite: keep the

@@ -72,7 +72,12 @@ def test_converged_state_is_a_grid_minimum(orc, syn, seed):
     res = tr.track_frame(I34)
     base = tr.debug_linearize(0, res["T"], res["a"], res["b"], per_sample=False)
     c0 = base["E"] / base["n"]
-    assert abs(c0 - res["cost"]) <= 1e-12 * c0
+    # the reported cost is that of the last evaluated state (the final step,
+    # below eps_step, is taken without a pass of its own): the trace's last
+    # accepted finest-level evaluation, within 1e-6 of the cost at the pose
+    last = [e["cost"] for e in res["trace"] if e["level"] == 0 and (e["accepted"] or not e["candidate"])][-1]
+    assert res["cost"] == last
+    assert abs(c0 - res["cost"]) <= 1e-6 * c0
     steps = [1e-3] * 6 + [1e-3, 1e-1]
     for i in range(8):
         for sgn in (-1, 1):
@@ -107,7 +112,7 @@ def test_initial_state_far_is_worse_than_converged(orc, syn):
     # step of a coarse level that ends on its step threshold (taken unevaluated)
     evaluated = [sum(1 for e in res["trace"] if e["candidate"] and e["level"] == l) for l in range(3)]
     unevaluated = [res["iters"][l] - evaluated[l] for l in range(3)]
-    assert unevaluated[0] == 0 and all(u in (0, 1) for u in unevaluated)
+    assert all(u in (0, 1) for u in unevaluated) and sum(unevaluated) >= 1
     assert res["passes"] == len(res["trace"]) == res["iters_total"] + 3 - sum(unevaluated)
 
 
