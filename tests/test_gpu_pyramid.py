@@ -67,3 +67,19 @@ def test_constant_and_extreme_images(glt, orc):
         for l, ref in enumerate(orc.pyramid(img, 4)):
             np.testing.assert_array_equal(trk.get_pyramid(glt.GLT_CUR, l), ref)
         trk.close()
+
+
+@pytest.mark.parametrize("W,H", [(640, 480), (752, 480), (1280, 720), (336, 200), (1920, 1080)])
+def test_large_frames_match_the_oracle(glt, orc, W, H):
+    """The frame sizes of the benchmark workloads and larger ones, five levels,
+    with saturated and black borders (the clamp reads them): every level is
+    byte for byte the oracle's."""
+    rng = np.random.default_rng(W + H)
+    img = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    img[:, :3] = 255
+    img[-2:, :] = 0
+    trk = glt.Tracker(W, H, (W, W, W / 2, H / 2), levels=5, max_points=16)
+    trk.build_pyramid(glt.GLT_CUR, img)
+    for l, ref in enumerate(orc.pyramid(img, 5)):
+        np.testing.assert_array_equal(trk.get_pyramid(glt.GLT_CUR, l), ref, err_msg=f"level {l}")
+    trk.close()
