@@ -234,6 +234,20 @@ __global__ void to_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict__
     if (i < n) wbf[i] = __float2bfloat16_rn(w[i]);
 }
 
+// conv2 / conv3 BF16 weights transposed to [K][O] (K = input channel x tap),
+// the layout the proposal stage stages into shared memory as one contiguous
+// copy; rewritten after every change of the BF16 weights.
+constexpr int kW2 = 144 * 32, kW3 = 288 * 64;
+
+__global__ void conv_relayout(const __nv_bfloat16* __restrict__ wbf, __nv_bfloat16* __restrict__ wt)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < kW2)
+        wt[(q % 144) * 32 + q / 144] = wbf[kC2.w + q];
+    else if (q < kW2 + kW3)
+        wt[kW2 + ((q - kW2) % 288) * 64 + (q - kW2) / 288] = wbf[kC3.w + (q - kW2)];
+}
+
 }  // namespace nn
 }  // namespace glt
 
@@ -242,6 +256,7 @@ struct glt_nn {
     int step = 0;
     float* w = nullptr;               // FP32 master
     __nv_bfloat16* wbf = nullptr;     // BF16 copy used by the kernels
+    __nv_bfloat16* wt = nullptr;      // conv2 / conv3 BF16 weights as [K][O] (proposal stage)
     float* g = nullptr;
     float* m = nullptr;
     float* v = nullptr;
@@ -263,6 +278,7 @@ int nn_alloc(glt_nn* n)
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = al(&n->w, kParams);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&n->wbf), kParams * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&n->wt), (kW2 + kW3) * sizeof(__nv_bfloat16));
     if (e == cudaSuccess) e = al(&n->g, kParams);
     if (e == cudaSuccess) e = al(&n->m, kParams);
     if (e == cudaSuccess) e = al(&n->v, kParams);
@@ -293,6 +309,7 @@ void nn_free(glt_nn* n)
                      n->y, n->dy, n->dh, n->d3, n->d2, n->d1, n->loss})
         cudaFree(p);
     cudaFree(n->wbf);
+    cudaFree(n->wt);
     delete n;
 }
 
@@ -353,19 +370,22 @@ namespace nn {
 // read-only cache (they stay L2-resident across blocks):
 //   x = (I_cur - I_ref) / 64 on the 40 x 30 coarsest level,
 //   conv1 -> conv2 -> conv3 (ReLU) -> fc1 (ReLU) on [flatten, motion] -> fc2,
-//   then T' = T exp(0.01 y[0:6]), a' = a + 0.01 y[6], b' = b + y[7] in FP64.
+//   then T' = T exp(0.01 y[0:6]), a' = a + 0.01 y[6], b' = b + y[7].
 // Conv inputs are stored with a one-pixel zero border, so every 3x3 window is
 // read without bounds tests.  conv1 gives each thread 4 output channels of one
 // pixel; conv2 and conv3 run as small GEMMs (output pixels x channels, K =
-// input channel x tap) with register tiles of PT pixels x 4 channels and the
-// layer's weights staged once per block in shared memory as BF16, transposed
-// to [K][O] so a tile's 4 weights are one 8-byte load.  The sum order per
-// output (bias, then channel, row, column) is that of conv_fwd.
+// input channel x tap) with register tiles of PT pixels x 4 channels, on the
+// layer's weights in the [K][O] layout (a tile's 4 weights are one 8-byte
+// load), copied into shared memory with asynchronous 16-byte copies issued at
+// the start and awaited just before conv2.  The sum order per output (bias,
+// then channel, row, column) is that of conv_fwd.
 constexpr int kPropThreads = 512;
 constexpr int kXp = 32 * 42, kA1p = 16 * 17 * 22, kA2p = 32 * 10 * 12;
-constexpr int kW2 = 144 * 32, kW3 = 288 * 64;       // BF16 weights, [K][O]
 constexpr int kPropSmemFloats = kXp + kA1p + kA2p + (kF + 2) + kHid + kOut;
 constexpr size_t kPropSmemBytes = kPropSmemFloats * sizeof(float) + (kW2 + kW3) * sizeof(__nv_bfloat16);
+static_assert(kPropSmemFloats % 4 == 0, "the BF16 weights must start on a 16-byte boundary");
+static_assert((kXp + kA1p + kA2p) % 4 == 0, "the bordered planes are cleared as float4");
+static_assert((kW2 + kW3) * sizeof(__nv_bfloat16) % 16 == 0, "the weight copy is made of 16-byte pieces");
 
 // GEMM form of a stride-2 3x3 conv on a zero-bordered input: thread t < tasks
 // computes PT consecutive output pixels (row-major) x 4 channels.
@@ -377,6 +397,7 @@ __device__ __forceinline__ void conv_gemm(const float* __restrict__ in, const __
     constexpr int Ho = (H + 1) / 2, Wo = (W + 1) / 2, Wp = W + 2, plane = (H + 2) * (W + 2);
     constexpr int PG = Ho * Wo / PT, tasks = PG * (O / 4);
     static_assert(Ho * Wo % PT == 0, "pixel tiles must cover the output");
+    static_assert(tasks <= kPropThreads, "one tile per thread");
     const int t = threadIdx.x;
     if (t >= tasks) return;
     const int pg = t % PG, cg = t / PG;
@@ -473,65 +494,75 @@ __device__ __forceinline__ void conv_block(const float* __restrict__ in, const _
 }
 
 // Network motion input from the stream's last inter-frame motion M = [R | t]
-// (FP64, row-major 3x4): log(M) / 0.02 as (upsilon, omega).  The rotation
-// angle is atan2 of the skew part's half norm and (trace - 1) / 2; omega =
-// th / (2 sin th) vee(R - R^T) (its series below th = 1e-4; near pi the axis
-// comes from the symmetric part instead); upsilon = V^-1 t with
+// (row-major 3x4): log(M) / 0.02 as (upsilon, omega).  The input is FP32, and
+// so is this evaluation after the differences of M's entries it starts from
+// (vee(R - R^T), trace R - 1 and, near pi, the symmetric part), which are
+// formed in FP64.  sin th = |vee| / 2 and cos th = (trace - 1) / 2, th their
+// atan2; omega = th / (2 sin th) vee (its series below th = 1e-4; near pi the
+// axis comes from the symmetric part instead); upsilon = V^-1 t with
 // V^-1 = I - W/2 + k W^2, k = (1 - A / (2 B)) / th^2, A = sin th / th,
-// B = (1 - cos th) / th^2 (the series of k below th = 0.1).
-constexpr double kMotionScale = 0.02;
+// B = (1 - cos th) / th^2, taken below th = 0.5 as its series
+// k = sum_n |B_2n| th^(2n-2) / (2n)! (Bernoulli numbers), to th^8.
+constexpr float kMotionScale = 0.02f;
 
 __device__ void motion_feature(const double* __restrict__ M, float* __restrict__ f6)
 {
-    const double R[9] = {M[0], M[1], M[2], M[4], M[5], M[6], M[8], M[9], M[10]};
-    const double t[3] = {M[3], M[7], M[11]};
-    const double vee[3] = {R[7] - R[5], R[2] - R[6], R[3] - R[1]};
-    const double sn = 0.5 * sqrt(vee[0] * vee[0] + vee[1] * vee[1] + vee[2] * vee[2]);
-    const double cs = 0.5 * (R[0] + R[4] + R[8] - 1.0);
-    const double th = atan2(sn, cs);
-    const double pi = 3.14159265358979323846;
-    double w[3];
-    if (th < 1e-4) {
-        const double k = 0.5 * (1.0 + th * th / 6.0);
+    const float vee[3] = {(float)(M[9] - M[6]), (float)(M[2] - M[8]), (float)(M[4] - M[1])};
+    const float t[3] = {(float)M[3], (float)M[7], (float)M[11]};
+    const float sn = 0.5f * sqrtf(vee[0] * vee[0] + vee[1] * vee[1] + vee[2] * vee[2]);
+    const float cs = (float)(0.5 * (M[0] + M[5] + M[10] - 1.0));
+    const float th = atan2f(sn, cs);
+    const float pi = 3.14159265358979f;
+    float w[3];
+    if (th < 1e-4f) {
+        const float k = 0.5f * (1.0f + th * th / 6.0f);
         for (int i = 0; i < 3; ++i) w[i] = k * vee[i];
-    } else if (th < pi - 1e-4) {
-        const double k = th / (2.0 * sin(th));
+    } else if (th < pi - 1e-4f) {
+        const float k = th / (2.0f * sn);
         for (int i = 0; i < 3; ++i) w[i] = k * vee[i];
     } else {
+        const double Rd[3] = {M[0], M[5], M[10]};
         int m = 0;
         for (int i = 1; i < 3; ++i)
-            if (R[4 * i] > R[4 * m]) m = i;
-        const double d = sqrt(0.5 * (R[4 * m] + 1.0));
-        double a[3];
-        for (int i = 0; i < 3; ++i) a[i] = i == m ? d : 0.5 * (R[3 * i + m] + R[3 * m + i]) / (2.0 * d);
-        const double na = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-        const double sg = (a[0] * vee[0] + a[1] * vee[1] + a[2] * vee[2]) < 0.0 ? -1.0 : 1.0;
+            if (Rd[i] > Rd[m]) m = i;
+        const float d = sqrtf((float)(0.5 * (Rd[m] + 1.0)));
+        float a[3];
+        for (int i = 0; i < 3; ++i)
+            a[i] = i == m ? d : (float)(0.5 * (M[4 * i + m] + M[4 * m + i])) / (2.0f * d);
+        const float na = sqrtf(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+        const float sg = (a[0] * vee[0] + a[1] * vee[1] + a[2] * vee[2]) < 0.0f ? -1.0f : 1.0f;
         for (int i = 0; i < 3; ++i) w[i] = sg * th * a[i] / na;
     }
-    const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-    double k;
-    if (th < 0.1) {
-        const double t4 = th2 * th2;
-        k = 1.0 / 12.0 + th2 / 720.0 + t4 / 30240.0 + t4 * th2 / 1209600.0;
+    const float th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    float k;
+    if (th < 0.5f) {
+        k = 1.0f / 12.0f + th2 * (1.0f / 720.0f + th2 * (1.0f / 30240.0f +
+                                 th2 * (1.0f / 1209600.0f + th2 * (1.0f / 47900160.0f))));
     } else {
-        const double sh = sin(0.5 * th);
-        const double A = sin(th) / th, B = 2.0 * sh * sh / th2;
-        k = (1.0 - A / (2.0 * B)) / th2;
+        const float sh = sinf(0.5f * th);
+        const float A = sinf(th) / th, B = 2.0f * sh * sh / th2;
+        k = (1.0f - A / (2.0f * B)) / th2;
     }
     // W = [w]x;  V^-1 t = t - (w x t) / 2 + k w x (w x t)
-    const double wt[3] = {w[1] * t[2] - w[2] * t[1], w[2] * t[0] - w[0] * t[2], w[0] * t[1] - w[1] * t[0]};
-    const double wwt[3] = {w[1] * wt[2] - w[2] * wt[1], w[2] * wt[0] - w[0] * wt[2],
-                           w[0] * wt[1] - w[1] * wt[0]};
+    const float wt[3] = {w[1] * t[2] - w[2] * t[1], w[2] * t[0] - w[0] * t[2], w[0] * t[1] - w[1] * t[0]};
+    const float wwt[3] = {w[1] * wt[2] - w[2] * wt[1], w[2] * wt[0] - w[0] * wt[2],
+                          w[0] * wt[1] - w[1] * wt[0]};
     for (int i = 0; i < 3; ++i) {
-        f6[i] = (float)((t[i] - 0.5 * wt[i] + k * wwt[i]) / kMotionScale);
-        f6[3 + i] = (float)(w[i] / kMotionScale);
+        f6[i] = (t[i] - 0.5f * wt[i] + k * wwt[i]) / kMotionScale;
+        f6[3 + i] = w[i] / kMotionScale;
     }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
 __global__ void __launch_bounds__(kPropThreads)
 proposal_kernel(const PropJob* __restrict__ jobs, const double* __restrict__ motion,
                 const double* __restrict__ init, const __nv_bfloat16* __restrict__ w,
-                double* __restrict__ out)
+                const __nv_bfloat16* __restrict__ wt, double* __restrict__ out)
 {
     extern __shared__ __align__(16) float sm[];
     float* xp = sm;
@@ -544,28 +575,21 @@ proposal_kernel(const PropJob* __restrict__ jobs, const double* __restrict__ mot
     __nv_bfloat16* w3t = w2t + kW2;
     const int s = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int q = tid; q < kXp + kA1p + kA2p; q += kPropThreads) sm[q] = 0.0f;
-    // conv2 / conv3 weights -> [K][O] (K = c * 9 + tap), read as 16-byte
-    // vectors (both layers start on a 16-byte boundary of the flat layout)
-    {
-        const uint4* g2 = reinterpret_cast<const uint4*>(w + kC2.w);
-        const uint4* g3 = reinterpret_cast<const uint4*>(w + kC3.w);
-        for (int v = tid; v < (kW2 + kW3) / 8; v += kPropThreads) {
-            const bool l2 = v < kW2 / 8;
-            const uint4 raw = __ldg(l2 ? g2 + v : g3 + (v - kW2 / 8));
-            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&raw);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                if (l2) {
-                    const int q = 8 * v + u;
-                    w2t[(q % 144) * 32 + q / 144] = e[u];
-                } else {
-                    const int q = 8 * (v - kW2 / 8) + u;
-                    w3t[(q % 288) * 64 + q / 288] = e[u];
-                }
-            }
+    // conv2 / conv3 weights: one contiguous [K][O] copy, in flight until conv2
+    for (int v = tid; v < (kW2 + kW3) / 8; v += kPropThreads) cp_async16(w2t + 8 * v, wt + 8 * v);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    // the rows of T each lane of warp 0 composes at the end (lanes 12, 13: a, b)
+    double Tr[4] = {0.0, 0.0, 0.0, 0.0};
+    if (warp == 0 && lane < 14) {
+        const double* T = init + 14 * s;
+        if (lane < 12) {
+            for (int k = 0; k < 4; ++k) Tr[k] = T[4 * (lane >> 2) + k];
+        } else {
+            Tr[0] = T[lane];
         }
     }
+    float4* z4 = reinterpret_cast<float4*>(sm);
+    for (int q = tid; q < (kXp + kA1p + kA2p) / 4; q += kPropThreads) z4[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     __syncthreads();
     const PropJob J = jobs[s];
     for (int p = tid; p < kIn; p += kPropThreads) {
@@ -575,12 +599,13 @@ proposal_kernel(const PropJob* __restrict__ jobs, const double* __restrict__ mot
     }
     __syncthreads();
     conv_block<1, 30, 40, 16, 4, true>(xp, w, kC1.w, kC1.b, a1);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    // the motion input, on a thread that conv2's 160 tiles leave idle
+    // the motion input, on a thread that conv2's 320 tiles leave idle
     if (tid == kPropThreads - 1) motion_feature(motion + 12 * s, f + kFlat);
-    conv_gemm<16, 15, 20, 32, 4, true>(a1, w2t, w, kC2.b, a2);
+    conv_gemm<16, 15, 20, 32, 2, true>(a1, w2t, w, kC2.b, a2);
     __syncthreads();
-    conv_gemm<32, 8, 10, 64, 2, false>(a2, w3t, w, kC3.b, f);
+    conv_gemm<32, 8, 10, 64, 1, false>(a2, w3t, w, kC3.b, f);
     __syncthreads();
     // fc1: each warp takes 4 output rows at a time, BF16 pairs along the rows
     for (int o0 = warp * 4; o0 < kHid; o0 += 4 * (kPropThreads / 32)) {
@@ -619,48 +644,59 @@ proposal_kernel(const PropJob* __restrict__ jobs, const double* __restrict__ mot
         if (lane == 0) y[warp] = acc + wv(w, kF2.b + warp);
     }
     __syncthreads();
-    if (tid != 0) return;
-    // FP64 exponential (closed form, Taylor series below theta^2 = 0.01) and
-    // composition on the right
-    const double* T = init + 14 * s;
-    double d[8];
-    for (int k = 0; k < 8; ++k) d[k] = (double)y[k] * (k < 7 ? 0.01 : 1.0);
-    const double w0 = d[3], w1 = d[4], w2 = d[5];
-    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
-    double A, B, C;
-    if (th2 < 0.01) {
-        A = 1.0 + th2 * (-1.0 / 6.0 + th2 * (1.0 / 120.0 + th2 * (-1.0 / 5040.0 + th2 / 362880.0)));
-        B = 0.5 + th2 * (-1.0 / 24.0 + th2 * (1.0 / 720.0 + th2 * (-1.0 / 40320.0 + th2 / 3628800.0)));
-        C = 1.0 / 6.0 + th2 * (-1.0 / 120.0 + th2 * (1.0 / 5040.0 + th2 * (-1.0 / 362880.0 + th2 / 39916800.0)));
-    } else {
-        const double th = sqrt(th2);
-        const double sh = sin(0.5 * th);
-        A = sin(th) / th;
-        B = 2.0 * sh * sh / th2;
-        C = (th - sin(th)) / (th2 * th);
-    }
-    const double Wm[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
-    const double ww[3] = {w0, w1, w2};
-    double E[12];
-    for (int r = 0; r < 3; ++r) {
-        double tr = 0.0;
-        for (int c = 0; c < 3; ++c) {
-            const double W2 = ww[r] * ww[c] - (r == c ? th2 : 0.0);
-            const double I = r == c ? 1.0 : 0.0;
-            E[4 * r + c] = I + A * Wm[3 * r + c] + B * W2;
-            tr += (I + B * Wm[3 * r + c] + C * W2) * d[c];
-        }
-        E[4 * r + 3] = tr;
-    }
+    if (warp != 0 || lane >= 14) return;
+    // T' = T exp(d) = T + T (exp(d) - I): the increment exp(d) - I, whose
+    // entries are O(|d|), in FP32 (every lane the whole 3 x 4 matrix;
+    // A = sin th / th, B = (1 - cos th) / th^2, C = (th - sin th) / th^3 as
+    // series below th^2 = 0.25, truncation below 1e-10 relative), the
+    // composition in FP64: lane 4 r + c writes entry (r, c), lanes 12 and 13
+    // the affine pair
     double* O = out + 14 * s;
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 4; ++c) {
-            double v = c == 3 ? T[4 * r + 3] : 0.0;
-            for (int k = 0; k < 3; ++k) v += T[4 * r + k] * E[4 * k + c];
-            O[4 * r + c] = v;
+    if (lane >= 12) {
+        O[lane] = Tr[0] + (double)y[lane - 6] * (lane == 12 ? 0.01 : 1.0);
+        return;
+    }
+    float d[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) d[k] = y[k] * 0.01f;
+    const float w0 = d[3], w1 = d[4], w2 = d[5];
+    const float th2 = w0 * w0 + w1 * w1 + w2 * w2;
+    float A, B, C;
+    if (th2 < 0.25f) {
+        A = 1.0f - th2 * (1.0f / 6.0f - th2 * (1.0f / 120.0f - th2 * (1.0f / 5040.0f - th2 * (1.0f / 362880.0f))));
+        B = 0.5f - th2 * (1.0f / 24.0f - th2 * (1.0f / 720.0f - th2 * (1.0f / 40320.0f - th2 * (1.0f / 3628800.0f))));
+        C = 1.0f / 6.0f - th2 * (1.0f / 120.0f - th2 * (1.0f / 5040.0f - th2 * (1.0f / 362880.0f - th2 * (1.0f / 39916800.0f))));
+    } else {
+        const float th = sqrtf(th2), sn = sinf(th), sh = sinf(0.5f * th);
+        A = sn / th;
+        B = 2.0f * sh * sh / th2;
+        C = (th - sn) / (th2 * th);
+    }
+    // W = [w]x, W^2 = w w^T - th^2 I; rotation increment A W + B W^2,
+    // translation V t - t = B W t + C W^2 t with t = d[0:3]
+    const float Wm[3][3] = {{0.0f, -w2, w1}, {w2, 0.0f, -w0}, {-w1, w0, 0.0f}};
+    const float ww[3] = {w0, w1, w2};
+    float dE[3][4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float wt = 0.0f, w2t = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float W2 = ww[k] * ww[j] - (k == j ? th2 : 0.0f);
+            dE[k][j] = fmaf(A, Wm[k][j], B * W2);
+            wt = fmaf(Wm[k][j], d[j], wt);
+            w2t = fmaf(W2, d[j], w2t);
         }
-    O[12] = T[12] + d[6];
-    O[13] = T[13] + d[7];
+        dE[k][3] = d[k] + fmaf(B, wt, C * w2t);
+    }
+    const int c = lane & 3;
+    double v = c == 0 ? Tr[0] : c == 1 ? Tr[1] : c == 2 ? Tr[2] : Tr[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float e = c == 0 ? dE[k][0] : c == 1 ? dE[k][1] : c == 2 ? dE[k][2] : dE[k][3];
+        v = fma(Tr[k], (double)e, v);
+    }
+    O[lane] = v;
 }
 
 }  // namespace nn
@@ -668,7 +704,7 @@ proposal_kernel(const PropJob* __restrict__ jobs, const double* __restrict__ mot
 cudaError_t launch_proposal(glt_batch* b, const double* init_dev, cudaStream_t s)
 {
     nn::proposal_kernel<<<b->S, nn::kPropThreads, nn::kPropSmemBytes, s>>>(
-        b->prop_jobs, b->motion_dev, init_dev, b->nn->wbf, b->prop_init);
+        b->prop_jobs, b->motion_dev, init_dev, b->nn->wbf, b->nn->wt, b->prop_init);
     return cudaGetLastError();
 }
 
@@ -747,6 +783,7 @@ int glt_nn_set_params(glt_nn* n, const float* host, int count)
     if (e == cudaSuccess) e = cudaMemset(n->v, 0, kParams * sizeof(float));
     if (e != cudaSuccess) return cuda_fail(e, "glt_nn_set_params");
     to_bf16<<<grid_for(kParams, 256), 256>>>(n->w, n->wbf, kParams);
+    conv_relayout<<<grid_for(kW2 + kW3, 256), 256>>>(n->wbf, n->wt);
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "glt_nn_set_params");
     n->step = 0;
@@ -805,6 +842,7 @@ int glt_nn_train_step(glt_nn* n, const float* x_dev, const float* m_dev, const f
     const float c2 = (float)(1.0 / (1.0 - std::pow(b2, n->step)));
     adam<<<grid_for(kParams, 256), 256, 0, s>>>(n->w, n->wbf, n->g, n->m, n->v, kParams, lr, (float)b1,
                                                 (float)b2, 1e-8f, c1, c2);
+    conv_relayout<<<grid_for(kW2 + kW3, 256), 256, 0, s>>>(n->wbf, n->wt);
     if (loss_dev) e = cudaMemcpyAsync(loss_dev, n->loss, sizeof(float), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? GLT_OK : cuda_fail(e, "glt_nn_train_step");
@@ -955,6 +993,7 @@ int glt_nn_load(glt_nn* n, const char* path)
     if (e == cudaSuccess) e = cudaMemcpy(n->v, v.data(), kParams * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "glt_nn_load");
     to_bf16<<<grid_for(kParams, 256), 256>>>(n->w, n->wbf, kParams);
+    conv_relayout<<<grid_for(kW2 + kW3, 256), 256>>>(n->wbf, n->wt);
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "glt_nn_load");
     n->step = step;
