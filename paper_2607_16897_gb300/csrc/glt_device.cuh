@@ -734,19 +734,27 @@ __device__ __forceinline__ void block_reduce(float (&acc)[kAccPad], float (*red)
 }
 
 // ---------------------------------------------------------------------------
-// FP64 solver tail, run by one warp of every CTA
+// Solver tail, run by one warp of every CTA
 //
 // GB300 runs FP64 at a small fraction of its FP32 rate with long dependent
 // latencies (measured on the part: ~64 cycles per DFMA, ~420 per divide or
 // reciprocal, ~670 per square root, ~1700 per sincos), and this tail sits on
-// the critical path of every pass.  So it is laid out for latency:
+// the critical path of every pass.  The state, the normal equations, the
+// accept/reject decision and the composition stay in FP64; work whose inputs
+// carry FP32 rounding anyway, or whose result is a small increment, is FP32:
 //  * the damped normal matrix is factored as L D L^T (no square roots), one
-//    row per lane, columns eliminated right-looking with warp shuffles;
-//  * pivot reciprocals are an FP32 seed refined by one Newton step in FP64
+//    row per lane, columns eliminated right-looking with warp shuffles, in
+//    FP32, followed by one refinement step whose residual is formed in FP64;
+//    a pivot below 1e-4 of its damped diagonal sends the system to the same
+//    elimination in FP64, which alone decides "not positive definite";
+//  * FP64 pivot reciprocals are an FP32 seed refined by one Newton step
 //    (relative error ~4e-15);
-//  * the SE(3) exponential uses the power series of its coefficients in
-//    theta^2 below theta = 0.1 (sincos only beyond), each lane one element;
-//  * accept/reject compares E' n <= E n' instead of dividing.
+//  * exp(delta) - I is evaluated in FP32 (its entries are O(|delta|)) and
+//    composed with the FP64 pose as T + T (exp(delta) - I), each lane one
+//    element;
+//  * FP64 <-> FP32 conversions go through the bit pattern (integer
+//    instructions), and accept/reject compares E' n <= E n' instead of
+//    dividing.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double rcp_d(double d)
 {
@@ -771,6 +779,45 @@ __device__ __forceinline__ double rcp_d(double d)
     double r = __hiloint2double(rhi, (int)(rb << 29));
     const double e = fma(-d, r, 1.0);
     return fma(r, e, r);
+}
+
+// FP64 -> FP32 through the bit pattern (integer instructions only, nothing on
+// the FP64 pipe): the significand truncated to 23 bits (relative error
+// < 2^-23); magnitudes below 2^-126 give a signed zero and above FP32's range
+// infinity; infinities and NaN are kept.
+__device__ __forceinline__ float f32_of(double x)
+{
+    const int hi = __double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const int eb = (hi >> 20) & 0x7ff;
+    const unsigned sign = (unsigned)hi & 0x80000000u;
+    const unsigned man = (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29);
+    unsigned b;
+    if (eb == 0x7ff)
+        b = sign | 0x7f800000u | ((((unsigned)hi & 0xfffffu) | lo) ? 0x400000u : 0u);
+    else if (eb > 1023 + 127)
+        b = sign | 0x7f800000u;
+    else if (eb < 1023 - 126)
+        b = sign;
+    else
+        b = sign | ((unsigned)(eb - 896) << 23) | man;
+    return __uint_as_float(b);
+}
+
+// FP32 -> FP64 through the bit pattern: exact for zero and normal numbers
+// (subnormals give a signed zero); infinities and NaN are kept.
+__device__ __forceinline__ double f64_of(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned sign = b & 0x80000000u;
+    unsigned hi = sign, lo = 0u;
+    if (e != 0u) {
+        hi = sign | ((e == 0xffu ? 0x7ffu : e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+        if (e == 0xffu && (b & 0x7fffffu)) hi |= 0x80000u;
+        lo = b << 29;
+    }
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 // |x| compared through the bit pattern: for non-negative doubles the IEEE
@@ -827,6 +874,27 @@ __device__ __forceinline__ void make_pass_params_warp(const double* T, double a,
     }
 }
 
+// Same, with lane l < 12 holding pose entry l in `v` (no shared-memory read).
+__device__ __forceinline__ void make_pass_params_lane(double v, double a, double b, int level,
+                                                      PassParams& P, int lane)
+{
+    if (lane < 12) {
+        const int r = lane >> 2, c = lane & 3;
+        const double m = v - ((c == r) ? 1.0 : 0.0);
+        if (c < 3)
+            P.Rm[3 * r + c] = (float)m;
+        else
+            P.t[r] = (float)m;
+    } else if (lane == 12) {
+        P.ea = expf((float)a);
+    } else if (lane == 13) {
+        P.b = (float)b;
+        P.level = level;
+        P.scale = ldexpf(1.0f, -level);
+        P.done = 0;
+    }
+}
+
 // LM state machine, replicated in every CTA of a stream's cluster (each CTA
 // runs it on bit-identical inputs, so all take the same decisions).
 enum { PH_START = 0, PH_CAND = 1 };
@@ -839,6 +907,7 @@ struct Solver {
     double E, nd, lambda, res_E;   // energy / samples (as double) at the accepted state
     long long maxstep_bits;   // max |delta_xi| of the candidate, as abs_bits
     int n, res_n, level, it, phase, status, passes, done;
+    int moved;                // the pose changed since the initial state
     int iters[kMaxLevels];
 };
 
@@ -876,6 +945,7 @@ __device__ inline void solver_init(const StreamDesc& D, const double* init, Solv
     S.res_n = 0;
     S.res_E = __longlong_as_double(0x7ff8000000000000ll);
     S.done = 0;
+    S.moved = 0;
     for (int l = 0; l < kMaxLevels; ++l) S.iters[l] = 0;
     S.ema = (D.Hc && finite_start) ? exp(-S.a) : 1.0;
     int l = D.L - 1;
@@ -912,9 +982,10 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
     const double nd = tot[HC ? kHcN : kIdxN];   // exact integer count
     const int n = (int)nd;
     // sums that are not finite (an FP32 overflow) make the pass unusable
-    bool sums_finite = abs_bits(E) < kInfBits;
+    bool fin = true;
 #pragma unroll
-    for (int i = 0; i < (HC ? kHcE : kIdxE); ++i) sums_finite &= abs_bits(tot[i]) < kInfBits;
+    for (int i = lane; i < (HC ? kHcE : kIdxE); i += 32) fin &= abs_bits(tot[i]) < kInfBits;
+    const bool sums_finite = __all_sync(full, fin) && abs_bits(E) < kInfBits;
     const bool enough = n >= D.min_valid && n > 0 && sums_finite;
     int status = S.status;
     if (!sums_finite) status |= GLT_TRACK_DIVERGED;
@@ -987,6 +1058,7 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
         if (accept) {
             S.a = S.ac;
             S.b = S.bc;
+            S.moved = 1;
         }
         if (load_normal) {
             S.E = E;
@@ -1028,63 +1100,156 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
         const int ek = lane < 7 ? 0 : lane < 13 ? 1 : lane < 18 ? 2 : lane < 22 ? 3 : lane < 25 ? 4
                      : lane < 27 ? 5 : lane < 28 ? 6 : 7;
         const int ei = lane < 28 ? lane - (ek * 7 - (ek * (ek - 1)) / 2) + ek + 1 : 8;
-        double e = lane < 28 ? S.H[8 * ei + ek] : 0.0;
-        const double diag = S.H[8 * row + row];
-        const double a0 = fma(lambda, diag, diag);   // damped diagonal (lanes 0-7)
-        double dg = a0;
-        double dinv = 0.0;
-        // the forward substitution L y = -g rides along: y_i -= l_ij y_j with the
-        // l_ij the diagonal update already fetched (lanes 0-7 hold y_i)
-        double y = -S.g[row];
+        // First in FP32 (the sums it factorises carry FP32 rounding already):
+        // the same elimination, then one refinement step x += A^-1 (b - A x)
+        // with the residual in FP64 against the FP64 system.  Accepted when
+        // every FP32 pivot is above 1e-4 of its damped diagonal, where its
+        // rounding (~1e-6 of the diagonal) cannot change its sign and the
+        // refinement's contraction (~cond x 2^-23) is below 1e-2; otherwise the
+        // FP64 elimination below decides, as for every system it accepts or
+        // rejects as not positive definite.
+        bool ok32;
+        {
+            float e = lane < 28 ? f32_of(S.H[8 * ei + ek]) : 0.0f;
+            const double diag = S.H[8 * row + row];
+            const double a0 = fma(lambda, diag, diag);
+            const float a0f = f32_of(a0);
+            float dg = a0f, dinv = 0.0f;
+            float y = -f32_of(S.g[row]);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const double d = __shfl_sync(full, dg, j);
-            const double r = rcp_d(d);
-            if (lane == j) dinv = r;
-            if (j < 7) {
-                const double l = e * r;                         // l_ij on the lanes of column j
-                const int cj = j * 7 - (j * (j - 1)) / 2 - j - 1;   // lane of (i, j) is cj + i
-                const bool trail = lane < 28 && ek > j;        // entry (i, k), k > j: -= l_ij a_kj
-                const bool drow = lane > j && lane < 8;          // diagonal d_i, i > j: -= l_ij a_ij
-                const double li = __shfl_sync(full, l, cj + (trail ? ei : j + 1));
-                const double ak = __shfl_sync(full, e, cj + (trail ? ek : j + 1));
-                const double ld = __shfl_sync(full, l, cj + (drow ? lane : j + 1));
-                const double ad = __shfl_sync(full, e, cj + (drow ? lane : j + 1));
-                const double yj = __shfl_sync(full, y, j);
-                if (trail) e = fma(-li, ak, e);
-                if (drow) {
-                    dg = fma(-ld, ad, dg);
-                    y = fma(-ld, yj, y);
+            for (int j = 0; j < 8; ++j) {
+                const float d = __shfl_sync(full, dg, j);
+                const float r = __frcp_rn(d);
+                if (lane == j) dinv = r;
+                if (j < 7) {
+                    const float l = e * r;
+                    const int cj = j * 7 - (j * (j - 1)) / 2 - j - 1;
+                    const bool trail = lane < 28 && ek > j;
+                    const bool drow = lane > j && lane < 8;
+                    const float li = __shfl_sync(full, l, cj + (trail ? ei : j + 1));
+                    const float ak = __shfl_sync(full, e, cj + (trail ? ek : j + 1));
+                    const float ld = __shfl_sync(full, l, cj + (drow ? lane : j + 1));
+                    const float ad = __shfl_sync(full, e, cj + (drow ? lane : j + 1));
+                    const float yj = __shfl_sync(full, y, j);
+                    if (trail) e = fmaf(-li, ak, e);
+                    if (drow) {
+                        dg = fmaf(-ld, ad, dg);
+                        y = fmaf(-ld, yj, y);
+                    }
+                    if (lane < 28 && ek == j) e = l;
                 }
-                if (lane < 28 && ek == j) e = l;
+            }
+            ok32 = __all_sync(full, dg > 1e-4f * a0f || lane >= 8);
+            if (ok32) {
+                // row `row` of L (left of the diagonal) and column `row` (below it)
+                float Lrow[8], Lcol[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int ck = k * 7 - (k * (k - 1)) / 2 - k - 1;   // lane of (i, k) is ck + i
+                    const float v = __shfl_sync(full, e, k < row ? ck + row : 0);
+                    Lrow[k] = k < row ? v : 0.0f;
+                }
+#pragma unroll
+                for (int i = 1; i < 8; ++i) {
+                    const int cr = row * 7 - (row * (row - 1)) / 2 - row - 1;
+                    const float v = __shfl_sync(full, e, row < i ? cr + i : 0);
+                    Lcol[i] = row < i ? v : 0.0f;
+                }
+                float x = y * dinv;
+#pragma unroll
+                for (int j = 7; j >= 1; --j) {
+                    const float xj = __shfl_sync(full, x, j);
+                    if (row < j) x = fmaf(-Lcol[j], xj, x);
+                }
+                // refinement: r = -g - A x in FP64, then L D L^T z = r in FP32
+                double x64 = f64_of(x);
+                double xs[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) xs[c] = __shfl_sync(full, x64, c);
+                double r0 = -S.g[row], r1 = 0.0;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    r0 = fma(-(c == row ? a0 : S.H[8 * row + c]), xs[c], r0);
+                    r1 = fma(-(c + 4 == row ? a0 : S.H[8 * row + c + 4]), xs[c + 4], r1);
+                }
+                float z = f32_of(r0 + r1);
+#pragma unroll
+                for (int j = 0; j < 7; ++j) {
+                    const float zj = __shfl_sync(full, z, j);
+                    if (row > j) z = fmaf(-Lrow[j], zj, z);
+                }
+                z *= dinv;
+#pragma unroll
+                for (int j = 7; j >= 1; --j) {
+                    const float zj = __shfl_sync(full, z, j);
+                    if (row < j) z = fmaf(-Lcol[j], zj, z);
+                }
+                x64 += f64_of(z);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) dl[c] = __shfl_sync(full, x64, c);
+                solved = true;
             }
         }
-        // pivots checked once, each lane its own: d > 0 and d > 1e-13 * damped diagonal
-        const bool piv_ok = dg > 1e-13 * a0 && dg > 0.0;
-        const bool ok = __all_sync(full, piv_ok || lane >= 8);
-        if (!ok) {
-            if (lane == 0) S.status |= GLT_TRACK_NOT_PD;
-            finish = true;
-            next_level = true;
-        } else {
-            // column `row` of L (entries below the diagonal) gathered into the row's lane
-            double Lcol[8];
+        if (!ok32) {
+            // ---- the FP64 elimination (the layout above, FP64 reciprocals)
+            double e = lane < 28 ? S.H[8 * ei + ek] : 0.0;
+            const double diag = S.H[8 * row + row];
+            const double a0 = fma(lambda, diag, diag);   // damped diagonal (lanes 0-7)
+            double dg = a0;
+            double dinv = 0.0;
+            // the forward substitution L y = -g rides along: y_i -= l_ij y_j with the
+            // l_ij the diagonal update already fetched (lanes 0-7 hold y_i)
+            double y = -S.g[row];
 #pragma unroll
-            for (int i = 1; i < 8; ++i) {
-                const int cr = row * 7 - (row * (row - 1)) / 2 - row - 1;
-                const double v = __shfl_sync(full, e, row < i ? cr + i : 0);
-                Lcol[i] = row < i ? v : 0.0;
+            for (int j = 0; j < 8; ++j) {
+                const double d = __shfl_sync(full, dg, j);
+                const double r = rcp_d(d);
+                if (lane == j) dinv = r;
+                if (j < 7) {
+                    const double l = e * r;                         // l_ij on the lanes of column j
+                    const int cj = j * 7 - (j * (j - 1)) / 2 - j - 1;   // lane of (i, j) is cj + i
+                    const bool trail = lane < 28 && ek > j;        // entry (i, k), k > j: -= l_ij a_kj
+                    const bool drow = lane > j && lane < 8;          // diagonal d_i, i > j: -= l_ij a_ij
+                    const double li = __shfl_sync(full, l, cj + (trail ? ei : j + 1));
+                    const double ak = __shfl_sync(full, e, cj + (trail ? ek : j + 1));
+                    const double ld = __shfl_sync(full, l, cj + (drow ? lane : j + 1));
+                    const double ad = __shfl_sync(full, e, cj + (drow ? lane : j + 1));
+                    const double yj = __shfl_sync(full, y, j);
+                    if (trail) e = fma(-li, ak, e);
+                    if (drow) {
+                        dg = fma(-ld, ad, dg);
+                        y = fma(-ld, yj, y);
+                    }
+                    if (lane < 28 && ek == j) e = l;
+                }
             }
-            // diagonal, backward (L^T x = D^-1 y)
-            double x = y * dinv;
+            // pivots checked once, each lane its own: d > 0 and d > 1e-13 * damped diagonal
+            const bool piv_ok = dg > 1e-13 * a0 && dg > 0.0;
+            const bool ok = __all_sync(full, piv_ok || lane >= 8);
+            if (!ok) {
+                if (lane == 0) S.status |= GLT_TRACK_NOT_PD;
+                finish = true;
+                next_level = true;
+            } else {
+                // column `row` of L (entries below the diagonal) gathered into the row's lane
+                double Lcol[8];
 #pragma unroll
-            for (int j = 7; j >= 1; --j) {
-                const double xj = __shfl_sync(full, x, j);
-                if (row < j) x = fma(-Lcol[j], xj, x);
+                for (int i = 1; i < 8; ++i) {
+                    const int cr = row * 7 - (row * (row - 1)) / 2 - row - 1;
+                    const double v = __shfl_sync(full, e, row < i ? cr + i : 0);
+                    Lcol[i] = row < i ? v : 0.0;
+                }
+                // diagonal, backward (L^T x = D^-1 y)
+                double x = y * dinv;
+#pragma unroll
+                for (int j = 7; j >= 1; --j) {
+                    const double xj = __shfl_sync(full, x, j);
+                    if (row < j) x = fma(-Lcol[j], xj, x);
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) dl[c] = __shfl_sync(full, x, c);
+                solved = true;
             }
-#pragma unroll
-            for (int c = 0; c < 8; ++c) dl[c] = __shfl_sync(full, x, c);
-            solved = true;
         }
     }
     if (solved) {
@@ -1092,59 +1257,58 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
             long long mbits = 0;
 #pragma unroll
             for (int c = 0; c < 6; ++c) mbits = max(mbits, abs_bits(dl[c]));
-            // ---- exp(delta_xi): R_e = I + A [w]x + B [w]x^2, t_e = v + B (w x v) + C w x (w x v)
-            const double w0 = dl[3], w1 = dl[4], w2 = dl[5];
-            const double th2 = fma(w0, w0, fma(w1, w1, w2 * w2));
-            double A, B, Cc;
-            if (th2 < 1e-4) {
-                A = fma(fma(th2, 1.0 / 120.0, -1.0 / 6.0), th2, 1.0);
-                B = fma(fma(th2, 1.0 / 720.0, -1.0 / 24.0), th2, 0.5);
-                Cc = fma(fma(th2, 1.0 / 5040.0, -1.0 / 120.0), th2, 1.0 / 6.0);
-            } else if (th2 < 0.01) {
-                A = fma(fma(fma(fma(th2, 1.0 / 362880.0, -1.0 / 5040.0), th2, 1.0 / 120.0), th2, -1.0 / 6.0), th2, 1.0);
-                B = fma(fma(fma(fma(th2, 1.0 / 3628800.0, -1.0 / 40320.0), th2, 1.0 / 720.0), th2, -1.0 / 24.0), th2, 0.5);
-                Cc = fma(fma(fma(fma(th2, 1.0 / 39916800.0, -1.0 / 362880.0), th2, 1.0 / 5040.0), th2, -1.0 / 120.0), th2, 1.0 / 6.0);
+            // ---- exp(delta_xi) - I in FP32: its entries are O(|delta|), so FP32
+            // rounding leaves ~1e-7 |delta| (absolute); the product with T is FP64.
+            //   R_e - I = A [w]x + B [w]x^2,  t_e = v + B (w x v) + C w x (w x v),
+            // A = sin th / th, B = (1 - cos th) / th^2, C = (th - sin th) / th^3
+            // (power series below th^2 = 0.25, truncation < 3e-11 relative)
+            const float v0 = f32_of(dl[0]), v1 = f32_of(dl[1]), v2 = f32_of(dl[2]);
+            const float w0 = f32_of(dl[3]), w1 = f32_of(dl[4]), w2 = f32_of(dl[5]);
+            const float th2 = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
+            float A, B, Cc;
+            if (th2 < 0.25f) {
+                A = fmaf(fmaf(fmaf(fmaf(th2, 1.0f / 362880.0f, -1.0f / 5040.0f), th2, 1.0f / 120.0f), th2, -1.0f / 6.0f), th2, 1.0f);
+                B = fmaf(fmaf(fmaf(fmaf(th2, 1.0f / 3628800.0f, -1.0f / 40320.0f), th2, 1.0f / 720.0f), th2, -1.0f / 24.0f), th2, 0.5f);
+                Cc = fmaf(fmaf(fmaf(fmaf(th2, 1.0f / 39916800.0f, -1.0f / 362880.0f), th2, 1.0f / 5040.0f), th2, -1.0f / 120.0f), th2, 1.0f / 6.0f);
             } else {
-                const double th = sqrt(th2);
-                double sn, cs, sh, ch;
-                sincos(th, &sn, &cs);
-                sincos(0.5 * th, &sh, &ch);
+                const float th = sqrtf(th2);
+                const float sn = sinf(th), sh = sinf(0.5f * th);
                 A = sn / th;
-                B = 2.0 * sh * sh / th2;
+                B = 2.0f * sh * sh / th2;
                 Cc = (th - sn) / (th2 * th);
             }
-            // ---- E = exp(delta_xi) as a 3x4 [R_e | t_e], one element (r, c) per lane
-            // 0-11, every lane running the same FP64 instructions on its own operands:
-            //   R_e(r, c) = d_rc + A W_rc + B (w_r w_c - d_rc th2)            (W = [w]x)
-            //   t_e(r)    = v_r + B (w x v)_r + C (w_r (w . v) - v_r th2)
+            // one element (r, c) of the 3x4 increment per lane 0-11, every lane
+            // running the same instructions on its own operands:
+            //   (R_e - I)(r, c) = A W_rc + B (w_r w_c - d_rc th2)        (W = [w]x)
+            //   t_e(r)          = v_r + B (w x v)_r + C (w_r (w . v) - v_r th2)
             // as  base + cA (a1 b1 - a2 b2) + cB (p q - d th2).
-            const double v0 = dl[0], v1 = dl[1], v2 = dl[2];
-            const double wv = fma(w0, v0, fma(w1, v1, w2 * v2));
+            const float wv = fmaf(w0, v0, fmaf(w1, v1, w2 * v2));
             const int er = (lane >> 2) % 3, ec = lane & 3;
-            const double wr = er == 0 ? w0 : (er == 1 ? w1 : w2);
-            const double wr1 = er == 0 ? w1 : (er == 1 ? w2 : w0);   // w_{r+1}
-            const double wr2 = er == 0 ? w2 : (er == 1 ? w0 : w1);   // w_{r+2}
-            const double vr = er == 0 ? v0 : (er == 1 ? v1 : v2);
-            const double vr1 = er == 0 ? v1 : (er == 1 ? v2 : v0);
-            const double vr2 = er == 0 ? v2 : (er == 1 ? v0 : v1);
-            const double wc = ec == 0 ? w0 : (ec == 1 ? w1 : w2);
+            const float wr = er == 0 ? w0 : (er == 1 ? w1 : w2);
+            const float wr1 = er == 0 ? w1 : (er == 1 ? w2 : w0);   // w_{r+1}
+            const float wr2 = er == 0 ? w2 : (er == 1 ? w0 : w1);   // w_{r+2}
+            const float vr = er == 0 ? v0 : (er == 1 ? v1 : v2);
+            const float vr1 = er == 0 ? v1 : (er == 1 ? v2 : v0);
+            const float vr2 = er == 0 ? v2 : (er == 1 ? v0 : v1);
+            const float wc = ec == 0 ? w0 : (ec == 1 ? w1 : w2);
             const bool rot = ec < 3;
-            const double drc = (rot && er == ec) ? 1.0 : 0.0;
+            const float drc = (rot && er == ec) ? 1.0f : 0.0f;
             // W_rc = +w_{r+2} if c = r+1, -w_{r+1} if c = r+2, 0 on the diagonal
-            const double Wrc = ec == (er + 1) % 3 ? -wr2 : (ec == (er + 2) % 3 ? wr1 : 0.0);
-            const double base = rot ? drc : vr;
-            const double a1 = rot ? Wrc : wr1, b1 = rot ? 1.0 : vr2;
-            const double a2 = rot ? 0.0 : wr2, b2 = rot ? 0.0 : vr1;
-            const double pq = rot ? wc : wv, dd = rot ? drc : vr;
-            const double ex = fma(a1, b1, -(a2 * b2));
-            const double ey = fma(wr, pq, -(dd * th2));
-            const double E = fma(rot ? B : Cc, ey, fma(rot ? A : B, ex, base));
-            // ---- Tc = T E: Tc(r, c) = sum_k T(r, k) E(k, c) (+ T(r, 3) for c = 3)
-            const double e0 = __shfl_sync(full, E, ec);
-            const double e1 = __shfl_sync(full, E, 4 + ec);
-            const double e2 = __shfl_sync(full, E, 8 + ec);
+            const float Wrc = ec == (er + 1) % 3 ? -wr2 : (ec == (er + 2) % 3 ? wr1 : 0.0f);
+            const float base = rot ? 0.0f : vr;
+            const float a1 = rot ? Wrc : wr1, b1 = rot ? 1.0f : vr2;
+            const float a2 = rot ? 0.0f : wr2, b2 = rot ? 0.0f : vr1;
+            const float pq = rot ? wc : wv, dd = rot ? drc : vr;
+            const float ex = fmaf(a1, b1, -(a2 * b2));
+            const float ey = fmaf(wr, pq, -(dd * th2));
+            const float dE = fmaf(rot ? B : Cc, ey, fmaf(rot ? A : B, ex, base));
+            // ---- Tc = T exp(delta) = T + T (exp(delta) - I) in FP64:
+            // Tc(r, c) = T(r, c) + sum_k T(r, k) dE(k, c)   (c = 3: dE(k, 3) = t_e(k))
+            const double e0 = f64_of(__shfl_sync(full, dE, ec));
+            const double e1 = f64_of(__shfl_sync(full, dE, 4 + ec));
+            const double e2 = f64_of(__shfl_sync(full, dE, 8 + ec));
             const double tc = lane < 12 ? fma(S.T[4 * er], e0, fma(S.T[4 * er + 1], e1,
-                                                  fma(S.T[4 * er + 2], e2, rot ? 0.0 : S.T[4 * er + 3])))
+                                                  fma(S.T[4 * er + 2], e2, S.T[4 * er + ec])))
                                         : 0.0;
             const double ac = S.a + dl[6], bc = S.b + dl[7];
             const bool cand_finite = __all_sync(full, abs_bits(tc) < kInfBits) &&
@@ -1168,6 +1332,7 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
                 if (lane == 0) {
                     S.a = ac;
                     S.b = bc;
+                    S.moved = 1;
                 }
                 ++it;
                 finish = true;
@@ -1180,8 +1345,7 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
                     S.maxstep_bits = mbits;
                     S.phase = PH_CAND;
                 }
-                __syncwarp();
-                make_pass_params_warp(S.Tc, ac, bc, level, P, lane);
+                make_pass_params_lane(tc, ac, bc, level, P, lane);
             }
         }
     }
@@ -1195,6 +1359,28 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
         int l = level - 1;
         while (l >= 0 && D.max_iters[l] <= 0) --l;
         if (l < 0) {
+            // the poses composed from FP32 increments drift from orthonormal
+            // by ~1e-9 per step: one Newton step R' = R (3 I - R^T R) / 2 =
+            // R + R (I - R^T R) / 2 on the final pose (FP64; the deviation
+            // becomes its square)
+            if (S.moved) {
+                const int i = lane / 3, j = lane % 3;
+                double dlt = lane < 9 ? (i == j ? 1.0 : 0.0) : 0.0;
+                if (lane < 9) {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) dlt = fma(-S.T[4 * k + i], S.T[4 * k + j], dlt);
+                }
+                const int r = lane >> 2, c = lane & 3;
+                const int cc = c < 3 ? c : 0;
+                const double d0 = __shfl_sync(full, dlt, cc), d1 = __shfl_sync(full, dlt, 3 + cc),
+                             d2 = __shfl_sync(full, dlt, 6 + cc);
+                double v = 0.0;
+                if (lane < 12 && c < 3)
+                    v = fma(0.5, fma(S.T[4 * r], d0, fma(S.T[4 * r + 1], d1, S.T[4 * r + 2] * d2)),
+                            S.T[lane]);
+                __syncwarp();
+                if (lane < 12 && c < 3) S.T[lane] = v;
+            }
             if (lane == 0) {
                 S.done = 1;
                 P.done = 1;
