@@ -63,6 +63,9 @@ extern "C" {
 #define GLT_TRACK_NOT_PD 2         /* the damped normal matrix was not positive definite */
 #define GLT_TRACK_DIVERGED 4       /* a non-finite start, pass sum (FP32 overflow) or
                                       candidate state; the state before it is returned */
+#define GLT_TRACK_TIMEOUT 8        /* a CTA of the stream's cluster waited longer than its
+                                      limit (about a second) for a peer's partial sums; the
+                                      accepted state before that pass is returned */
 
 /* pyramid slots */
 #define GLT_REF 0
@@ -329,6 +332,16 @@ int glt_debug_rcp(const double* d_dev, double* r_dev, int n, void* stream);
  * launch: cached needs 512 threads), CUDA. */
 int glt_debug_pass_floor(int cluster, int threads, int cached, int passes, float* us_per_pass,
                          void* stream);
+
+/* Failure test of the cluster exchange (no counterpart in the paper): one
+ * pass of the latency-floor kernel on a `cluster`-CTA cluster whose CTA 0
+ * withholds its partial sums, so every CTA's bounded wait runs out (about a
+ * second, twice: the wait and the drain before the CTAs leave together).
+ * *status = GLT_TRACK_TIMEOUT when the kernel reported the timeout, else 0;
+ * the context stays usable.  Synchronous.
+ * Errors: INVALID_ARG (cluster outside [2, 16], a shape that cannot launch),
+ * CUDA. */
+int glt_debug_exchange_timeout(int cluster, int threads, int* status, void* stream);
 
 /* The (cluster, threads) shape the tracker's solve launches with (chosen at
  * glt_create and again when the point count changes, or set in the config). */

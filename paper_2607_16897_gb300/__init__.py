@@ -32,6 +32,7 @@ GLT_ERR_IO = -6
 GLT_TRACK_TOO_FEW_POINTS = 1
 GLT_TRACK_NOT_PD = 2
 GLT_TRACK_DIVERGED = 4
+GLT_TRACK_TIMEOUT = 8
 GLT_REF, GLT_CUR = 0, 1
 GLT_FP32, GLT_MIXED = 0, 1
 GLT_FORWARD, GLT_IC = 0, 1
@@ -103,6 +104,7 @@ SIGNATURES = {
                                  _P(ctypes.c_float), _vp]),
     "glt_debug_rcp": (_i, [_vp, _vp, _i, _vp]),
     "glt_debug_pass_floor": (_i, [_i, _i, _i, _i, _P(ctypes.c_float), _vp]),
+    "glt_debug_exchange_timeout": (_i, [_i, _i, _P(ctypes.c_int), _vp]),
     "glt_get_shape": (_i, [_vp, _P(_i), _P(_i)]),
     "glt_get_pyramid": (_i, [_vp, _i, _i, _P(ctypes.c_uint8), _vp]),
     "glt_get_trace": (_i, [_vp, _P(_d), _P(_i), _i, _P(_i), _vp]),

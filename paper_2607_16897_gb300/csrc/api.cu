@@ -186,12 +186,15 @@ const char* glt_status_string(int code)
     case GLT_ERR_IO: return "file error";
     default: break;
     }
-    // status bits: every combination of the three per-frame outcomes
-    static const char* const kBits[8] = {
+    // status bits: every combination of the four per-frame outcomes
+    static const char* const kBits[16] = {
         "ok", "too few points", "not positive definite", "too few points|not positive definite",
         "diverged", "too few points|diverged", "not positive definite|diverged",
-        "too few points|not positive definite|diverged"};
-    if (code > 0 && code < 8) return kBits[code];
+        "too few points|not positive definite|diverged", "timeout", "too few points|timeout",
+        "not positive definite|timeout", "too few points|not positive definite|timeout",
+        "diverged|timeout", "too few points|diverged|timeout", "not positive definite|diverged|timeout",
+        "too few points|not positive definite|diverged|timeout"};
+    if (code > 0 && code < 16) return kBits[code];
     return "unknown";
 }
 

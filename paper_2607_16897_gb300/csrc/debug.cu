@@ -54,3 +54,22 @@ extern "C" int glt_debug_pass_floor(int cluster, int threads, int cached, int pa
     *us_per_pass = 1000.0f * ms / (float)passes;
     return GLT_OK;
 }
+
+extern "C" int glt_debug_exchange_timeout(int cluster, int threads, int* status, void* stream)
+{
+    if (!status || cluster < 2 || cluster > 16)
+        return invalid_arg_msg("glt_debug_exchange_timeout: bad argument");
+    if (!track_shape_ok(cluster, threads, 0))
+        return invalid_arg_msg("glt_debug_exchange_timeout: shape cannot launch");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    long long* cyc = nullptr;
+    long long host = 0;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&cyc), sizeof(long long));
+    if (e == cudaSuccess) e = launch_pass_floor(cluster, threads, false, 1, cyc, s, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host, cyc, sizeof(long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(cyc);
+    if (e != cudaSuccess) return cuda_fail(e, "glt_debug_exchange_timeout");
+    *status = host < 0 ? GLT_TRACK_TIMEOUT : 0;
+    return GLT_OK;
+}

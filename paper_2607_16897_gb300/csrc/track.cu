@@ -19,6 +19,82 @@ namespace glt {
 
 constexpr int kMaxCluster = 16;   // largest cluster a stream may use (config.cluster)
 
+// ---------------------------------------------------------------------------
+// Cluster exchange of the CTA partial sums.  Every CTA pushes its partial
+// (48 floats; with the Kahan compensations 96) into a slot of every CTA of
+// the cluster, itself included, with st.async stores that complete bytes on
+// the receiver's mbarrier; a CTA sums its slots in rank order once its
+// barrier's phase has completed.  One mbarrier and one slot array per pass
+// parity: pass k + 2 writes a CTA's parity-k slots only after every CTA has
+// finished pass k + 1, which needs this CTA's pass k + 1 partial, pushed after
+// it read its pass k slots.  Waits are bounded (kExchangeLimit cycles); a
+// wait that runs out ends the solve with GLT_TRACK_TIMEOUT.
+constexpr long long kExchangeLimit = 1ll << 31;    // ~1 s at 2 GHz
+
+template <int W>
+struct Exchange {
+    float slot[2][kMaxCluster][W];
+    unsigned long long mbar[2];
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* m, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long* m, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes)
+                 : "memory");
+}
+
+// true once the phase of parity `parity` has completed; false after `limit` cycles
+__device__ __forceinline__ bool mbar_wait(unsigned long long* m, unsigned parity, long long limit)
+{
+    const long long t0 = clock64();
+    while (true) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(smem_addr(m)), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
+// 16 bytes to CTA `cta`'s copy of the local address `dst`, completing on its copy of `m`
+__device__ __forceinline__ void push16(float* dst, float4 v, unsigned long long* m, unsigned cta)
+{
+    unsigned rd, rm;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rd) : "r"(smem_addr(dst)), "r"(cta));
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rm) : "r"(smem_addr(m)), "r"(cta));
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
+                 ::"r"(rd), "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
+                   "r"(__float_as_uint(v.w)), "r"(rm)
+                 : "memory");
+}
+
+// Arm this pass's receive, push the CTA partial src[0:W] (16-byte chunks) to
+// every CTA of the cluster.  Called by all threads after the block reduction.
+template <int THREADS, int W>
+__device__ __forceinline__ void exchange_push(Exchange<W>& X, int par, const float* src, int C, int rank)
+{
+    constexpr int CH = W / 4;
+    if (threadIdx.x == 0) mbar_arrive_expect(&X.mbar[par], (unsigned)(C * W * 4));
+    for (int t = threadIdx.x; t < C * CH; t += THREADS) {
+        const int r = t / CH, q = t % CH;
+        push16(&X.slot[par][rank][4 * q], reinterpret_cast<const float4*>(src)[q], &X.mbar[par], (unsigned)r);
+    }
+}
+
 // The 128-thread shape is capped at 128 registers so four CTAs fit on an SM
 // (batches of many small clusters); the wider shapes keep the registers the
 // compiler wants (a single stream's latency).
@@ -40,13 +116,16 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
     constexpr bool MIXED = VAR == 1, SQUARE = VAR == 2 || VAR == 4, IC = VAR != 0, HC = VAR == 4;
     constexpr int NACC = HC ? kHcAcc : kAccPad;    // accumulators per thread
     constexpr int NSUM = HC ? kHcAcc : kNumAcc;    // sums exchanged per pass
+    // CTA partial per pass parity: the sums (MIXED: their compensations at +kAccPad)
+    constexpr int XW = HC ? kHcAcc : MIXED ? 2 * kAccPad : kAccPad;
     __shared__ StreamDesc sD;
     __shared__ PassParams P;
     __shared__ Solver S;
     __shared__ float red[NW][kAccPad];
-    __shared__ float part[2][kAccPad];
-    __shared__ float part_c[2][kAccPad];
+    __shared__ __align__(16) float part[2][XW];
+    __shared__ __align__(16) Exchange<XW> X;
     __shared__ double tot[kAccPad];
+    __shared__ int xfail;
 
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
@@ -61,8 +140,20 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
         for (int i = tid; i < (int)(sizeof(StreamDesc) / sizeof(int)); i += THREADS) dst[i] = src[i];
     }
     __syncthreads();
-    if (tid == 0) solver_init(sD, init + 14 * user, S, P);
-    __syncthreads();
+    if (tid == 0) {
+        solver_init(sD, init + 14 * user, S, P);
+        xfail = 0;
+        if (C > 1) {
+            mbar_init(&X.mbar[0], 1);
+            mbar_init(&X.mbar[1], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+    }
+    // every CTA's barriers exist before the first push
+    if (C > 1)
+        cluster.sync();
+    else
+        __syncthreads();
     // Everything above reads data that was final before the previous kernel
     // of the stream started; the CUR levels it may still be writing are read
     // only after this wait (a no-op unless launched as a programmatic
@@ -72,6 +163,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
 
     const int tail_warp = (int)(blockIdx.x % NW);
     int par = 0;
+    unsigned xph = 0;    // bit p: parity of the phase of X.mbar[p] the next wait completes
     PointCache pc;
     pc.p = -1;
     pc.level = -1;
@@ -100,20 +192,21 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
         if constexpr (HC)
             block_reduce8<THREADS>(acc, red, part[par]);
         else
-            block_reduce<THREADS, MIXED>(acc, red, part[par], part_c[par]);
-        if (C > 1) cluster.sync();
+            block_reduce<THREADS, MIXED>(acc, red, part[par], MIXED ? part[par] + kAccPad : nullptr);
+        if (C > 1) exchange_push<THREADS, XW>(X, par, part[par], C, rank);
         if (tid < NSUM) {
             // finish over the CTAs of the cluster: a compensated FP32 sum
-            // (TwoSum, error-free per step) converted to FP64 once; the FP64
-            // pipe of this GPU is too slow to carry a chain of C adds
-            // (all remote loads are issued before the first add: one
-            // distributed-shared-memory round trip instead of C)
+            // (TwoSum, error-free per step) of the pushed partials in rank
+            // order, converted to FP64 once; the FP64 pipe of this GPU is too
+            // slow to carry a chain of C adds
+            if (C > 1 && !mbar_wait(&X.mbar[par], (xph >> par) & 1u, kExchangeLimit)) xfail = 1;
+            const float* src = C > 1 ? &X.slot[par][0][0] : &part[par][0];
             float v[kMaxCluster], vc[kMaxCluster];
 #pragma unroll
             for (int r = 0; r < kMaxCluster; ++r) {
                 if (r < C) {
-                    v[r] = C > 1 ? cluster.map_shared_rank(&part[par][0], r)[tid] : part[par][tid];
-                    if (MIXED) vc[r] = C > 1 ? cluster.map_shared_rank(&part_c[par][0], r)[tid] : part_c[par][tid];
+                    v[r] = src[r * XW + tid];
+                    if (MIXED) vc[r] = src[r * XW + kAccPad + tid];
                 }
             }
             float hi = 0.0f, lo = 0.0f;
@@ -129,14 +222,28 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
             }
             tot[tid] = (double)hi + (double)lo;
         }
+        xph ^= 1u << par;
         __syncthreads();
+        if (xfail) {
+            // a peer's partial did not arrive within the limit: end the solve
+            // with the accepted state
+            if (tid == 0) {
+                S.status |= GLT_TRACK_TIMEOUT;
+                S.done = 1;
+            }
+            break;
+        }
         // the FP64 tail runs on one warp; CTAs of different streams that share an
         // SM use different warps so their tails spread over the SM's sub-partitions
         if ((tid >> 5) == tail_warp) solver_step_warp<HC>(sD, tot, S, P, tid & 31, rank == 0);
         __syncthreads();
         par ^= 1;
     }
-    // peers may still read this CTA's partial sums: leave together
+    if (xfail && tid == 0) {
+        // let pushes still in flight into this CTA land (bounded) before it leaves
+        mbar_wait(&X.mbar[par], ((xph >> par) & 1u) ^ 1u, kExchangeLimit);
+    }
+    // leave together: no CTA exits while a peer may still push into it
     if (C > 1) cluster.sync();
     if (rank == 0 && tid == 0) solver_write_result(sD, S, results + user);
 }
@@ -151,16 +258,20 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
 __device__ double g_floor_Hc[72];   // H and H^-1 of the cached-Hessian floor (device data)
 
 template <int THREADS, bool HC>
-__global__ void __launch_bounds__(THREADS, 1) pass_floor_kernel(int passes, long long* __restrict__ cycles)
+__global__ void __launch_bounds__(THREADS, 1) pass_floor_kernel(int passes, int drop_rank,
+                                                                 long long* __restrict__ cycles)
 {
     constexpr int NW = THREADS / 32;
     constexpr int NSUM = HC ? kHcAcc : kNumAcc;
+    constexpr int XW = HC ? kHcAcc : kAccPad;
     __shared__ StreamDesc sD;
     __shared__ PassParams P;
     __shared__ Solver S;
     __shared__ float red[NW][kAccPad];
-    __shared__ float part[2][kAccPad];
+    __shared__ __align__(16) float part[2][XW];
+    __shared__ __align__(16) Exchange<XW> X;
     __shared__ double tot[kAccPad];
+    __shared__ int xfail;
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
@@ -185,11 +296,18 @@ __global__ void __launch_bounds__(THREADS, 1) pass_floor_kernel(int passes, long
         double init[14];
         for (int i = 0; i < 14; ++i) init[i] = (i < 12 && i % 5 == 0) ? 1.0 : 0.0;
         solver_init(sD, init, S, P);
+        xfail = 0;
+        if (C > 1) {
+            mbar_init(&X.mbar[0], 1);
+            mbar_init(&X.mbar[1], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
     }
     if (C > 1) cluster.sync();
     __syncthreads();
     const long long t0 = clock64();
     int par = 0;
+    unsigned xph = 0;
     for (int it = 0; it < passes; ++it) {
         float acc[kAccPad];
 #pragma unroll
@@ -202,12 +320,15 @@ __global__ void __launch_bounds__(THREADS, 1) pass_floor_kernel(int passes, long
         } else {
             block_reduce<THREADS, false>(acc, red, part[par], nullptr);
         }
-        if (C > 1) cluster.sync();
+        // drop_rank >= 0 (the timeout test): that CTA withholds its first push
+        if (C > 1 && !(it == 0 && rank == drop_rank)) exchange_push<THREADS, XW>(X, par, part[par], C, rank);
         if (tid < NSUM) {
+            if (C > 1 && !mbar_wait(&X.mbar[par], (xph >> par) & 1u, kExchangeLimit)) xfail = 1;
+            const float* src = C > 1 ? &X.slot[par][0][0] : &part[par][0];
             float v[kMaxCluster];
 #pragma unroll
             for (int r = 0; r < kMaxCluster; ++r)
-                if (r < C) v[r] = C > 1 ? cluster.map_shared_rank(&part[par][0], r)[tid] : part[par][tid];
+                if (r < C) v[r] = src[r * XW + tid];
             float hi = 0.0f, lo = 0.0f;
 #pragma unroll
             for (int r = 0; r < kMaxCluster; ++r) {
@@ -229,14 +350,17 @@ __global__ void __launch_bounds__(THREADS, 1) pass_floor_kernel(int passes, long
             }
             tot[tid] = x + (double)hi + (double)lo;
         }
+        xph ^= 1u << par;
         __syncthreads();
+        if (xfail) break;
         if ((tid >> 5) == (int)(blockIdx.x % NW)) solver_step_warp<HC>(sD, tot, S, P, tid & 31, false);
         __syncthreads();
         par ^= 1;
     }
     const long long t1 = clock64();
+    if (xfail && tid == 0) mbar_wait(&X.mbar[par], ((xph >> par) & 1u) ^ 1u, kExchangeLimit);
     if (C > 1) cluster.sync();
-    if (blockIdx.x == 0 && tid == 0) cycles[0] = t1 - t0;
+    if (blockIdx.x == 0 && tid == 0) cycles[0] = xfail ? -1 : t1 - t0;
 }
 
 // One linearisation pass over all points of one tracker, many blocks, with a
@@ -466,7 +590,7 @@ cudaError_t launch_linearize(const glt_tracker* t, const PassParams& P, bool wan
 namespace glt {
 
 cudaError_t launch_pass_floor(int cluster, int threads, bool cached, int passes, long long* cycles,
-                              cudaStream_t s)
+                              cudaStream_t s, int drop_rank)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)cluster, 1, 1);
@@ -486,7 +610,7 @@ cudaError_t launch_pass_floor(int cluster, int threads, bool cached, int passes,
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1); \
             if (e != cudaSuccess) return e;                                                     \
         }                                                                                       \
-        return cudaLaunchKernelEx(&cfg, k, passes, cycles);                                     \
+        return cudaLaunchKernelEx(&cfg, k, passes, drop_rank, cycles);                          \
     }
     if (cached) {
         if (threads == 512) GLT_FLOOR(512, true)

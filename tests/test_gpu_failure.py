@@ -1,8 +1,10 @@
 """Failure detection on the GPU without a GPU fault: a start that is not
 finite, and pass sums that overflow FP32, end the solve with the DIVERGED
 status bit (the state before the failure is returned); the FP64 oracle
-flags the same inputs.  Also the solver's FP64 reciprocal (one Newton-Raphson
-step on an FP32 seed) against IEEE division across the exponent range."""
+flags the same inputs.  A cluster exchange whose partial sums do not arrive
+ends with the TIMEOUT status after its bounded wait.  Also the solver's FP64
+reciprocal (one Newton-Raphson step on an FP32 seed) against IEEE division
+across the exponent range."""
 import numpy as np
 import pytest
 
@@ -102,3 +104,18 @@ def test_reciprocal_against_ieee_division(glt):
     ok = ~np.isnan(ref[out])
     assert np.array_equal(r[out][ok], ref[out][ok])
     assert glt.glt_debug_rcp(0, 0, -1, None) == glt.GLT_ERR_INVALID_ARG
+
+
+def test_cluster_exchange_wait_runs_out_and_reports(glt):
+    """A CTA that withholds its partial sums: every bounded wait of the
+    cluster exchange runs out, the kernel reports GLT_TRACK_TIMEOUT, and the
+    context stays usable (the next floor launch completes normally)."""
+    import ctypes
+    st = ctypes.c_int(-1)
+    assert glt.glt_debug_exchange_timeout(4, 256, ctypes.byref(st), None) == 0
+    assert st.value == glt.GLT_TRACK_TIMEOUT
+    assert glt.glt_status_string(st.value) == b"timeout"
+    assert glt.pass_floor(4, 256, passes=20) > 0.0
+    with pytest.raises(Exception):
+        glt.pass_floor(4, 300)
+    assert glt.glt_debug_exchange_timeout(1, 256, ctypes.byref(st), None) == glt.GLT_ERR_INVALID_ARG
