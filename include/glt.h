@@ -72,8 +72,10 @@ extern "C" {
 #define GLT_CUR 1
 
 /* precision modes */
-#define GLT_FP32 0  /* uint8 levels, FP32 residuals/Jacobians/sums, FP64 solve */
-#define GLT_MIXED 1 /* FP16 (I, gx, gy) levels, FP32 math, Kahan FP32 block sums, FP64 solve */
+#define GLT_FP32 0  /* uint8 levels, FP32 residuals/Jacobians/sums; FP32 L D L^T solve (FP64 for
+                       near-singular systems), FP64 state and pose update */
+#define GLT_MIXED 1 /* FP16 (I, gx, gy) levels, FP32 math, Kahan FP32 block sums; solve and
+                       state as GLT_FP32 */
 
 /* Jacobian forms (Sec. IV-B) */
 #define GLT_FORWARD 0 /* current image's gradient at the warped location, every pass */

@@ -744,9 +744,9 @@ __device__ __forceinline__ void block_reduce(float (&acc)[kAccPad], float (*red)
 // carry FP32 rounding anyway, or whose result is a small increment, is FP32:
 //  * the damped normal matrix is factored as L D L^T (no square roots), one
 //    row per lane, columns eliminated right-looking with warp shuffles, in
-//    FP32, followed by one refinement step whose residual is formed in FP64;
-//    a pivot below 1e-4 of its damped diagonal sends the system to the same
-//    elimination in FP64, which alone decides "not positive definite";
+//    FP32 (its entries are FP32 sums); a pivot below 1e-4 of its damped
+//    diagonal sends the system to the same elimination in FP64, which alone
+//    decides "not positive definite";
 //  * FP64 pivot reciprocals are an FP32 seed refined by one Newton step
 //    (relative error ~4e-15);
 //  * exp(delta) - I is evaluated in FP32 (its entries are O(|delta|)) and
@@ -1100,14 +1100,13 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
         const int ek = lane < 7 ? 0 : lane < 13 ? 1 : lane < 18 ? 2 : lane < 22 ? 3 : lane < 25 ? 4
                      : lane < 27 ? 5 : lane < 28 ? 6 : 7;
         const int ei = lane < 28 ? lane - (ek * 7 - (ek * (ek - 1)) / 2) + ek + 1 : 8;
-        // First in FP32 (the sums it factorises carry FP32 rounding already):
-        // the same elimination, then one refinement step x += A^-1 (b - A x)
-        // with the residual in FP64 against the FP64 system.  Accepted when
-        // every FP32 pivot is above 1e-4 of its damped diagonal, where its
-        // rounding (~1e-6 of the diagonal) cannot change its sign and the
-        // refinement's contraction (~cond x 2^-23) is below 1e-2; otherwise the
-        // FP64 elimination below decides, as for every system it accepts or
-        // rejects as not positive definite.
+        // In FP32: H and g are FP32 sums (relative error ~1e-7), so the step
+        // they define is known to ~cond x 1e-7 however it is solved, and an
+        // FP32 elimination adds an error of the same order (~cond x 2^-23).
+        // Accepted when every FP32 pivot is above 1e-4 of its damped diagonal,
+        // where its rounding (~1e-6 of the diagonal) cannot change its sign;
+        // otherwise the FP64 elimination below decides, as for every system it
+        // accepts or rejects as not positive definite.
         bool ok32;
         {
             float e = lane < 28 ? f32_of(S.H[8 * ei + ek]) : 0.0f;
@@ -1141,50 +1140,22 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
             }
             ok32 = __all_sync(full, dg > 1e-4f * a0f || lane >= 8);
             if (ok32) {
-                // row `row` of L (left of the diagonal) and column `row` (below it)
-                float Lrow[8], Lcol[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int ck = k * 7 - (k * (k - 1)) / 2 - k - 1;   // lane of (i, k) is ck + i
-                    const float v = __shfl_sync(full, e, k < row ? ck + row : 0);
-                    Lrow[k] = k < row ? v : 0.0f;
-                }
+                // column `row` of L (entries below the diagonal) gathered into the row's lane
+                float Lcol[8];
 #pragma unroll
                 for (int i = 1; i < 8; ++i) {
                     const int cr = row * 7 - (row * (row - 1)) / 2 - row - 1;
                     const float v = __shfl_sync(full, e, row < i ? cr + i : 0);
                     Lcol[i] = row < i ? v : 0.0f;
                 }
+                // diagonal, backward (L^T x = D^-1 y)
                 float x = y * dinv;
 #pragma unroll
                 for (int j = 7; j >= 1; --j) {
                     const float xj = __shfl_sync(full, x, j);
                     if (row < j) x = fmaf(-Lcol[j], xj, x);
                 }
-                // refinement: r = -g - A x in FP64, then L D L^T z = r in FP32
-                double x64 = f64_of(x);
-                double xs[8];
-#pragma unroll
-                for (int c = 0; c < 8; ++c) xs[c] = __shfl_sync(full, x64, c);
-                double r0 = -S.g[row], r1 = 0.0;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    r0 = fma(-(c == row ? a0 : S.H[8 * row + c]), xs[c], r0);
-                    r1 = fma(-(c + 4 == row ? a0 : S.H[8 * row + c + 4]), xs[c + 4], r1);
-                }
-                float z = f32_of(r0 + r1);
-#pragma unroll
-                for (int j = 0; j < 7; ++j) {
-                    const float zj = __shfl_sync(full, z, j);
-                    if (row > j) z = fmaf(-Lrow[j], zj, z);
-                }
-                z *= dinv;
-#pragma unroll
-                for (int j = 7; j >= 1; --j) {
-                    const float zj = __shfl_sync(full, z, j);
-                    if (row < j) z = fmaf(-Lcol[j], zj, z);
-                }
-                x64 += f64_of(z);
+                const double x64 = f64_of(x);
 #pragma unroll
                 for (int c = 0; c < 8; ++c) dl[c] = __shfl_sync(full, x64, c);
                 solved = true;
