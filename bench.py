@@ -1196,6 +1196,7 @@ def run_batch(args):
     else:
         shape = batch.autotune(init_dev, out_dev, reps=3, stream=sh)
     classes = batch.classes()
+    class_table = batch.class_table()
 
     def measure(form):
         """Captures the step graph of `form` ("plain" / "proposal") and times it."""
@@ -1291,7 +1292,9 @@ def run_batch(args):
                            "autotuned_shape": {"cluster": shape[0], "threads": shape[1],
                                                "ms": shape[2],
                                                "heavy_streams": classes["heavy"],
-                                               "light_shape": list(classes["light_shape"])},
+                                               "light_shape": list(classes["light_shape"]),
+                                               "classes": [{"first": f, "streams": n, "cluster": c,
+                                                            "threads": t} for f, n, c, t in class_table]},
                            "l2": "flushed between steps (256 MB write, outside the step events)",
                            "timing": "sum of per-step CUDA-event times around the graph replay"},
                 "step_ms_percentiles": step_percentiles(dev_ms),

@@ -394,15 +394,17 @@ int glt_batch_replay(glt_batch* batch, void* stream);
 
 /* Autotuner: times the batched track on the current inputs (`reps` timed
  * launches each) over the candidate launch configurations and keeps the
- * fastest: one (cluster, threads) shape for every stream, or two launch
- * classes (see glt_batch_set_classes) with the first quarter or half of the
- * launch order as the heavy class on a wide shape and the rest on a narrow
- * one.  Results are cached for the process, keyed by the batch's signature
- * (kernel variant and, in launch order, every stream's width, height, point
- * capacity and levels): a batch with a known signature takes the cached
- * configuration without timing.  Reports the heavy class's shape (the only
- * one for a single class) and the measured ms per track.  Synchronous;
- * invalidates a captured graph.  The proposal stage is not timed. */
+ * fastest: one (cluster, threads) shape for every stream; two launch classes
+ * (see glt_batch_set_classes) with the first quarter or half of the launch
+ * order as the heavy class on a wide shape and the rest on a narrow one; or
+ * clusters in proportion to each stream's points (glt_batch_set_proportional)
+ * at several points per CTA.  Results are cached for the process, keyed by
+ * the batch's signature (kernel variant and, in launch order, every stream's
+ * width, height, point capacity and levels): a batch with a known signature
+ * takes the cached configuration without timing.  Reports the first class's
+ * shape (the only one for a single class; glt_batch_get_class_table gives all
+ * of them) and the measured ms per track.  Synchronous; invalidates a
+ * captured graph.  The proposal stage is not timed. */
 int glt_batch_autotune(glt_batch* batch, const double* init_dev, glt_result* out_dev, int reps,
                        int* best_cluster, int* best_threads, float* best_ms, void* stream);
 
@@ -423,9 +425,31 @@ int glt_batch_set_shape(glt_batch* batch, int cluster, int threads);
 int glt_batch_set_classes(glt_batch* batch, int heavy, int heavy_cluster, int heavy_threads,
                           int light_cluster, int light_threads);
 
-/* The batch's current launch classes (any pointer may be NULL). */
+/* The batch's first two launch classes (any pointer may be NULL): heavy = the
+ * first stream of class 1 (S with one class), the shapes of classes 0 and 1
+ * (class 0's twice with one class). */
 int glt_batch_get_classes(const glt_batch* batch, int* heavy, int* heavy_cluster,
                           int* heavy_threads, int* light_cluster, int* light_threads);
+
+/* Launch classes in proportion to work (the paper has no counterpart: a
+ * batching policy).  Stream i of the launch order gets the smallest
+ * power-of-two cluster c <= 16 with c * points_per_cta >= its point capacity
+ * in 8-sample units (max_points * samples per point / 8), reduced to the
+ * largest size that can launch with `threads`; the streams of one cluster
+ * size form a class (at most 5, contiguous in the launch order) and the
+ * classes run as concurrent launches, as in glt_batch_set_classes.  Keeps the
+ * points per thread about equal across streams, so that the streams with the
+ * most points do not set the batch's critical path.  Invalidates a captured
+ * graph.  Errors: INVALID_ARG (points_per_cta < 1, a thread count with which
+ * no cluster size can launch). */
+int glt_batch_set_proportional(glt_batch* batch, int points_per_cta, int threads);
+
+/* All launch classes: *nclass = their number; for k < min(*nclass, max),
+ * first[k] = the class's first stream in the launch order (it runs to the
+ * next class's first, the last to S), cluster[k] and threads[k] its shape
+ * (any array may be NULL). */
+int glt_batch_get_class_table(const glt_batch* batch, int max, int* first, int* cluster,
+                              int* threads, int* nclass);
 
 /* Allocation-free linearisation.  The paper has no counterpart.  It serves
  * callers that may not allocate device memory at the point where they need a

@@ -122,6 +122,8 @@ SIGNATURES = {
     "glt_batch_set_shape": (_i, [_vp, _i, _i]),
     "glt_batch_set_classes": (_i, [_vp, _i, _i, _i, _i, _i]),
     "glt_batch_get_classes": (_i, [_vp, _P(_i), _P(_i), _P(_i), _P(_i), _P(_i)]),
+    "glt_batch_set_proportional": (_i, [_vp, _i, _i]),
+    "glt_batch_get_class_table": (_i, [_vp, _i, _P(_i), _P(_i), _P(_i), _P(_i)]),
     "glt_linearize_noalloc": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _d, _d, _d, _d, _vp, _i, _P(_d),
                                    _d, _d, _d, _d, _vp, _vp]),
     "glt_nn_create": (_i, [_i, _P(_vp)]),
@@ -464,6 +466,25 @@ class Batch:
         _check(_lib.glt_batch_set_classes(self.handle, int(heavy), int(heavy_shape[0]),
                                           int(heavy_shape[1]), int(light_shape[0]),
                                           int(light_shape[1])), "glt_batch_set_classes")
+
+    def set_proportional(self, points_per_cta, threads=128):
+        """Clusters in proportion to each stream's points (one class per
+        cluster size, concurrent launches)."""
+        _check(_lib.glt_batch_set_proportional(self.handle, int(points_per_cta), int(threads)),
+               "glt_batch_set_proportional")
+
+    def class_table(self) -> list:
+        """[(first stream in launch order, count, cluster, threads)] per class."""
+        k = 5
+        first, cl, th = (ctypes.c_int * k)(), (ctypes.c_int * k)(), (ctypes.c_int * k)()
+        n = ctypes.c_int()
+        _check(_lib.glt_batch_get_class_table(self.handle, k, first, cl, th, ctypes.byref(n)),
+               "glt_batch_get_class_table")
+        out = []
+        for i in range(n.value):
+            end = first[i + 1] if i + 1 < n.value else self.S
+            out.append((first[i], end - first[i], cl[i], th[i]))
+        return out
 
     def classes(self) -> dict:
         v = [ctypes.c_int() for _ in range(5)]

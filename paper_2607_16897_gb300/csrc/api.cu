@@ -38,11 +38,92 @@ static int invalid(const char* msg)
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Autotuner results of this process, keyed by the batch signature.
-struct TuneResult {
-    int heavy, cluster, threads, cluster_light, threads_light;
-    float ms;
+// A batch's launch classes (see glt_batch) and, for the autotuner, their time.
+struct ClassTable {
+    int nclass = 1;
+    int first[kMaxBatchClasses + 1] = {};
+    int cluster[kMaxBatchClasses] = {};
+    int threads[kMaxBatchClasses] = {};
+    float ms = 0.0f;
 };
+// Autotuner results of this process, keyed by the batch signature.
+using TuneResult = ClassTable;
+
+static void apply_table(glt_batch* b, const ClassTable& c)
+{
+    b->nclass = c.nclass;
+    for (int k = 0; k <= c.nclass; ++k) b->cls_first[k] = c.first[k];
+    for (int k = 0; k < c.nclass; ++k) {
+        b->cls_cluster[k] = c.cluster[k];
+        b->cls_threads[k] = c.threads[k];
+    }
+}
+
+static ClassTable uniform_table(int S, int cluster, int threads)
+{
+    ClassTable c;
+    c.nclass = 1;
+    c.first[0] = 0;
+    c.first[1] = S;
+    c.cluster[0] = cluster;
+    c.threads[0] = threads;
+    return c;
+}
+
+static void set_uniform(glt_batch* b, int cluster, int threads)
+{
+    apply_table(b, uniform_table(b->S, cluster, threads));
+}
+
+// Two classes: the first `heavy` streams of the launch order and the rest
+// (one class when heavy is 0 or S).
+static ClassTable split_table(int S, int heavy, int hc, int ht, int lc, int lt)
+{
+    if (heavy >= S) return uniform_table(S, hc, ht);
+    if (heavy <= 0) return uniform_table(S, lc, lt);
+    ClassTable c;
+    c.nclass = 2;
+    c.first[0] = 0;
+    c.first[1] = heavy;
+    c.first[2] = S;
+    c.cluster[0] = hc;
+    c.threads[0] = ht;
+    c.cluster[1] = lc;
+    c.threads[1] = lt;
+    return c;
+}
+
+// Clusters in proportion to work: stream i of the launch order gets the
+// smallest power-of-two cluster c <= 16 with c * points_per_cta >= its point
+// capacity in 8-sample units (max_points * K / 8), reduced to the largest
+// size that can launch with `threads`; streams of equal c form a class.  The
+// launch order is by descending capacity x K, so c never grows along it and
+// the classes are contiguous ranges (at most one per size).  False if no
+// cluster size can launch with `threads`.
+static bool proportional_table(const glt_batch* b, int points_per_cta, int threads, ClassTable& c)
+{
+    c = ClassTable{};
+    c.nclass = 0;
+    int prev = 0;
+    for (int i = 0; i < b->S; ++i) {
+        const glt_tracker* t = b->trk[b->order[i]];
+        const long long work = (long long)t->cfg.max_points * t->K / 8;
+        int cl = 1;
+        while (cl < 16 && (long long)cl * points_per_cta < work) cl *= 2;
+        while (cl > 1 && !track_shape_ok(cl, threads, b->variant)) cl /= 2;
+        if (!track_shape_ok(cl, threads, b->variant)) return false;
+        if (cl != prev) {
+            if (c.nclass == kMaxBatchClasses) return false;
+            c.first[c.nclass] = i;
+            c.cluster[c.nclass] = cl;
+            c.threads[c.nclass] = threads;
+            ++c.nclass;
+            prev = cl;
+        }
+    }
+    c.first[c.nclass] = b->S;
+    return c.nclass > 0;
+}
 static std::mutex g_tune_mutex;
 static std::map<std::string, TuneResult> g_tune_cache;
 
@@ -791,8 +872,10 @@ static void free_batch(glt_batch* b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-    if (b->ev_join) cudaEventDestroy(b->ev_join);
-    if (b->aux) cudaStreamDestroy(b->aux);
+    for (int k = 0; k < kMaxBatchClasses - 1; ++k) {
+        if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+        if (b->aux[k]) cudaStreamDestroy(b->aux[k]);
+    }
     cudaFree(b->descs_dev);
     cudaFree(b->users_dev);
     cudaFree(b->copy_dev);
@@ -908,8 +991,6 @@ int glt_batch_create(glt_tracker* const* trackers, int S, glt_batch** out)
     BALLOC(cudaMemcpy(b->jobs_dev, jobs.data(), jobs.size() * sizeof(PyrJob), cudaMemcpyHostToDevice));
     BALLOC(cudaMemcpy(b->pack_dev, packs.data(), packs.size() * sizeof(PackJob), cudaMemcpyHostToDevice));
 #undef BALLOC
-    b->cluster = 2;
-    b->threads = 256;
     // one kernel variant for the whole batch: the most general one any stream needs
     b->variant = 0;
     for (int i = 0; i < S; ++i) {
@@ -917,14 +998,16 @@ int glt_batch_create(glt_tracker* const* trackers, int S, glt_batch** out)
         if (v == 1 || v == 2 || v == 4) b->variant = v;
         else if (v == 3 && b->variant == 0) b->variant = 3;
     }
-    if (b->variant == 4) b->threads = 512;   // the cached-Hessian kernel's only width
-    if (!track_shape_ok(b->cluster, b->threads, b->variant)) b->cluster = 1;
-    b->heavy = S;
-    b->cluster_light = b->cluster;
-    b->threads_light = b->threads;
-    cudaError_t e = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+    {
+        int cl = 2, th = b->variant == 4 ? 512 : 256;   // the cached-Hessian kernel's only width
+        if (!track_shape_ok(cl, th, b->variant)) cl = 1;
+        set_uniform(b, cl, th);
+    }
+    cudaError_t e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    for (int k = 0; k < kMaxBatchClasses - 1 && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         free_batch(b);
         return cuda_fail(e, "batch stream / events");
@@ -933,28 +1016,31 @@ int glt_batch_create(glt_tracker* const* trackers, int S, glt_batch** out)
     return GLT_OK;
 }
 
-// The track launch(es) of a batch: one launch when every stream is in class
-// 0, else class 0 on `s` and class 1 on the auxiliary stream, forked from and
-// joined back into `s` (under stream capture: two parallel graph nodes).
-// pdl applies to the single-launch form only.
+// The track launch(es) of a batch: one launch when there is one class, else
+// class 0 on `s` and class k > 0 on side stream aux[k - 1], each forked from
+// and joined back into `s` (under stream capture: parallel graph nodes).
+// pdl applies to the launch on `s` (the single launch, or class 0: the
+// heaviest streams, whose setup then overlaps the pyramids); the side
+// classes wait for the fork point to complete.
 static cudaError_t launch_batch_track(glt_batch* b, const double* init, glt_result* out,
                                       cudaStream_t s, bool pdl)
 {
-    if (b->heavy >= b->S || b->heavy <= 0) {
-        const int cl = b->heavy <= 0 ? b->cluster_light : b->cluster;
-        const int th = b->heavy <= 0 ? b->threads_light : b->threads;
-        return launch_track(b->descs_dev, b->users_dev, b->S, cl, th, b->variant, init, out, s, pdl);
-    }
+    if (b->nclass == 1)
+        return launch_track(b->descs_dev, b->users_dev, b->S, b->cls_cluster[0], b->cls_threads[0],
+                            b->variant, init, out, s, pdl);
     cudaError_t e = cudaEventRecord(b->ev_fork, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_fork, 0);
+    for (int k = 1; k < b->nclass && e == cudaSuccess; ++k) {
+        const int f = b->cls_first[k], n = b->cls_first[k + 1] - f;
+        e = cudaStreamWaitEvent(b->aux[k - 1], b->ev_fork, 0);
+        if (e == cudaSuccess)
+            e = launch_track(b->descs_dev + f, b->users_dev + f, n, b->cls_cluster[k], b->cls_threads[k],
+                             b->variant, init, out, b->aux[k - 1], false);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_join[k - 1], b->aux[k - 1]);
+    }
     if (e == cudaSuccess)
-        e = launch_track(b->descs_dev, b->users_dev, b->heavy, b->cluster, b->threads, b->variant,
-                         init, out, s, false);
-    if (e == cudaSuccess)
-        e = launch_track(b->descs_dev + b->heavy, b->users_dev + b->heavy, b->S - b->heavy,
-                         b->cluster_light, b->threads_light, b->variant, init, out, b->aux, false);
-    if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->aux);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join, 0);
+        e = launch_track(b->descs_dev, b->users_dev, b->cls_first[1], b->cls_cluster[0], b->cls_threads[0],
+                         b->variant, init, out, s, pdl);
+    for (int k = 1; k < b->nclass && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(s, b->ev_join[k - 1], 0);
     return e;
 }
 
@@ -1089,9 +1175,7 @@ int glt_batch_set_shape(glt_batch* b, int cluster, int threads)
 {
     if (!b) return invalid("batch is NULL");
     if (!track_shape_ok(cluster, threads, b->variant)) return invalid("shape cannot launch");
-    b->cluster = b->cluster_light = cluster;
-    b->threads = b->threads_light = threads;
-    b->heavy = b->S;
+    set_uniform(b, cluster, threads);
     drop_graph(b);
     return GLT_OK;
 }
@@ -1104,11 +1188,18 @@ int glt_batch_set_classes(glt_batch* b, int heavy, int heavy_cluster, int heavy_
     if ((heavy > 0 && !track_shape_ok(heavy_cluster, heavy_threads, b->variant)) ||
         (heavy < b->S && !track_shape_ok(light_cluster, light_threads, b->variant)))
         return invalid("shape cannot launch");
-    b->heavy = heavy;
-    b->cluster = heavy > 0 ? heavy_cluster : light_cluster;
-    b->threads = heavy > 0 ? heavy_threads : light_threads;
-    b->cluster_light = heavy < b->S ? light_cluster : b->cluster;
-    b->threads_light = heavy < b->S ? light_threads : b->threads;
+    apply_table(b, split_table(b->S, heavy, heavy_cluster, heavy_threads, light_cluster, light_threads));
+    drop_graph(b);
+    return GLT_OK;
+}
+
+int glt_batch_set_proportional(glt_batch* b, int points_per_cta, int threads)
+{
+    if (!b) return invalid("batch is NULL");
+    if (points_per_cta < 1) return invalid("points_per_cta must be >= 1");
+    ClassTable c;
+    if (!proportional_table(b, points_per_cta, threads, c)) return invalid("threads cannot launch");
+    apply_table(b, c);
     drop_graph(b);
     return GLT_OK;
 }
@@ -1117,11 +1208,26 @@ int glt_batch_get_classes(const glt_batch* b, int* heavy, int* heavy_cluster, in
                           int* light_cluster, int* light_threads)
 {
     if (!b) return invalid("batch is NULL");
-    if (heavy) *heavy = b->heavy;
-    if (heavy_cluster) *heavy_cluster = b->cluster;
-    if (heavy_threads) *heavy_threads = b->threads;
-    if (light_cluster) *light_cluster = b->cluster_light;
-    if (light_threads) *light_threads = b->threads_light;
+    const int k1 = b->nclass > 1 ? 1 : 0;
+    if (heavy) *heavy = b->nclass > 1 ? b->cls_first[1] : b->S;
+    if (heavy_cluster) *heavy_cluster = b->cls_cluster[0];
+    if (heavy_threads) *heavy_threads = b->cls_threads[0];
+    if (light_cluster) *light_cluster = b->cls_cluster[k1];
+    if (light_threads) *light_threads = b->cls_threads[k1];
+    return GLT_OK;
+}
+
+int glt_batch_get_class_table(const glt_batch* b, int max, int* first, int* cluster, int* threads,
+                              int* nclass)
+{
+    if (!b || !nclass) return invalid("NULL argument");
+    if (max < 0) return invalid("max must be >= 0");
+    *nclass = b->nclass;
+    for (int k = 0; k < b->nclass && k < max; ++k) {
+        if (first) first[k] = b->cls_first[k];
+        if (cluster) cluster[k] = b->cls_cluster[k];
+        if (threads) threads[k] = b->cls_threads[k];
+    }
     return GLT_OK;
 }
 
@@ -1151,16 +1257,19 @@ int glt_batch_autotune(glt_batch* b, const double* init_dev, glt_result* out_dev
         }
     }
     if (!cached) {
-        // candidates: one shape for every stream, then a heavy class (the
-        // first quarter or half of the launch order) with a wide shape and
-        // the light rest with a narrow one, run concurrently
+        // candidates: one shape for every stream; a heavy class (the first
+        // quarter or half of the launch order) with a wide shape and the light
+        // rest with a narrow one; clusters in proportion to each stream's
+        // points (glt_batch_set_proportional) at several points per CTA
         const int uniform[][2] = {{1, 128}, {1, 256}, {2, 128}, {2, 256}, {4, 128}, {4, 256},
                                   {8, 128}, {8, 256}, {1, 512}, {2, 512}, {4, 512}, {8, 512}};
         const int wide[][2] = {{8, 128}, {16, 128}, {8, 256}, {4, 512}, {8, 512}};
         const int narrow[][2] = {{1, 128}, {2, 128}, {4, 128}, {8, 128}, {2, 256}, {2, 512}};
+        const int prop[][2] = {{256, 128}, {320, 128}, {384, 128}, {448, 128}, {512, 128}, {768, 128},
+                               {512, 256}, {768, 256}, {1024, 256}, {1024, 512}, {1536, 512}};
         std::vector<TuneResult> cands;
         for (auto& u : uniform)
-            if (track_shape_ok(u[0], u[1], b->variant)) cands.push_back({b->S, u[0], u[1], u[0], u[1], 0.f});
+            if (track_shape_ok(u[0], u[1], b->variant)) cands.push_back(uniform_table(b->S, u[0], u[1]));
         if (b->S >= 4) {
             for (int part = 4; part >= 2; part /= 2) {
                 const int heavy = std::max(1, b->S / part);
@@ -1168,8 +1277,14 @@ int glt_batch_autotune(glt_batch* b, const double* init_dev, glt_result* out_dev
                     if (!track_shape_ok(w[0], w[1], b->variant)) continue;
                     for (auto& n : narrow)
                         if (track_shape_ok(n[0], n[1], b->variant))
-                            cands.push_back({heavy, w[0], w[1], n[0], n[1], 0.f});
+                            cands.push_back(split_table(b->S, heavy, w[0], w[1], n[0], n[1]));
                 }
+            }
+        }
+        if (b->S >= 2) {
+            for (auto& pp : prop) {
+                ClassTable c;
+                if (proportional_table(b, pp[0], pp[1], c) && c.nclass > 1) cands.push_back(c);
             }
         }
         cudaEvent_t e0, e1;
@@ -1177,11 +1292,7 @@ int glt_batch_autotune(glt_batch* b, const double* init_dev, glt_result* out_dev
         GLT_CHECK(cudaEventCreate(&e1), "event");
         best.ms = 1e30f;
         for (TuneResult& c : cands) {
-            b->heavy = c.heavy;
-            b->cluster = c.cluster;
-            b->threads = c.threads;
-            b->cluster_light = c.cluster_light;
-            b->threads_light = c.threads_light;
+            apply_table(b, c);
             cudaError_t e = launch_batch_track(b, init_dev, out_dev, s, false);   // warm-up
             if (e != cudaSuccess) {
                 cudaGetLastError();
@@ -1207,14 +1318,10 @@ int glt_batch_autotune(glt_batch* b, const double* init_dev, glt_result* out_dev
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         g_tune_cache[key] = best;
     }
-    b->heavy = best.heavy;
-    b->cluster = best.cluster;
-    b->threads = best.threads;
-    b->cluster_light = best.cluster_light;
-    b->threads_light = best.threads_light;
+    apply_table(b, best);
     drop_graph(b);
-    if (best_cluster) *best_cluster = best.cluster;
-    if (best_threads) *best_threads = best.threads;
+    if (best_cluster) *best_cluster = best.cluster[0];
+    if (best_threads) *best_threads = best.threads[0];
     if (best_ms) *best_ms = best.ms;
     return GLT_OK;
 }

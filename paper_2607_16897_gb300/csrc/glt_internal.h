@@ -38,6 +38,9 @@ struct PropJob {            // coarsest levels (40 x 30) of one stream, for the 
     int pitch;
 };
 
+// launch classes of a batch: at most one per cluster size 16, 8, 4, 2, 1
+constexpr int kMaxBatchClasses = 5;
+
 struct PackJob {            // one level -> FP16 (I, gx, gy, 0) copy (mixed form)
     const uint8_t* src;
     uint2* dst;
@@ -108,15 +111,17 @@ struct glt_batch {
     glt::PackJob* pack_dev = nullptr;     // [Lmax][S]
     int Lmax = 0;
     int variant = 0;                      // kernel variant (track_variant of the streams)
-    // launch classes over the launch order: class 0 = the first `heavy`
-    // streams (all of them when heavy = S), class 1 = the rest, each with its
-    // own (cluster, threads); the two run as concurrent launches (graph
-    // branches), class 1 on the batch's auxiliary stream
-    int heavy = 0;
-    int cluster = 2, threads = 256;       // class 0
-    int cluster_light = 2, threads_light = 256;   // class 1
-    cudaStream_t aux = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // launch classes over the launch order: class k = the streams
+    // [cls_first[k], cls_first[k + 1]), each class with its own (cluster,
+    // threads); the classes run as concurrent launches (graph branches):
+    // class 0 on the caller's stream, class k > 0 on side stream aux[k - 1]
+    int nclass = 1;
+    int cls_first[glt::kMaxBatchClasses + 1] = {};
+    int cls_cluster[glt::kMaxBatchClasses] = {};
+    int cls_threads[glt::kMaxBatchClasses] = {};
+    cudaStream_t aux[glt::kMaxBatchClasses - 1] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[glt::kMaxBatchClasses - 1] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     // learned initial-pose proposal (optional)

@@ -48,7 +48,7 @@ def make_streams(syn, orc, glt, precision):
     return streams
 
 
-def run_batch(glt, streams, shape=None, graph=False, classes=None):
+def run_batch(glt, streams, shape=None, graph=False, classes=None, proportional=None):
     import torch
     S = len(streams)
     batch = glt.Batch([s["trk"] for s in streams])
@@ -56,6 +56,8 @@ def run_batch(glt, streams, shape=None, graph=False, classes=None):
         batch.set_shape(*shape)
     if classes:
         batch.set_classes(*classes)
+    if proportional:
+        batch.set_proportional(*proportional)
     ptrs = torch.tensor([s["cur"].data_ptr() for s in streams], dtype=torch.int64).cuda()
     init = torch.tensor(np.stack([np.concatenate([s["T_init"].ravel(), [0.0, 0.0]])
                                   for s in streams]), dtype=torch.float64).cuda()
@@ -162,6 +164,41 @@ def test_two_launch_classes_match_oracle_and_graph(glt, orc, syn):
             ang, dt = pose_diff(g["T"], o["T"])
             assert ang <= ROT_TOL and dt <= TRANS_TOL, (classes, i, ang, dt)
             assert g["status"] == o["status"], (classes, i)
+    for s in streams:
+        s["trk"].close()
+
+
+def test_proportional_classes(glt, orc, syn):
+    """Clusters in proportion to each stream's points: one class per cluster
+    size, contiguous in the launch order (heaviest first), run as concurrent
+    launches; direct launches and graph replay agree bit for bit, and every
+    stream matches the oracle."""
+    streams = make_streams(syn, orc, glt, "fp32")
+    b = glt.Batch([s["trk"] for s in streams])
+    # capacities 4000, 2000, 1000, 300, 37, 1 (8 samples each) at 256 points per CTA
+    b.set_proportional(256, 128)
+    assert b.class_table() == [(0, 1, 16, 128), (1, 1, 8, 128), (2, 1, 4, 128), (3, 1, 2, 128),
+                               (4, 2, 1, 128)]
+    assert b.classes() == {"heavy": 1, "heavy_shape": (16, 128), "light_shape": (8, 128)}
+    b.set_proportional(1000, 256)
+    assert b.class_table() == [(0, 1, 4, 256), (1, 1, 2, 256), (2, 4, 1, 256)]
+    b.set_shape(8, 128)
+    assert b.class_table() == [(0, 6, 8, 128)]
+    with pytest.raises(glt.GltError):
+        b.set_proportional(0, 128)
+    with pytest.raises(glt.GltError):
+        b.set_proportional(256, 100)
+    b.close()
+    for prop in [(256, 128), (512, 256)]:
+        direct = run_batch(glt, streams, proportional=prop)
+        graph = run_batch(glt, streams, proportional=prop, graph=True)
+        for d, g in zip(direct, graph):
+            assert np.array_equal(d["T"], g["T"]) and d["passes"] == g["passes"], prop
+        for i, (s, g) in enumerate(zip(streams, direct)):
+            o = s["orc"].track_frame(s["T_init"])
+            ang, dt = pose_diff(g["T"], o["T"])
+            assert ang <= ROT_TOL and dt <= TRANS_TOL, (prop, i, ang, dt)
+            assert g["status"] == o["status"], (prop, i)
     for s in streams:
         s["trk"].close()
 
