@@ -45,7 +45,7 @@ def flops_per_sample(wl):
 # (dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
 # launch as in the timed steps) on the workload named by the key; a value is
 # removed whenever the kernel changes after it was taken.
-TRACK_TRAFFIC = {"c2": 798208, "c2p": 6193664}
+TRACK_TRAFFIC = {}
 # the trained proposal network's parameters (data file; read here as plain
 # numbers so that the oracle legs need nothing but oracle/ and synth/)
 WEIGHTS_PATH = os.path.join(ROOT, "paper_2607_16897_gb300", "proposal_weights.npy")
@@ -114,6 +114,10 @@ def parse():
     ap.add_argument("--precision", default=None, choices=["fp32", "mixed"],
                     help="storage precision of the levels: c4 / c4b default to mixed (FP16 "
                          "levels and gradients, Kahan sums), every other workload to fp32")
+    ap.add_argument("--solve", default=None, choices=["fp64", "fp32"],
+                    help="the tracker's 8x8 solve and SE(3) step: fp64 (default: FP64 L D L^T and "
+                         "exponential) or fp32 (FP32 factors and exponential increment, FP64 "
+                         "state and composition)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-launch-overhead", action="store_true",
                     help="skip the launch-overhead measurement (e.g. for a profiler's launch list)")
@@ -149,6 +153,7 @@ class Workload:
         self.refs = {}
         self._tw = {}
         self.jacobian = jacobian
+        self.solve = "fp64"          # glt_config.solve of the GPU run (the oracle is FP64)
         if solver:
             self.name = (f"{label}: {W}x{H} uint8, fx=fy={f:g}, {frames}-frame sequence "
                          f"({speed:g} m/s, {ang:g} deg/s, no exposure change), N={N} points, "
@@ -558,7 +563,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
     trk = glt.Tracker(Wd, Hd, wl.cam.K, levels=L, max_points=N, precision=precision,
-                      jacobian=wl.jacobian, **wl.solver)
+                      jacobian=wl.jacobian, solve=wl.solve, **wl.solver)
     frames_dev = torch.from_numpy(np.stack(wl.frames)).to(f"cuda:{local}")
     frames_pin = torch.from_numpy(np.stack(wl.frames)).pin_memory()
     init_dev = torch.zeros(14, dtype=torch.float64, device=f"cuda:{local}")
@@ -693,7 +698,8 @@ def run_ours(args):
     # the chain's own yardstick: the fixed part of a pass (reduction, cluster
     # barrier, distributed-shared-memory finish, FP64 tail) with no points
     cl, th = trk.shape()
-    floor_us = glt.pass_floor(cl, th, cached=wl.solver.get("hessian") == "cached", stream=sh)
+    floor_us = glt.pass_floor(cl, th, cached=wl.solver.get("hessian") == "cached", stream=sh,
+                              solve=wl.solve)
     floor_ms = statistics.mean(passes) * floor_us / 1000.0
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": TRACK_TRAFFIC.get(args.workload),
@@ -716,7 +722,8 @@ def run_ours(args):
                 "dtype": "f16 storage / f32 math" if precision == "mixed" else "f32",
                 "data": "synthetic",
                 "config": {"workload": wl.name, "jacobian": wl.jacobian,
-                           "hessian": wl.solver.get("hessian", "pass"), "global_batch": world,
+                           "hessian": wl.solver.get("hessian", "pass"), "solve": wl.solve,
+                           "global_batch": world,
                            "streams_per_gpu": 1,
                            "parallelism": f"replicas x{world}",
                            "l2": "flushed between steps (256 MB write, outside the step events)",
@@ -885,7 +892,7 @@ def linearization_error(glt, wl, rec_entry, precision):
     import oracle
     k, r, T_init, ab, _ = rec_entry
     trk = glt.Tracker(wl.cam.W, wl.cam.H, wl.cam.K, levels=wl.L, max_points=wl.N, precision=precision,
-                      jacobian=wl.jacobian, **wl.solver)
+                      jacobian=wl.jacobian, solve=wl.solve, **wl.solver)
     trk.build_pyramid(glt.GLT_REF, wl.frames[r])
     trk.set_map_points(wl.ref_points(r))
     trk.build_pyramid(glt.GLT_CUR, wl.frames[k])
@@ -916,12 +923,14 @@ PAPER_SOLVER = dict(affine=False, lambda0=0.0, accept_step=1e30, eps_step=0.0,
 
 
 def apply_overrides(wl, args):
-    """--jacobian / --hessian on a workload (the cached Hessian exists only
-    with the inverse-compositional rows)."""
+    """--jacobian / --hessian / --solve on a workload (the cached Hessian
+    exists only with the inverse-compositional rows)."""
     if args.jacobian:
         wl.jacobian = args.jacobian
     if getattr(args, "hessian", None) and "hessian" in wl.solver:
         wl.solver["hessian"] = args.hessian
+    if getattr(args, "solve", None):
+        wl.solve = args.solve
     if wl.jacobian != "ic" and wl.solver.get("hessian") == "cached":
         wl.solver["hessian"] = "pass"
 
@@ -1016,7 +1025,7 @@ def run_batch(args):
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
     trks = [glt.Tracker(w.cam.W, w.cam.H, w.cam.K, levels=w.L, max_points=w.N, precision=precision,
-                        jacobian=w.jacobian, **w.solver) for w in wls]
+                        jacobian=w.jacobian, solve=w.solve, **w.solver) for w in wls]
     batch = glt.Batch(trks)
     frames_dev = [torch.from_numpy(np.stack(w.frames)).to(dev) for w in wls]
     # host frames in pinned memory, laid out per step (every stream's frame k
@@ -1286,7 +1295,7 @@ def run_batch(args):
                 "config": {"workload": (f"{args.workload.upper()} batched: {S} streams in one graph "
                                         f"replay (pyramids + one persistent track launch); " + desc
                                         + f", {F}-frame sequences, reference every 8 frames"),
-                           "jacobian": wls[0].jacobian,
+                           "jacobian": wls[0].jacobian, "solve": wls[0].solve,
                            "global_batch": world * S, "streams_per_gpu": S,
                            "parallelism": f"replicas x{world}",
                            "autotuned_shape": {"cluster": shape[0], "threads": shape[1],
@@ -1493,6 +1502,22 @@ def nested_batched(args):
     return out
 
 
+def nested_solve_fp32(args):
+    """The default workload with the FP32 solve (--solve fp32), measured in the
+    same run with the same step counts: its frames/s, roofline and latency
+    floor, and its pose difference against the oracle."""
+    sub = argparse.Namespace(**vars(args))
+    sub.solve = "fp32"
+    sub.no_e2e = True
+    sub.no_launch_overhead = True
+    rec = run_ours(sub)
+    if rec is None:
+        return None
+    keep = ("value", "unit", "ms_per_step", "dtype", "config", "roofline", "cpu_baseline",
+            "parity_vs_oracle", "accuracy_vs_truth", "passes_per_frame", "clocks", "gpu_launches")
+    return {k: rec[k] for k in keep if k in rec}
+
+
 def main():
     args = parse()
     if args.table3:
@@ -1505,6 +1530,10 @@ def main():
         line = run_batch(args)
     else:
         line = run_ours(args)
+        if args.workload == "c2" and args.solve is None and not args.no_batched:
+            variant = nested_solve_fp32(args)
+            if line is not None and variant is not None:
+                line["solve_fp32"] = variant
         if args.workload == "c2" and not args.no_batched:
             batched = nested_batched(args)
             if line is not None:

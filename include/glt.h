@@ -77,6 +77,10 @@ extern "C" {
 #define GLT_MIXED 1 /* FP16 (I, gx, gy) levels, FP32 math, Kahan FP32 block sums; solve and
                        state as GLT_FP32 */
 
+/* solve modes (glt_config.solve) */
+#define GLT_SOLVE_FP64 0
+#define GLT_SOLVE_FP32 2
+
 /* Jacobian forms (Sec. IV-B) */
 #define GLT_FORWARD 0 /* current image's gradient at the warped location, every pass */
 #define GLT_IC 1      /* inverse compositional: reference-side rows cached per reference */
@@ -148,6 +152,17 @@ typedef struct glt_config {
                                    threads (7 x 7 and 11 x 11 patches are split over four
                                    threads each); an H that is not positive definite ends
                                    the level with GLT_TRACK_NOT_PD */
+    int solve;                  /* the 8x8 solve and the SE(3) step (the state, the
+                                   accept/reject decision and the composition are FP64 in
+                                   both modes): GLT_SOLVE_FP64 (default) the L D L^T
+                                   factorisation and the exponential in FP64;
+                                   GLT_SOLVE_FP32 the factorisation and exp(delta) - I in
+                                   FP32 (H and g are FP32 sums; the increment's entries
+                                   are O(|delta|)), the composition in FP64 and one FP64
+                                   orthonormalisation of the frame's final pose; a
+                                   system with an FP32 pivot below 1e-4 of its damped
+                                   diagonal is factorised in FP64, so "not positive
+                                   definite" is always the FP64 decision */
 } glt_config;
 
 typedef struct glt_result {
@@ -323,17 +338,18 @@ int glt_debug_rcp(const double* d_dev, double* r_dev, int n, void* stream);
 /* Latency floor of one tracker pass: times (CUDA events, after one warm-up
  * launch) a launch of one stream's cluster (`cluster` CTAs of `threads`
  * threads) that runs `passes` passes of the track kernel's fixed part --
- * the block reduction, the cluster barrier, the distributed-shared-memory
- * finish and the FP64 tail (the LM decision, the solve -- the L D L^T
- * factorisation, or with `cached` the product with a cached H^-1 -- and
- * the SE(3) exponential and composition) on a fixed normal system -- with no
- * map point, and writes the microseconds per pass to *us_per_pass.  What a
- * real pass costs beyond it is the linearisation of its points.  Not part of
- * the method; no paper counterpart.  Synchronous; allocates 8 bytes.
- * Errors: INVALID_ARG (passes outside [1, 100000], a shape that cannot
- * launch: cached needs 512 threads), CUDA. */
-int glt_debug_pass_floor(int cluster, int threads, int cached, int passes, float* us_per_pass,
-                         void* stream);
+ * the block reduction, the cluster exchange of the CTA partials and the
+ * solver tail (the LM decision, the solve -- the L D L^T factorisation, or
+ * with `cached` the product with a cached H^-1 -- and the SE(3) exponential
+ * and composition, in solve mode `solve`: GLT_SOLVE_FP64 or GLT_SOLVE_FP32)
+ * on a fixed normal system -- with no map point, and writes the
+ * microseconds per pass to *us_per_pass.  What a real pass costs beyond it
+ * is the linearisation of its points.  Not part of the method; no paper
+ * counterpart.  Synchronous; allocates 8 bytes.
+ * Errors: INVALID_ARG (passes outside [1, 100000], an unknown solve mode, a
+ * shape that cannot launch: cached needs 512 threads), CUDA. */
+int glt_debug_pass_floor(int cluster, int threads, int cached, int solve, int passes,
+                         float* us_per_pass, void* stream);
 
 /* Failure test of the cluster exchange (no counterpart in the paper): one
  * pass of the latency-floor kernel on a `cluster`-CTA cluster whose CTA 0

@@ -33,6 +33,7 @@ GLT_TRACK_TOO_FEW_POINTS = 1
 GLT_TRACK_NOT_PD = 2
 GLT_TRACK_DIVERGED = 4
 GLT_TRACK_TIMEOUT = 8
+GLT_SOLVE_FP64, GLT_SOLVE_FP32 = 0, 2
 GLT_REF, GLT_CUR = 0, 1
 GLT_FP32, GLT_MIXED = 0, 1
 GLT_FORWARD, GLT_IC = 0, 1
@@ -56,7 +57,7 @@ class glt_config(ctypes.Structure):
                 ("min_valid", ctypes.c_int),
                 ("zmin", ctypes.c_double), ("precision", ctypes.c_int), ("cluster", ctypes.c_int),
                 ("threads", ctypes.c_int), ("jacobian", ctypes.c_int), ("pattern", ctypes.c_int),
-                ("affine", ctypes.c_int), ("hessian", ctypes.c_int)]
+                ("affine", ctypes.c_int), ("hessian", ctypes.c_int), ("solve", ctypes.c_int)]
 
 
 class glt_result(ctypes.Structure):
@@ -103,7 +104,7 @@ SIGNATURES = {
     "glt_debug_linearize": (_i, [_vp, _i, _P(_d), _d, _d, _P(_d), _P(_d), _P(_d), _P(_i),
                                  _P(ctypes.c_float), _vp]),
     "glt_debug_rcp": (_i, [_vp, _vp, _i, _vp]),
-    "glt_debug_pass_floor": (_i, [_i, _i, _i, _i, _P(ctypes.c_float), _vp]),
+    "glt_debug_pass_floor": (_i, [_i, _i, _i, _i, _i, _P(ctypes.c_float), _vp]),
     "glt_debug_exchange_timeout": (_i, [_i, _i, _P(ctypes.c_int), _vp]),
     "glt_get_shape": (_i, [_vp, _P(_i), _P(_i)]),
     "glt_get_pyramid": (_i, [_vp, _i, _i, _P(ctypes.c_uint8), _vp]),
@@ -227,6 +228,8 @@ def default_config(width, height, K, **kw) -> glt_config:
             c.jacobian = {"forward": GLT_FORWARD, "ic": GLT_IC}[v]
         elif k == "hessian" and isinstance(v, str):
             c.hessian = {"pass": GLT_HESSIAN_PASS, "cached": GLT_HESSIAN_CACHED}[v]
+        elif k == "solve" and isinstance(v, str):
+            c.solve = {"fp64": GLT_SOLVE_FP64, "fp32": GLT_SOLVE_FP32}[v]
         else:
             if not hasattr(c, k):
                 raise KeyError(k)
@@ -571,12 +574,14 @@ class NN:
                                       _stream_handle(stream)), "glt_nn_train_step")
 
 
-def pass_floor(cluster, threads, cached=False, passes=400, stream=None) -> float:
+def pass_floor(cluster, threads, cached=False, passes=400, stream=None, solve="fp64") -> float:
     """Microseconds per pass of the track kernel's fixed part (no points) for
-    one stream's (cluster, threads) shape (glt_debug_pass_floor)."""
+    one stream's (cluster, threads) shape and solve mode (glt_debug_pass_floor)."""
     us = ctypes.c_float()
-    _check(_lib.glt_debug_pass_floor(int(cluster), int(threads), int(bool(cached)), int(passes),
-                                     ctypes.byref(us), _stream_handle(stream)), "glt_debug_pass_floor")
+    mode = {"fp64": GLT_SOLVE_FP64, "fp32": GLT_SOLVE_FP32}.get(solve, solve)
+    _check(_lib.glt_debug_pass_floor(int(cluster), int(threads), int(bool(cached)), int(mode),
+                                     int(passes), ctypes.byref(us), _stream_handle(stream)),
+           "glt_debug_pass_floor")
     return us.value
 
 

@@ -221,6 +221,8 @@ static int check_config(const glt_config* c)
     if (c->affine != 0 && c->affine != 1) return invalid("affine must be 0 or 1");
     if (c->hessian != GLT_HESSIAN_PASS && c->hessian != GLT_HESSIAN_CACHED)
         return invalid("hessian must be GLT_HESSIAN_PASS or GLT_HESSIAN_CACHED");
+    if (c->solve != GLT_SOLVE_FP64 && c->solve != GLT_SOLVE_FP32)
+        return invalid("solve must be GLT_SOLVE_FP64 or GLT_SOLVE_FP32");
     if (c->hessian == GLT_HESSIAN_CACHED &&
         (c->jacobian != GLT_IC || c->affine != 0 || c->lambda0 != 0.0 || c->precision != GLT_FP32 ||
          (c->threads != 0 && c->threads != 512)))
@@ -313,6 +315,8 @@ void glt_default_config(glt_config* c, int width, int height, double fx, double 
     c->jacobian = GLT_FORWARD;
     c->pattern = 0;
     c->affine = 1;
+    c->hessian = GLT_HESSIAN_PASS;
+    c->solve = GLT_SOLVE_FP64;
 }
 
 int glt_create(const glt_config* cfg, glt_tracker** out)
@@ -414,6 +418,7 @@ int glt_create(const glt_config* cfg, glt_tracker** out)
     D.I0 = t->I0;
     D.G0 = t->G0;
     D.Hc = t->Hc;
+    D.solve = t->cfg.solve;
     D.pattern = cfg->pattern;
     D.K = t->K;
     D.affine = cfg->affine;

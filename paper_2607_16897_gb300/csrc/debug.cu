@@ -26,10 +26,11 @@ extern "C" int glt_debug_rcp(const double* d_dev, double* r_dev, int n, void* st
     return e == cudaSuccess ? GLT_OK : cuda_fail(e, "glt_debug_rcp kernel");
 }
 
-extern "C" int glt_debug_pass_floor(int cluster, int threads, int cached, int passes,
+extern "C" int glt_debug_pass_floor(int cluster, int threads, int cached, int solve, int passes,
                                     float* us_per_pass, void* stream)
 {
-    if (!us_per_pass || passes < 1 || passes > 100000 || cluster < 1 || cluster > 16)
+    if (!us_per_pass || passes < 1 || passes > 100000 || cluster < 1 || cluster > 16 ||
+        (solve != GLT_SOLVE_FP64 && solve != GLT_SOLVE_FP32))
         return invalid_arg_msg("glt_debug_pass_floor: bad argument");
     if (!track_shape_ok(cluster, threads, cached ? 4 : 0))
         return invalid_arg_msg("glt_debug_pass_floor: shape cannot launch");
@@ -40,9 +41,9 @@ extern "C" int glt_debug_pass_floor(int cluster, int threads, int cached, int pa
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     // one launch to warm up, then the timed one
-    if (e == cudaSuccess) e = launch_pass_floor(cluster, threads, cached != 0, passes, cyc, s);
+    if (e == cudaSuccess) e = launch_pass_floor(cluster, threads, cached != 0, passes, cyc, s, -1, solve);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-    if (e == cudaSuccess) e = launch_pass_floor(cluster, threads, cached != 0, passes, cyc, s);
+    if (e == cudaSuccess) e = launch_pass_floor(cluster, threads, cached != 0, passes, cyc, s, -1, solve);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.0f;

@@ -78,6 +78,7 @@ struct StreamDesc {
     int* trace_n;          // [max_trace] valid samples of each pass
     int* trace_info;       // [max_trace] level * 4 + 2 * accepted + is_candidate
     int* trace_count;      // passes of the last track, or null
+    int solve;             // GLT_SOLVE_FP64 or GLT_SOLVE_FP32
 };
 
 // The state one linearisation pass is evaluated at, in the form the FP32
@@ -740,18 +741,22 @@ __device__ __forceinline__ void block_reduce(float (&acc)[kAccPad], float (*red)
 // latencies (measured on the part: ~64 cycles per DFMA, ~420 per divide or
 // reciprocal, ~670 per square root, ~1700 per sincos), and this tail sits on
 // the critical path of every pass.  The state, the normal equations, the
-// accept/reject decision and the composition stay in FP64; work whose inputs
-// carry FP32 rounding anyway, or whose result is a small increment, is FP32:
+// accept/reject decision and the composition are FP64 in both solve modes;
+// GLT_SOLVE_FP64 (the default) also factorises and exponentiates in FP64,
+// GLT_SOLVE_FP32 does those two in FP32 (their inputs carry FP32 rounding
+// anyway, or their result is a small increment):
 //  * the damped normal matrix is factored as L D L^T (no square roots), one
-//    row per lane, columns eliminated right-looking with warp shuffles, in
-//    FP32 (its entries are FP32 sums); a pivot below 1e-4 of its damped
-//    diagonal sends the system to the same elimination in FP64, which alone
-//    decides "not positive definite";
+//    row per lane, columns eliminated right-looking with warp shuffles; in
+//    GLT_SOLVE_FP32 first in FP32, and a pivot below 1e-4 of its damped
+//    diagonal sends the system to the FP64 elimination, which alone decides
+//    "not positive definite";
 //  * FP64 pivot reciprocals are an FP32 seed refined by one Newton step
 //    (relative error ~4e-15);
-//  * exp(delta) - I is evaluated in FP32 (its entries are O(|delta|)) and
-//    composed with the FP64 pose as T + T (exp(delta) - I), each lane one
-//    element;
+//  * the SE(3) exponential uses the power series of its coefficients in
+//    theta^2 below theta = 0.1 (sincos only beyond), each lane one element
+//    of exp(delta) (GLT_SOLVE_FP32: of exp(delta) - I in FP32, composed with
+//    the FP64 pose as T + T (exp(delta) - I), and the frame's final pose
+//    orthonormalised once in FP64);
 //  * FP64 <-> FP32 conversions go through the bit pattern (integer
 //    instructions), and accept/reject compares E' n <= E n' instead of
 //    dividing.
@@ -1100,15 +1105,16 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
         const int ek = lane < 7 ? 0 : lane < 13 ? 1 : lane < 18 ? 2 : lane < 22 ? 3 : lane < 25 ? 4
                      : lane < 27 ? 5 : lane < 28 ? 6 : 7;
         const int ei = lane < 28 ? lane - (ek * 7 - (ek * (ek - 1)) / 2) + ek + 1 : 8;
-        // In FP32: H and g are FP32 sums (relative error ~1e-7), so the step
-        // they define is known to ~cond x 1e-7 however it is solved, and an
-        // FP32 elimination adds an error of the same order (~cond x 2^-23).
-        // Accepted when every FP32 pivot is above 1e-4 of its damped diagonal,
-        // where its rounding (~1e-6 of the diagonal) cannot change its sign;
-        // otherwise the FP64 elimination below decides, as for every system it
-        // accepts or rejects as not positive definite.
-        bool ok32;
-        {
+        // GLT_SOLVE_FP32 first factorises in FP32 (H and g are FP32 sums,
+        // relative error ~1e-7, so the step they define is known to ~cond x
+        // 1e-7 however it is solved; the FP32 elimination adds an error of the
+        // same order, ~cond x 2^-23).  Used when every FP32 pivot is above 1e-4
+        // of its damped diagonal, where its rounding (~1e-6 of the diagonal)
+        // cannot change its sign; otherwise, and always for GLT_SOLVE_FP64
+        // (the default), the FP64 elimination below decides, as for every
+        // system it accepts or rejects as not positive definite.
+        bool ok32 = false;
+        if (D.solve != GLT_SOLVE_FP64) {
             float e = lane < 28 ? f32_of(S.H[8 * ei + ek]) : 0.0f;
             const double diag = S.H[8 * row + row];
             const double a0 = fma(lambda, diag, diag);
@@ -1228,59 +1234,116 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
             long long mbits = 0;
 #pragma unroll
             for (int c = 0; c < 6; ++c) mbits = max(mbits, abs_bits(dl[c]));
-            // ---- exp(delta_xi) - I in FP32: its entries are O(|delta|), so FP32
-            // rounding leaves ~1e-7 |delta| (absolute); the product with T is FP64.
-            //   R_e - I = A [w]x + B [w]x^2,  t_e = v + B (w x v) + C w x (w x v),
-            // A = sin th / th, B = (1 - cos th) / th^2, C = (th - sin th) / th^3
-            // (power series below th^2 = 0.25, truncation < 3e-11 relative)
-            const float v0 = f32_of(dl[0]), v1 = f32_of(dl[1]), v2 = f32_of(dl[2]);
-            const float w0 = f32_of(dl[3]), w1 = f32_of(dl[4]), w2 = f32_of(dl[5]);
-            const float th2 = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
-            float A, B, Cc;
-            if (th2 < 0.25f) {
-                A = fmaf(fmaf(fmaf(fmaf(th2, 1.0f / 362880.0f, -1.0f / 5040.0f), th2, 1.0f / 120.0f), th2, -1.0f / 6.0f), th2, 1.0f);
-                B = fmaf(fmaf(fmaf(fmaf(th2, 1.0f / 3628800.0f, -1.0f / 40320.0f), th2, 1.0f / 720.0f), th2, -1.0f / 24.0f), th2, 0.5f);
-                Cc = fmaf(fmaf(fmaf(fmaf(th2, 1.0f / 39916800.0f, -1.0f / 362880.0f), th2, 1.0f / 5040.0f), th2, -1.0f / 120.0f), th2, 1.0f / 6.0f);
+            double tc;
+            if (D.solve == GLT_SOLVE_FP32) {
+                // ---- exp(delta_xi) - I in FP32: its entries are O(|delta|), so FP32
+                // rounding leaves ~1e-7 |delta| (absolute); the product with T is FP64.
+                //   R_e - I = A [w]x + B [w]x^2,  t_e = v + B (w x v) + C w x (w x v),
+                // A = sin th / th, B = (1 - cos th) / th^2, C = (th - sin th) / th^3
+                // (power series below th^2 = 0.25, truncation < 3e-11 relative)
+                const float v0 = f32_of(dl[0]), v1 = f32_of(dl[1]), v2 = f32_of(dl[2]);
+                const float w0 = f32_of(dl[3]), w1 = f32_of(dl[4]), w2 = f32_of(dl[5]);
+                const float th2 = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
+                float A, B, Cc;
+                if (th2 < 0.25f) {
+                    A = fmaf(fmaf(fmaf(fmaf(th2, 1.0f / 362880.0f, -1.0f / 5040.0f), th2, 1.0f / 120.0f), th2, -1.0f / 6.0f), th2, 1.0f);
+                    B = fmaf(fmaf(fmaf(fmaf(th2, 1.0f / 3628800.0f, -1.0f / 40320.0f), th2, 1.0f / 720.0f), th2, -1.0f / 24.0f), th2, 0.5f);
+                    Cc = fmaf(fmaf(fmaf(fmaf(th2, 1.0f / 39916800.0f, -1.0f / 362880.0f), th2, 1.0f / 5040.0f), th2, -1.0f / 120.0f), th2, 1.0f / 6.0f);
+                } else {
+                    const float th = sqrtf(th2);
+                    const float sn = sinf(th), sh = sinf(0.5f * th);
+                    A = sn / th;
+                    B = 2.0f * sh * sh / th2;
+                    Cc = (th - sn) / (th2 * th);
+                }
+                // one element (r, c) of the 3x4 increment per lane 0-11, every lane
+                // running the same instructions on its own operands:
+                //   (R_e - I)(r, c) = A W_rc + B (w_r w_c - d_rc th2)        (W = [w]x)
+                //   t_e(r)          = v_r + B (w x v)_r + C (w_r (w . v) - v_r th2)
+                // as  base + cA (a1 b1 - a2 b2) + cB (p q - d th2).
+                const float wv = fmaf(w0, v0, fmaf(w1, v1, w2 * v2));
+                const int er = (lane >> 2) % 3, ec = lane & 3;
+                const float wr = er == 0 ? w0 : (er == 1 ? w1 : w2);
+                const float wr1 = er == 0 ? w1 : (er == 1 ? w2 : w0);   // w_{r+1}
+                const float wr2 = er == 0 ? w2 : (er == 1 ? w0 : w1);   // w_{r+2}
+                const float vr = er == 0 ? v0 : (er == 1 ? v1 : v2);
+                const float vr1 = er == 0 ? v1 : (er == 1 ? v2 : v0);
+                const float vr2 = er == 0 ? v2 : (er == 1 ? v0 : v1);
+                const float wc = ec == 0 ? w0 : (ec == 1 ? w1 : w2);
+                const bool rot = ec < 3;
+                const float drc = (rot && er == ec) ? 1.0f : 0.0f;
+                // W_rc = +w_{r+2} if c = r+1, -w_{r+1} if c = r+2, 0 on the diagonal
+                const float Wrc = ec == (er + 1) % 3 ? -wr2 : (ec == (er + 2) % 3 ? wr1 : 0.0f);
+                const float base = rot ? 0.0f : vr;
+                const float a1 = rot ? Wrc : wr1, b1 = rot ? 1.0f : vr2;
+                const float a2 = rot ? 0.0f : wr2, b2 = rot ? 0.0f : vr1;
+                const float pq = rot ? wc : wv, dd = rot ? drc : vr;
+                const float ex = fmaf(a1, b1, -(a2 * b2));
+                const float ey = fmaf(wr, pq, -(dd * th2));
+                const float dE = fmaf(rot ? B : Cc, ey, fmaf(rot ? A : B, ex, base));
+                // ---- Tc = T exp(delta) = T + T (exp(delta) - I) in FP64:
+                // Tc(r, c) = T(r, c) + sum_k T(r, k) dE(k, c)   (c = 3: dE(k, 3) = t_e(k))
+                const double e0 = f64_of(__shfl_sync(full, dE, ec));
+                const double e1 = f64_of(__shfl_sync(full, dE, 4 + ec));
+                const double e2 = f64_of(__shfl_sync(full, dE, 8 + ec));
+                tc = lane < 12 ? fma(S.T[4 * er], e0, fma(S.T[4 * er + 1], e1, fma(S.T[4 * er + 2], e2, S.T[4 * er + ec])))
+                               : 0.0;
             } else {
-                const float th = sqrtf(th2);
-                const float sn = sinf(th), sh = sinf(0.5f * th);
-                A = sn / th;
-                B = 2.0f * sh * sh / th2;
-                Cc = (th - sn) / (th2 * th);
+                // ---- exp(delta_xi): R_e = I + A [w]x + B [w]x^2, t_e = v + B (w x v) + C w x (w x v)
+                const double w0 = dl[3], w1 = dl[4], w2 = dl[5];
+                const double th2 = fma(w0, w0, fma(w1, w1, w2 * w2));
+                double A, B, Cc;
+                if (th2 < 1e-4) {
+                    A = fma(fma(th2, 1.0 / 120.0, -1.0 / 6.0), th2, 1.0);
+                    B = fma(fma(th2, 1.0 / 720.0, -1.0 / 24.0), th2, 0.5);
+                    Cc = fma(fma(th2, 1.0 / 5040.0, -1.0 / 120.0), th2, 1.0 / 6.0);
+                } else if (th2 < 0.01) {
+                    A = fma(fma(fma(fma(th2, 1.0 / 362880.0, -1.0 / 5040.0), th2, 1.0 / 120.0), th2, -1.0 / 6.0), th2, 1.0);
+                    B = fma(fma(fma(fma(th2, 1.0 / 3628800.0, -1.0 / 40320.0), th2, 1.0 / 720.0), th2, -1.0 / 24.0), th2, 0.5);
+                    Cc = fma(fma(fma(fma(th2, 1.0 / 39916800.0, -1.0 / 362880.0), th2, 1.0 / 5040.0), th2, -1.0 / 120.0), th2, 1.0 / 6.0);
+                } else {
+                    const double th = sqrt(th2);
+                    double sn, cs, sh, ch;
+                    sincos(th, &sn, &cs);
+                    sincos(0.5 * th, &sh, &ch);
+                    A = sn / th;
+                    B = 2.0 * sh * sh / th2;
+                    Cc = (th - sn) / (th2 * th);
+                }
+                // ---- E = exp(delta_xi) as a 3x4 [R_e | t_e], one element (r, c) per lane
+                // 0-11, every lane running the same FP64 instructions on its own operands:
+                //   R_e(r, c) = d_rc + A W_rc + B (w_r w_c - d_rc th2)            (W = [w]x)
+                //   t_e(r)    = v_r + B (w x v)_r + C (w_r (w . v) - v_r th2)
+                // as  base + cA (a1 b1 - a2 b2) + cB (p q - d th2).
+                const double v0 = dl[0], v1 = dl[1], v2 = dl[2];
+                const double wv = fma(w0, v0, fma(w1, v1, w2 * v2));
+                const int er = (lane >> 2) % 3, ec = lane & 3;
+                const double wr = er == 0 ? w0 : (er == 1 ? w1 : w2);
+                const double wr1 = er == 0 ? w1 : (er == 1 ? w2 : w0);   // w_{r+1}
+                const double wr2 = er == 0 ? w2 : (er == 1 ? w0 : w1);   // w_{r+2}
+                const double vr = er == 0 ? v0 : (er == 1 ? v1 : v2);
+                const double vr1 = er == 0 ? v1 : (er == 1 ? v2 : v0);
+                const double vr2 = er == 0 ? v2 : (er == 1 ? v0 : v1);
+                const double wc = ec == 0 ? w0 : (ec == 1 ? w1 : w2);
+                const bool rot = ec < 3;
+                const double drc = (rot && er == ec) ? 1.0 : 0.0;
+                // W_rc = +w_{r+2} if c = r+1, -w_{r+1} if c = r+2, 0 on the diagonal
+                const double Wrc = ec == (er + 1) % 3 ? -wr2 : (ec == (er + 2) % 3 ? wr1 : 0.0);
+                const double base = rot ? drc : vr;
+                const double a1 = rot ? Wrc : wr1, b1 = rot ? 1.0 : vr2;
+                const double a2 = rot ? 0.0 : wr2, b2 = rot ? 0.0 : vr1;
+                const double pq = rot ? wc : wv, dd = rot ? drc : vr;
+                const double ex = fma(a1, b1, -(a2 * b2));
+                const double ey = fma(wr, pq, -(dd * th2));
+                const double E = fma(rot ? B : Cc, ey, fma(rot ? A : B, ex, base));
+                // ---- Tc = T E: Tc(r, c) = sum_k T(r, k) E(k, c) (+ T(r, 3) for c = 3)
+                const double e0 = __shfl_sync(full, E, ec);
+                const double e1 = __shfl_sync(full, E, 4 + ec);
+                const double e2 = __shfl_sync(full, E, 8 + ec);
+                tc = lane < 12 ? fma(S.T[4 * er], e0, fma(S.T[4 * er + 1], e1,
+                                      fma(S.T[4 * er + 2], e2, rot ? 0.0 : S.T[4 * er + 3])))
+                               : 0.0;
             }
-            // one element (r, c) of the 3x4 increment per lane 0-11, every lane
-            // running the same instructions on its own operands:
-            //   (R_e - I)(r, c) = A W_rc + B (w_r w_c - d_rc th2)        (W = [w]x)
-            //   t_e(r)          = v_r + B (w x v)_r + C (w_r (w . v) - v_r th2)
-            // as  base + cA (a1 b1 - a2 b2) + cB (p q - d th2).
-            const float wv = fmaf(w0, v0, fmaf(w1, v1, w2 * v2));
-            const int er = (lane >> 2) % 3, ec = lane & 3;
-            const float wr = er == 0 ? w0 : (er == 1 ? w1 : w2);
-            const float wr1 = er == 0 ? w1 : (er == 1 ? w2 : w0);   // w_{r+1}
-            const float wr2 = er == 0 ? w2 : (er == 1 ? w0 : w1);   // w_{r+2}
-            const float vr = er == 0 ? v0 : (er == 1 ? v1 : v2);
-            const float vr1 = er == 0 ? v1 : (er == 1 ? v2 : v0);
-            const float vr2 = er == 0 ? v2 : (er == 1 ? v0 : v1);
-            const float wc = ec == 0 ? w0 : (ec == 1 ? w1 : w2);
-            const bool rot = ec < 3;
-            const float drc = (rot && er == ec) ? 1.0f : 0.0f;
-            // W_rc = +w_{r+2} if c = r+1, -w_{r+1} if c = r+2, 0 on the diagonal
-            const float Wrc = ec == (er + 1) % 3 ? -wr2 : (ec == (er + 2) % 3 ? wr1 : 0.0f);
-            const float base = rot ? 0.0f : vr;
-            const float a1 = rot ? Wrc : wr1, b1 = rot ? 1.0f : vr2;
-            const float a2 = rot ? 0.0f : wr2, b2 = rot ? 0.0f : vr1;
-            const float pq = rot ? wc : wv, dd = rot ? drc : vr;
-            const float ex = fmaf(a1, b1, -(a2 * b2));
-            const float ey = fmaf(wr, pq, -(dd * th2));
-            const float dE = fmaf(rot ? B : Cc, ey, fmaf(rot ? A : B, ex, base));
-            // ---- Tc = T exp(delta) = T + T (exp(delta) - I) in FP64:
-            // Tc(r, c) = T(r, c) + sum_k T(r, k) dE(k, c)   (c = 3: dE(k, 3) = t_e(k))
-            const double e0 = f64_of(__shfl_sync(full, dE, ec));
-            const double e1 = f64_of(__shfl_sync(full, dE, 4 + ec));
-            const double e2 = f64_of(__shfl_sync(full, dE, 8 + ec));
-            const double tc = lane < 12 ? fma(S.T[4 * er], e0, fma(S.T[4 * er + 1], e1,
-                                                  fma(S.T[4 * er + 2], e2, S.T[4 * er + ec])))
-                                        : 0.0;
             const double ac = S.a + dl[6], bc = S.b + dl[7];
             const bool cand_finite = __all_sync(full, abs_bits(tc) < kInfBits) &&
                                      abs_bits(ac) < kInfBits && abs_bits(bc) < kInfBits;
@@ -1330,11 +1393,11 @@ __device__ inline void solver_step_warp(const StreamDesc& D, const double* tot, 
         int l = level - 1;
         while (l >= 0 && D.max_iters[l] <= 0) --l;
         if (l < 0) {
-            // the poses composed from FP32 increments drift from orthonormal
-            // by ~1e-9 per step: one Newton step R' = R (3 I - R^T R) / 2 =
+            // GLT_SOLVE_FP32: the poses composed from FP32 increments drift
+            // from orthonormal by ~1e-9 per step: one Newton step R' = R (3 I - R^T R) / 2 =
             // R + R (I - R^T R) / 2 on the final pose (FP64; the deviation
             // becomes its square)
-            if (S.moved) {
+            if (S.moved && D.solve == GLT_SOLVE_FP32) {
                 const int i = lane / 3, j = lane % 3;
                 double dlt = lane < 9 ? (i == j ? 1.0 : 0.0) : 0.0;
                 if (lane < 9) {

@@ -178,10 +178,11 @@ cudaError_t launch_track(const StreamDesc* const* descs, const int* users, int S
 cudaError_t launch_linearize(const glt_tracker* t, const PassParams& P, bool want_res,
                              cudaStream_t s);
 bool track_shape_ok(int cluster, int threads, int variant);
-// the fixed part of `passes` tracker passes (no points), CTA 0's cycles to
-// *cycles (-1 when an exchange wait ran out); drop_rank >= 0: that CTA
-// withholds its first partial, so every wait of the cluster runs out
+// the fixed part of `passes` tracker passes (no points) in solve mode
+// `solve`, CTA 0's cycles to *cycles (-1 when an exchange wait ran out);
+// drop_rank >= 0: that CTA withholds its first partial, so every wait of the
+// cluster runs out
 cudaError_t launch_pass_floor(int cluster, int threads, bool cached, int passes, long long* cycles,
-                              cudaStream_t s, int drop_rank = -1);
+                              cudaStream_t s, int drop_rank = -1, int solve = GLT_SOLVE_FP64);
 
 }  // namespace glt

@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 1) track_kernel(
 __device__ double g_floor_Hc[72];   // H and H^-1 of the cached-Hessian floor (device data)
 
 template <int THREADS, bool HC>
-__global__ void __launch_bounds__(THREADS, 1) pass_floor_kernel(int passes, int drop_rank,
+__global__ void __launch_bounds__(THREADS, 1) pass_floor_kernel(int passes, int drop_rank, int solve,
                                                                  long long* __restrict__ cycles)
 {
     constexpr int NW = THREADS / 32;
@@ -287,6 +287,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_floor_kernel(int passes, int 
         sD.lambda_up = 4.0;
         sD.lambda_down = 0.5;
         sD.accept_step = 1e-3;
+        sD.solve = solve;
         sD.Hc = HC ? g_floor_Hc : nullptr;
         if (HC && blockIdx.x == 0)
             for (int i = 0; i < 72; ++i) {
@@ -590,7 +591,7 @@ cudaError_t launch_linearize(const glt_tracker* t, const PassParams& P, bool wan
 namespace glt {
 
 cudaError_t launch_pass_floor(int cluster, int threads, bool cached, int passes, long long* cycles,
-                              cudaStream_t s, int drop_rank)
+                              cudaStream_t s, int drop_rank, int solve)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)cluster, 1, 1);
@@ -610,7 +611,7 @@ cudaError_t launch_pass_floor(int cluster, int threads, bool cached, int passes,
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1); \
             if (e != cudaSuccess) return e;                                                     \
         }                                                                                       \
-        return cudaLaunchKernelEx(&cfg, k, passes, drop_rank, cycles);                          \
+        return cudaLaunchKernelEx(&cfg, k, passes, drop_rank, solve, cycles);                   \
     }
     if (cached) {
         if (threads == 512) GLT_FLOOR(512, true)

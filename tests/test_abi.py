@@ -52,7 +52,7 @@ def test_binding_covers_header_and_layouts(lib_path):
     assert bytes(buf[200:]) == bytes([0xA5] * 56)
     cfg = glt.glt_config.from_buffer_copy(bytes(buf[:200]))
     assert cfg.affine == 1 and cfg.pattern == 0 and cfg.jacobian == 0 and cfg.width == 640
-    assert cfg.hessian == glt.GLT_HESSIAN_PASS
+    assert cfg.hessian == glt.GLT_HESSIAN_PASS and cfg.solve == glt.GLT_SOLVE_FP64
     assert ctypes.sizeof(glt.glt_result) == 168
     assert glt.RESULT_DTYPE.itemsize == glt.RESULT_BYTES
     c = glt.default_config(640, 480, (525, 525, 320, 240))

@@ -162,6 +162,10 @@ def test_pass_floor_is_below_a_real_pass(glt, orc, syn):
     floor = glt.pass_floor(4, 256)
     assert 0.5 < floor < per_pass, (floor, per_pass)
     assert glt.pass_floor(4, 512, cached=True) < glt.pass_floor(4, 512)
+    # the FP32 solve's tail is shorter than the FP64 one
+    assert glt.pass_floor(4, 256, solve="fp32") < floor
     with pytest.raises(glt.GltError):
         glt.pass_floor(4, 256, cached=True)       # the cached-Hessian kernel runs 512 threads
+    with pytest.raises(glt.GltError):
+        glt.pass_floor(4, 256, solve=1)
     trk.close()
