@@ -72,8 +72,8 @@ extern "C" {
 #define GLT_CUR 1
 
 /* precision modes */
-#define GLT_FP32 0  /* uint8 levels, FP32 residuals/Jacobians/sums; FP32 L D L^T solve (FP64 for
-                       near-singular systems), FP64 state and pose update */
+#define GLT_FP32 0  /* uint8 levels, FP32 residuals/Jacobians/sums; the solve and the state
+                       update in the precision glt_config.solve selects (FP64 by default) */
 #define GLT_MIXED 1 /* FP16 (I, gx, gy) levels, FP32 math, Kahan FP32 block sums; solve and
                        state as GLT_FP32 */
 
