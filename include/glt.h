@@ -361,6 +361,18 @@ int glt_debug_pass_floor(int cluster, int threads, int cached, int solve, int pa
  * CUDA. */
 int glt_debug_exchange_timeout(int cluster, int threads, int* status, void* stream);
 
+/* Bounds-checked build (libglt_checked.so, the same sources compiled with
+ * GLT_CHECKED; the paper has no counterpart): every gather and table access
+ * of the pyramid, map-point and track kernels checks its range against its
+ * buffer, and an access outside sets a flag bit (1: uint8 level window, 2:
+ * FP16-packed texels, 4: per-point reference tables, 8: point arrays, 16:
+ * pyramid source, 32: pyramid destination, 64: map-point table writes) and
+ * goes to the buffer's first element instead.  Waits for the device, writes
+ * the flags of every kernel run since the last call to *flags and clears
+ * them.  Errors: INVALID_ARG (flags NULL), UNSUPPORTED (the normal build:
+ * *flags = 0), CUDA. */
+int glt_debug_checked_flags(unsigned* flags);
+
 /* The (cluster, threads) shape the tracker's solve launches with (chosen at
  * glt_create and again when the point count changes, or set in the config). */
 int glt_get_shape(const glt_tracker* trk, int* cluster, int* threads);

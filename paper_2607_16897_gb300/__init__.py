@@ -20,7 +20,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libglt.so")
+# GLT_LIBRARY=checked selects the bounds-checked build (libglt_checked.so)
+LIB_PATH = os.path.join(_HERE, "libglt_checked.so" if os.environ.get("GLT_LIBRARY") == "checked"
+                        else "libglt.so")
 
 GLT_OK = 0
 GLT_ERR_INVALID_ARG = -1
@@ -106,6 +108,7 @@ SIGNATURES = {
     "glt_debug_rcp": (_i, [_vp, _vp, _i, _vp]),
     "glt_debug_pass_floor": (_i, [_i, _i, _i, _i, _i, _P(ctypes.c_float), _vp]),
     "glt_debug_exchange_timeout": (_i, [_i, _i, _P(ctypes.c_int), _vp]),
+    "glt_debug_checked_flags": (_i, [_P(ctypes.c_uint)]),
     "glt_get_shape": (_i, [_vp, _P(_i), _P(_i)]),
     "glt_get_pyramid": (_i, [_vp, _i, _i, _P(ctypes.c_uint8), _vp]),
     "glt_get_trace": (_i, [_vp, _P(_d), _P(_i), _i, _P(_i), _vp]),

@@ -74,3 +74,18 @@ extern "C" int glt_debug_exchange_timeout(int cluster, int threads, int* status,
     *status = host < 0 ? GLT_TRACK_TIMEOUT : 0;
     return GLT_OK;
 }
+
+extern "C" int glt_debug_checked_flags(unsigned* flags)
+{
+    if (!flags) return invalid_arg_msg("glt_debug_checked_flags: flags is NULL");
+#ifdef GLT_CHECKED
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "glt_debug_checked_flags");
+    *flags = check_flags_track() | check_flags_pyramid() | check_flags_points();
+    return GLT_OK;
+#else
+    *flags = 0;
+    set_error("glt_debug_checked_flags: not a bounds-checked build (libglt_checked.so)");
+    return GLT_ERR_UNSUPPORTED;
+#endif
+}

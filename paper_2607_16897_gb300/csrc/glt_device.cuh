@@ -81,6 +81,40 @@ struct StreamDesc {
     int solve;             // GLT_SOLVE_FP64 or GLT_SOLVE_FP32
 };
 
+// Bounds-checked build (compiled with -DGLT_CHECKED into libglt_checked.so):
+// every gather and table access of the hot path checks its element range
+// [p, p + n) against its buffer [base, base + size); an access outside sets
+// bit `site` of this translation unit's check flags and goes to the buffer's
+// first element instead (no trap, no access outside the buffer).  In the
+// normal build checked() is the pointer itself.
+enum CheckSite {
+    CK_IMAGE = 0,      // uint8 level window rows
+    CK_PACKED = 1,     // FP16-packed level texels
+    CK_TABLE = 2,      // per-point reference tables (I0, G0)
+    CK_POINTS = 3,     // point arrays (pt, dz)
+    CK_PYR_SRC = 4,    // pyramid source rows
+    CK_PYR_DST = 5,    // pyramid destination and level-0 copy
+    CK_SET_POINTS = 6  // reference-table writes of set_points
+};
+#ifdef GLT_CHECKED
+static __device__ unsigned g_check_flags;
+template <class T>
+__device__ __forceinline__ T* checked(T* p, size_t n, T* base, size_t size, int site)
+{
+    if (p < base || p + n > base + size) {
+        atomicOr(&g_check_flags, 1u << site);
+        return base;
+    }
+    return p;
+}
+#else
+template <class T>
+__device__ __forceinline__ T* checked(T* p, size_t, T*, size_t, int)
+{
+    return p;
+}
+#endif
+
 // The state one linearisation pass is evaluated at, in the form the FP32
 // gather uses: R - I and t rounded from the FP64 pose, e^a, b.
 struct PassParams {
@@ -124,9 +158,10 @@ struct PointCache {
 
 __device__ __forceinline__ void load_point(const StreamDesc& D, int level, int p, PointCache& c)
 {
-    c.q = D.pt[p];
-    c.dz = D.dz[p];
-    const float* I0b = D.I0 + ((size_t)level * D.Npad + p) * D.K;
+    c.q = *checked(D.pt + p, 1, D.pt, (size_t)D.Npad, CK_POINTS);
+    c.dz = *checked(D.dz + p, 1, D.dz, (size_t)D.Npad, CK_POINTS);
+    const size_t tab = (size_t)D.L * D.Npad * D.K;
+    const float* I0b = checked(D.I0 + ((size_t)level * D.Npad + p) * D.K, (size_t)D.K, D.I0, tab, CK_TABLE);
     if (D.pattern) {
         c.ia = make_float4(I0b[0], 0.f, 0.f, 0.f);   // the p x p path reads its samples itself
         c.ib = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -265,8 +300,8 @@ __device__ __forceinline__ void hc_fold(const PointGeom& G, float sx, float sy, 
 // inverse-compositional form.
 __device__ __forceinline__ void ic_geometry(const StreamDesc& D, const PassParams& P, int p, PointGeom& G)
 {
-    const float4 q = D.pt[p];
-    const float rho = D.dz[p].y;
+    const float4 q = *checked(D.pt + p, 1, D.pt, (size_t)D.Npad, CK_POINTS);
+    const float rho = checked(D.dz + p, 1, D.dz, (size_t)D.Npad, CK_POINTS)->y;
     const float fxl = D.fx * P.scale * rho, fyl = D.fy * P.scale * rho;
     G.a0[0] = fxl;
     G.a0[1] = 0.0f;
@@ -297,7 +332,8 @@ __device__ __forceinline__ void linearize_square_t(const StreamDesc& D, const Pa
     uint32_t win[R][NWD];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const uint2* rp = reinterpret_cast<const uint2*>(base + (size_t)r * lv.pitch);
+        const uint2* rp = checked(reinterpret_cast<const uint2*>(base + (size_t)r * lv.pitch), 3,
+                                  reinterpret_cast<const uint2*>(lv.img), (size_t)lv.pitch * lv.H / 8, CK_IMAGE);
         const uint2 u0 = __ldca(rp), u1 = __ldca(rp + 1), u2 = __ldca(rp + 2);
         const uint32_t v[6] = {u0.x, u0.y, u1.x, u1.y, u2.x, u2.y};
 #pragma unroll
@@ -310,8 +346,12 @@ __device__ __forceinline__ void linearize_square_t(const StreamDesc& D, const Pa
 #define GLT_WX(r, c) ((float)((win[(r)][(c) >> 2] >> (8 * ((c) & 3))) & 0xffu))
     const float w00 = (1.0f - G.al) * (1.0f - G.be), w10 = G.al * (1.0f - G.be);
     const float w01 = (1.0f - G.al) * G.be, w11 = G.al * G.be;
-    const float* I0p = D.I0 + ((size_t)P.level * D.Npad + p) * (PS * PS);
-    const float2* G0p = ICF ? D.G0 + ((size_t)P.level * D.Npad + p) * (PS * PS) : nullptr;
+    const size_t tab = (size_t)D.L * D.Npad * (PS * PS);
+    const float* I0p = checked(D.I0 + ((size_t)P.level * D.Npad + p) * (PS * PS), (size_t)(PS * PS), D.I0,
+                               tab, CK_TABLE);
+    const float2* G0p = ICF ? checked(D.G0 + ((size_t)P.level * D.Npad + p) * (PS * PS), (size_t)(PS * PS),
+                                      D.G0, tab, CK_TABLE)
+                            : nullptr;
 #pragma unroll
     for (int j = 0; j < PS; ++j) {
 #pragma unroll
@@ -361,11 +401,15 @@ __device__ __forceinline__ void linearize_square_any(const StreamDesc& D, const 
     if (ic) ic_geometry(D, P, p, G);
     const float w00 = (1.0f - G.al) * (1.0f - G.be), w10 = G.al * (1.0f - G.be);
     const float w01 = (1.0f - G.al) * G.be, w11 = G.al * G.be;
-    const float* I0p = D.I0 + ((size_t)P.level * D.Npad + p) * K;
-    const float2* G0p = ic ? D.G0 + ((size_t)P.level * D.Npad + p) * K : nullptr;
+    const size_t tab = (size_t)D.L * D.Npad * K;
+    const float* I0p = checked(D.I0 + ((size_t)P.level * D.Npad + p) * K, (size_t)K, D.I0, tab, CK_TABLE);
+    const float2* G0p = ic ? checked(D.G0 + ((size_t)P.level * D.Npad + p) * K, (size_t)K, D.G0, tab, CK_TABLE)
+                           : nullptr;
     for (int k = 0; k < K; ++k) {
         const int dx = k % D.pattern - h, dy = k / D.pattern - h;
-        const uint8_t* t = lv.img + (size_t)(G.yb + dy) * S + (G.xb + dx);
+        // taps t - S - 1 .. t + 2 S + 2 (intensity and central differences)
+        const uint8_t* t = checked(lv.img + (size_t)(G.yb + dy - 1) * S + (G.xb + dx - 1), (size_t)3 * S + 4,
+                                   lv.img, (size_t)S * lv.H, CK_IMAGE) + S + 1;
         const float I00 = __ldca(t), I10 = __ldca(t + 1), I01 = __ldca(t + S), I11 = __ldca(t + S + 1);
         const float I = fmaf(w00, I00, fmaf(w10, I10, fmaf(w01, I01, w11 * I11)));
         if (HC) {
@@ -442,7 +486,9 @@ __device__ __forceinline__ void linearize_rows_hc(const StreamDesc& D, const Pas
     for (int r = 0; r < R; ++r) {
         // rows of the patch (and the lower bilinear tap of its last row) only
         if (j0 + r <= PS) {
-            const uint2* rp = reinterpret_cast<const uint2*>(base + (size_t)r * lv.pitch);
+            const uint2* rp = checked(reinterpret_cast<const uint2*>(base + (size_t)r * lv.pitch), 3,
+                                      reinterpret_cast<const uint2*>(lv.img), (size_t)lv.pitch * lv.H / 8,
+                                      CK_IMAGE);
             const uint2 u0 = __ldca(rp), u1 = __ldca(rp + 1), u2 = __ldca(rp + 2);
             const uint32_t v[6] = {u0.x, u0.y, u1.x, u1.y, u2.x, u2.y};
 #pragma unroll
@@ -459,8 +505,11 @@ __device__ __forceinline__ void linearize_rows_hc(const StreamDesc& D, const Pas
 #define GLT_WR(r, c) ((float)((win[(r)][(c) >> 2] >> (8 * ((c) & 3))) & 0xffu))
     const float w00 = (1.0f - G.al) * (1.0f - G.be), w10 = G.al * (1.0f - G.be);
     const float w01 = (1.0f - G.al) * G.be, w11 = G.al * G.be;
-    const float* I0p = D.I0 + ((size_t)P.level * D.Npad + p) * (PS * PS);
-    const float2* G0p = D.G0 + ((size_t)P.level * D.Npad + p) * (PS * PS);
+    const size_t tab = (size_t)D.L * D.Npad * (PS * PS);
+    const float* I0p = checked(D.I0 + ((size_t)P.level * D.Npad + p) * (PS * PS), (size_t)(PS * PS), D.I0,
+                               tab, CK_TABLE);
+    const float2* G0p = checked(D.G0 + ((size_t)P.level * D.Npad + p) * (PS * PS), (size_t)(PS * PS), D.G0,
+                                tab, CK_TABLE);
     float sx = 0.0f, sy = 0.0f;
 #pragma unroll
     for (int j = 0; j < RG; ++j) {
@@ -512,7 +561,8 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
     const float2* G0p = nullptr;
     if (ic) {
         ic_geometry(D, P, p, G);
-        G0p = D.G0 + ((size_t)P.level * D.Npad + p) * 8;
+        G0p = checked(D.G0 + ((size_t)P.level * D.Npad + p) * 8, (size_t)8, D.G0, (size_t)D.L * D.Npad * 8,
+                      CK_TABLE);
     }
     const float w00 = (1.0f - G.al) * (1.0f - G.be), w10 = G.al * (1.0f - G.be);
     const float w01 = (1.0f - G.al) * G.be, w11 = G.al * G.be;
@@ -527,7 +577,9 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
         uint32_t rw[8][2];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
-            const uint2* rp = reinterpret_cast<const uint2*>(base + (size_t)r * lv.pitch);
+            const uint2* rp = checked(reinterpret_cast<const uint2*>(base + (size_t)r * lv.pitch), 2,
+                                      reinterpret_cast<const uint2*>(lv.img), (size_t)lv.pitch * lv.H / 8,
+                                      CK_IMAGE);
             const uint2 w0 = __ldca(rp), w1 = __ldca(rp + 1);
             if (sh < 32) {
                 rw[r][0] = __funnelshift_r(w0.x, w0.y, sh);
@@ -575,7 +627,8 @@ __device__ __forceinline__ void linearize_point(const StreamDesc& D, const PassP
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int x0 = G.xb + pat_dx(k), y0 = G.yb + pat_dy(k);
-            const uint2* t0 = pk + (size_t)y0 * lv.W + x0;
+            const uint2* t0 = checked(pk + (size_t)y0 * lv.W + x0, (size_t)lv.W + 2, pk, (size_t)lv.W * lv.H,
+                                      CK_PACKED);
             const uint2* t1 = t0 + lv.W;
             const uint2 p00 = __ldca(t0), p10 = __ldca(t0 + 1), p01 = __ldca(t1), p11 = __ldca(t1 + 1);
             const float2 a00 = __half22float2(*reinterpret_cast<const __half2*>(&p00.x));

@@ -159,6 +159,14 @@ cudaError_t launch_set_points(const glt_tracker* t, const float* uvd_dev, int n,
 // per-reference Hessian of every level and its inverse (GLT_HESSIAN_CACHED)
 cudaError_t launch_ic_hessian(const glt_tracker* t, cudaStream_t s);
 
+#ifdef GLT_CHECKED
+// bounds-checked build: each translation unit's check flags (CheckSite bits),
+// read and cleared
+unsigned check_flags_track();
+unsigned check_flags_pyramid();
+unsigned check_flags_points();
+#endif
+
 // track.cu
 // kernel variant of a configuration: 0 FP32 forward, 1 GLT_MIXED, 2 FP32 with
 // p x p patches, 3 FP32 inverse compositional, 4 the cached Hessian (FP32, IC)

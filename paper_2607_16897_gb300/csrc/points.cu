@@ -27,12 +27,13 @@ __global__ void set_points_kernel(StreamDesc* __restrict__ desc, int n, RefLevel
     const float u0 = uvd[3 * p], v0 = uvd[3 * p + 1], d = uvd[3 * p + 2];
     const bool finite = isfinite(u0) && isfinite(v0) && isfinite(d) && d > 0.0f &&
                         fabsf(u0) < 1e7f && fabsf(v0) < 1e7f;
-    pt[p] = make_float4(u0, v0, (u0 - cx) / D.fx, (v0 - cy) / D.fy);
-    dz[p] = make_float2(d, 1.0f / d);
+    *checked(pt + p, 1, pt, (size_t)D.Npad, CK_SET_POINTS) = make_float4(u0, v0, (u0 - cx) / D.fx, (v0 - cy) / D.fy);
+    *checked(dz + p, 1, dz, (size_t)D.Npad, CK_SET_POINTS) = make_float2(d, 1.0f / d);
     const int K = D.K, h = D.pattern ? (D.pattern - 1) / 2 : 2;
     for (int l = 0; l < D.L; ++l) {
-        float* out = I0 + ((size_t)l * D.Npad + p) * K;
-        float2* gout = G0 ? G0 + ((size_t)l * D.Npad + p) * K : nullptr;
+        const size_t tab = (size_t)D.L * D.Npad * K;
+        float* out = checked(I0 + ((size_t)l * D.Npad + p) * K, (size_t)K, I0, tab, CK_SET_POINTS);
+        float2* gout = G0 ? checked(G0 + ((size_t)l * D.Npad + p) * K, (size_t)K, G0, tab, CK_SET_POINTS) : nullptr;
         const LevelDev& lv = D.lv[l];
         const float s = ldexpf(1.0f, -l);
         const float U = u0 * s, V = v0 * s;
@@ -197,4 +198,15 @@ cudaError_t launch_set_points(const glt_tracker* t, const float* uvd_dev, int n,
     return cudaGetLastError();
 }
 
+#ifdef GLT_CHECKED
+unsigned check_flags_points()
+{
+    unsigned v = 0, z = 0;
+    cudaMemcpyFromSymbol(&v, g_check_flags, sizeof(v));
+    cudaMemcpyToSymbol(g_check_flags, &z, sizeof(z));
+    return v;
+}
+#endif
+
 }  // namespace glt
+

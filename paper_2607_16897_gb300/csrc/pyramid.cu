@@ -78,11 +78,13 @@ constexpr int kPer = (kWords + PYR_THREADS - 1) / PYR_THREADS;
 // the read-only path.
 __device__ __forceinline__ uint32_t src_word(const Tile& t, const uint8_t* p)
 {
+    p = checked(p, 4, t.J.src, (size_t)t.J.sp * t.J.sH, CK_PYR_SRC);
     const unsigned int* w = reinterpret_cast<const unsigned int*>(p);
     return t.copy0 ? __ldg(w) : __ldcg(w);
 }
 __device__ __forceinline__ uint8_t src_byte(const Tile& t, const uint8_t* p)
 {
+    p = checked(p, 1, t.J.src, (size_t)t.J.sp * t.J.sH, CK_PYR_SRC);
     return t.copy0 ? __ldg(p) : __ldcg(p);
 }
 
@@ -168,13 +170,16 @@ __device__ __forceinline__ void tile_outputs(const Tile& t, uint8_t (*in)[IW], u
         for (int i = threadIdx.x; i < (y1 - y0) * 32; i += PYR_THREADS) {
             const int r = i >> 5, k = i & 31;
             if (k < nw)
-                reinterpret_cast<uint32_t*>(t.copy0 + (size_t)(y0 + r) * t.cp + x0)[k] =
+                *reinterpret_cast<uint32_t*>(checked(t.copy0 + (size_t)(y0 + r) * t.cp + x0 + 4 * k, 4, t.copy0,
+                                                     (size_t)t.cp * J.sH, CK_PYR_DST)) =
                     *reinterpret_cast<const uint32_t*>(&in[r + 2][4 + 4 * k]);
         }
         if (tail) {
             for (int i = threadIdx.x; i < (y1 - y0) * 4; i += PYR_THREADS) {
                 const int r = i >> 2, k = i & 3;
-                if (k < tail) t.copy0[(size_t)(y0 + r) * t.cp + x0 + 4 * nw + k] = in[r + 2][4 + 4 * nw + k];
+                if (k < tail)
+                    *checked(t.copy0 + (size_t)(y0 + r) * t.cp + x0 + 4 * nw + k, 1, t.copy0, (size_t)t.cp * J.sH,
+                             CK_PYR_DST) = in[r + 2][4 + 4 * nw + k];
             }
         }
     }
@@ -220,6 +225,7 @@ __device__ __forceinline__ void tile_outputs(const Tile& t, uint8_t (*in)[IW], u
         const uint32_t packed = __byte_perm(s01 >> 8, s23 >> 8, 0x6420);
         const int gx = ox0 + x4;
         uint8_t* dst = J.dst + (size_t)gy * J.dp + gx;
+        if (gx < J.dW) dst = checked(dst, (size_t)min(4, J.dW - gx), J.dst, (size_t)J.dp * J.dH, CK_PYR_DST);
         if (gx + 4 <= J.dW && ((reinterpret_cast<uintptr_t>(dst) & 3) == 0)) {
             *reinterpret_cast<uint32_t*>(dst) = packed;
         } else {
@@ -348,4 +354,15 @@ cudaError_t launch_pack(const PackJob* jobs, int njobs, int max_pixels, cudaStre
     return launch_ex(pack_kernel, dim3((unsigned)bx, (unsigned)njobs), threads, s, pdl, jobs);
 }
 
+#ifdef GLT_CHECKED
+unsigned check_flags_pyramid()
+{
+    unsigned v = 0, z = 0;
+    cudaMemcpyFromSymbol(&v, g_check_flags, sizeof(v));
+    cudaMemcpyToSymbol(g_check_flags, &z, sizeof(z));
+    return v;
+}
+#endif
+
 }  // namespace glt
+

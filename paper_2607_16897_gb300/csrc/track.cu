@@ -624,4 +624,15 @@ cudaError_t launch_pass_floor(int cluster, int threads, bool cached, int passes,
     return cudaErrorInvalidValue;
 }
 
+#ifdef GLT_CHECKED
+unsigned check_flags_track()
+{
+    unsigned v = 0, z = 0;
+    cudaMemcpyFromSymbol(&v, g_check_flags, sizeof(v));
+    cudaMemcpyToSymbol(g_check_flags, &z, sizeof(z));
+    return v;
+}
+#endif
+
 }  // namespace glt
+
