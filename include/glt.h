@@ -373,6 +373,14 @@ int glt_debug_exchange_timeout(int cluster, int threads, int* status, void* stre
  * *flags = 0), CUDA. */
 int glt_debug_checked_flags(unsigned* flags);
 
+/* Positive control of the bounds-checked build: a one-thread kernel reads
+ * one element inside a 64-float device buffer and one 5 elements past its
+ * end through the range check, which sends the second to the buffer's first
+ * element and sets flag 4; *flags = the flags that kernel set.  Synchronous.
+ * Errors: INVALID_ARG (flags NULL), UNSUPPORTED (the normal build: nothing is
+ * launched, *flags = 0), CUDA. */
+int glt_debug_checked_probe(unsigned* flags);
+
 /* The (cluster, threads) shape the tracker's solve launches with (chosen at
  * glt_create and again when the point count changes, or set in the config). */
 int glt_get_shape(const glt_tracker* trk, int* cluster, int* threads);

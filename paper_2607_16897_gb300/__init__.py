@@ -109,6 +109,7 @@ SIGNATURES = {
     "glt_debug_pass_floor": (_i, [_i, _i, _i, _i, _i, _P(ctypes.c_float), _vp]),
     "glt_debug_exchange_timeout": (_i, [_i, _i, _P(ctypes.c_int), _vp]),
     "glt_debug_checked_flags": (_i, [_P(ctypes.c_uint)]),
+    "glt_debug_checked_probe": (_i, [_P(ctypes.c_uint)]),
     "glt_get_shape": (_i, [_vp, _P(_i), _P(_i)]),
     "glt_get_pyramid": (_i, [_vp, _i, _i, _P(ctypes.c_uint8), _vp]),
     "glt_get_trace": (_i, [_vp, _P(_d), _P(_i), _i, _P(_i), _vp]),

@@ -75,6 +75,51 @@ extern "C" int glt_debug_exchange_timeout(int cluster, int threads, int* status,
     return GLT_OK;
 }
 
+#ifdef GLT_CHECKED
+namespace glt {
+namespace {
+// Positive control of the bounds-checked build: one index inside a buffer of
+// n floats and one 5 elements past its end go through checked(); the second
+// is redirected to the buffer's first element (no access outside it) and
+// sets the CK_TABLE flag.  Compiled only into the checked build.
+__global__ void checked_probe_kernel(const float* __restrict__ buf, int n, float* __restrict__ out)
+{
+    out[0] = *checked(buf + n / 2, 1, buf, (size_t)n, CK_TABLE);
+    out[1] = *checked(buf + n + 5, 1, buf, (size_t)n, CK_TABLE);
+}
+}  // namespace
+unsigned check_flags_debug()
+{
+    unsigned v = 0, z = 0;
+    cudaMemcpyFromSymbol(&v, g_check_flags, sizeof(v));
+    cudaMemcpyToSymbol(g_check_flags, &z, sizeof(z));
+    return v;
+}
+}  // namespace glt
+#endif
+
+extern "C" int glt_debug_checked_probe(unsigned* flags)
+{
+    if (!flags) return invalid_arg_msg("glt_debug_checked_probe: flags is NULL");
+    *flags = 0;
+#ifdef GLT_CHECKED
+    float* buf = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&buf), 66 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(buf, 0, 66 * sizeof(float));
+    if (e == cudaSuccess) {
+        checked_probe_kernel<<<1, 1>>>(buf, 64, buf + 64);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) *flags = check_flags_debug();
+    cudaFree(buf);
+    return e == cudaSuccess ? GLT_OK : cuda_fail(e, "glt_debug_checked_probe");
+#else
+    set_error("glt_debug_checked_probe: not a bounds-checked build (libglt_checked.so)");
+    return GLT_ERR_UNSUPPORTED;
+#endif
+}
+
 extern "C" int glt_debug_checked_flags(unsigned* flags)
 {
     if (!flags) return invalid_arg_msg("glt_debug_checked_flags: flags is NULL");

@@ -2,7 +2,8 @@
 map-point, tracking and batch parity suites run against it in a child
 process, where every test also asserts that no gather or table access left
 its buffer (glt_debug_checked_flags); the normal build reports that it is
-not a checked build."""
+not a checked build; a positive control shows that a read past a buffer is
+caught."""
 import ctypes
 import os
 import subprocess
@@ -19,6 +20,25 @@ def test_normal_build_is_not_checked():
     flags = ctypes.c_uint(7)
     assert glt.glt_debug_checked_flags(ctypes.byref(flags)) == glt.GLT_ERR_UNSUPPORTED
     assert flags.value == 0
+    flags.value = 7
+    assert glt.glt_debug_checked_probe(ctypes.byref(flags)) == glt.GLT_ERR_UNSUPPORTED
+    assert flags.value == 0
+
+
+def test_checked_build_flags_an_out_of_range_read():
+    """Positive control, in a child process on the checked library: the
+    probe's read past its buffer is redirected and flagged (flag 4), and the
+    flags of the kernels are clear again afterwards."""
+    code = ("import ctypes, paper_2607_16897_gb300 as glt\n"
+            "f = ctypes.c_uint(0)\n"
+            "assert glt.glt_debug_checked_probe(ctypes.byref(f)) == 0, glt.glt_last_error()\n"
+            "assert f.value == 4, f.value\n"
+            "assert glt.glt_debug_checked_flags(ctypes.byref(f)) == 0 and f.value == 0\n"
+            "print('probe ok')\n")
+    env = dict(os.environ, GLT_LIBRARY="checked")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0 and "probe ok" in r.stdout, r.stdout[-2000:] + r.stderr[-2000:]
 
 
 def test_parity_suites_in_the_checked_build():
