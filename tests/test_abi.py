@@ -40,6 +40,24 @@ def test_library_exports_every_declared_symbol(lib_path):
     assert not missing, missing
 
 
+def test_checked_library_exports_the_same_api():
+    """The bounds-checked twin (GLT_CHECKED) is the same ABI."""
+    spec = importlib.util.spec_from_file_location(
+        "_glt_build", os.path.join(ROOT, "paper_2607_16897_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    lib = ctypes.CDLL(mod.build(checked=True))
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    # no GPU is needed to see that it is the checked build: the call fails on
+    # the device, not with "not a checked build"
+    flags = ctypes.c_uint(0)
+    lib.glt_debug_checked_flags.argtypes = [ctypes.POINTER(ctypes.c_uint)]
+    lib.glt_last_error.restype = ctypes.c_char_p
+    rc = lib.glt_debug_checked_flags(ctypes.byref(flags))
+    assert rc != -5 or b"not a bounds-checked build" not in lib.glt_last_error()
+
+
 def test_binding_covers_header_and_layouts(lib_path):
     import paper_2607_16897_gb300 as glt
     assert set(glt.SIGNATURES) == set(declared_functions())
