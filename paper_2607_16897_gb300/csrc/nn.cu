@@ -387,25 +387,35 @@ static_assert(kPropSmemFloats % 4 == 0, "the BF16 weights must start on a 16-byt
 static_assert((kXp + kA1p + kA2p) % 4 == 0, "the bordered planes are cleared as float4");
 static_assert((kW2 + kW3) * sizeof(__nv_bfloat16) % 16 == 0, "the weight copy is made of 16-byte pieces");
 
-// GEMM form of a stride-2 3x3 conv on a zero-bordered input: thread t < tasks
-// computes PT consecutive output pixels (row-major) x 4 channels.
+// Bordered activation planes keep each row as its even columns followed by
+// its odd columns (column c of a row of Wp at (c & 1) * Wp / 2 + c / 2): the
+// stride-2 3x3 windows of consecutive output pixels then read consecutive
+// words, where the plain layout read every other one (two-way bank
+// conflicts).
+__device__ __forceinline__ int split_col(int c, int Wp) { return (c & 1) * (Wp >> 1) + (c >> 1); }
+
+// GEMM form of a stride-2 3x3 conv on a zero-bordered, column-split input:
+// thread t < tasks computes PT output pixels p = pg + u PG (consecutive
+// lanes, consecutive pixels) x 4 channels.  Output planes bordered and
+// column-split if PADOUT, else flat.
 template <int C, int H, int W, int O, int PT, bool PADOUT>
 __device__ __forceinline__ void conv_gemm(const float* __restrict__ in, const __nv_bfloat16* __restrict__ wt,
                                           const __nv_bfloat16* __restrict__ w, int boff,
                                           float* __restrict__ out)
 {
-    constexpr int Ho = (H + 1) / 2, Wo = (W + 1) / 2, Wp = W + 2, plane = (H + 2) * (W + 2);
+    constexpr int Ho = (H + 1) / 2, Wo = (W + 1) / 2, Wp = W + 2, plane = (H + 2) * (W + 2), half = Wp / 2;
     constexpr int PG = Ho * Wo / PT, tasks = PG * (O / 4);
     static_assert(Ho * Wo % PT == 0, "pixel tiles must cover the output");
     static_assert(tasks <= kPropThreads, "one tile per thread");
+    static_assert(Wp % 2 == 0, "column-split rows need an even padded width");
     const int t = threadIdx.x;
     if (t >= tasks) return;
     const int pg = t % PG, cg = t / PG;
     int base[PT];
 #pragma unroll
     for (int u = 0; u < PT; ++u) {
-        const int p = pg * PT + u;
-        base[u] = 2 * (p / Wo) * Wp + 2 * (p % Wo);
+        const int p = pg + u * PG;
+        base[u] = 2 * (p / Wo) * Wp + (p % Wo);     // window row 2i, split column of 2j
     }
     float acc[PT][4];
 #pragma unroll
@@ -422,7 +432,8 @@ __device__ __forceinline__ void conv_gemm(const float* __restrict__ in, const __
             const uint2 raw = *reinterpret_cast<const uint2*>(wc + q * O);
             const float2 w01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.x));
             const float2 w23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.y));
-            const int off = (q / 3) * Wp + (q % 3);
+            const int di = q / 3, dj = q % 3;
+            const int off = di * Wp + (dj & 1) * half + (dj >> 1);   // column 2j + dj
 #pragma unroll
             for (int u = 0; u < PT; ++u) {
                 const float a = xc[base[u] + off];
@@ -435,13 +446,13 @@ __device__ __forceinline__ void conv_gemm(const float* __restrict__ in, const __
     }
 #pragma unroll
     for (int u = 0; u < PT; ++u) {
-        const int p = pg * PT + u, i = p / Wo, j = p % Wo;
+        const int p = pg + u * PG, i = p / Wo, j = p % Wo;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int o = cg * 4 + k;
             const float r = fmaxf(acc[u][k], 0.0f);
             if (PADOUT)
-                out[o * (Ho + 2) * (Wo + 2) + (i + 1) * (Wo + 2) + (j + 1)] = r;
+                out[o * (Ho + 2) * (Wo + 2) + (i + 1) * (Wo + 2) + split_col(j + 1, Wo + 2)] = r;
             else
                 out[(o * Ho + i) * Wo + j] = r;
         }
@@ -453,8 +464,9 @@ __device__ __forceinline__ float2 wv2(const __nv_bfloat16* w, int i)
     return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(w + i));
 }
 
-// in: C planes of (H+2) x (W+2) with a zero border; out: O planes of the
-// (H+1)/2 x (W+1)/2 result, with a zero border if PADOUT, else flat.
+// in: C planes of (H+2) x (W+2) with a zero border, rows column-split; out: O
+// planes of the (H+1)/2 x (W+1)/2 result, bordered and column-split if
+// PADOUT, else flat.
 template <int C, int H, int W, int O, int KO, bool PADOUT>
 __device__ __forceinline__ void conv_block(const float* __restrict__ in, const __nv_bfloat16* __restrict__ w,
                                            int woff, int boff, float* __restrict__ out)
@@ -467,13 +479,14 @@ __device__ __forceinline__ void conv_block(const float* __restrict__ in, const _
         float acc[KO];
 #pragma unroll
         for (int k = 0; k < KO; ++k) acc[k] = __bfloat162float(__ldg(w + boff + og * KO + k));
-        const float* xb = in + (2 * i) * Wp + 2 * j;
+        const float* xb = in + (2 * i) * Wp + j;      // column-split rows: column 2j + dj
         for (int c = 0; c < C; ++c) {
             float v[9];
 #pragma unroll
             for (int di = 0; di < 3; ++di)
 #pragma unroll
-                for (int dj = 0; dj < 3; ++dj) v[di * 3 + dj] = xb[c * plane + di * Wp + dj];
+                for (int dj = 0; dj < 3; ++dj)
+                    v[di * 3 + dj] = xb[c * plane + di * Wp + (dj & 1) * (Wp >> 1) + (dj >> 1)];
 #pragma unroll
             for (int k = 0; k < KO; ++k) {
                 const __nv_bfloat16* wk = w + woff + ((og * KO + k) * C + c) * 9;
@@ -486,7 +499,7 @@ __device__ __forceinline__ void conv_block(const float* __restrict__ in, const _
             const int o = og * KO + k;
             const float r = fmaxf(acc[k], 0.0f);
             if (PADOUT)
-                out[o * (Ho + 2) * (Wo + 2) + (i + 1) * (Wo + 2) + (j + 1)] = r;
+                out[o * (Ho + 2) * (Wo + 2) + (i + 1) * (Wo + 2) + split_col(j + 1, Wo + 2)] = r;
             else
                 out[(o * Ho + i) * Wo + j] = r;
         }
@@ -594,7 +607,7 @@ proposal_kernel(const PropJob* __restrict__ jobs, const double* __restrict__ mot
     const PropJob J = jobs[s];
     for (int p = tid; p < kIn; p += kPropThreads) {
         const int r = p / 40, c = p % 40;
-        xp[(r + 1) * 42 + (c + 1)] =
+        xp[(r + 1) * 42 + split_col(c + 1, 42)] =
             ((float)J.cur[r * J.pitch + c] - (float)J.ref[r * J.pitch + c]) * (1.0f / 64.0f);
     }
     __syncthreads();
