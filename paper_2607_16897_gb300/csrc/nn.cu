@@ -17,6 +17,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "glt_internal.h"
 
 namespace glt {
@@ -572,11 +574,24 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
+// fc1 is shared by the kPropCluster blocks of a thread-block cluster (one
+// stream each; blocks past the last stream only help): block r computes
+// hidden units [r kHid / kPropCluster, (r + 1) kHid / kPropCluster) for every
+// stream of its cluster, from the streams' feature vectors copied out of the
+// peers' shared memory, and writes each result into its stream's block, so
+// the 329 KB of fc1 weights are read from L2 once per cluster instead of once
+// per stream.  Each output keeps conv_fwd's lane split and reduction order.
+constexpr int kPropCluster = 4;
+static_assert(kHid % (kPropCluster * (kPropThreads / 32)) == 0, "whole rows per warp");
+static_assert(kPropCluster * (kF + 2) <= kA1p, "the peers' feature vectors fit where conv1's output was");
+
 __global__ void __launch_bounds__(kPropThreads)
 proposal_kernel(const PropJob* __restrict__ jobs, const double* __restrict__ motion,
                 const double* __restrict__ init, const __nv_bfloat16* __restrict__ w,
-                const __nv_bfloat16* __restrict__ wt, double* __restrict__ out)
+                const __nv_bfloat16* __restrict__ wt, double* __restrict__ out, int S)
 {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) float sm[];
     float* xp = sm;
     float* a1 = xp + kXp;
@@ -587,13 +602,14 @@ proposal_kernel(const PropJob* __restrict__ jobs, const double* __restrict__ mot
     __nv_bfloat16* w2t = reinterpret_cast<__nv_bfloat16*>(y + kOut);
     __nv_bfloat16* w3t = w2t + kW2;
     const int s = blockIdx.x;
+    const bool valid = s < S;      // block-uniform: blocks past the last stream only share fc1
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // conv2 / conv3 weights: one contiguous [K][O] copy, in flight until conv2
     for (int v = tid; v < (kW2 + kW3) / 8; v += kPropThreads) cp_async16(w2t + 8 * v, wt + 8 * v);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     // the rows of T each lane of warp 0 composes at the end (lanes 12, 13: a, b)
     double Tr[4] = {0.0, 0.0, 0.0, 0.0};
-    if (warp == 0 && lane < 14) {
+    if (valid && warp == 0 && lane < 14) {
         const double* T = init + 14 * s;
         if (lane < 12) {
             for (int k = 0; k < 4; ++k) Tr[k] = T[4 * (lane >> 2) + k];
@@ -604,46 +620,83 @@ proposal_kernel(const PropJob* __restrict__ jobs, const double* __restrict__ mot
     float4* z4 = reinterpret_cast<float4*>(sm);
     for (int q = tid; q < (kXp + kA1p + kA2p) / 4; q += kPropThreads) z4[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     __syncthreads();
-    const PropJob J = jobs[s];
-    for (int p = tid; p < kIn; p += kPropThreads) {
-        const int r = p / 40, c = p % 40;
-        xp[(r + 1) * 42 + split_col(c + 1, 42)] =
-            ((float)J.cur[r * J.pitch + c] - (float)J.ref[r * J.pitch + c]) * (1.0f / 64.0f);
+    if (valid) {
+        const PropJob J = jobs[s];
+        for (int p = tid; p < kIn; p += kPropThreads) {
+            const int r = p / 40, c = p % 40;
+            xp[(r + 1) * 42 + split_col(c + 1, 42)] =
+                ((float)J.cur[r * J.pitch + c] - (float)J.ref[r * J.pitch + c]) * (1.0f / 64.0f);
+        }
+        __syncthreads();
+        conv_block<1, 30, 40, 16, 4, true>(xp, w, kC1.w, kC1.b, a1);
     }
-    __syncthreads();
-    conv_block<1, 30, 40, 16, 4, true>(xp, w, kC1.w, kC1.b, a1);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    // the motion input, on a thread that conv2's 320 tiles leave idle
-    if (tid == kPropThreads - 1) motion_feature(motion + 12 * s, f + kFlat);
-    conv_gemm<16, 15, 20, 32, 2, true>(a1, w2t, w, kC2.b, a2);
+    if (valid) {
+        // the motion input, on a thread that conv2's 320 tiles leave idle
+        if (tid == kPropThreads - 1) motion_feature(motion + 12 * s, f + kFlat);
+        conv_gemm<16, 15, 20, 32, 2, true>(a1, w2t, w, kC2.b, a2);
+        __syncthreads();
+        conv_gemm<32, 8, 10, 64, 1, false>(a2, w3t, w, kC3.b, f);
+    } else {
+        for (int i = tid; i < kF + 2; i += kPropThreads) f[i] = 0.0f;
+    }
+    // every block's feature vector is complete; copy the cluster's into the
+    // (dead) conv1 output area
+    cluster.sync();
+    float* fl = a1;
+    for (int q = 0; q < kPropCluster; ++q) {
+        const float* src = cluster.map_shared_rank(f, q);
+        for (int i = tid; i < kF + 2; i += kPropThreads) fl[q * (kF + 2) + i] = src[i];
+    }
     __syncthreads();
-    conv_gemm<32, 8, 10, 64, 1, false>(a2, w3t, w, kC3.b, f);
-    __syncthreads();
-    // fc1: each warp takes 4 output rows at a time, BF16 pairs along the rows
-    for (int o0 = warp * 4; o0 < kHid; o0 += 4 * (kPropThreads / 32)) {
-        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    // fc1: this block's kHid / kPropCluster rows for every stream of the
+    // cluster, two rows per warp, BF16 pairs along the rows; each result goes
+    // to its stream's block
+    {
+        constexpr int RPB = kHid / kPropCluster, RPW = RPB / (kPropThreads / 32);
+        const int rank = (int)cluster.block_rank();
+        const int o0 = rank * RPB + warp * RPW;
+        float acc[RPW][kPropCluster];
+#pragma unroll
+        for (int k = 0; k < RPW; ++k)
+#pragma unroll
+            for (int q = 0; q < kPropCluster; ++q) acc[k][q] = 0.0f;
 #pragma unroll 4
         for (int i = 2 * lane; i < kF; i += 64) {
-            const float f0 = f[i], f1 = f[i + 1];
+            float2 fq[kPropCluster];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int q = 0; q < kPropCluster; ++q) fq[q] = make_float2(fl[q * (kF + 2) + i], fl[q * (kF + 2) + i + 1]);
+#pragma unroll
+            for (int k = 0; k < RPW; ++k) {
                 const float2 wp = wv2(w, kF1.w + (o0 + k) * kF + i);
-                acc[k] = fmaf(wp.x, f0, acc[k]);
-                acc[k] = fmaf(wp.y, f1, acc[k]);
+#pragma unroll
+                for (int q = 0; q < kPropCluster; ++q) {
+                    acc[k][q] = fmaf(wp.x, fq[q].x, acc[k][q]);
+                    acc[k][q] = fmaf(wp.y, fq[q].y, acc[k][q]);
+                }
             }
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < RPW; ++k)
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
-        }
-        if (lane < 4) {
-            const float v = lane == 0 ? acc[0] : lane == 1 ? acc[1] : lane == 2 ? acc[2] : acc[3];
-            h[o0 + lane] = fmaxf(v + wv(w, kF1.b + o0 + lane), 0.0f);
+            for (int q = 0; q < kPropCluster; ++q)
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) acc[k][q] += __shfl_xor_sync(0xffffffffu, acc[k][q], off);
+        if (lane < RPW * kPropCluster) {
+            const int k = lane / kPropCluster, q = lane % kPropCluster;
+            float v = 0.0f;
+#pragma unroll
+            for (int kk = 0; kk < RPW; ++kk)
+#pragma unroll
+                for (int qq = 0; qq < kPropCluster; ++qq)
+                    if (kk == k && qq == q) v = acc[kk][qq];
+            cluster.map_shared_rank(h, q)[o0 + k] = fmaxf(v + wv(w, kF1.b + o0 + k), 0.0f);
         }
     }
-    __syncthreads();
+    // every stream's hidden vector is complete (and no block reads a peer after this)
+    cluster.sync();
+    if (!valid) return;
     if (warp < kOut) {
         const int row = kF2.w + warp * kHid;
         float acc = 0.0f;
@@ -716,9 +769,21 @@ proposal_kernel(const PropJob* __restrict__ jobs, const double* __restrict__ mot
 
 cudaError_t launch_proposal(glt_batch* b, const double* init_dev, cudaStream_t s)
 {
-    nn::proposal_kernel<<<b->S, nn::kPropThreads, nn::kPropSmemBytes, s>>>(
-        b->prop_jobs, b->motion_dev, init_dev, b->nn->wbf, b->nn->wt, b->prop_init);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((b->S + nn::kPropCluster - 1) / nn::kPropCluster * nn::kPropCluster), 1, 1);
+    cfg.blockDim = dim3(nn::kPropThreads, 1, 1);
+    cfg.dynamicSmemBytes = nn::kPropSmemBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = nn::kPropCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, nn::proposal_kernel, b->prop_jobs, b->motion_dev, init_dev,
+                              (const __nv_bfloat16*)b->nn->wbf, (const __nv_bfloat16*)b->nn->wt,
+                              b->prop_init, b->S);
 }
 
 }  // namespace glt
