@@ -79,7 +79,7 @@ extern "C" {
 
 /* solve modes (glt_config.solve) */
 #define GLT_SOLVE_FP64 0
-#define GLT_SOLVE_FP32 2
+#define GLT_SOLVE_FP32 1
 
 /* Jacobian forms (Sec. IV-B) */
 #define GLT_FORWARD 0 /* current image's gradient at the warped location, every pass */
@@ -483,7 +483,8 @@ int glt_batch_set_proportional(glt_batch* batch, int points_per_cta, int threads
 /* All launch classes: *nclass = their number; for k < min(*nclass, max),
  * first[k] = the class's first stream in the launch order (it runs to the
  * next class's first, the last to S), cluster[k] and threads[k] its shape
- * (any array may be NULL). */
+ * (any array may be NULL).  Errors: INVALID_ARG (batch or nclass NULL,
+ * max < 0). */
 int glt_batch_get_class_table(const glt_batch* batch, int max, int* first, int* cluster,
                               int* threads, int* nclass);
 

@@ -35,7 +35,7 @@ GLT_TRACK_TOO_FEW_POINTS = 1
 GLT_TRACK_NOT_PD = 2
 GLT_TRACK_DIVERGED = 4
 GLT_TRACK_TIMEOUT = 8
-GLT_SOLVE_FP64, GLT_SOLVE_FP32 = 0, 2
+GLT_SOLVE_FP64, GLT_SOLVE_FP32 = 0, 1
 GLT_REF, GLT_CUR = 0, 1
 GLT_FP32, GLT_MIXED = 0, 1
 GLT_FORWARD, GLT_IC = 0, 1

@@ -77,4 +77,4 @@ def test_modes_decide_definiteness_as_fp64(glt, orc, syn, solve):
 
 def test_solve_mode_is_checked(glt):
     with pytest.raises(glt.GltError):
-        glt.Tracker(320, 240, (256.0, 256.0, 160.0, 120.0), solve=1)
+        glt.Tracker(320, 240, (256.0, 256.0, 160.0, 120.0), solve=2)

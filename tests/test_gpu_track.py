@@ -167,5 +167,5 @@ def test_pass_floor_is_below_a_real_pass(glt, orc, syn):
     with pytest.raises(glt.GltError):
         glt.pass_floor(4, 256, cached=True)       # the cached-Hessian kernel runs 512 threads
     with pytest.raises(glt.GltError):
-        glt.pass_floor(4, 256, solve=1)
+        glt.pass_floor(4, 256, solve=2)
     trk.close()
